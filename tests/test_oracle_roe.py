@@ -1,0 +1,142 @@
+"""Pins of the oracle's convective flux and Roe upwinding (arXiv 2211.16718, Sec. 2.1
+flux vectors, Sec. 2.2 Eq. Roe) against the mathematics of the Euler equations."""
+import numpy as np
+import pytest
+
+GAMMA = 1.4
+
+
+def _state(rho, u, v, w, p, gamma=GAMMA):
+    return np.array([rho, rho * u, rho * v, rho * w, p / (gamma - 1) + 0.5 * rho * (u * u + v * v + w * w)])
+
+
+def _random_state(rng, mach=0.8):
+    rho = rng.uniform(0.5, 2.0)
+    p = rng.uniform(0.3, 1.5)
+    c = np.sqrt(GAMMA * p / rho)
+    u, v, w = rng.uniform(-mach, mach, size=3) * c
+    return _state(rho, u, v, w, p)
+
+
+def _fd_jacobian(oracle, U, d, h=1e-6):
+    J = np.zeros((5, 5))
+    for m in range(5):
+        e = np.zeros(5)
+        e[m] = h * max(1.0, abs(U[m]))
+        J[:, m] = (oracle.flux(U + e, d) - oracle.flux(U - e, d)) / (2 * e[m])
+    return J
+
+
+def test_flux_at_rest_is_pressure_only(oracle):
+    U = _state(1.3, 0.0, 0.0, 0.0, 0.9)
+    for d in range(3):
+        F = oracle.flux(U, d)
+        expect = np.zeros(5)
+        expect[1 + d] = 0.9
+        np.testing.assert_allclose(F, expect, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_flux_jacobian_has_euler_characteristic_speeds(oracle, seed):
+    """Eigenvalues of df/du are u_d - c, u_d (x3), u_d + c with c^2 = gamma p/rho."""
+    rng = np.random.default_rng(seed)
+    U = _random_state(rng)
+    rho = U[0]
+    vel = U[1:4] / rho
+    p = (GAMMA - 1) * (U[4] - 0.5 * rho * vel @ vel)
+    c = np.sqrt(GAMMA * p / rho)
+    for d in range(3):
+        ev = np.sort(np.linalg.eigvals(_fd_jacobian(oracle, U, d)).real)
+        np.testing.assert_allclose(ev, np.sort([vel[d] - c, vel[d], vel[d], vel[d], vel[d] + c]), atol=2e-6)
+
+
+def test_flux_rotation_covariance(oracle):
+    """Permuting the axes together with the velocity components permutes the flux."""
+    rng = np.random.default_rng(11)
+    U = _random_state(rng)
+    perm = [1, 2, 0]  # new axis a holds old axis perm[a]
+    Up = np.array([U[0], U[1 + perm[0]], U[1 + perm[1]], U[1 + perm[2]], U[4]])
+    for a in range(3):
+        F = oracle.flux(U, perm[a])
+        Fp = oracle.flux(Up, a)
+        np.testing.assert_allclose(Fp, [F[0], F[1 + perm[0]], F[1 + perm[1]], F[1 + perm[2]], F[4]], rtol=1e-15, atol=1e-16)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_eigenvectors_are_inverse_and_diagonalise_jacobian(oracle, seed):
+    rng = np.random.default_rng(20 + seed)
+    U = _random_state(rng)
+    for d in range(3):
+        X, Xi, lam = oracle.roe_eigensystem(U, U, d)
+        np.testing.assert_allclose(Xi @ X, np.eye(5), atol=1e-13)
+        A = oracle.roe_matrix(U, U, d)
+        np.testing.assert_allclose(A, X @ np.diag(lam) @ Xi, atol=1e-13)
+        np.testing.assert_allclose(A, _fd_jacobian(oracle, U, d), atol=5e-7)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_roe_property(oracle, seed):
+    """Roe's average makes A~ (U_R - U_L) = f(U_R) - f(U_L) exactly (Roe 1981)."""
+    rng = np.random.default_rng(40 + seed)
+    UL, UR = _random_state(rng), _random_state(rng)
+    for d in range(3):
+        A = oracle.roe_matrix(UL, UR, d)
+        lhs = A @ (UR - UL)
+        rhs = oracle.flux(UR, d) - oracle.flux(UL, d)
+        np.testing.assert_allclose(lhs, rhs, atol=1e-13 * max(1.0, np.abs(rhs).max()))
+
+
+def test_dissipation_matrix_eigenvalues_with_harten_fix(oracle):
+    """|A| has eigenvalues |lambda_k|; Harten's fix lifts |u-c| < delta to (l^2+d^2)/(2d)."""
+    rho, p = 1.0, 1.0 / GAMMA  # c = 1
+    for un, fix in [(0.3, 0.1), (0.97, 0.1), (1.02, 0.2), (-0.99, 0.1)]:
+        U = _state(rho, un, 0.1, -0.05, p)
+        vel = np.array([un, 0.1, -0.05])
+        q2 = vel @ vel
+        H = (U[4] + p) / rho
+        c = np.sqrt((GAMMA - 1) * (H - 0.5 * q2))
+        lam = np.array([un - c, un, un, un, un + c])
+        delta = fix * c
+        absl = np.abs(lam)
+        for k in (0, 4):
+            if absl[k] < delta:
+                absl[k] = (lam[k] ** 2 + delta ** 2) / (2 * delta)
+        A = oracle.roe_matrix(U, U, 0, absval=True, harten_delta=fix)
+        ev = np.sort(np.linalg.eigvals(A).real)
+        np.testing.assert_allclose(ev, np.sort(absl), atol=1e-12)
+
+
+def test_harten_fix_inactive_below_mach_09(oracle):
+    """With |u| < 0.9 c the fix (delta = 0.1 c) never triggers: bitwise equal fluxes."""
+    rng = np.random.default_rng(5)
+    from oracle.oracle import Params
+    for _ in range(20):
+        us = np.array([_random_state(rng, mach=0.85) for _ in range(6)])
+        for d in range(3):
+            a = oracle.interface_flux(Params(8, 8, 8, harten_delta=0.1), d, us)
+            b = oracle.interface_flux(Params(8, 8, 8, harten_delta=0.0), d, us)
+            assert np.array_equal(a, b)
+
+
+def test_interface_flux_consistency(oracle):
+    """A uniform stencil gives the exact physical flux f(U) (consistency of Eq. Roe)."""
+    from oracle.oracle import Params
+    rng = np.random.default_rng(9)
+    U = _random_state(rng)
+    for d in range(3):
+        F = oracle.interface_flux(Params(8, 8, 8), d, np.tile(U, (6, 1)))
+        np.testing.assert_allclose(F, oracle.flux(U, d), rtol=1e-14, atol=1e-15)
+
+
+def test_upwinding_selects_upwind_state_for_supersonic_flow(oracle):
+    """All eigenvalues positive: F = f(uL) when uL, uR come from smooth linear data with
+    optimal weights, i.e. the dissipation term equals (f^R - f^L)/2 exactly for a
+    linear flux; here checked for a supersonic uniform-gradient density wave."""
+    from oracle.oracle import Params
+    P = Params(8, 8, 8, weno_linear=1, harten_delta=0.0)
+    us = np.array([_state(1.0 + 0.01 * m, 2.0, 0.0, 0.0, 1.0 / GAMMA) for m in range(6)])
+    F = oracle.interface_flux(P, 0, us)
+    # left-biased reconstruction of each flux component, independently through weno5
+    fl = np.array([oracle.flux(s, 0) for s in us])
+    expect = np.array([oracle.weno5(fl[0:5, m], linear=True) for m in range(5)])
+    np.testing.assert_allclose(F, expect, rtol=1e-9, atol=1e-12)
