@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark of the compressible Navier-Stokes RHS + RK4 hot path on GB300.
+
+Workload: decaying isotropic turbulence on a 256^3 triply periodic grid (FP64,
+rho = 1, p = 1/gamma, u0 = 0.3, k0 = 4, mu_eff for Re_lambda = 50, dt at CFL 0.4),
+one step = one classical RK4 step (4 right-hand-side evaluations) plus the
+statistics (kinetic energy, enstrophy, conservation sums, CFL) of the new state,
+as in a run that logs them every step.  Metric: grid-point RHS evaluations per
+second (Gpts/s) = points * 4 * steps / time, summed over ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores (one RHS of the
+same 256^3 state per step).  Multi-GPU: independent replicas, one per rank
+(no collective on the data path), barrier + max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "grid-point RHS evals/sec (Gpts/s) and HBM roofline fraction; FP32-bulk/adjoint vs FP64"
+UNIT = "Gpts/s"
+RK_STAGES = 4
+# Algorithmic FP64 flops per grid point of one launch (FMA = 2, add/mul/div/sqrt = 1),
+# counted from the kernels' formulation without halo recomputation:
+#   direction pass: point fluxes 6, smoothness indicators 9 x 20, candidates +
+#   weighted combinations 9 x 46, Roe flux 96, difference + viscous divergence 34.
+FLOPS_DIR = 6 + 9 * 20 + 9 * 46 + 96 + 34
+FLOPS_RK_EPI = 15          # RK4 stage update in the z pass (5 components)
+FLOPS_PRIM = 17            # primitives (incl. 1 division, 1 square root)
+FLOPS_VISC = 111           # 12 gradients + 3 viscous flux vectors
+SMS, FP64_LANES_PER_SM, SM_MAX_MHZ = 152, 2, 2070.0
+FP64_PEAK_TFLOPS = SMS * FP64_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 1.2586
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=256, help="grid points per direction")
+    ap.add_argument("--cfl", type=float, default=0.4)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if os.environ.get("NS3D_BENCH_GLOO") is None else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="ns3d_clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def hit_state(n: int):
+    from paper_2211_16718_gb300 import inputs as I
+    return I.isotropic_turbulence(n, seed=0), I.hit_mu_eff()
+
+
+def workload_config(n: int, cfl: float, mu: float, dt: float) -> dict:
+    return {"workload": f"decaying isotropic turbulence {n}^3, FP64, RK4 + KE/enstrophy each step",
+            "grid": [n, n, n], "domain": "[0,2pi)^3 periodic", "integrator": "classical RK4",
+            "rhs_per_step": RK_STAGES, "u0": 0.3, "k0": 4, "re_lambda": 50, "mu_eff": mu, "cfl": cfl,
+            "dt": dt, "seed": 0,
+            "l2": f"inputs larger than L2: state {5 * n ** 3 * 8 / 1e6:.0f} MB, working set "
+                  f"{(5 * 4 + 7 + 12) * n ** 3 * 8 / 1e9:.2f} GB vs 129 MB L2",
+            "parallelism": "replicas (one independent grid per GPU)"}
+
+
+def cpu_oracle_sample(u0, mu, n, dt, full_step: bool):
+    """Time the oracle as it stands on all host cores: one RK4 step (or one RHS)."""
+    from oracle import oracle as O
+    O.build()
+    threads = os.cpu_count() or 1
+    O.set_threads(threads)
+    P = O.Params(n, n, n, mu_eff=mu)
+    t0 = time.perf_counter()
+    if full_step:
+        O.rk_step(P, u0, dt, 1)
+        pts = n ** 3 * RK_STAGES
+        what = f"one RK4 step (4 RHS) of the {n}^3 state"
+    else:
+        O.rhs(P, u0)
+        pts = n ** 3
+        what = f"one RHS of the {n}^3 state"
+    el = time.perf_counter() - t0
+    return pts / el / 1e9, el, O.get_threads() if O.has_openmp() else 1, what
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    u0, mu = hit_state(args.n)
+    dt = 0.0025
+    times = []
+    for s in range(args.warmup + args.steps):
+        g, el, cores, what = cpu_oracle_sample(u0, mu, args.n, dt, full_step=False)
+        if s >= args.warmup:
+            times.append(el)
+    tot = sum(times)
+    value = args.n ** 3 * len(times) / tot / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / len(times) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args.n, args.cfl, mu, dt),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"per step: {what} (plain FP64 C oracle, OpenMP over lines/points)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_2211_16718_gb300 import build as B
+    B.build()
+    from paper_2211_16718_gb300 import ns3d
+
+    n = args.n
+    u0, mu = hit_state(n)
+    solver = ns3d.Solver(n, n, n, mu_eff=mu)
+    ud = torch.from_numpy(u0.copy()).cuda()
+    dt = solver.dt_from_cfl(ud, args.cfl)
+    K, W = args.steps, args.warmup
+    stats_buf = torch.zeros((W + K, ns3d.NS3D_STATS_NDOUBLE), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        solver.rk_step(ud, dt, 1)
+        solver.stats_async(ud, stats_buf[i])
+
+    for i in range(W):
+        step(i)
+    torch.cuda.synchronize()
+    # flush L2 between warm-up and the timed region (the state alone exceeds L2 every step)
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device="cuda")
+    flush.fill_(1.0)
+    del flush
+    solver.timing_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(W, W + K):
+        step(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms_local = e0.elapsed_time(e1)
+    ktimes = solver.timing_read()
+    solver.timing_enable(False)
+    ms = max_over_ranks(ms_local, world)
+    pts_total = sum_over_ranks(float(n ** 3 * RK_STAGES * K), world)
+    value = pts_total / (ms * 1e-3) / 1e9
+    st = stats_buf.cpu().numpy()
+    status_ok = bool(np.all(st[:, 10] == 0))
+    launches = int(sum(c for _, c in ktimes.values()))
+
+    # dominant kernel: the direction pass (x, y, z launches of the same kernel)
+    dir_ms = sum(ktimes[k][0] for k in ("dir_x", "dir_y", "dir_z"))
+    dir_launches = sum(ktimes[k][1] for k in ("dir_x", "dir_y", "dir_z"))
+    flops_per_launch = (FLOPS_DIR + FLOPS_RK_EPI / 3.0) * n ** 3
+    avg_launch_s = dir_ms / dir_launches * 1e-3
+    achieved = flops_per_launch / avg_launch_s / 1e12
+    step_ms_total = sum(v[0] for v in ktimes.values())
+    roofline = {"bound": "alu", "kernel": "k_dir (fused WENO5 + Roe + difference + viscous divergence)",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2070 MHz (unit counts and max clock)",
+                "flops_per_point": FLOPS_DIR + FLOPS_RK_EPI / 3.0, "avg_launch_ms": avg_launch_s * 1e3,
+                "share_of_device_time": dir_ms / step_ms_total if step_ms_total > 0 else None,
+                "algorithmic_bytes_per_point": 8 * (5 + 6 + 4 + 5 + 5),
+                "hbm_gbs_algorithmic": 8 * (5 + 6 + 4 + 5 + 5) * n ** 3 / avg_launch_s / 1e9}
+
+    # end to end through the C ABI with host buffers (pinned): H2D state, RK4 step,
+    # statistics, D2H state + statistics, every step
+    uh_t = torch.from_numpy(u0.copy()).pin_memory()
+    uh = uh_t.numpy()
+    solver.step_host(uh, dt, 1)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        solver.step_host(uh, dt, 1)
+    el = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_pts = sum_over_ranks(float(n ** 3 * RK_STAGES * args.e2e_steps), world)
+    state_bytes = 5 * n ** 3 * 8
+    e2e = {"value": e2e_pts / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+           "d2h_bytes_per_step": state_bytes + 8 * ns3d.NS3D_STATS_NDOUBLE,
+           "call": "ns3d_step_host (pinned host state in, 1 RK4 step + statistics, state out)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        g, el_cpu, cores, what = cpu_oracle_sample(u0, mu, n, dt, full_step=True)
+        cpu = {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{what}, {el_cpu:.1f} s on the host cores (plain FP64 C oracle)"}
+
+    solver.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "config": workload_config(n, args.cfl, mu, dt),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "kernel_ms": {k: v[0] for k, v in ktimes.items()}, "clocks": clk,
+                "final_stats": {"ke": float(st[-1, 5]), "enstrophy": float(st[-1, 6]), "status_ok": status_ok}}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        # the oracle runs on the host of rank 0 only; other ranks exit without work
+        run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
+        return
+    world, rank, local = dist_init()
+    run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

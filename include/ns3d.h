@@ -1,0 +1,169 @@
+/*
+ * ns3d.h -- C ABI of libns3d.so: GB300 (sm_103a) evaluation of the right-hand
+ * side of the 3D compressible Navier-Stokes equations on a triply periodic
+ * Cartesian grid, and its Runge-Kutta time integration, as stated in
+ * arXiv 2211.16718 (Kim, Ghosh, Constantinescu, Balakrishnan):
+ *
+ *   du/dt = R(u) = -(df/dx + dg/dy + dh/dz) + (df^v/dx + dg^v/dy + dh^v/dz)
+ *
+ * (Sec. 2.1, Eq. NS), u = [rho, rho u, rho v, rho w, e], with
+ *  - convective terms: conservative finite differences of interface fluxes
+ *    (Sec. 2.2), each scalar component of u and f reconstructed by WENO5 with
+ *    the Jiang-Shu weights (Sec. 2.2), upwinded by the Roe flux with Harten's
+ *    entropy fix (Sec. 2.2, Eq. Roe);
+ *  - viscous and heat-flux terms: 4th-order central finite differences
+ *    (Sec. 2.1 stresses and heat flux; Sec. 2.2);
+ *  - time integration: classical RK4 or the three-stage TVD (SSP) RK
+ *    (Sec. 2.2).
+ *
+ * Conventions shared by every call
+ *  - State layout: contiguous FP64 structure-of-arrays u[5][nz][ny][nx]
+ *    (variable slowest, x fastest), i.e. element (v, k, j, i) at
+ *    v*N + (k*ny + j)*nx + i with N = nx*ny*nz.  Grid point i has
+ *    x_i = i*lx/nx (periodic).  Pointers named *_dev are device memory of the
+ *    current CUDA device, 16-byte aligned; *_host are host memory (pinned or
+ *    pageable).  The caller owns every buffer it passes.
+ *  - Streams: all device work of a call is enqueued on the context's stream
+ *    (given to ns3d_init, changeable with ns3d_set_stream).  Only the calls
+ *    that return host data (ns3d_stats, ns3d_check, ns3d_step_host,
+ *    ns3d_timing_read) synchronise that stream.
+ *  - Errors: every int-returning call returns NS3D_OK (0) or a negative code;
+ *    nothing aborts or traps.  ns3d_last_error(ctx) gives a message.
+ *    Non-physical states (rho <= 0, p <= 0, a non-finite value, or a negative
+ *    Roe-averaged sound speed squared) set a sticky device status word that
+ *    ns3d_stats / ns3d_check report as NS3D_ENONPHYSICAL and then clear.
+ *  - Not thread-safe per context; distinct contexts are independent.
+ */
+#ifndef NS3D_H
+#define NS3D_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  NS3D_OK = 0,
+  NS3D_EINVAL = -1,        /* bad parameter, size, null or aliasing pointer */
+  NS3D_ENOMEM = -2,        /* device or pinned-host allocation failed */
+  NS3D_ECUDA = -3,         /* CUDA launch/runtime error (see ns3d_last_error) */
+  NS3D_ENONPHYSICAL = -4,  /* non-physical state detected by a kernel */
+  NS3D_ETIMEOUT = -5       /* a bounded device-side wait gave up */
+};
+
+enum { NS3D_RK4 = 0, NS3D_SSPRK3 = 1 };           /* time integrators (Sec. 2.2) */
+enum { NS3D_FP64 = 0, NS3D_FP32_BULK = 1 };       /* arithmetic of reconstruction + upwinding */
+
+typedef struct ns3d_ctx ns3d_ctx;                 /* opaque; owned by the library */
+
+typedef struct {
+  int nx, ny, nz;       /* points per direction, each >= 1 */
+  int rk;               /* NS3D_RK4 (default) or NS3D_SSPRK3 */
+  int precision;        /* NS3D_FP64 (default) or NS3D_FP32_BULK */
+  int weno_p;           /* exponent p of the WENO weights; only 2 is supported */
+  double lx, ly, lz;    /* periodic box lengths (> 0); default 2*pi */
+  double gamma;         /* ratio of specific heats, default 1.4 (Sec. 2.1) */
+  double mu_eff;        /* mu * M_inf / Re_inf (Sec. 2.1), >= 0; 0 = Euler */
+  double prandtl;       /* Prandtl number, default 0.72 (Sec. 2.1) */
+  double weno_eps;      /* epsilon of the WENO weights, default 1e-6 (Sec. 2.2) */
+  double harten_delta;  /* entropy-fix width as a fraction of the Roe sound speed, >= 0 */
+} ns3d_params;
+
+/* Statistics of a state (all FP64 reductions over the grid). */
+typedef struct {
+  double mass, momx, momy, momz, energy;  /* sum of rho, rho u, rho v, rho w, e times dx dy dz */
+  double ke;                              /* mean of rho |v|^2 / 2 */
+  double enstrophy;                       /* mean of rho |omega|^2 / 2, omega by 4th-order central differences */
+  double rho_min, p_min;
+  double max_wavespeed_over_dx;           /* max over points, d of (|u_d| + c)/dx_d; CFL = dt * this */
+  int status;                             /* NS3D_OK or NS3D_ENONPHYSICAL */
+  int reserved;
+} ns3d_stats_t;
+
+/* Number of doubles ns3d_stats_async writes: the 10 fields above in order, then
+ * the status word as a double, then one reserved slot. */
+#define NS3D_STATS_NDOUBLE 12
+
+/* Fill *p with the paper's defaults for an nx x ny x nz grid on [0, 2pi)^3:
+ * gamma 1.4, Pr 0.72, eps 1e-6, p = 2, harten_delta 0.1, mu_eff 0, RK4, FP64. */
+void ns3d_default_params(ns3d_params *p, int nx, int ny, int nz);
+
+/* Create a context: validates *p (NS3D_EINVAL), allocates the library-owned
+ * device scratch (NS3D_ENOMEM): primitive variables 7*N, viscous fluxes 12*N
+ * (only if mu_eff > 0), RHS accumulator 5*N, two RK stage states 10*N, RK
+ * accumulator 5*N doubles, reduction partials and a status word.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream). */
+int ns3d_init(const ns3d_params *p, void *cuda_stream, ns3d_ctx **out);
+
+/* Release every resource of ctx (NULL is a no-op).  Synchronises its stream. */
+void ns3d_free(ns3d_ctx *ctx);
+
+/* Change the stream that later calls enqueue on. */
+int ns3d_set_stream(ns3d_ctx *ctx, void *cuda_stream);
+
+/* rhs_dev = R(u_dev) (Sec. 2.1 Eq. NS with the Sec. 2.2 discretisation).
+ * u_dev, rhs_dev: 5*N doubles each, must not overlap. */
+int ns3d_rhs(ns3d_ctx *ctx, const double *u_dev, double *rhs_dev);
+
+/* Advance u_dev in place by nsteps (>= 0) steps of size dt (finite) with the
+ * context's integrator (Sec. 2.2).  No host synchronisation. */
+int ns3d_rk_step(ns3d_ctx *ctx, double *u_dev, double dt, int nsteps);
+
+/* Statistics of u_dev copied into *out_host; synchronises the stream.  Returns
+ * NS3D_ENONPHYSICAL (with out_host->status set) if the sticky status word was
+ * set by any earlier call or by this one, and clears it. */
+int ns3d_stats(ns3d_ctx *ctx, const double *u_dev, ns3d_stats_t *out_host);
+
+/* Same statistics written to out_dev[NS3D_STATS_NDOUBLE] on the device without
+ * synchronising (for logging every step inside a captured or timed loop).  The
+ * status slot holds the sticky status word at that point (not cleared). */
+int ns3d_stats_async(ns3d_ctx *ctx, const double *u_dev, double *out_dev);
+
+/* End-to-end call with host buffers: copies u_host to library-owned device
+ * memory, advances nsteps steps of size dt, computes the statistics of the
+ * final state into *stats_host (may be NULL), copies the state back into
+ * u_host.  Synchronises. */
+int ns3d_step_host(ns3d_ctx *ctx, double *u_host, double dt, int nsteps, ns3d_stats_t *stats_host);
+
+/* Read and clear the sticky status word (synchronises): NS3D_OK or NS3D_ENONPHYSICAL. */
+int ns3d_check(ns3d_ctx *ctx);
+
+/* Static description of a code. */
+const char *ns3d_strerror(int code);
+
+/* Message of the last failure of ctx (empty if none). */
+const char *ns3d_last_error(const ns3d_ctx *ctx);
+
+/* ---- measurement support (no counterpart in the paper) -------------------- */
+/* Kernel identifiers used by the timing calls. */
+enum {
+  NS3D_K_PRIM = 0,       /* primitive variables */
+  NS3D_K_VISC = 1,       /* velocity/temperature gradients -> viscous fluxes */
+  NS3D_K_DIR_X = 2,      /* fused WENO5 + Roe + conservative difference (+ viscous divergence), x */
+  NS3D_K_DIR_Y = 3,
+  NS3D_K_DIR_Z = 4,      /* ... z, with the RK stage update fused in */
+  NS3D_K_STATS = 5,      /* statistics partial reductions */
+  NS3D_K_STATS_FINAL = 6,
+  NS3D_K_COUNT = 7
+};
+
+/* on != 0: record CUDA events around every kernel launch of ctx (on its stream)
+ * and accumulate their durations; on == 0 stops recording.  Resets counters. */
+int ns3d_timing_enable(ns3d_ctx *ctx, int on);
+
+/* Synchronise and read the accumulated device time (ms_out[k], milliseconds)
+ * and launch counts (launches_out[k]) per kernel id, k < n (<= NS3D_K_COUNT);
+ * either pointer may be NULL. */
+int ns3d_timing_read(ns3d_ctx *ctx, double *ms_out, long long *launches_out, int n);
+
+/* FP64 / FP32 arithmetic throughput of the current device in G lane-ops/s,
+ * measured with register-only kernels: out[0] DFMA, out[1] DADD, out[2] DDIV,
+ * out[3] DSQRT, out[4] FFMA.  Synchronises the device; allocates 2.5 MB. */
+int ns3d_alu_probe(double out[5]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NS3D_H */

@@ -1,0 +1,385 @@
+// Fused per-direction pass of the right-hand side (arXiv 2211.16718, Sec. 2.2):
+// for every grid line along direction D, component-wise WENO5 reconstruction of
+// u and f_D (left- and right-biased, Jiang-Shu weights), Roe flux with Harten's
+// entropy fix at every interface, conservative difference of the interface
+// fluxes, 4th-order central divergence of the viscous flux along D, and the
+// accumulation / Runge-Kutta stage epilogue.
+//
+// One CTA owns a tile of TP points along D times W lines (periodic halo of 3
+// points each side, fetched with wrapped indices).  Everything is staged in
+// shared memory and computed in five phases separated by barriers:
+//   A  load state, primitives, viscous flux; point fluxes f_D        [NP x W]
+//   B  smoothness indicators of every 3-point window, squared,
+//      for the 9 reconstructed scalars (u_0..u_4, f_1..f_4)            [9 x NW x W]
+//   C  left/right WENO5 values of the 9 scalars at every interface     [9 x NI x W]
+//   D  Roe flux at every interface                                     [NI x W]
+//   E  flux difference + viscous divergence + epilogue, global writes  [TP x W]
+// The mass flux f_0 = (rho u_D) is the momentum component u_{1+D} itself, so its
+// reconstructions are those of u_{1+D}.
+//
+// WENO weights in division-reduced form: with b_k = 4(eps + beta_k) and
+// B_k = b_k^2, omega_k = c_k/B_k / sum_j c_j/B_j, so
+//   fhat = (c1 B2 B3 F1 + c2 B1 B3 F2 + c3 B1 B2 F3) / (c1 B2 B3 + c2 B1 B3 + c3 B1 B2),
+// one division per reconstruction.  The squared indicators of a window are shared
+// by the left-biased reconstruction at one interface and the right-biased one at
+// another, so each is computed once per window.
+#include <math.h>
+
+#include "ns3d_internal.cuh"
+
+namespace ns3d {
+
+namespace {
+
+constexpr int TP = 32;            // points per tile along the pencil
+constexpr int W = 4;              // lines per tile
+constexpr int NP = TP + 6;        // points incl. 3-point halo each side
+constexpr int NW = TP + 4;        // 3-point windows centred at -2 .. TP+1
+constexpr int NI = TP + 1;        // interfaces -1/2 .. TP-1/2
+constexpr int NQ = 9;             // reconstructed scalars
+constexpr int NTHREADS = 128;
+
+// shared-memory plan (doubles)
+constexpr int OFF_Q = 0;                          // [NQ][NP*W]
+constexpr int OFF_ROE = OFF_Q + NQ * NP * W;      // [5][NP*W]: sqrt(rho), u, v, w, H
+constexpr int OFF_FV = OFF_ROE + 5 * NP * W;      // [4][NP*W]
+constexpr int OFF_B = OFF_FV + 4 * NP * W;        // [NQ][3][NW*W]
+constexpr int OFF_R = OFF_B + NQ * 3 * NW * W;    // [18][NI*W], later [5][NI*W] fluxes
+constexpr int SMEM_DOUBLES = OFF_R + 18 * NI * W;
+constexpr int SMEM_BYTES = SMEM_DOUBLES * 8;
+
+// Position-major for y/z lines (consecutive threads = consecutive x lines),
+// line-major for x lines (consecutive threads = consecutive x points).
+template <int D>
+__device__ __forceinline__ int sidx(int pos, int line, int npos) {
+  return D == 0 ? line * npos + pos : pos * W + line;
+}
+template <int D>
+__device__ __forceinline__ void split(int item, int npos, int& pos, int& line) {
+  if (D == 0) {
+    pos = item % npos;
+    line = item / npos;
+  } else {
+    line = item % W;
+    pos = item / W;
+  }
+}
+
+__device__ __forceinline__ double weno_combine(double B1, double B2, double B3, double F1, double F2, double F3) {
+  const double p23 = B2 * B3;
+  const double t13 = 6.0 * (B1 * B3);
+  const double t12 = 3.0 * (B1 * B2);
+  const double num = fma(p23, F1, fma(t13, F2, t12 * F3));
+  const double den = p23 + t13 + t12;
+  return num / den;
+}
+
+template <int D>
+__global__ void __launch_bounds__(NTHREADS) k_dir(const DirArgs a) {
+  extern __shared__ double sm[];
+  const int nD = a.g.n[D];
+  constexpr int AX = (D == 0) ? 1 : 0;   // axis of the W lines
+  constexpr int BX = (D == 2) ? 1 : 2;   // axis of blockIdx.z
+  const int na = a.g.n[AX];
+  const int nx = a.g.n[0], ny = a.g.n[1];
+  const long long N = a.g.N;
+  const int s0 = blockIdx.x * TP;
+  const int a0 = blockIdx.y * W;
+  const int bz = blockIdx.z;
+  const int tid = threadIdx.x;
+
+  auto flat = [&](int c, int la) -> long long {
+    int idx[3];
+    idx[D] = c;
+    idx[AX] = la;
+    idx[BX] = bz;
+    return ((long long)idx[2] * ny + idx[1]) * nx + idx[0];
+  };
+
+  // ---- A: load --------------------------------------------------------------
+  for (int item = tid; item < NP * W; item += NTHREADS) {
+    int pos, line;
+    split<D>(item, NP, pos, line);
+    const int c = wrap_idx(s0 - 3 + pos, nD);
+    const int la = min(a0 + line, na - 1);
+    const long long p = flat(c, la);
+    double U[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) U[v] = __ldg(a.u + v * N + p);
+    const double vx = __ldg(a.pm + PM_U * N + p), vy = __ldg(a.pm + PM_V * N + p), vz = __ldg(a.pm + PM_W * N + p);
+    const double pr = __ldg(a.pm + PM_P * N + p);
+    const double un = (D == 0) ? vx : (D == 1) ? vy : vz;
+    const int s = sidx<D>(pos, line, NP);
+    double* q = sm + OFF_Q;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) q[v * NP * W + s] = U[v];
+    q[5 * NP * W + s] = (D == 0) ? fma(U[1], un, pr) : U[1] * un;
+    q[6 * NP * W + s] = (D == 1) ? fma(U[2], un, pr) : U[2] * un;
+    q[7 * NP * W + s] = (D == 2) ? fma(U[3], un, pr) : U[3] * un;
+    q[8 * NP * W + s] = (U[4] + pr) * un;
+    double* r = sm + OFF_ROE;
+    r[0 * NP * W + s] = __ldg(a.pm + PM_SR * N + p);
+    r[1 * NP * W + s] = vx;
+    r[2 * NP * W + s] = vy;
+    r[3 * NP * W + s] = vz;
+    r[4 * NP * W + s] = __ldg(a.pm + PM_H * N + p);
+    if (a.fv != nullptr) {
+      double* f = sm + OFF_FV;
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) f[cc * NP * W + s] = __ldg(a.fv + (long long)(4 * D + cc) * N + p);
+    }
+  }
+  __syncthreads();
+
+  // ---- B: squared scaled smoothness indicators of every window ----------------
+  {
+    const double eps4 = a.eps4;
+    const double* q = sm + OFF_Q;
+    double* bw = sm + OFF_B;
+    for (int item = tid; item < NQ * NW * W; item += NTHREADS) {
+      const int m = item / (NW * W);
+      int w, line;
+      split<D>(item - m * NW * W, NW, w, line);
+      const double* qm = q + m * NP * W;
+      const double x = qm[sidx<D>(w, line, NP)];
+      const double y = qm[sidx<D>(w + 1, line, NP)];
+      const double z = qm[sidx<D>(w + 2, line, NP)];
+      const double gm = y - x, gp = z - y, s = gp - gm;
+      const double aa = fma((13.0 / 3.0) * s, s, eps4);
+      const double u1 = fma(3.0, gp, -gm);   // x - 4y + 3z
+      const double u2 = gm + gp;             // z - x
+      const double u3 = fma(-3.0, gm, gp);   // 3x - 4y + z
+      const double b1 = fma(u1, u1, aa), b2 = fma(u2, u2, aa), b3 = fma(u3, u3, aa);
+      const int o = sidx<D>(w, line, NW);
+      bw[(m * 3 + 0) * NW * W + o] = b1 * b1;
+      bw[(m * 3 + 1) * NW * W + o] = b2 * b2;
+      bw[(m * 3 + 2) * NW * W + o] = b3 * b3;
+    }
+  }
+  __syncthreads();
+
+  // ---- C: left/right WENO5 values at every interface --------------------------
+  {
+    const double* q = sm + OFF_Q;
+    const double* bw = sm + OFF_B;
+    double* rec = sm + OFF_R;
+    for (int item = tid; item < NQ * NI * W; item += NTHREADS) {
+      const int m = item / (NI * W);
+      int f, line;
+      split<D>(item - m * NI * W, NI, f, line);
+      const double* qm = q + m * NP * W;
+      const double P0 = qm[sidx<D>(f, line, NP)], P1 = qm[sidx<D>(f + 1, line, NP)];
+      const double P2 = qm[sidx<D>(f + 2, line, NP)], P3 = qm[sidx<D>(f + 3, line, NP)];
+      const double P4 = qm[sidx<D>(f + 4, line, NP)], P5 = qm[sidx<D>(f + 5, line, NP)];
+      // third-order candidates at the interface between P2 and P3
+      const double xR = fma(11.0 / 6.0, P2, fma(-7.0 / 6.0, P1, (1.0 / 3.0) * P0));
+      const double eR = fma(1.0 / 3.0, P3, fma(5.0 / 6.0, P2, (-1.0 / 6.0) * P1));
+      const double eL = fma(-1.0 / 6.0, P4, fma(5.0 / 6.0, P3, (1.0 / 3.0) * P2));
+      const double xL = fma(1.0 / 3.0, P5, fma(-7.0 / 6.0, P4, (11.0 / 6.0) * P3));
+      const double* b = bw + m * 3 * NW * W;
+      const double B1f = b[0 * NW * W + sidx<D>(f, line, NW)];
+      const double B2f1 = b[1 * NW * W + sidx<D>(f + 1, line, NW)];
+      const double B3f2 = b[2 * NW * W + sidx<D>(f + 2, line, NW)];
+      const double B3f3 = b[2 * NW * W + sidx<D>(f + 3, line, NW)];
+      const double B2f2 = b[1 * NW * W + sidx<D>(f + 2, line, NW)];
+      const double B1f1 = b[0 * NW * W + sidx<D>(f + 1, line, NW)];
+      const double vL = weno_combine(B1f, B2f1, B3f2, xR, eR, eL);
+      const double vR = weno_combine(B3f3, B2f2, B1f1, xL, eL, eR);
+      const int o = sidx<D>(f, line, NI);
+      rec[(2 * m) * NI * W + o] = vL;
+      rec[(2 * m + 1) * NI * W + o] = vR;
+    }
+  }
+  __syncthreads();
+
+  // ---- D: Roe flux at every interface -------------------------------------------
+  {
+    const double gm1 = a.gamma - 1.0;
+    const double* r = sm + OFF_ROE;
+    double* rec = sm + OFF_R;
+    int bad = 0;
+    for (int item = tid; item < NI * W; item += NTHREADS) {
+      int f, line;
+      split<D>(item, NI, f, line);
+      const int o = sidx<D>(f, line, NI);
+      double uL[5], uR[5], fL[5], fR[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        uL[v] = rec[(2 * v) * NI * W + o];
+        uR[v] = rec[(2 * v + 1) * NI * W + o];
+      }
+#pragma unroll
+      for (int v = 1; v < 5; ++v) {
+        fL[v] = rec[(2 * (4 + v)) * NI * W + o];
+        fR[v] = rec[(2 * (4 + v) + 1) * NI * W + o];
+      }
+      fL[0] = uL[1 + D];
+      fR[0] = uR[1 + D];
+      const int sa = sidx<D>(f + 2, line, NP), sb = sidx<D>(f + 3, line, NP);
+      const double ra = r[sa], rb = r[sb];
+      const double rs = 1.0 / (ra + rb);
+      const double wa = ra * rs, wb = rb * rs;
+      double V[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) V[m] = fma(wa, r[(1 + m) * NP * W + sa], wb * r[(1 + m) * NP * W + sb]);
+      const double H = fma(wa, r[4 * NP * W + sa], wb * r[4 * NP * W + sb]);
+      const double q2h = 0.5 * fma(V[0], V[0], fma(V[1], V[1], V[2] * V[2]));
+      const double c2 = gm1 * (H - q2h);
+      bad |= !(c2 > 0.0);
+      const double c = sqrt(c2);
+      const double rc = 1.0 / c;
+      double du[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) du[v] = uR[v] - uL[v];
+      constexpr int T1 = (D == 0) ? 1 : 0;
+      constexpr int T2 = (D == 2) ? 1 : 2;
+      const double un = V[D], vt1 = V[T1], vt2 = V[T2];
+      const double b1 = gm1 * (rc * rc);
+      const double vdm = fma(V[0], du[1], fma(V[1], du[2], V[2] * du[3]));
+      const double phi = b1 * (fma(q2h, du[0], du[4]) - vdm);
+      const double a2 = du[0] - phi;
+      const double a3 = fma(-vt1, du[0], du[1 + T1]);
+      const double a4 = fma(-vt2, du[0], du[1 + T2]);
+      const double ach = 0.5 * (fma(un, du[0], -du[1 + D]) * rc);
+      const double ph = 0.5 * phi;
+      const double a1 = ph + ach, a5 = ph - ach;
+      double l1 = fabs(un - c), l5 = fabs(un + c);
+      const double l2 = fabs(un);
+      const double delta = a.hdelta * c;
+      if (l1 < delta) l1 = (l1 * l1 + delta * delta) / (2.0 * delta);
+      if (l5 < delta) l5 = (l5 * l5 + delta * delta) / (2.0 * delta);
+      const double A1 = l1 * a1, A2 = l2 * a2, A3 = l2 * a3, A4 = l2 * a4, A5 = l5 * a5;
+      const double S = A1 + A5;
+      const double d0 = S + A2;
+      const double cD = c * (A5 - A1);
+      double diss[5];
+      diss[0] = d0;
+      diss[1 + D] = fma(d0, un, cD);
+      diss[1 + T1] = fma(d0, vt1, A3);
+      diss[1 + T2] = fma(d0, vt2, A4);
+      diss[4] = fma(S, H, fma(cD, un, fma(A2, q2h, fma(A3, vt1, A4 * vt2))));
+#pragma unroll
+      for (int v = 0; v < 5; ++v) rec[v * NI * W + o] = 0.5 * (fL[v] + fR[v] - diss[v]);
+    }
+    if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(a.status, ST_NONPHYS);
+  }
+  __syncthreads();
+
+  // ---- E: conservative difference + viscous divergence + epilogue ----------------
+  {
+    const double rdx = 1.0 / a.g.h[D];
+    const double r12 = 1.0 / (12.0 * a.g.h[D]);
+    const double* F = sm + OFF_R;
+    const double* fvs = sm + OFF_FV;
+    for (int item = tid; item < TP * W; item += NTHREADS) {
+      int pp, line;
+      split<D>(item, TP, pp, line);
+      if (s0 + pp >= nD || a0 + line >= na) continue;
+      double cv[5];
+      const int op = sidx<D>(pp + 1, line, NI), om = sidx<D>(pp, line, NI);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) cv[v] = (F[v * NI * W + om] - F[v * NI * W + op]) * rdx;
+      if (a.fv != nullptr) {
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          const double* fc = fvs + cc * NP * W;
+          const double d1 = fc[sidx<D>(pp + 4, line, NP)] - fc[sidx<D>(pp + 2, line, NP)];
+          const double d2 = fc[sidx<D>(pp + 5, line, NP)] - fc[sidx<D>(pp + 1, line, NP)];
+          cv[1 + cc] = fma(fma(8.0, d1, -d2), r12, cv[1 + cc]);
+        }
+      }
+      const long long p = flat(s0 + pp, a0 + line);
+      switch (a.epi) {
+        case EPI_ACC_WRITE:
+#pragma unroll
+          for (int v = 0; v < 5; ++v) a.k[v * N + p] = cv[v];
+          break;
+        case EPI_ACC_ADD:
+#pragma unroll
+          for (int v = 0; v < 5; ++v) a.k[v * N + p] += cv[v];
+          break;
+        case EPI_RHS_OUT:
+#pragma unroll
+          for (int v = 0; v < 5; ++v) a.out[v * N + p] = a.k[v * N + p] + cv[v];
+          break;
+        case EPI_RK4_FIRST:
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            const double K = a.k[v * N + p] + cv[v];
+            a.out[v * N + p] = fma(a.a, K, a.un[v * N + p]);
+            a.acc[v * N + p] = K;
+          }
+          break;
+        case EPI_RK4_MID:
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            const double K = a.k[v * N + p] + cv[v];
+            a.out[v * N + p] = fma(a.a, K, a.un[v * N + p]);
+            a.acc[v * N + p] = fma(2.0, K, a.acc[v * N + p]);
+          }
+          break;
+        case EPI_RK4_LAST:
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            const double K = a.k[v * N + p] + cv[v];
+            a.out[v * N + p] = fma(a.a, a.acc[v * N + p] + K, a.un[v * N + p]);
+          }
+          break;
+        case EPI_SSP_1:
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            const double K = a.k[v * N + p] + cv[v];
+            a.out[v * N + p] = fma(a.a, K, a.un[v * N + p]);
+          }
+          break;
+        case EPI_SSP_2:
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            const double K = a.k[v * N + p] + cv[v];
+            a.out[v * N + p] = 0.75 * a.un[v * N + p] + 0.25 * fma(a.a, K, a.u[v * N + p]);
+          }
+          break;
+        case EPI_SSP_3:
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            const double K = a.k[v * N + p] + cv[v];
+            a.out[v * N + p] = (1.0 / 3.0) * a.un[v * N + p] + (2.0 / 3.0) * fma(a.a, K, a.u[v * N + p]);
+          }
+          break;
+        default:
+          break;
+      }
+    }
+  }
+}
+
+template <int D>
+cudaError_t launch_d(const DirArgs& a, cudaStream_t s) {
+  constexpr int AX = (D == 0) ? 1 : 0;
+  constexpr int BX = (D == 2) ? 1 : 2;
+  dim3 grid((a.g.n[D] + TP - 1) / TP, (a.g.n[AX] + W - 1) / W, a.g.n[BX]);
+  k_dir<D><<<grid, NTHREADS, SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t prepare_dir_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(k_dir<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dir<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dir<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  return e;
+}
+
+cudaError_t launch_dir(int d, const DirArgs& a, cudaStream_t s) {
+  switch (d) {
+    case 0:
+      return launch_d<0>(a, s);
+    case 1:
+      return launch_d<1>(a, s);
+    default:
+      return launch_d<2>(a, s);
+  }
+}
+
+}  // namespace ns3d

@@ -1,0 +1,295 @@
+// Pointwise and stencil-reduction kernels of libns3d.so:
+//  - primitive variables (Sec. 2.1 equation of state),
+//  - velocity/temperature gradients -> viscous flux vectors f^v, g^v, h^v
+//    (Sec. 2.1 stresses and heat flux, 4th-order central differences),
+//  - statistics (conservation sums, kinetic energy, enstrophy, extrema, CFL)
+//    with a deterministic two-level FP64 reduction (warp shuffles + fixed-order
+//    partials).
+#include <math.h>
+
+#include "ns3d_internal.cuh"
+
+namespace ns3d {
+
+namespace {
+
+constexpr int PW_THREADS = 256;
+
+int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  long long cap = 152LL * 16;
+  return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+// Primitive variables of one point: u, v, w, p, T = gamma p / rho, H = (e + p)/rho, sqrt(rho).
+__global__ void __launch_bounds__(PW_THREADS) k_prim(const double* __restrict__ u, double* __restrict__ pm,
+                                                     long long N, double gamma, int* __restrict__ status) {
+  int bad = 0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    const double rho = u[p], mx = u[N + p], my = u[2 * N + p], mz = u[3 * N + p], e = u[4 * N + p];
+    const double ri = 1.0 / rho;
+    const double vx = mx * ri, vy = my * ri, vz = mz * ri;
+    const double ke = 0.5 * (mx * vx + my * vy + mz * vz);
+    const double pr = (gamma - 1.0) * (e - ke);
+    pm[PM_U * N + p] = vx;
+    pm[PM_V * N + p] = vy;
+    pm[PM_W * N + p] = vz;
+    pm[PM_P * N + p] = pr;
+    pm[PM_T * N + p] = gamma * pr * ri;
+    pm[PM_H * N + p] = (e + pr) * ri;
+    pm[PM_SR * N + p] = sqrt(rho);
+    bad |= !(rho > 0.0) | !(pr > 0.0) | !isfinite(e) | !isfinite(mx + my + mz);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONPHYS);
+}
+
+__device__ __forceinline__ long long flat3(int i, int j, int k, int nx, int ny) {
+  return ((long long)k * ny + j) * nx + i;
+}
+
+// 4th-order central first derivative, difference form, times 1/(12 h).
+__device__ __forceinline__ double d4(double qm2, double qm1, double qp1, double qp2, double r12h) {
+  return fma(8.0, qp1 - qm1, -(qp2 - qm2)) * r12h;
+}
+
+// Gradients of (u, v, w, T) at every point, then the three viscous flux vectors.
+__global__ void __launch_bounds__(PW_THREADS) k_visc(const double* __restrict__ pm, double* __restrict__ fv,
+                                                     int nx, int ny, int nz, double r12hx, double r12hy,
+                                                     double r12hz, double mu, double kappa) {
+  const long long N = (long long)nx * ny * nz;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(p % nx);
+    const int j = (int)((p / nx) % ny);
+    const int k = (int)(p / ((long long)nx * ny));
+    double G[4][3];
+    const int n3[3] = {nx, ny, nz};
+    const double r12[3] = {r12hx, r12hy, r12hz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      long long nb[4];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const int off = (o < 2) ? (o - 2) : (o - 1);  // -2, -1, +1, +2
+        int c[3] = {i, j, k};
+        c[d] = wrap_idx(c[d] + off, n3[d]);
+        nb[o] = flat3(c[0], c[1], c[2], nx, ny);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int plane = (q < 3) ? q : PM_T;
+        const double* A = pm + (long long)plane * N;
+        G[q][d] = d4(__ldg(A + nb[0]), __ldg(A + nb[1]), __ldg(A + nb[2]), __ldg(A + nb[3]), r12[d]);
+      }
+    }
+    const double vel[3] = {pm[PM_U * N + p], pm[PM_V * N + p], pm[PM_W * N + p]};
+    const double tdiv = (2.0 / 3.0) * (G[0][0] + G[1][1] + G[2][2]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double tau[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) tau[m] = (m == d) ? mu * fma(2.0, G[d][d], -tdiv) : mu * (G[m][d] + G[d][m]);
+      const double en = fma(vel[0], tau[0], fma(vel[1], tau[1], fma(vel[2], tau[2], kappa * G[3][d])));
+      fv[(long long)(4 * d + 0) * N + p] = tau[0];
+      fv[(long long)(4 * d + 1) * N + p] = tau[1];
+      fv[(long long)(4 * d + 2) * N + p] = tau[2];
+      fv[(long long)(4 * d + 3) * N + p] = en;
+    }
+  }
+}
+
+// ---- statistics ------------------------------------------------------------
+constexpr int ST_THREADS = 256;
+constexpr int ST_MAX_BLOCKS = 1024;
+constexpr int NSUM = 7;   // mass, 3 momenta, energy, ke, enstrophy
+constexpr int NRED = 10;  // + rho_min, p_min, max wavespeed/dx
+
+struct Red {
+  double s[NSUM];
+  double rmin, pmin, wmax;
+};
+
+__device__ __forceinline__ void red_combine(Red& a, const Red& b) {
+#pragma unroll
+  for (int m = 0; m < NSUM; ++m) a.s[m] += b.s[m];
+  a.rmin = fmin(a.rmin, b.rmin);
+  a.pmin = fmin(a.pmin, b.pmin);
+  a.wmax = fmax(a.wmax, b.wmax);
+}
+
+__device__ __forceinline__ Red warp_reduce(Red r) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    Red o;
+#pragma unroll
+    for (int m = 0; m < NSUM; ++m) o.s[m] = __shfl_down_sync(0xffffffffu, r.s[m], off);
+    o.rmin = __shfl_down_sync(0xffffffffu, r.rmin, off);
+    o.pmin = __shfl_down_sync(0xffffffffu, r.pmin, off);
+    o.wmax = __shfl_down_sync(0xffffffffu, r.wmax, off);
+    red_combine(r, o);
+  }
+  return r;
+}
+
+// Fixed-shape block reduction: lane order, then warp order.  Result valid in thread 0.
+__device__ Red block_reduce(Red r) {
+  __shared__ double sh[ST_THREADS / 32][NRED];
+  r = warp_reduce(r);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int m = 0; m < NSUM; ++m) sh[wid][m] = r.s[m];
+    sh[wid][7] = r.rmin;
+    sh[wid][8] = r.pmin;
+    sh[wid][9] = r.wmax;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    Red t;
+    if (lane < ST_THREADS / 32) {
+#pragma unroll
+      for (int m = 0; m < NSUM; ++m) t.s[m] = sh[lane][m];
+      t.rmin = sh[lane][7];
+      t.pmin = sh[lane][8];
+      t.wmax = sh[lane][9];
+    } else {
+#pragma unroll
+      for (int m = 0; m < NSUM; ++m) t.s[m] = 0.0;
+      t.rmin = INFINITY;
+      t.pmin = INFINITY;
+      t.wmax = 0.0;
+    }
+    r = warp_reduce(t);
+  }
+  return r;
+}
+
+__global__ void __launch_bounds__(ST_THREADS) k_stats(const double* __restrict__ u, const double* __restrict__ pm,
+                                                      int nx, int ny, int nz, double hx, double hy, double hz,
+                                                      double* __restrict__ partials) {
+  const long long N = (long long)nx * ny * nz;
+  const int n3[3] = {nx, ny, nz};
+  const double r12[3] = {1.0 / (12.0 * hx), 1.0 / (12.0 * hy), 1.0 / (12.0 * hz)};
+  const double rh[3] = {1.0 / hx, 1.0 / hy, 1.0 / hz};
+  Red r;
+#pragma unroll
+  for (int m = 0; m < NSUM; ++m) r.s[m] = 0.0;
+  r.rmin = INFINITY;
+  r.pmin = INFINITY;
+  r.wmax = 0.0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(p % nx);
+    const int j = (int)((p / nx) % ny);
+    const int k = (int)(p / ((long long)nx * ny));
+    const double rho = u[p];
+    const double vel[3] = {pm[PM_U * N + p], pm[PM_V * N + p], pm[PM_W * N + p]};
+    const double pr = pm[PM_P * N + p];
+    r.s[0] += rho;
+    r.s[1] += u[N + p];
+    r.s[2] += u[2 * N + p];
+    r.s[3] += u[3 * N + p];
+    r.s[4] += u[4 * N + p];
+    r.s[5] += 0.5 * rho * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
+    // velocity gradient entries needed by the vorticity: dv_m/dx_d, m != d
+    double G[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      long long nb[4];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const int off = (o < 2) ? (o - 2) : (o - 1);
+        int c[3] = {i, j, k};
+        c[d] = wrap_idx(c[d] + off, n3[d]);
+        nb[o] = flat3(c[0], c[1], c[2], nx, ny);
+      }
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        if (m == d) continue;
+        const double* A = pm + (long long)m * N;
+        G[m][d] = d4(__ldg(A + nb[0]), __ldg(A + nb[1]), __ldg(A + nb[2]), __ldg(A + nb[3]), r12[d]);
+      }
+    }
+    const double wx = G[2][1] - G[1][2], wy = G[0][2] - G[2][0], wz = G[1][0] - G[0][1];
+    r.s[6] += 0.5 * rho * (wx * wx + wy * wy + wz * wz);
+    r.rmin = fmin(r.rmin, rho);
+    r.pmin = fmin(r.pmin, pr);
+    const double c = sqrt(pm[PM_T * N + p]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) r.wmax = fmax(r.wmax, (fabs(vel[d]) + c) * rh[d]);
+  }
+  r = block_reduce(r);
+  if (threadIdx.x == 0) {
+    double* o = partials + (long long)blockIdx.x * NRED;
+#pragma unroll
+    for (int m = 0; m < NSUM; ++m) o[m] = r.s[m];
+    o[7] = r.rmin;
+    o[8] = r.pmin;
+    o[9] = r.wmax;
+  }
+}
+
+__global__ void __launch_bounds__(ST_THREADS) k_stats_final(const double* __restrict__ partials, int nblocks,
+                                                            const int* __restrict__ status, double vol,
+                                                            double inv_n, double* __restrict__ out) {
+  Red r;
+#pragma unroll
+  for (int m = 0; m < NSUM; ++m) r.s[m] = 0.0;
+  r.rmin = INFINITY;
+  r.pmin = INFINITY;
+  r.wmax = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    const double* q = partials + (long long)b * NRED;
+    Red t;
+#pragma unroll
+    for (int m = 0; m < NSUM; ++m) t.s[m] = q[m];
+    t.rmin = q[7];
+    t.pmin = q[8];
+    t.wmax = q[9];
+    red_combine(r, t);
+  }
+  r = block_reduce(r);
+  if (threadIdx.x == 0) {
+    for (int m = 0; m < 5; ++m) out[m] = r.s[m] * vol;
+    out[5] = r.s[5] * inv_n;
+    out[6] = r.s[6] * inv_n;
+    out[7] = r.rmin;
+    out[8] = r.pmin;
+    out[9] = r.wmax;
+    out[10] = (double)(*status);
+    out[11] = 0.0;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_prim(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s) {
+  k_prim<<<grid_for(g.N, PW_THREADS), PW_THREADS, 0, s>>>(u, pm, g.N, gamma, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_visc(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s) {
+  k_visc<<<grid_for(g.N, PW_THREADS), PW_THREADS, 0, s>>>(pm, fv, g.n[0], g.n[1], g.n[2], 1.0 / (12.0 * g.h[0]),
+                                                          1.0 / (12.0 * g.h[1]), 1.0 / (12.0 * g.h[2]), mu, kappa);
+  return cudaGetLastError();
+}
+
+int stats_num_blocks(const Grid& g) {
+  long long b = (g.N + ST_THREADS - 1) / ST_THREADS;
+  return (int)(b < ST_MAX_BLOCKS ? (b > 0 ? b : 1) : ST_MAX_BLOCKS);
+}
+
+cudaError_t launch_stats(const Grid& g, const double* u, const double* pm, double gamma, double* partials,
+                         cudaStream_t s) {
+  (void)gamma;
+  k_stats<<<stats_num_blocks(g), ST_THREADS, 0, s>>>(u, pm, g.n[0], g.n[1], g.n[2], g.h[0], g.h[1], g.h[2],
+                                                     partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stats_final(const Grid& g, const double* partials, int nblocks, const int* status, double* out,
+                               cudaStream_t s) {
+  k_stats_final<<<1, ST_THREADS, 0, s>>>(partials, nblocks, status, g.h[0] * g.h[1] * g.h[2], 1.0 / (double)g.N,
+                                         out);
+  return cudaGetLastError();
+}
+
+}  // namespace ns3d

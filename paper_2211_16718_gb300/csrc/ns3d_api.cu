@@ -1,0 +1,463 @@
+// Host side of the C ABI declared in include/ns3d.h: parameter validation,
+// library-owned device scratch, launch sequences of the right-hand side and of
+// the Runge-Kutta stages, statistics, error reporting and kernel timing.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "ns3d_internal.cuh"
+
+using namespace ns3d;
+
+struct TimedLaunch {
+  int kid;
+  cudaEvent_t e0, e1;
+};
+
+struct ns3d_ctx {
+  ns3d_params p;
+  Grid g;
+  cudaStream_t stream;
+  int device;
+  double* pm = nullptr;        // [NPRIM][N]
+  double* fv = nullptr;        // [NVISC][N] (viscous only)
+  double* k = nullptr;         // [5][N] RHS accumulator
+  double* ua = nullptr;        // [5][N] stage state
+  double* ub = nullptr;        // [5][N] stage state
+  double* acc = nullptr;       // [5][N] RK4 accumulator
+  double* partials = nullptr;  // [stats blocks][10]
+  double* stats_dev = nullptr; // [NS3D_STATS_NDOUBLE]
+  int* status = nullptr;       // sticky status word
+  double* uhost_dev = nullptr; // device state for ns3d_step_host (lazy)
+  double* stats_host = nullptr;// pinned [NS3D_STATS_NDOUBLE]
+  int nstat_blocks = 0;
+  char err[512] = {0};
+  // timing
+  bool timing = false;
+  std::vector<TimedLaunch> pending;
+  std::vector<cudaEvent_t> pool;
+  double ms[NS3D_K_COUNT] = {0};
+  long long launches[NS3D_K_COUNT] = {0};
+};
+
+namespace {
+
+int set_err(ns3d_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+int cuda_fail(ns3d_ctx* c, cudaError_t e, const char* what) {
+  return set_err(c, NS3D_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+cudaEvent_t pool_get(ns3d_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch wrapper: records events around the launch when timing is on.
+template <typename F>
+int timed(ns3d_ctx* c, int kid, F&& fn, const char* what) {
+  TimedLaunch t{kid, nullptr, nullptr};
+  if (c->timing) {
+    t.e0 = pool_get(c);
+    t.e1 = pool_get(c);
+    cudaEventRecord(t.e0, c->stream);
+  }
+  cudaError_t e = fn();
+  if (c->timing) {
+    cudaEventRecord(t.e1, c->stream);
+    c->pending.push_back(t);
+  }
+  c->launches[kid] += 1;
+  if (e != cudaSuccess) return cuda_fail(c, e, what);
+  return NS3D_OK;
+}
+
+bool overlaps(const void* a, const void* b, size_t bytes) {
+  const char* x = (const char*)a;
+  const char* y = (const char*)b;
+  return x < y + bytes && y < x + bytes;
+}
+
+DirArgs base_args(ns3d_ctx* c, const double* u) {
+  DirArgs a;
+  a.g = c->g;
+  a.u = u;
+  a.pm = c->pm;
+  a.fv = (c->p.mu_eff > 0.0) ? c->fv : nullptr;
+  a.k = c->k;
+  a.epi = EPI_ACC_WRITE;
+  a.out = nullptr;
+  a.un = nullptr;
+  a.acc = c->acc;
+  a.a = 0.0;
+  a.gamma = c->p.gamma;
+  a.eps4 = 4.0 * c->p.weno_eps;
+  a.hdelta = c->p.harten_delta;
+  a.status = c->status;
+  return a;
+}
+
+// One full right-hand-side evaluation of state u: primitives, viscous fluxes,
+// x and y passes accumulating into k, z pass with the given epilogue.
+int rhs_pass(ns3d_ctx* c, const double* u, int epi, double* out, const double* un, double coef) {
+  int rc = timed(c, NS3D_K_PRIM, [&] { return launch_prim(c->g, u, c->pm, c->p.gamma, c->status, c->stream); },
+                 "primitive kernel");
+  if (rc) return rc;
+  if (c->p.mu_eff > 0.0) {
+    const double kappa = c->p.mu_eff / ((c->p.gamma - 1.0) * c->p.prandtl);
+    rc = timed(c, NS3D_K_VISC, [&] { return launch_visc(c->g, c->pm, c->fv, c->p.mu_eff, kappa, c->stream); },
+               "viscous-flux kernel");
+    if (rc) return rc;
+  }
+  DirArgs a = base_args(c, u);
+  a.epi = EPI_ACC_WRITE;
+  rc = timed(c, NS3D_K_DIR_X, [&] { return launch_dir(0, a, c->stream); }, "x-direction kernel");
+  if (rc) return rc;
+  a.epi = EPI_ACC_ADD;
+  rc = timed(c, NS3D_K_DIR_Y, [&] { return launch_dir(1, a, c->stream); }, "y-direction kernel");
+  if (rc) return rc;
+  a.epi = epi;
+  a.out = out;
+  a.un = un;
+  a.a = coef;
+  return timed(c, NS3D_K_DIR_Z, [&] { return launch_dir(2, a, c->stream); }, "z-direction kernel");
+}
+
+int stats_pass(ns3d_ctx* c, const double* u, double* out_dev) {
+  int rc = timed(c, NS3D_K_PRIM, [&] { return launch_prim(c->g, u, c->pm, c->p.gamma, c->status, c->stream); },
+                 "primitive kernel");
+  if (rc) return rc;
+  rc = timed(c, NS3D_K_STATS, [&] { return launch_stats(c->g, u, c->pm, c->p.gamma, c->partials, c->stream); },
+             "statistics kernel");
+  if (rc) return rc;
+  return timed(c, NS3D_K_STATS_FINAL,
+               [&] { return launch_stats_final(c->g, c->partials, c->nstat_blocks, c->status, out_dev, c->stream); },
+               "statistics final kernel");
+}
+
+int rk_one_step(ns3d_ctx* c, double* u, double dt) {
+  int rc;
+  if (c->p.rk == NS3D_RK4) {
+    if ((rc = rhs_pass(c, u, EPI_RK4_FIRST, c->ua, u, 0.5 * dt))) return rc;
+    if ((rc = rhs_pass(c, c->ua, EPI_RK4_MID, c->ub, u, 0.5 * dt))) return rc;
+    if ((rc = rhs_pass(c, c->ub, EPI_RK4_MID, c->ua, u, dt))) return rc;
+    return rhs_pass(c, c->ua, EPI_RK4_LAST, u, u, dt / 6.0);
+  }
+  if ((rc = rhs_pass(c, u, EPI_SSP_1, c->ua, u, dt))) return rc;
+  if ((rc = rhs_pass(c, c->ua, EPI_SSP_2, c->ub, u, dt))) return rc;
+  return rhs_pass(c, c->ub, EPI_SSP_3, u, u, dt);
+}
+
+int collect_timing(ns3d_ctx* c) {
+  for (auto& t : c->pending) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventElapsedTime(&ms, t.e0, t.e1);
+    if (e != cudaSuccess) return cuda_fail(c, e, "event timing");
+    c->ms[t.kid] += ms;
+    c->pool.push_back(t.e0);
+    c->pool.push_back(t.e1);
+  }
+  c->pending.clear();
+  return NS3D_OK;
+}
+
+int validate(const ns3d_params* p, char* msg, size_t n) {
+  if (!p) return snprintf(msg, n, "params is NULL"), NS3D_EINVAL;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return snprintf(msg, n, "grid sizes must be >= 1"), NS3D_EINVAL;
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  if (N > (1LL << 32)) return snprintf(msg, n, "grid too large (%lld points)", N), NS3D_EINVAL;
+  if (p->nx > 65535 * 4 || p->ny > 65535 || p->nz > 65535)
+    return snprintf(msg, n, "grid dimension beyond launch limits"), NS3D_EINVAL;
+  if (!(p->lx > 0) || !(p->ly > 0) || !(p->lz > 0) || !isfinite(p->lx) || !isfinite(p->ly) || !isfinite(p->lz))
+    return snprintf(msg, n, "box lengths must be finite and > 0"), NS3D_EINVAL;
+  if (!(p->gamma > 1.0) || !isfinite(p->gamma)) return snprintf(msg, n, "gamma must be > 1"), NS3D_EINVAL;
+  if (!(p->mu_eff >= 0.0) || !isfinite(p->mu_eff)) return snprintf(msg, n, "mu_eff must be >= 0"), NS3D_EINVAL;
+  if (p->mu_eff > 0.0 && (!(p->prandtl > 0.0) || !isfinite(p->prandtl)))
+    return snprintf(msg, n, "prandtl must be > 0"), NS3D_EINVAL;
+  if (!(p->weno_eps > 0.0) || !isfinite(p->weno_eps)) return snprintf(msg, n, "weno_eps must be > 0"), NS3D_EINVAL;
+  if (p->weno_p != 2) return snprintf(msg, n, "only weno_p = 2 is supported"), NS3D_EINVAL;
+  if (!(p->harten_delta >= 0.0) || !isfinite(p->harten_delta))
+    return snprintf(msg, n, "harten_delta must be >= 0"), NS3D_EINVAL;
+  if (p->rk != NS3D_RK4 && p->rk != NS3D_SSPRK3) return snprintf(msg, n, "unknown rk scheme"), NS3D_EINVAL;
+  if (p->precision != NS3D_FP64) return snprintf(msg, n, "unsupported precision mode"), NS3D_EINVAL;
+  return NS3D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ns3d_default_params(ns3d_params* p, int nx, int ny, int nz) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->nx = nx;
+  p->ny = ny;
+  p->nz = nz;
+  p->rk = NS3D_RK4;
+  p->precision = NS3D_FP64;
+  p->weno_p = 2;
+  p->lx = p->ly = p->lz = 2.0 * M_PI;
+  p->gamma = 1.4;
+  p->mu_eff = 0.0;
+  p->prandtl = 0.72;
+  p->weno_eps = 1e-6;
+  p->harten_delta = 0.1;
+}
+
+const char* ns3d_strerror(int code) {
+  switch (code) {
+    case NS3D_OK: return "ok";
+    case NS3D_EINVAL: return "invalid argument";
+    case NS3D_ENOMEM: return "out of memory";
+    case NS3D_ECUDA: return "CUDA error";
+    case NS3D_ENONPHYSICAL: return "non-physical state (rho <= 0, p <= 0, or non-finite value)";
+    case NS3D_ETIMEOUT: return "device-side wait timed out";
+    default: return "unknown error";
+  }
+}
+
+const char* ns3d_last_error(const ns3d_ctx* c) { return c ? c->err : "context is NULL"; }
+
+int ns3d_init(const ns3d_params* p, void* cuda_stream, ns3d_ctx** out) {
+  if (!out) return NS3D_EINVAL;
+  *out = nullptr;
+  char msg[256];
+  int rc = validate(p, msg, sizeof(msg));
+  if (rc) return rc;
+  ns3d_ctx* c = new (std::nothrow) ns3d_ctx();
+  if (!c) return NS3D_ENOMEM;
+  c->p = *p;
+  c->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&c->device);
+  c->g.n[0] = p->nx;
+  c->g.n[1] = p->ny;
+  c->g.n[2] = p->nz;
+  c->g.N = (long long)p->nx * p->ny * p->nz;
+  c->g.h[0] = p->lx / p->nx;
+  c->g.h[1] = p->ly / p->ny;
+  c->g.h[2] = p->lz / p->nz;
+  const size_t N = (size_t)c->g.N;
+  c->nstat_blocks = stats_num_blocks(c->g);
+  cudaError_t e = prepare_dir_kernels();
+  if (e != cudaSuccess) {
+    rc = cuda_fail(c, e, "kernel attributes");
+    ns3d_free(c);
+    return rc;
+  }
+  struct {
+    void** ptr;
+    size_t bytes;
+  } allocs[] = {
+      {(void**)&c->pm, sizeof(double) * NPRIM * N},
+      {(void**)&c->k, sizeof(double) * 5 * N},
+      {(void**)&c->ua, sizeof(double) * 5 * N},
+      {(void**)&c->ub, sizeof(double) * 5 * N},
+      {(void**)&c->acc, sizeof(double) * 5 * N},
+      {(void**)&c->partials, sizeof(double) * 16 * (size_t)c->nstat_blocks},
+      {(void**)&c->stats_dev, sizeof(double) * NS3D_STATS_NDOUBLE},
+      {(void**)&c->status, sizeof(int)},
+  };
+  for (auto& a : allocs) {
+    if (cudaMalloc(a.ptr, a.bytes) != cudaSuccess) {
+      cudaGetLastError();
+      ns3d_free(c);
+      return NS3D_ENOMEM;
+    }
+  }
+  if (p->mu_eff > 0.0 && cudaMalloc((void**)&c->fv, sizeof(double) * NVISC * N) != cudaSuccess) {
+    cudaGetLastError();
+    ns3d_free(c);
+    return NS3D_ENOMEM;
+  }
+  if (cudaMallocHost((void**)&c->stats_host, sizeof(double) * NS3D_STATS_NDOUBLE) != cudaSuccess) {
+    cudaGetLastError();
+    ns3d_free(c);
+    return NS3D_ENOMEM;
+  }
+  e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    ns3d_free(c);
+    return NS3D_ECUDA;
+  }
+  *out = c;
+  return NS3D_OK;
+}
+
+void ns3d_free(ns3d_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto& t : c->pending) {
+    cudaEventDestroy(t.e0);
+    cudaEventDestroy(t.e1);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
+  cudaFree(c->pm);
+  cudaFree(c->fv);
+  cudaFree(c->k);
+  cudaFree(c->ua);
+  cudaFree(c->ub);
+  cudaFree(c->acc);
+  cudaFree(c->partials);
+  cudaFree(c->stats_dev);
+  cudaFree(c->status);
+  cudaFree(c->uhost_dev);
+  if (c->stats_host) cudaFreeHost(c->stats_host);
+  delete c;
+}
+
+int ns3d_set_stream(ns3d_ctx* c, void* s) {
+  if (!c) return NS3D_EINVAL;
+  c->stream = (cudaStream_t)s;
+  return NS3D_OK;
+}
+
+int ns3d_rhs(ns3d_ctx* c, const double* u, double* rhs) {
+  if (!c) return NS3D_EINVAL;
+  if (!u || !rhs) return set_err(c, NS3D_EINVAL, "null state or rhs pointer");
+  const size_t bytes = sizeof(double) * 5 * (size_t)c->g.N;
+  if (overlaps(u, rhs, bytes)) return set_err(c, NS3D_EINVAL, "u and rhs overlap");
+  return rhs_pass(c, u, EPI_RHS_OUT, rhs, nullptr, 0.0);
+}
+
+int ns3d_rk_step(ns3d_ctx* c, double* u, double dt, int nsteps) {
+  if (!c) return NS3D_EINVAL;
+  if (!u) return set_err(c, NS3D_EINVAL, "null state pointer");
+  if (nsteps < 0 || !isfinite(dt)) return set_err(c, NS3D_EINVAL, "nsteps must be >= 0 and dt finite");
+  for (int s = 0; s < nsteps; ++s) {
+    int rc = rk_one_step(c, u, dt);
+    if (rc) return rc;
+  }
+  return NS3D_OK;
+}
+
+int ns3d_stats_async(ns3d_ctx* c, const double* u, double* out_dev) {
+  if (!c) return NS3D_EINVAL;
+  if (!u || !out_dev) return set_err(c, NS3D_EINVAL, "null pointer");
+  return stats_pass(c, u, out_dev);
+}
+
+static void fill_stats(const double* s, ns3d_stats_t* o) {
+  o->mass = s[0];
+  o->momx = s[1];
+  o->momy = s[2];
+  o->momz = s[3];
+  o->energy = s[4];
+  o->ke = s[5];
+  o->enstrophy = s[6];
+  o->rho_min = s[7];
+  o->p_min = s[8];
+  o->max_wavespeed_over_dx = s[9];
+  o->status = (s[10] != 0.0) ? NS3D_ENONPHYSICAL : NS3D_OK;
+  o->reserved = 0;
+}
+
+int ns3d_stats(ns3d_ctx* c, const double* u, ns3d_stats_t* out) {
+  if (!c) return NS3D_EINVAL;
+  if (!u || !out) return set_err(c, NS3D_EINVAL, "null pointer");
+  int rc = stats_pass(c, u, c->stats_dev);
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpyAsync(c->stats_host, c->stats_dev, sizeof(double) * NS3D_STATS_NDOUBLE,
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "statistics copy");
+  fill_stats(c->stats_host, out);
+  if (out->status) return set_err(c, NS3D_ENONPHYSICAL, "non-physical state detected");
+  return NS3D_OK;
+}
+
+int ns3d_check(ns3d_ctx* c) {
+  if (!c) return NS3D_EINVAL;
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "status read");
+  if (h) return set_err(c, NS3D_ENONPHYSICAL, "non-physical state detected");
+  return NS3D_OK;
+}
+
+int ns3d_step_host(ns3d_ctx* c, double* u_host, double dt, int nsteps, ns3d_stats_t* stats_host) {
+  if (!c) return NS3D_EINVAL;
+  if (!u_host) return set_err(c, NS3D_EINVAL, "null host state");
+  if (nsteps < 0 || !isfinite(dt)) return set_err(c, NS3D_EINVAL, "nsteps must be >= 0 and dt finite");
+  const size_t bytes = sizeof(double) * 5 * (size_t)c->g.N;
+  if (!c->uhost_dev && cudaMalloc((void**)&c->uhost_dev, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(c, NS3D_ENOMEM, "device state for host stepping");
+  }
+  cudaError_t e = cudaMemcpyAsync(c->uhost_dev, u_host, bytes, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
+  int rc = ns3d_rk_step(c, c->uhost_dev, dt, nsteps);
+  if (rc) return rc;
+  if (stats_host) {
+    rc = stats_pass(c, c->uhost_dev, c->stats_dev);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(c->stats_host, c->stats_dev, sizeof(double) * NS3D_STATS_NDOUBLE, cudaMemcpyDeviceToHost,
+                        c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "statistics copy");
+  }
+  e = cudaMemcpyAsync(u_host, c->uhost_dev, bytes, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
+  if (stats_host) {
+    fill_stats(c->stats_host, stats_host);
+    if (stats_host->status) return set_err(c, NS3D_ENONPHYSICAL, "non-physical state detected");
+  }
+  return NS3D_OK;
+}
+
+int ns3d_timing_enable(ns3d_ctx* c, int on) {
+  if (!c) return NS3D_EINVAL;
+  cudaStreamSynchronize(c->stream);
+  for (auto& t : c->pending) {
+    c->pool.push_back(t.e0);
+    c->pool.push_back(t.e1);
+  }
+  c->pending.clear();
+  for (int k = 0; k < NS3D_K_COUNT; ++k) {
+    c->ms[k] = 0.0;
+    c->launches[k] = 0;
+  }
+  c->timing = (on != 0);
+  return NS3D_OK;
+}
+
+int ns3d_timing_read(ns3d_ctx* c, double* ms_out, long long* launches_out, int n) {
+  if (!c || n < 0 || n > NS3D_K_COUNT) return NS3D_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "timing sync");
+  int rc = collect_timing(c);
+  if (rc) return rc;
+  for (int k = 0; k < n; ++k) {
+    if (ms_out) ms_out[k] = c->ms[k];
+    if (launches_out) launches_out[k] = c->launches[k];
+  }
+  return NS3D_OK;
+}
+
+int ns3d_alu_probe(double out[5]) {
+  if (!out) return NS3D_EINVAL;
+  return alu_probe(out);
+}
+
+}  // extern "C"

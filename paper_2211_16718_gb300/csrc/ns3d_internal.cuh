@@ -1,0 +1,74 @@
+// Internal declarations shared by the CUDA translation units of libns3d.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ns3d.h"
+
+namespace ns3d {
+
+// Primitive-variable planes written by the primitive kernel ([NPRIM][N]).
+enum { PM_U = 0, PM_V = 1, PM_W = 2, PM_P = 3, PM_T = 4, PM_H = 5, PM_SR = 6, NPRIM = 7 };
+// Viscous flux planes ([12][N]): direction d occupies planes 4d..4d+3 holding
+// (tau_xd, tau_yd, tau_zd, u tau_xd + v tau_yd + w tau_zd - q_d).
+enum { NVISC = 12 };
+
+// Status bits of the sticky device status word.
+enum { ST_NONPHYS = 1 };
+
+// Epilogue of the z-direction kernel (the last of the three direction passes).
+enum Epi {
+  EPI_ACC_WRITE = 0,  // k = contribution                      (first direction)
+  EPI_ACC_ADD = 1,    // k += contribution                     (middle direction)
+  EPI_RHS_OUT = 2,    // out = k + contribution                (ns3d_rhs)
+  EPI_RK4_FIRST = 3,  // K = k + c; uout = un + a K; acc = K
+  EPI_RK4_MID = 4,    // K; uout = un + a K; acc += 2 K
+  EPI_RK4_LAST = 5,   // K; uout = un + (dt/6)(acc + K)
+  EPI_SSP_1 = 6,      // uout = un + dt K
+  EPI_SSP_2 = 7,      // uout = 3/4 un + 1/4 (us + dt K)
+  EPI_SSP_3 = 8       // uout = 1/3 un + 2/3 (us + dt K)
+};
+
+struct Grid {
+  int n[3];          // nx, ny, nz
+  long long N;       // nx*ny*nz
+  double h[3];       // dx, dy, dz
+};
+
+struct DirArgs {
+  Grid g;
+  const double* u;   // stage input state [5][N]
+  const double* pm;  // primitives of u [NPRIM][N]
+  const double* fv;  // viscous fluxes [NVISC][N] or nullptr (inviscid)
+  double* k;         // RHS accumulator [5][N]
+  int epi;           // Epi
+  double* out;       // EPI_RHS_OUT: destination; RK modes: next stage state
+  const double* un;  // RK base state U_n
+  double* acc;       // RK4 accumulator
+  double a;          // RK stage coefficient (a_s * dt, or dt)
+  double gamma;
+  double eps4;       // 4 * weno_eps (smoothness indicators are scaled by 4)
+  double hdelta;     // Harten entropy-fix fraction
+  int* status;
+};
+
+// Launchers (return cudaGetLastError() of the launch).
+cudaError_t launch_prim(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s);
+cudaError_t launch_visc(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s);
+cudaError_t prepare_dir_kernels();  // per device, before the first launch
+cudaError_t launch_dir(int d, const DirArgs& a, cudaStream_t s);
+int stats_num_blocks(const Grid& g);
+cudaError_t launch_stats(const Grid& g, const double* u, const double* pm, double gamma, double* partials,
+                         cudaStream_t s);
+cudaError_t launch_stats_final(const Grid& g, const double* partials, int nblocks, const int* status,
+                               double* out, cudaStream_t s);
+int alu_probe(double out[5]);
+
+// Periodic wrap of an index that may be off by less than a few periods.
+__host__ __device__ inline int wrap_idx(int i, int n) {
+  int r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+}  // namespace ns3d

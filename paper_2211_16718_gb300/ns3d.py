@@ -1,0 +1,228 @@
+"""Thin ctypes binding of libns3d.so (include/ns3d.h): argument marshalling only.
+
+Every step of the right-hand side, the Runge-Kutta update and the statistics
+runs in the library's CUDA kernels; this module only passes torch tensors'
+device pointers and the current torch stream.  If the library is missing or
+cannot be loaded, every call raises ``RuntimeError`` (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(PKG, "libns3d.so")
+
+NS3D_OK, NS3D_EINVAL, NS3D_ENOMEM, NS3D_ECUDA, NS3D_ENONPHYSICAL, NS3D_ETIMEOUT = 0, -1, -2, -3, -4, -5
+NS3D_RK4, NS3D_SSPRK3 = 0, 1
+NS3D_FP64, NS3D_FP32_BULK = 0, 1
+NS3D_STATS_NDOUBLE = 12
+KERNELS = ("prim", "visc", "dir_x", "dir_y", "dir_z", "stats", "stats_final")
+EXPORTS = ("ns3d_default_params", "ns3d_init", "ns3d_free", "ns3d_set_stream", "ns3d_rhs", "ns3d_rk_step",
+           "ns3d_stats", "ns3d_stats_async", "ns3d_step_host", "ns3d_check", "ns3d_strerror", "ns3d_last_error",
+           "ns3d_timing_enable", "ns3d_timing_read", "ns3d_alu_probe")
+
+
+class Ns3dError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"ns3d error {code}: {msg}")
+        self.code = code
+
+
+class NonPhysicalError(Ns3dError):
+    pass
+
+
+class CParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("rk", ctypes.c_int), ("precision", ctypes.c_int), ("weno_p", ctypes.c_int),
+        ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("mu_eff", ctypes.c_double), ("prandtl", ctypes.c_double),
+        ("weno_eps", ctypes.c_double), ("harten_delta", ctypes.c_double),
+    ]
+
+
+class CStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("mass", "momx", "momy", "momz", "energy", "ke", "enstrophy",
+                                                 "rho_min", "p_min", "max_wavespeed_over_dx")] + \
+               [("status", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+STATS_FIELDS = tuple(n for n, _ in CStats._fields_[:10])
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libns3d.so once; raise RuntimeError if it is absent (no CPU fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIBPATH):
+                raise RuntimeError(f"{LIBPATH} is missing: build it with paper_2211_16718_gb300.build.build() "
+                                   "(nvcc for sm_103a); there is no CPU fallback")
+            L = ctypes.CDLL(LIBPATH)
+            P, D, I = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+            pp = ctypes.POINTER(CParams)
+            sigs = {
+                "ns3d_default_params": (None, [pp, I, I, I]),
+                "ns3d_init": (I, [pp, P, ctypes.POINTER(P)]),
+                "ns3d_free": (None, [P]),
+                "ns3d_set_stream": (I, [P, P]),
+                "ns3d_rhs": (I, [P, P, P]),
+                "ns3d_rk_step": (I, [P, P, D, I]),
+                "ns3d_stats": (I, [P, P, ctypes.POINTER(CStats)]),
+                "ns3d_stats_async": (I, [P, P, P]),
+                "ns3d_step_host": (I, [P, P, D, I, ctypes.POINTER(CStats)]),
+                "ns3d_check": (I, [P]),
+                "ns3d_strerror": (ctypes.c_char_p, [I]),
+                "ns3d_last_error": (ctypes.c_char_p, [P]),
+                "ns3d_timing_enable": (I, [P, I]),
+                "ns3d_timing_read": (I, [P, P, P, I]),
+                "ns3d_alu_probe": (I, [P]),
+            }
+            for name, (res, args) in sigs.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def default_params(nx: int, ny: int, nz: int, **kw) -> CParams:
+    p = CParams()
+    lib().ns3d_default_params(ctypes.byref(p), nx, ny, nz)
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+def _stream_handle():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dptr(t, n: int):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError("expected a CUDA float64 tensor")
+    if not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"expected a contiguous tensor of {n} elements, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One ns3d context (library-owned scratch) for a fixed grid and parameters."""
+
+    def __init__(self, nx: int, ny: int, nz: int, **kw):
+        self.params = default_params(nx, ny, nz, **kw)
+        self.N = nx * ny * nz
+        self.shape = (5, nz, ny, nx)
+        self._ctx = ctypes.c_void_p()
+        rc = lib().ns3d_init(ctypes.byref(self.params), _stream_handle(), ctypes.byref(self._ctx))
+        if rc != NS3D_OK:
+            raise Ns3dError(rc, lib().ns3d_strerror(rc).decode())
+
+    def _check(self, rc: int):
+        if rc == NS3D_OK:
+            return
+        msg = lib().ns3d_last_error(self._ctx).decode() or lib().ns3d_strerror(rc).decode()
+        if rc == NS3D_ENONPHYSICAL:
+            raise NonPhysicalError(rc, msg)
+        raise Ns3dError(rc, msg)
+
+    def _sync_stream(self):
+        self._check(lib().ns3d_set_stream(self._ctx, _stream_handle()))
+
+    def rhs(self, u, out=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(u)
+        self._sync_stream()
+        self._check(lib().ns3d_rhs(self._ctx, _dptr(u, 5 * self.N), _dptr(out, 5 * self.N)))
+        return out
+
+    def rk_step(self, u, dt: float, nsteps: int = 1):
+        self._sync_stream()
+        self._check(lib().ns3d_rk_step(self._ctx, _dptr(u, 5 * self.N), float(dt), int(nsteps)))
+        return u
+
+    def stats(self, u) -> dict:
+        self._sync_stream()
+        s = CStats()
+        rc = lib().ns3d_stats(self._ctx, _dptr(u, 5 * self.N), ctypes.byref(s))
+        if rc not in (NS3D_OK, NS3D_ENONPHYSICAL):
+            self._check(rc)
+        d = {n: getattr(s, n) for n in STATS_FIELDS}
+        d["status"] = s.status
+        return d
+
+    def stats_async(self, u, out):
+        """Write NS3D_STATS_NDOUBLE doubles of statistics into the device tensor out (no sync)."""
+        self._sync_stream()
+        self._check(lib().ns3d_stats_async(self._ctx, _dptr(u, 5 * self.N), _dptr(out, NS3D_STATS_NDOUBLE)))
+        return out
+
+    def step_host(self, u_host, dt: float, nsteps: int = 1) -> dict:
+        """End to end with a host numpy array (float64, C-contiguous, 5*N): copied in, stepped, copied back."""
+        import numpy as np
+        if not (isinstance(u_host, np.ndarray) and u_host.dtype == np.float64 and u_host.flags.c_contiguous
+                and u_host.size == 5 * self.N):
+            raise ValueError("expected a C-contiguous float64 numpy array of 5*N elements")
+        self._sync_stream()
+        s = CStats()
+        rc = lib().ns3d_step_host(self._ctx, ctypes.c_void_p(u_host.ctypes.data), float(dt), int(nsteps),
+                                  ctypes.byref(s))
+        if rc not in (NS3D_OK, NS3D_ENONPHYSICAL):
+            self._check(rc)
+        d = {n: getattr(s, n) for n in STATS_FIELDS}
+        d["status"] = s.status
+        return d
+
+    def check(self):
+        self._sync_stream()
+        self._check(lib().ns3d_check(self._ctx))
+
+    def timing_enable(self, on: bool = True):
+        self._check(lib().ns3d_timing_enable(self._ctx, int(bool(on))))
+
+    def timing_read(self) -> dict:
+        n = len(KERNELS)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_longlong * n)()
+        self._check(lib().ns3d_timing_read(self._ctx, ctypes.cast(ms, ctypes.c_void_p),
+                                           ctypes.cast(cnt, ctypes.c_void_p), n))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNELS)}
+
+    def close(self):
+        if self._ctx:
+            lib().ns3d_free(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def dt_from_cfl(self, u, cfl: float) -> float:
+        """dt = CFL / max over points and directions of (|u_d| + c)/dx_d (on the device)."""
+        w = self.stats(u)["max_wavespeed_over_dx"]
+        if not (w > 0 and math.isfinite(w)):
+            raise Ns3dError(NS3D_ENONPHYSICAL, "no finite positive wave speed")
+        return cfl / w
+
+
+def alu_probe() -> dict:
+    """Measured arithmetic throughput of the current device, G lane-ops/s."""
+    out = (ctypes.c_double * 5)()
+    rc = lib().ns3d_alu_probe(ctypes.cast(out, ctypes.c_void_p))
+    if rc != NS3D_OK:
+        raise Ns3dError(rc, lib().ns3d_strerror(rc).decode())
+    return dict(zip(("dfma", "dadd", "ddiv", "dsqrt", "ffma"), list(out)))

@@ -1,0 +1,29 @@
+"""Shared helpers of the test-suite (no method arithmetic)."""
+import numpy as np
+
+
+def rel_err(x, y) -> float:
+    """Relative max-norm of the whole vector: ||x - y||_inf / ||y||_inf (all 5 variables)."""
+    x = np.asarray(x)
+    y = np.asarray(y)
+    return float(np.abs(x - y).max() / np.abs(y).max())
+
+
+def rel_err_var(x, y) -> float:
+    """Per-variable normalised max-norm, max over the 5 conserved variables:
+    ||x_v - y_v||_inf / max(||y_v||_inf, 1e-3 max_w ||y_w||_inf).  Stricter than rel_err for
+    components that are small cancellation residues (e.g. the mass RHS of a solenoidal
+    field), whose absolute rounding is ~eps |f| / dx."""
+    x = np.asarray(x).reshape(5, -1)
+    y = np.asarray(y).reshape(5, -1)
+    scale = np.abs(y).max(axis=1)
+    floor = 1e-3 * scale.max()
+    return float((np.abs(x - y).max(axis=1) / np.maximum(scale, floor)).max())
+
+
+def inc_rel_err(x, y, u0) -> float:
+    """Relative max-norm error of the increment: ||(x - u0) - (y - u0)||_inf / ||y - u0||_inf."""
+    x = np.asarray(x)
+    y = np.asarray(y)
+    d = y - np.asarray(u0)
+    return float(np.abs(x - y).max() / np.abs(d).max())
