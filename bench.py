@@ -146,6 +146,22 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def ncu_traffic_per_point(kernel: str, source: str):
+    """DRAM bytes per grid point of one launch (dram__bytes_read.sum + dram__bytes_write.sum
+    from a committed ncu summary under profiles/), or None if the kernel source has changed
+    since the counters were taken."""
+    import glob
+    import hashlib
+    import re
+    sha = hashlib.sha256(open(source, "rb").read()).hexdigest()[:16]
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            m = re.match(rf"TRAFFIC {kernel} bytes_per_point=([0-9.]+) grid=(\d+) \S+ source_sha256=(\w+)", line)
+            if m and m.group(3) == sha:
+                return float(m.group(1)), os.path.basename(path), int(m.group(2))
+    return None
+
+
 def hit_state(n: int):
     from paper_2211_16718_gb300 import inputs as I
     return I.isotropic_turbulence(n, seed=0), I.hit_mu_eff()
@@ -271,6 +287,13 @@ def run_ours(args, world, rank, local):
                 "share_of_device_time": dir_ms / step_ms_total if step_ms_total > 0 else None,
                 "algorithmic_bytes_per_point": 8 * (5 + 6 + 4 + 5 + 5),
                 "hbm_gbs_algorithmic": 8 * (5 + 6 + 4 + 5 + 5) * n ** 3 / avg_launch_s / 1e9}
+    tr = ncu_traffic_per_point("k_dir", os.path.join(ROOT, "paper_2211_16718_gb300", "csrc", "k_dir.cu"))
+    if tr is not None:
+        bpp, src, grid = tr
+        roofline["traffic"] = bpp * n ** 3
+        roofline["traffic_note"] = (f"ncu dram read+write of one x-pass launch at {grid}^3 ({src}), "
+                                    f"{bpp:.1f} B/point scaled to {n}^3 (streaming kernel: traffic ~ points)")
+        roofline["hbm_frac_measured"] = bpp * n ** 3 / avg_launch_s / 1e9 / 6713.6
 
     # end to end through the C ABI with host buffers (pinned): H2D state, RK4 step,
     # statistics, D2H state + statistics, every step
