@@ -120,6 +120,33 @@ int ns3d_stats(ns3d_ctx *ctx, const double *u_dev, ns3d_stats_t *out_host);
  * status slot holds the sticky status word at that point (not cleared). */
 int ns3d_stats_async(ns3d_ctx *ctx, const double *u_dev, double *out_dev);
 
+/* Statistics of u_dev without any device allocation (the paper has no
+ * counterpart; this serves callers that must not let a library allocate device
+ * memory, e.g. a host code that owns all GPU memory through its own pool and
+ * budget, or an in-situ monitoring hook inside another solver's time loop:
+ * creating a context allocates scratch, and cudaMalloc/cudaFree bypass such a
+ * pool, can fail under memory pressure and synchronise the device).
+ *  - p: grid and gas parameters (nx, ny, nz >= 1, lx, ly, lz > 0, gamma > 1;
+ *    the other fields are ignored).  No context is needed.
+ *  - u_dev: the state, layout as above; out_dev: NS3D_STATS_NDOUBLE doubles on
+ *    the device, written in the order of ns3d_stats_async, with the status slot
+ *    1.0 if this state is non-physical (rho <= 0, p <= 0, non-finite), else 0.
+ *  - Work is enqueued on cuda_stream (a cudaStream_t; NULL = legacy default
+ *    stream); the call does not synchronise.
+ *  - Scratch: a fixed 96 KB array of per-block partial sums (1024 slots) held in
+ *    device memory by every GPU that loads the library, until the process
+ *    exits.  The kernel strides over the grid, so every grid up to 2^32 points
+ *    fits; larger grids return NS3D_EINVAL.  Every call overwrites the slots it
+ *    uses before reading them, so no state carries over between calls, but all
+ *    calls share the array: calls that overlap on the GPU (other streams,
+ *    other host threads) race and must be serialised by the caller.
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any stream
+ *    capture.
+ *  - Returns NS3D_OK, NS3D_EINVAL (null pointer, bad size) or NS3D_ECUDA.
+ *    Calls no cudaMalloc, cudaFree or other allocating routine. */
+int ns3d_stats_noalloc(const ns3d_params *p, const double *u_dev, double *out_dev, void *cuda_stream);
+
 /* End-to-end call with host buffers: copies u_host to library-owned device
  * memory, advances nsteps steps of size dt, computes the statistics of the
  * final state into *stats_host (may be NULL), copies the state back into

@@ -226,3 +226,20 @@ def alu_probe() -> dict:
     if rc != NS3D_OK:
         raise Ns3dError(rc, lib().ns3d_strerror(rc).decode())
     return dict(zip(("dfma", "dadd", "ddiv", "dsqrt", "ffma"), list(out)))
+
+
+def stats_noalloc(params: CParams, u, out):
+    """Statistics of the device state u into the device tensor out (NS3D_STATS_NDOUBLE
+    float64) through ns3d_stats_noalloc, which allocates no device memory: for callers that
+    own all GPU memory through their own pool or must not perturb another code's memory
+    footprint.  No context is needed; the work goes on the current torch stream without
+    synchronising.  Calls that overlap on the GPU share the library's fixed scratch array
+    and race; serialise them."""
+    fn = lib().ns3d_stats_noalloc
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.POINTER(CParams), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    n = params.nx * params.ny * params.nz
+    rc = fn(ctypes.byref(params), _dptr(u, 5 * n), _dptr(out, NS3D_STATS_NDOUBLE), _stream_handle())
+    if rc != NS3D_OK:
+        raise Ns3dError(rc, lib().ns3d_strerror(rc).decode())
+    return out
