@@ -38,6 +38,10 @@ RK_STAGES = 4
 #   direction pass: point fluxes 6, smoothness indicators 9 x 20, candidates +
 #   weighted combinations 9 x 46, Roe flux 96, difference + viscous divergence 34.
 FLOPS_DIR = 6 + 9 * 20 + 9 * 46 + 96 + 34
+# With the double-float weights (NS3D_FP64) the FP64 pipe executes per point and scalar:
+# window differences 3, third differences 3, two candidate chains 2 x 6, two weighted
+# sums 2 x 4; the weights themselves run on the FP32 pipe.
+FLOPS_DIR_DFW = 6 + 9 * (3 + 3 + 12 + 8) + 96 + 34
 FLOPS_RK_EPI = 15          # RK4 stage update in the z pass (5 components)
 FLOPS_PRIM = 17            # primitives (incl. 1 division, 1 square root)
 FLOPS_VISC = 111           # 12 gradients + 3 viscous flux vectors
@@ -55,6 +59,7 @@ def parse():
     ap.add_argument("--cfl", type=float, default=0.4)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-strict", action="store_true", help="skip the all-FP64 comparison run")
     return ap.parse_args()
 
 
@@ -230,63 +235,77 @@ def run_ours(args, world, rank, local):
 
     n = args.n
     u0, mu = hit_state(n)
-    solver = ns3d.Solver(n, n, n, mu_eff=mu)
-    ud = torch.from_numpy(u0.copy()).cuda()
-    dt = solver.dt_from_cfl(ud, args.cfl)
     K, W = args.steps, args.warmup
-    stats_buf = torch.zeros((W + K, ns3d.NS3D_STATS_NDOUBLE), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step(i):
-        solver.rk_step(ud, dt, 1)
-        solver.stats_async(ud, stats_buf[i])
+    def timed_loop(precision: int, K: int, W: int, sample_clocks: bool):
+        """W untimed + K timed steps (RK4 step + statistics into a device log)."""
+        solver = ns3d.Solver(n, n, n, mu_eff=mu, precision=precision)
+        ud = torch.from_numpy(u0.copy()).cuda()
+        dt = solver.dt_from_cfl(ud, args.cfl)
+        stats_buf = torch.zeros((W + K, ns3d.NS3D_STATS_NDOUBLE), dtype=torch.float64, device="cuda")
 
-    for i in range(W):
-        step(i)
-    torch.cuda.synchronize()
-    # flush L2 between warm-up and the timed region (the state alone exceeds L2 every step)
-    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device="cuda")
-    flush.fill_(1.0)
-    del flush
-    solver.timing_enable(True)
-    clocks = ClockSampler(local)
-    clocks.start()
-    barrier(world)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for i in range(W, W + K):
-        step(i)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    clk = clocks.stop()
-    ms_local = e0.elapsed_time(e1)
-    ktimes = solver.timing_read()
-    solver.timing_enable(False)
-    ms = max_over_ranks(ms_local, world)
+        def step(i):
+            solver.rk_step(ud, dt, 1)
+            solver.stats_async(ud, stats_buf[i])
+
+        for i in range(W):
+            step(i)
+        torch.cuda.synchronize()
+        # flush L2 before the timed region (the state alone exceeds L2 every step)
+        flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device="cuda")
+        flush.fill_(1.0)
+        del flush
+        solver.timing_enable(True)
+        clocks = ClockSampler(local) if sample_clocks else None
+        if clocks:
+            clocks.start()
+        barrier(world)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(W, W + K):
+            step(i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        clk = clocks.stop() if clocks else None
+        ms = max_over_ranks(e0.elapsed_time(e1), world)
+        ktimes = solver.timing_read()
+        solver.timing_enable(False)
+        st = stats_buf.cpu().numpy()
+        return solver, ud, dt, ms, ktimes, st, clk
+
+    # headline: NS3D_FP64 (FP64 values, double-float WENO weights)
+    solver, ud, dt, ms, ktimes, st, clk = timed_loop(ns3d.NS3D_FP64, K, W, True)
     pts_total = sum_over_ranks(float(n ** 3 * RK_STAGES * K), world)
     value = pts_total / (ms * 1e-3) / 1e9
-    st = stats_buf.cpu().numpy()
     status_ok = bool(np.all(st[:, 10] == 0))
     launches = int(sum(c for _, c in ktimes.values()))
 
-    # dominant kernel: the direction pass (x, y, z launches of the same kernel)
-    dir_ms = sum(ktimes[k][0] for k in ("dir_x", "dir_y", "dir_z"))
-    dir_launches = sum(ktimes[k][1] for k in ("dir_x", "dir_y", "dir_z"))
-    flops_per_launch = (FLOPS_DIR + FLOPS_RK_EPI / 3.0) * n ** 3
-    avg_launch_s = dir_ms / dir_launches * 1e-3
-    achieved = flops_per_launch / avg_launch_s / 1e12
-    step_ms_total = sum(v[0] for v in ktimes.values())
-    roofline = {"bound": "alu", "kernel": "k_dir (fused WENO5 + Roe + difference + viscous divergence)",
+    def roofline_of(kt, fp64_flops_dir):
+        # dominant kernel: the direction pass (x, y, z launches of the same kernel)
+        dir_ms = sum(kt[k][0] for k in ("dir_x", "dir_y", "dir_z"))
+        dir_launches = sum(kt[k][1] for k in ("dir_x", "dir_y", "dir_z"))
+        avg_launch_s = dir_ms / dir_launches * 1e-3
+        flops_pt = fp64_flops_dir + FLOPS_RK_EPI / 3.0
+        achieved = flops_pt * n ** 3 / avg_launch_s / 1e12
+        step_ms_total = sum(v[0] for v in kt.values())
+        return {"bound": "alu", "kernel": "k_dir (fused WENO5 + Roe + difference + viscous divergence)",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2070 MHz (unit counts and max clock)",
-                "flops_per_point": FLOPS_DIR + FLOPS_RK_EPI / 3.0, "avg_launch_ms": avg_launch_s * 1e3,
+                "fp64_flops_per_point": flops_pt, "avg_launch_ms": avg_launch_s * 1e3,
+                "method_equiv_tflops": (FLOPS_DIR + FLOPS_RK_EPI / 3.0) * n ** 3 / avg_launch_s / 1e12,
                 "share_of_device_time": dir_ms / step_ms_total if step_ms_total > 0 else None,
                 "algorithmic_bytes_per_point": 8 * (5 + 6 + 4 + 5 + 5),
                 "hbm_gbs_algorithmic": 8 * (5 + 6 + 4 + 5 + 5) * n ** 3 / avg_launch_s / 1e9}
+
+    roofline = roofline_of(ktimes, FLOPS_DIR_DFW)
+    roofline["fp32_work_note"] = ("the double-float weights add ~3.6k FP32-pipe instructions per point and "
+                                  "direction (FP32 runs 63x the FP64 rate), not counted in achieved")
+    avg_launch_s = roofline["avg_launch_ms"] * 1e-3
     tr = ncu_traffic_per_point("k_dir", os.path.join(ROOT, "paper_2211_16718_gb300", "csrc", "k_dir.cu"))
     if tr is not None:
         bpp, src, grid = tr
@@ -311,19 +330,35 @@ def run_ours(args, world, rank, local):
            "d2h_bytes_per_step": state_bytes + 8 * ns3d.NS3D_STATS_NDOUBLE,
            "call": "ns3d_step_host (pinned host state in, 1 RK4 step + statistics, state out)"}
 
+    solver.close()
+    del ud
+
+    # the all-FP64 evaluation of the same workload, for comparison
+    modes = {"fp64": {"value": value, "ms_per_step": ms / K,
+                      "weights": "double-float (FP32 pairs), all else FP64"}}
+    if not args.no_strict:
+        Ks = max(2, K // 2)
+        s2, u2, _, ms2, kt2, _, _ = timed_loop(ns3d.NS3D_FP64_STRICT, Ks, max(1, W - 1), False)
+        s2.close()
+        del u2
+        v2 = sum_over_ranks(float(n ** 3 * RK_STAGES * Ks), world) / (ms2 * 1e-3) / 1e9
+        modes["fp64_strict"] = {"value": v2, "ms_per_step": ms2 / Ks, "steps": Ks, "weights": "FP64",
+                                "roofline": roofline_of(kt2, FLOPS_DIR)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         g, el_cpu, cores, what = cpu_oracle_sample(u0, mu, n, dt, full_step=True)
         cpu = {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{what}, {el_cpu:.1f} s on the host cores (plain FP64 C oracle)"}
 
-    solver.close()
     if rank == 0:
+        cfg = workload_config(n, args.cfl, mu, dt)
+        cfg["precision"] = "NS3D_FP64: FP64 state/candidates/values/Roe/viscous/RK, WENO weights double-float"
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64", "data": "synthetic", "config": workload_config(n, args.cfl, mu, dt),
+                "dtype": "f64", "data": "synthetic", "config": cfg,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "kernel_ms": {k: v[0] for k, v in ktimes.items()}, "clocks": clk,
+                "kernel_ms": {k: v[0] for k, v in ktimes.items()}, "clocks": clk, "modes": modes,
                 "final_stats": {"ke": float(st[-1, 5]), "enstrophy": float(st[-1, 6]), "status_ok": status_ok}}
         print(json.dumps(line), flush=True)
 

@@ -31,7 +31,9 @@
  *    nothing aborts or traps.  ns3d_last_error(ctx) gives a message.
  *    Non-physical states (rho <= 0, p <= 0, a non-finite value, or a negative
  *    Roe-averaged sound speed squared) set a sticky device status word that
- *    ns3d_stats / ns3d_check report as NS3D_ENONPHYSICAL and then clear.
+ *    ns3d_stats / ns3d_check report as NS3D_ENONPHYSICAL and then clear;
+ *    data outside the range of the double-float weights set it too and are
+ *    reported as NS3D_ERANGE.
  *  - Not thread-safe per context; distinct contexts are independent.
  */
 #ifndef NS3D_H
@@ -49,18 +51,29 @@ enum {
   NS3D_ENOMEM = -2,        /* device or pinned-host allocation failed */
   NS3D_ECUDA = -3,         /* CUDA launch/runtime error (see ns3d_last_error) */
   NS3D_ENONPHYSICAL = -4,  /* non-physical state detected by a kernel */
-  NS3D_ETIMEOUT = -5       /* a bounded device-side wait gave up */
+  NS3D_ETIMEOUT = -5,      /* a bounded device-side wait gave up */
+  NS3D_ERANGE = -6         /* data beyond the range of the double-float WENO weights
+                              (differences of the data above ~1e9): use NS3D_FP64_STRICT */
 };
 
 enum { NS3D_RK4 = 0, NS3D_SSPRK3 = 1 };           /* time integrators (Sec. 2.2) */
-enum { NS3D_FP64 = 0, NS3D_FP32_BULK = 1 };       /* arithmetic of reconstruction + upwinding */
+/* Arithmetic of the reconstruction and upwinding:
+ *  NS3D_FP64        FP64 state, candidates, interpolated values, Roe flux, viscous terms
+ *                   and RK update; the nonlinear WENO weights (which only multiply
+ *                   third differences of the data) in double-float arithmetic (two
+ *                   FP32 words, ~48 bits) on the FP32 pipe.  Agrees with the all-FP64
+ *                   evaluation to FP64 rounding.  Requires weno_eps >= 1e-15.
+ *  NS3D_FP32_BULK   smoothness indicators, weights, interface values and Roe flux in
+ *                   FP32; state, RK accumulation and reductions in FP64.
+ *  NS3D_FP64_STRICT every operation in FP64 (one FP64 division per reconstruction). */
+enum { NS3D_FP64 = 0, NS3D_FP32_BULK = 1, NS3D_FP64_STRICT = 2 };
 
 typedef struct ns3d_ctx ns3d_ctx;                 /* opaque; owned by the library */
 
 typedef struct {
   int nx, ny, nz;       /* points per direction, each >= 1 */
   int rk;               /* NS3D_RK4 (default) or NS3D_SSPRK3 */
-  int precision;        /* NS3D_FP64 (default) or NS3D_FP32_BULK */
+  int precision;        /* NS3D_FP64 (default), NS3D_FP32_BULK or NS3D_FP64_STRICT */
   int weno_p;           /* exponent p of the WENO weights; only 2 is supported */
   double lx, ly, lz;    /* periodic box lengths (> 0); default 2*pi */
   double gamma;         /* ratio of specific heats, default 1.4 (Sec. 2.1) */
@@ -77,7 +90,7 @@ typedef struct {
   double enstrophy;                       /* mean of rho |omega|^2 / 2, omega by 4th-order central differences */
   double rho_min, p_min;
   double max_wavespeed_over_dx;           /* max over points, d of (|u_d| + c)/dx_d; CFL = dt * this */
-  int status;                             /* NS3D_OK or NS3D_ENONPHYSICAL */
+  int status;                             /* NS3D_OK, NS3D_ENONPHYSICAL or NS3D_ERANGE */
   int reserved;
 } ns3d_stats_t;
 

@@ -1,0 +1,148 @@
+// Double-float ("f32x2") arithmetic on the FP32 pipe for quantities that need
+// ~1e-13 relative accuracy but not the FP64 pipe (on GB300 FP32 runs 63x faster
+// than FP64).  Each value is an unevaluated sum hi + lo of two floats with
+// |lo| <= ulp(hi)/2, about 48 significant bits.
+//
+// Building blocks are the classical error-free transformations: Knuth's TwoSum,
+// Dekker's Fast2Sum and the FMA-based TwoProd; df_add/df_mul/df_div follow the
+// usual double-word algorithms (Dekker 1971; Joldes, Muller, Popescu 2017).
+// Conversions from and to FP64 use integer bit manipulation only, so they do
+// not occupy the FP64 pipe.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ns3d {
+
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df df_make(float hi, float lo) { return df{hi, lo}; }
+
+// Fast2Sum (Dekker): exact s + e = a + b when |a| >= |b| (or a == 0).
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float e = __fsub_rn(b, __fsub_rn(s, a));
+  return df{s, e};
+}
+
+// TwoSum (Knuth): exact s + e = a + b, no ordering requirement.
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return df{s, e};
+}
+
+// TwoProd with FMA: exact p + e = a * b (barring underflow).
+__device__ __forceinline__ df two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  return df{p, e};
+}
+
+// Accurate double-word addition (two TwoSums), safe under cancellation.
+__device__ __forceinline__ df df_add(df x, df y) {
+  df s = two_sum(x.hi, y.hi);
+  df t = two_sum(x.lo, y.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = fast_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+
+// Addition of two non-negative double-words (no cancellation possible).
+__device__ __forceinline__ df df_add_pos(df x, df y) {
+  df s = two_sum(x.hi, y.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+  return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ df df_neg(df x) { return df{-x.hi, -x.lo}; }
+
+__device__ __forceinline__ df df_mul(df x, df y) {
+  df p = two_prod(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.lo, p.lo);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return fast_two_sum(p.hi, e);
+}
+
+__device__ __forceinline__ df df_sqr(df x) {
+  df p = two_prod(x.hi, x.hi);
+  const float e = __fmaf_rn(__fadd_rn(x.hi, x.hi), x.lo, p.lo);
+  return fast_two_sum(p.hi, e);
+}
+
+// Multiplication by a float (exact small integers, or any float).
+__device__ __forceinline__ df df_mul_f(df x, float c) {
+  df p = two_prod(x.hi, c);
+  const float e = __fmaf_rn(x.lo, c, p.lo);
+  return fast_two_sum(p.hi, e);
+}
+
+// Division x / y (y != 0): one correction step of the float quotient.
+__device__ __forceinline__ df df_div(df x, df y) {
+  const float r = __frcp_rn(y.hi);
+  const float q1 = __fmul_rn(x.hi, r);
+  // remainder x - q1*y, evaluated with TwoProd
+  df p = two_prod(q1, y.hi);
+  float rem = __fsub_rn(x.hi, p.hi);
+  rem = __fsub_rn(rem, p.lo);
+  rem = __fadd_rn(rem, x.lo);
+  rem = __fmaf_rn(-q1, y.lo, rem);
+  const float q2 = __fmul_rn(rem, r);
+  return fast_two_sum(q1, q2);
+}
+
+// ---- conversions by bit manipulation (no FP64 instructions) -----------------
+// float -> double, exact for normal floats; zero and subnormals map to signed 0.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e8 = (b >> 23) & 0xffu;
+  const uint32_t sign = b & 0x80000000u;
+  if (e8 == 0u) return __hiloint2double((int)sign, 0);
+  const uint32_t m = b & 0x7fffffu;
+  const uint32_t e11 = (e8 == 0xffu) ? 0x7ffu : (e8 + 896u);
+  const uint32_t hi = sign | (e11 << 20) | (m >> 3);
+  const uint32_t lo = m << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// Power of two 2^k as a float for -126 <= k <= 127.
+__device__ __forceinline__ float pow2f(int k) { return __uint_as_float((uint32_t)(k + 127) << 23); }
+
+// double -> double-float: hi = x truncated to 24 significant bits, lo = the next
+// 24 bits (rounded).  Values below 2^-126 in magnitude become 0; the lo part of
+// values below 2^-74 is dropped (relative error 2^-24 only for such tiny x).
+__device__ __forceinline__ df d2df_bits(double x) {
+  const uint32_t h = (uint32_t)__double2hiint(x);
+  const uint32_t l = (uint32_t)__double2loint(x);
+  const uint32_t sign = h & 0x80000000u;
+  const int e11 = (int)((h >> 20) & 0x7ffu);
+  const int e8 = e11 - 896;
+  if (e8 <= 0) return df{__uint_as_float(sign), 0.0f};
+  if (e8 >= 255) {  // beyond the float range: +-inf, or NaN for a NaN input
+    const bool nan = (e11 == 0x7ff) && (((h & 0xfffffu) | l) != 0u);
+    return df{__uint_as_float(sign | 0x7f800000u | (nan ? 1u : 0u)), 0.0f};
+  }
+  const uint32_t m23 = ((h & 0xfffffu) << 3) | (l >> 29);
+  const float hi = __uint_as_float(sign | ((uint32_t)e8 << 23) | m23);
+  const uint32_t r29 = l & 0x1fffffffu;
+  float lo = 0.0f;
+  const int k = e11 - 1075;  // weight of the least significant mantissa bit
+  if (r29 != 0u && k >= -126) {
+    lo = __uint2float_rn(r29) * pow2f(k);
+    if (sign) lo = -lo;
+  }
+  return df{hi, lo};
+}
+
+// Nearest-float of a double (truncated to 24 bits; enough for correction terms).
+__device__ __forceinline__ float d2f_trunc(double x) { return d2df_bits(x).hi; }
+
+// Largest power of two not above |x| (x finite, nonzero, normal float).
+__device__ __forceinline__ int exponent_of(float x) { return (int)((__float_as_uint(x) >> 23) & 0xffu) - 127; }
+
+}  // namespace ns3d

@@ -9,44 +9,56 @@
 // points each side, fetched with wrapped indices).  Everything is staged in
 // shared memory and computed in five phases separated by barriers:
 //   A  load state, primitives, viscous flux; point fluxes f_D        [NP x W]
-//   B  smoothness indicators of every 3-point window, squared,
-//      for the 9 reconstructed scalars (u_0..u_4, f_1..f_4)            [9 x NW x W]
+//   B  smoothness indicators of every 3-point window for the 9
+//      reconstructed scalars (u_0..u_4, f_1..f_4)                      [9 x NW x W]
 //   C  left/right WENO5 values of the 9 scalars at every interface     [9 x NI x W]
 //   D  Roe flux at every interface                                     [NI x W]
 //   E  flux difference + viscous divergence + epilogue, global writes  [TP x W]
 // The mass flux f_0 = (rho u_D) is the momentum component u_{1+D} itself, so its
 // reconstructions are those of u_{1+D}.
 //
-// WENO weights in division-reduced form: with b_k = 4(eps + beta_k) and
-// B_k = b_k^2, omega_k = c_k/B_k / sum_j c_j/B_j, so
-//   fhat = (c1 B2 B3 F1 + c2 B1 B3 F2 + c3 B1 B2 F3) / (c1 B2 B3 + c2 B1 B3 + c3 B1 B2),
-// one division per reconstruction.  The squared indicators of a window are shared
-// by the left-biased reconstruction at one interface and the right-biased one at
-// another, so each is computed once per window.
+// With b_k = 4(eps + beta_k) and B_k = b_k^2, the weights are
+// omega_k = (c_k/B_k) / sum_j (c_j/B_j) = c_k prod_{m!=k} B_m / sum_j c_j prod_{m!=j} B_m.
+// The three squared indicators of a window serve the left-biased reconstruction
+// at one interface and the right-biased one at another, so each is computed once.
+//
+// MODE 0 (all FP64): fhat = sum_k omega_k F_k with one FP64 division.
+// MODE 1 (FP64 values, double-float weights): since sum omega = 1,
+//   fhat = F_2 + omega_1 (F_1 - F_2) + omega_3 (F_3 - F_2),
+// where F_1 - F_2 and F_3 - F_2 are third differences of the data (FP64, from the
+// window second differences s) and the weights, which only multiply these small
+// differences, are evaluated in double-float arithmetic (~48 bits) on the FP32
+// pipe.  The FP64 work per interface and scalar drops from ~60 to ~16
+// instructions; the result agrees with the all-FP64 evaluation to rounding.
 #include <math.h>
 
+#include "df.cuh"
 #include "ns3d_internal.cuh"
 
 namespace ns3d {
 
 namespace {
 
-constexpr int TP = 32;            // points per tile along the pencil
 constexpr int W = 4;              // lines per tile
-constexpr int NP = TP + 6;        // points incl. 3-point halo each side
-constexpr int NW = TP + 4;        // 3-point windows centred at -2 .. TP+1
-constexpr int NI = TP + 1;        // interfaces -1/2 .. TP-1/2
 constexpr int NQ = 9;             // reconstructed scalars
 constexpr int NTHREADS = 128;
 
-// shared-memory plan (doubles)
-constexpr int OFF_Q = 0;                          // [NQ][NP*W]
-constexpr int OFF_ROE = OFF_Q + NQ * NP * W;      // [5][NP*W]: sqrt(rho), u, v, w, H
-constexpr int OFF_FV = OFF_ROE + 5 * NP * W;      // [4][NP*W]
-constexpr int OFF_B = OFF_FV + 4 * NP * W;        // [NQ][3][NW*W]
-constexpr int OFF_R = OFF_B + NQ * 3 * NW * W;    // [18][NI*W], later [5][NI*W] fluxes
-constexpr int SMEM_DOUBLES = OFF_R + 18 * NI * W;
-constexpr int SMEM_BYTES = SMEM_DOUBLES * 8;
+template <int MODE>
+struct Plan {
+  static constexpr int TP = (MODE == 0) ? 32 : 28;  // points per tile along the pencil
+  static constexpr int NP = TP + 6;                 // points incl. 3-point halo each side
+  static constexpr int NW = TP + 4;                 // 3-point windows centred at -2 .. TP+1
+  static constexpr int NI = TP + 1;                 // interfaces -1/2 .. TP-1/2
+  // shared-memory plan (8-byte words)
+  static constexpr int OFF_Q = 0;                               // [NQ][NP*W] doubles
+  static constexpr int OFF_ROE = OFF_Q + NQ * NP * W;           // [5][NP*W]: sqrt(rho), u, v, w, H
+  static constexpr int OFF_FV = OFF_ROE + 5 * NP * W;           // [4][NP*W]
+  static constexpr int OFF_B = OFF_FV + 4 * NP * W;             // [NQ][3][NW*W] (double, or df pairs)
+  static constexpr int OFF_S = OFF_B + NQ * 3 * NW * W;         // [NQ][NW*W] second differences (MODE 1)
+  static constexpr int OFF_R = OFF_S + (MODE == 1 ? NQ * NW * W : 0);  // [18][NI*W], later [5][NI*W]
+  static constexpr int WORDS = OFF_R + 18 * NI * W;
+  static constexpr int BYTES = WORDS * 8;
+};
 
 // Position-major for y/z lines (consecutive threads = consecutive x lines),
 // line-major for x lines (consecutive threads = consecutive x points).
@@ -74,8 +86,27 @@ __device__ __forceinline__ double weno_combine(double B1, double B2, double B3, 
   return num / den;
 }
 
-template <int D>
+// Double-float weights of one reconstruction from its three squared, scaled
+// indicators (candidate order 1, 2, 3): w1 = omega_1/3, w3 = omega_3/6.
+__device__ __forceinline__ void df_weights(df B1, df B2, df B3, df& w1, df& w3) {
+  // common power-of-two scaling keeps the products in range (omega is scale-free)
+  const int E = max(exponent_of(B1.hi), max(exponent_of(B2.hi), exponent_of(B3.hi)));
+  const float sc = pow2f(-E);
+  B1 = df{B1.hi * sc, B1.lo * sc};
+  B2 = df{B2.hi * sc, B2.lo * sc};
+  B3 = df{B3.hi * sc, B3.lo * sc};
+  const df p23 = df_mul(B2, B3);
+  const df p13 = df_mul(B1, B3);
+  const df p12 = df_mul(B1, B2);
+  const df den = df_add_pos(p23, df_add_pos(df_mul_f(p13, 6.0f), df_mul_f(p12, 3.0f)));
+  w1 = df_div(p23, df_mul_f(den, 3.0f));
+  w3 = df_div(p12, df_mul_f(den, 2.0f));
+}
+
+template <int D, int MODE>
 __global__ void __launch_bounds__(NTHREADS) k_dir(const DirArgs a) {
+  using PL = Plan<MODE>;
+  constexpr int TP = PL::TP, NP = PL::NP, NW = PL::NW, NI = PL::NI;
   extern __shared__ double sm[];
   const int nD = a.g.n[D];
   constexpr int AX = (D == 0) ? 1 : 0;   // axis of the W lines
@@ -110,21 +141,21 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(const DirArgs a) {
     const double pr = __ldg(a.pm + PM_P * N + p);
     const double un = (D == 0) ? vx : (D == 1) ? vy : vz;
     const int s = sidx<D>(pos, line, NP);
-    double* q = sm + OFF_Q;
+    double* q = sm + PL::OFF_Q;
 #pragma unroll
     for (int v = 0; v < 5; ++v) q[v * NP * W + s] = U[v];
     q[5 * NP * W + s] = (D == 0) ? fma(U[1], un, pr) : U[1] * un;
     q[6 * NP * W + s] = (D == 1) ? fma(U[2], un, pr) : U[2] * un;
     q[7 * NP * W + s] = (D == 2) ? fma(U[3], un, pr) : U[3] * un;
     q[8 * NP * W + s] = (U[4] + pr) * un;
-    double* r = sm + OFF_ROE;
+    double* r = sm + PL::OFF_ROE;
     r[0 * NP * W + s] = __ldg(a.pm + PM_SR * N + p);
     r[1 * NP * W + s] = vx;
     r[2 * NP * W + s] = vy;
     r[3 * NP * W + s] = vz;
     r[4 * NP * W + s] = __ldg(a.pm + PM_H * N + p);
     if (a.fv != nullptr) {
-      double* f = sm + OFF_FV;
+      double* f = sm + PL::OFF_FV;
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) f[cc * NP * W + s] = __ldg(a.fv + (long long)(4 * D + cc) * N + p);
     }
@@ -133,9 +164,8 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(const DirArgs a) {
 
   // ---- B: squared scaled smoothness indicators of every window ----------------
   {
-    const double eps4 = a.eps4;
-    const double* q = sm + OFF_Q;
-    double* bw = sm + OFF_B;
+    const double* q = sm + PL::OFF_Q;
+    int range_bad = 0;
     for (int item = tid; item < NQ * NW * W; item += NTHREADS) {
       const int m = item / (NW * W);
       int w, line;
@@ -145,46 +175,92 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(const DirArgs a) {
       const double y = qm[sidx<D>(w + 1, line, NP)];
       const double z = qm[sidx<D>(w + 2, line, NP)];
       const double gm = y - x, gp = z - y, s = gp - gm;
-      const double aa = fma((13.0 / 3.0) * s, s, eps4);
-      const double u1 = fma(3.0, gp, -gm);   // x - 4y + 3z
-      const double u2 = gm + gp;             // z - x
-      const double u3 = fma(-3.0, gm, gp);   // 3x - 4y + z
-      const double b1 = fma(u1, u1, aa), b2 = fma(u2, u2, aa), b3 = fma(u3, u3, aa);
       const int o = sidx<D>(w, line, NW);
-      bw[(m * 3 + 0) * NW * W + o] = b1 * b1;
-      bw[(m * 3 + 1) * NW * W + o] = b2 * b2;
-      bw[(m * 3 + 2) * NW * W + o] = b3 * b3;
+      if (MODE == 0) {
+        double* bw = sm + PL::OFF_B;
+        const double aa = fma((13.0 / 3.0) * s, s, a.eps4);
+        const double u1 = fma(3.0, gp, -gm);   // x - 4y + 3z
+        const double u2 = gm + gp;             // z - x
+        const double u3 = fma(-3.0, gm, gp);   // 3x - 4y + z
+        const double b1 = fma(u1, u1, aa), b2 = fma(u2, u2, aa), b3 = fma(u3, u3, aa);
+        bw[(m * 3 + 0) * NW * W + o] = b1 * b1;
+        bw[(m * 3 + 1) * NW * W + o] = b2 * b2;
+        bw[(m * 3 + 2) * NW * W + o] = b3 * b3;
+      } else {
+        float2* bw = reinterpret_cast<float2*>(sm + PL::OFF_B);
+        (sm + PL::OFF_S)[m * NW * W + o] = s;
+        const df dgm = d2df_bits(gm), dgp = d2df_bits(gp), ds = d2df_bits(s);
+        const df aa = df_add_pos(df_mul(df_sqr(ds), df{a.c133_hi, a.c133_lo}), df{a.eps4_hi, a.eps4_lo});
+        const df u1 = df_add(df_mul_f(dgp, 3.0f), df_neg(dgm));
+        const df u2 = df_add(dgm, dgp);
+        const df u3 = df_add(dgp, df_neg(df_mul_f(dgm, 3.0f)));
+        const df B1 = df_sqr(df_add_pos(df_sqr(u1), aa));
+        const df B2 = df_sqr(df_add_pos(df_sqr(u2), aa));
+        const df B3 = df_sqr(df_add_pos(df_sqr(u3), aa));
+        bw[(m * 3 + 0) * NW * W + o] = make_float2(B1.hi, B1.lo);
+        bw[(m * 3 + 1) * NW * W + o] = make_float2(B2.hi, B2.lo);
+        bw[(m * 3 + 2) * NW * W + o] = make_float2(B3.hi, B3.lo);
+        // the float exponent range bounds the indicators (differences of the data
+        // up to ~1e9); beyond it the host reports NS3D_ERANGE instead of a NaN
+        range_bad |= !(fmaxf(B1.hi, fmaxf(B2.hi, B3.hi)) < 1e36f);
+      }
     }
+    if (MODE == 1 && __any_sync(0xffffffffu, range_bad) && (tid & 31) == 0) atomicOr(a.status, ST_DF_RANGE);
   }
   __syncthreads();
 
   // ---- C: left/right WENO5 values at every interface --------------------------
   {
-    const double* q = sm + OFF_Q;
-    const double* bw = sm + OFF_B;
-    double* rec = sm + OFF_R;
+    const double* q = sm + PL::OFF_Q;
+    double* rec = sm + PL::OFF_R;
     for (int item = tid; item < NQ * NI * W; item += NTHREADS) {
       const int m = item / (NI * W);
       int f, line;
       split<D>(item - m * NI * W, NI, f, line);
       const double* qm = q + m * NP * W;
-      const double P0 = qm[sidx<D>(f, line, NP)], P1 = qm[sidx<D>(f + 1, line, NP)];
+      const double P1 = qm[sidx<D>(f + 1, line, NP)];
       const double P2 = qm[sidx<D>(f + 2, line, NP)], P3 = qm[sidx<D>(f + 3, line, NP)];
-      const double P4 = qm[sidx<D>(f + 4, line, NP)], P5 = qm[sidx<D>(f + 5, line, NP)];
-      // third-order candidates at the interface between P2 and P3
-      const double xR = fma(11.0 / 6.0, P2, fma(-7.0 / 6.0, P1, (1.0 / 3.0) * P0));
-      const double eR = fma(1.0 / 3.0, P3, fma(5.0 / 6.0, P2, (-1.0 / 6.0) * P1));
-      const double eL = fma(-1.0 / 6.0, P4, fma(5.0 / 6.0, P3, (1.0 / 3.0) * P2));
-      const double xL = fma(1.0 / 3.0, P5, fma(-7.0 / 6.0, P4, (11.0 / 6.0) * P3));
-      const double* b = bw + m * 3 * NW * W;
-      const double B1f = b[0 * NW * W + sidx<D>(f, line, NW)];
-      const double B2f1 = b[1 * NW * W + sidx<D>(f + 1, line, NW)];
-      const double B3f2 = b[2 * NW * W + sidx<D>(f + 2, line, NW)];
-      const double B3f3 = b[2 * NW * W + sidx<D>(f + 3, line, NW)];
-      const double B2f2 = b[1 * NW * W + sidx<D>(f + 2, line, NW)];
-      const double B1f1 = b[0 * NW * W + sidx<D>(f + 1, line, NW)];
-      const double vL = weno_combine(B1f, B2f1, B3f2, xR, eR, eL);
-      const double vR = weno_combine(B3f3, B2f2, B1f1, xL, eL, eR);
+      const double P4 = qm[sidx<D>(f + 4, line, NP)];
+      double vL, vR;
+      if (MODE == 0) {
+        const double P0 = qm[sidx<D>(f, line, NP)], P5 = qm[sidx<D>(f + 5, line, NP)];
+        // third-order candidates at the interface between P2 and P3
+        const double xR = fma(11.0 / 6.0, P2, fma(-7.0 / 6.0, P1, (1.0 / 3.0) * P0));
+        const double eR = fma(1.0 / 3.0, P3, fma(5.0 / 6.0, P2, (-1.0 / 6.0) * P1));
+        const double eL = fma(-1.0 / 6.0, P4, fma(5.0 / 6.0, P3, (1.0 / 3.0) * P2));
+        const double xL = fma(1.0 / 3.0, P5, fma(-7.0 / 6.0, P4, (11.0 / 6.0) * P3));
+        const double* b = sm + PL::OFF_B + m * 3 * NW * W;
+        const double B1f = b[0 * NW * W + sidx<D>(f, line, NW)];
+        const double B2f1 = b[1 * NW * W + sidx<D>(f + 1, line, NW)];
+        const double B3f2 = b[2 * NW * W + sidx<D>(f + 2, line, NW)];
+        const double B3f3 = b[2 * NW * W + sidx<D>(f + 3, line, NW)];
+        const double B2f2 = b[1 * NW * W + sidx<D>(f + 2, line, NW)];
+        const double B1f1 = b[0 * NW * W + sidx<D>(f + 1, line, NW)];
+        vL = weno_combine(B1f, B2f1, B3f2, xR, eR, eL);
+        vR = weno_combine(B3f3, B2f2, B1f1, xL, eL, eR);
+      } else {
+        const double* sw = sm + PL::OFF_S + m * NW * W;
+        const double s0 = sw[sidx<D>(f, line, NW)], s1 = sw[sidx<D>(f + 1, line, NW)];
+        const double s2 = sw[sidx<D>(f + 2, line, NW)], s3 = sw[sidx<D>(f + 3, line, NW)];
+        // F1 - F2 (left) = (s0 - s1)/3, F3 - F2 (left) = (s1 - s2)/6 = -(F3 - F2) (right),
+        // F1 - F2 (right) = (s3 - s2)/3
+        const double d1L = s0 - s1, dC = s1 - s2, d1R = s3 - s2;
+        const float2* b = reinterpret_cast<const float2*>(sm + PL::OFF_B) + m * 3 * NW * W;
+        auto ld = [&](int k, int w) {
+          const float2 v = b[k * NW * W + sidx<D>(w, line, NW)];
+          return df{v.x, v.y};
+        };
+        df w1, w3, v1, v3;
+        df_weights(ld(0, f), ld(1, f + 1), ld(2, f + 2), w1, w3);
+        df_weights(ld(2, f + 3), ld(1, f + 2), ld(0, f + 1), v1, v3);
+        const float fd1L = d2f_trunc(d1L), fdC = d2f_trunc(dC), fd1R = d2f_trunc(d1R);
+        const float corrL = __fmaf_rn(w1.lo, fd1L, w3.lo * fdC);
+        const float corrR = __fmaf_rn(v1.lo, fd1R, -(v3.lo * fdC));
+        const double eRc = fma(1.0 / 3.0, P3, fma(5.0 / 6.0, P2, fma(-1.0 / 6.0, P1, f2d_bits(corrL))));
+        const double eLc = fma(-1.0 / 6.0, P4, fma(5.0 / 6.0, P3, fma(1.0 / 3.0, P2, f2d_bits(corrR))));
+        vL = fma(f2d_bits(w1.hi), d1L, fma(f2d_bits(w3.hi), dC, eRc));
+        vR = fma(f2d_bits(v1.hi), d1R, fma(-f2d_bits(v3.hi), dC, eLc));
+      }
       const int o = sidx<D>(f, line, NI);
       rec[(2 * m) * NI * W + o] = vL;
       rec[(2 * m + 1) * NI * W + o] = vR;
@@ -195,8 +271,8 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(const DirArgs a) {
   // ---- D: Roe flux at every interface -------------------------------------------
   {
     const double gm1 = a.gamma - 1.0;
-    const double* r = sm + OFF_ROE;
-    double* rec = sm + OFF_R;
+    const double* r = sm + PL::OFF_ROE;
+    double* rec = sm + PL::OFF_R;
     int bad = 0;
     for (int item = tid; item < NI * W; item += NTHREADS) {
       int f, line;
@@ -269,8 +345,8 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(const DirArgs a) {
   {
     const double rdx = 1.0 / a.g.h[D];
     const double r12 = 1.0 / (12.0 * a.g.h[D]);
-    const double* F = sm + OFF_R;
-    const double* fvs = sm + OFF_FV;
+    const double* F = sm + PL::OFF_R;
+    const double* fvs = sm + PL::OFF_FV;
     for (int item = tid; item < TP * W; item += NTHREADS) {
       int pp, line;
       split<D>(item, TP, pp, line);
@@ -353,32 +429,46 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(const DirArgs a) {
   }
 }
 
-template <int D>
+template <int D, int MODE>
 cudaError_t launch_d(const DirArgs& a, cudaStream_t s) {
+  using PL = Plan<MODE>;
   constexpr int AX = (D == 0) ? 1 : 0;
   constexpr int BX = (D == 2) ? 1 : 2;
-  dim3 grid((a.g.n[D] + TP - 1) / TP, (a.g.n[AX] + W - 1) / W, a.g.n[BX]);
-  k_dir<D><<<grid, NTHREADS, SMEM_BYTES, s>>>(a);
+  dim3 grid((a.g.n[D] + PL::TP - 1) / PL::TP, (a.g.n[AX] + W - 1) / W, a.g.n[BX]);
+  k_dir<D, MODE><<<grid, NTHREADS, PL::BYTES, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t set_attr() {
+  cudaError_t e = cudaFuncSetAttribute(k_dir<0, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, Plan<MODE>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_dir<1, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, Plan<MODE>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_dir<2, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, Plan<MODE>::BYTES);
+  return e;
 }
 
 }  // namespace
 
 cudaError_t prepare_dir_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(k_dir<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dir<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dir<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  cudaError_t e = set_attr<0>();
+  if (e == cudaSuccess) e = set_attr<1>();
   return e;
 }
 
 cudaError_t launch_dir(int d, const DirArgs& a, cudaStream_t s) {
+  if (a.mode == 1) {
+    switch (d) {
+      case 0: return launch_d<0, 1>(a, s);
+      case 1: return launch_d<1, 1>(a, s);
+      default: return launch_d<2, 1>(a, s);
+    }
+  }
   switch (d) {
-    case 0:
-      return launch_d<0>(a, s);
-    case 1:
-      return launch_d<1>(a, s);
-    default:
-      return launch_d<2>(a, s);
+    case 0: return launch_d<0, 0>(a, s);
+    case 1: return launch_d<1, 0>(a, s);
+    default: return launch_d<2, 0>(a, s);
   }
 }
 

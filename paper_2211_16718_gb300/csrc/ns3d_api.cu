@@ -112,7 +112,20 @@ DirArgs base_args(ns3d_ctx* c, const double* u) {
   a.eps4 = 4.0 * c->p.weno_eps;
   a.hdelta = c->p.harten_delta;
   a.status = c->status;
+  a.mode = (c->p.precision == NS3D_FP64_STRICT) ? 0 : 1;
+  const double c133 = 13.0 / 3.0, eps4 = 4.0 * c->p.weno_eps;
+  a.c133_hi = (float)c133;
+  a.c133_lo = (float)(c133 - (double)a.c133_hi);
+  a.eps4_hi = (float)eps4;
+  a.eps4_lo = (float)(eps4 - (double)a.eps4_hi);
   return a;
+}
+
+// Map the sticky status word to an error code.
+int status_code(int word) {
+  if (word & ST_NONPHYS) return NS3D_ENONPHYSICAL;
+  if (word & ST_DF_RANGE) return NS3D_ERANGE;
+  return NS3D_OK;
 }
 
 // One full right-hand-side evaluation of state u: primitives, viscous fluxes,
@@ -197,7 +210,10 @@ int validate(const ns3d_params* p, char* msg, size_t n) {
   if (!(p->harten_delta >= 0.0) || !isfinite(p->harten_delta))
     return snprintf(msg, n, "harten_delta must be >= 0"), NS3D_EINVAL;
   if (p->rk != NS3D_RK4 && p->rk != NS3D_SSPRK3) return snprintf(msg, n, "unknown rk scheme"), NS3D_EINVAL;
-  if (p->precision != NS3D_FP64) return snprintf(msg, n, "unsupported precision mode"), NS3D_EINVAL;
+  if (p->precision != NS3D_FP64 && p->precision != NS3D_FP64_STRICT)
+    return snprintf(msg, n, "unsupported precision mode"), NS3D_EINVAL;
+  if (p->precision == NS3D_FP64 && !(p->weno_eps >= 1e-15))
+    return snprintf(msg, n, "weno_eps below 1e-15 needs NS3D_FP64_STRICT"), NS3D_EINVAL;
   return NS3D_OK;
 }
 
@@ -230,6 +246,7 @@ const char* ns3d_strerror(int code) {
     case NS3D_ECUDA: return "CUDA error";
     case NS3D_ENONPHYSICAL: return "non-physical state (rho <= 0, p <= 0, or non-finite value)";
     case NS3D_ETIMEOUT: return "device-side wait timed out";
+    case NS3D_ERANGE: return "data beyond the range of the double-float WENO weights (use NS3D_FP64_STRICT)";
     default: return "unknown error";
   }
 }
@@ -366,7 +383,7 @@ static void fill_stats(const double* s, ns3d_stats_t* o) {
   o->rho_min = s[7];
   o->p_min = s[8];
   o->max_wavespeed_over_dx = s[9];
-  o->status = (s[10] != 0.0) ? NS3D_ENONPHYSICAL : NS3D_OK;
+  o->status = status_code((int)s[10]);
   o->reserved = 0;
 }
 
@@ -381,7 +398,7 @@ int ns3d_stats(ns3d_ctx* c, const double* u, ns3d_stats_t* out) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "statistics copy");
   fill_stats(c->stats_host, out);
-  if (out->status) return set_err(c, NS3D_ENONPHYSICAL, "non-physical state detected");
+  if (out->status) return set_err(c, out->status, "%s", ns3d_strerror(out->status));
   return NS3D_OK;
 }
 
@@ -392,7 +409,7 @@ int ns3d_check(ns3d_ctx* c) {
   if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "status read");
-  if (h) return set_err(c, NS3D_ENONPHYSICAL, "non-physical state detected");
+  if (h) return set_err(c, status_code(h), "%s", ns3d_strerror(status_code(h)));
   return NS3D_OK;
 }
 
@@ -421,7 +438,7 @@ int ns3d_step_host(ns3d_ctx* c, double* u_host, double dt, int nsteps, ns3d_stat
   if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
   if (stats_host) {
     fill_stats(c->stats_host, stats_host);
-    if (stats_host->status) return set_err(c, NS3D_ENONPHYSICAL, "non-physical state detected");
+    if (stats_host->status) return set_err(c, stats_host->status, "%s", ns3d_strerror(stats_host->status));
   }
   return NS3D_OK;
 }

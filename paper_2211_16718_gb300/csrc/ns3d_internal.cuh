@@ -15,7 +15,7 @@ enum { PM_U = 0, PM_V = 1, PM_W = 2, PM_P = 3, PM_T = 4, PM_H = 5, PM_SR = 6, NP
 enum { NVISC = 12 };
 
 // Status bits of the sticky device status word.
-enum { ST_NONPHYS = 1 };
+enum { ST_NONPHYS = 1, ST_DF_RANGE = 2 };
 
 // Epilogue of the z-direction kernel (the last of the three direction passes).
 enum Epi {
@@ -51,6 +51,9 @@ struct DirArgs {
   double eps4;       // 4 * weno_eps (smoothness indicators are scaled by 4)
   double hdelta;     // Harten entropy-fix fraction
   int* status;
+  int mode;          // 0: all-FP64 weights; 1: double-float weights
+  float c133_hi, c133_lo;  // 13/3 as a double-float
+  float eps4_hi, eps4_lo;  // 4 * weno_eps as a double-float
 };
 
 // Launchers (return cudaGetLastError() of the launch).

@@ -16,8 +16,9 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(PKG, "libns3d.so")
 
 NS3D_OK, NS3D_EINVAL, NS3D_ENOMEM, NS3D_ECUDA, NS3D_ENONPHYSICAL, NS3D_ETIMEOUT = 0, -1, -2, -3, -4, -5
+NS3D_ERANGE = -6
 NS3D_RK4, NS3D_SSPRK3 = 0, 1
-NS3D_FP64, NS3D_FP32_BULK = 0, 1
+NS3D_FP64, NS3D_FP32_BULK, NS3D_FP64_STRICT = 0, 1, 2
 NS3D_STATS_NDOUBLE = 12
 KERNELS = ("prim", "visc", "dir_x", "dir_y", "dir_z", "stats", "stats_final")
 EXPORTS = ("ns3d_default_params", "ns3d_init", "ns3d_free", "ns3d_set_stream", "ns3d_rhs", "ns3d_rk_step",
@@ -157,7 +158,7 @@ class Solver:
         self._sync_stream()
         s = CStats()
         rc = lib().ns3d_stats(self._ctx, _dptr(u, 5 * self.N), ctypes.byref(s))
-        if rc not in (NS3D_OK, NS3D_ENONPHYSICAL):
+        if rc not in (NS3D_OK, NS3D_ENONPHYSICAL, NS3D_ERANGE):
             self._check(rc)
         d = {n: getattr(s, n) for n in STATS_FIELDS}
         d["status"] = s.status
@@ -179,7 +180,7 @@ class Solver:
         s = CStats()
         rc = lib().ns3d_step_host(self._ctx, ctypes.c_void_p(u_host.ctypes.data), float(dt), int(nsteps),
                                   ctypes.byref(s))
-        if rc not in (NS3D_OK, NS3D_ENONPHYSICAL):
+        if rc not in (NS3D_OK, NS3D_ENONPHYSICAL, NS3D_ERANGE):
             self._check(rc)
         d = {n: getattr(s, n) for n in STATS_FIELDS}
         d["status"] = s.status

@@ -72,10 +72,14 @@ CASES = [
 ]
 
 
+PRECISIONS = {"fp64": 0, "fp64_strict": 2}
+
+
+@pytest.mark.parametrize("prec", list(PRECISIONS))
 @pytest.mark.parametrize("name,make,kw", CASES, ids=[c[0] for c in CASES])
-def test_rhs_matches_oracle(ns3d, orc, name, make, kw):
+def test_rhs_matches_oracle(ns3d, orc, name, make, kw, prec):
     u = make()
-    r_gpu, r_orc = _rhs_pair(ns3d, orc, u, **kw)
+    r_gpu, r_orc = _rhs_pair(ns3d, orc, u, precision=PRECISIONS[prec], **kw)
     err = rel_err(r_gpu, r_orc)
     tol = RHS_TOL_LOW_MACH if "mach01" in name else RHS_TOL
     assert err <= tol, f"{name}: rel err {err:.3e}"
@@ -106,14 +110,16 @@ def test_conservation_on_gpu(ns3d):
     assert np.all(np.abs(r.sum(axis=1)) <= 64 * np.finfo(float).eps * scale * r.shape[1])
 
 
+@pytest.mark.parametrize("prec", list(PRECISIONS))
 @pytest.mark.parametrize("rk", ["rk4", "ssprk3"])
-def test_tgv32_ten_steps_match_oracle(ns3d, orc, rk):
+def test_tgv32_ten_steps_match_oracle(ns3d, orc, rk, prec):
     """Taylor-Green 32^3, Re 1600, Mach 0.1, dt at CFL 0.5, 10 steps."""
     n, mu = 32, 6.25e-5
     u0 = I.taylor_green(n)
     P = orc.Params(n, n, n, mu_eff=mu)
     dt = 0.5 / orc.stats(P, u0)["max_wavespeed_over_dx"]
-    s = ns3d.Solver(n, n, n, mu_eff=mu, rk=ns3d.NS3D_RK4 if rk == "rk4" else ns3d.NS3D_SSPRK3)
+    s = ns3d.Solver(n, n, n, mu_eff=mu, rk=ns3d.NS3D_RK4 if rk == "rk4" else ns3d.NS3D_SSPRK3,
+                    precision=PRECISIONS[prec])
     ud = _gpu(u0)
     s.rk_step(ud, dt, 10)
     u_gpu = ud.cpu().numpy()
@@ -197,6 +203,26 @@ def test_aliasing_and_bad_calls_are_rejected(ns3d):
         s.rhs(torch.zeros(10, dtype=torch.float64, device="cuda"))
 
 
+def test_double_float_range_is_reported(ns3d):
+    """Differences of the data far beyond ~1e9 exceed the double-float weights: the FP64
+    mode reports NS3D_ERANGE instead of returning NaN; the strict mode handles them."""
+    n = 16
+    x = I.grid(n)
+    shp = (n, n, n)
+    p = 1e25 * (1.0 + 0.1 * np.sin(x))[None, None, :] * np.ones(shp)
+    zero = np.zeros(shp)
+    u = _gpu(I.to_conserved(np.ones(shp), zero, zero, zero, p))
+    s = ns3d.Solver(n, n, n, precision=ns3d.NS3D_FP64)
+    s.rhs(u)
+    with pytest.raises(ns3d.Ns3dError) as ei:
+        s.check()
+    assert ei.value.code == ns3d.NS3D_ERANGE
+    strict = ns3d.Solver(n, n, n, precision=ns3d.NS3D_FP64_STRICT)
+    r = strict.rhs(u)
+    strict.check()
+    assert bool(np.isfinite(r.cpu().numpy()).all())
+
+
 def test_zero_steps_is_identity(ns3d):
     u0 = I.taylor_green(8)
     s = ns3d.Solver(8, 8, 8)
@@ -216,13 +242,14 @@ def test_timing_counts_launches(ns3d):
 
 
 # ---- full sizes (the launch configuration the benchmark times) --------------------
-def test_hit256_rhs_sampled_points(ns3d, orc):
+@pytest.mark.parametrize("prec", list(PRECISIONS))
+def test_hit256_rhs_sampled_points(ns3d, orc, prec):
     """Isotropic turbulence 256^3 (seed 0): the GPU RHS at 4096 sampled points equals the
     oracle's local evaluation at those points."""
     n = 256
     u = I.isotropic_turbulence(n, seed=0)
     mu = I.hit_mu_eff()
-    s = ns3d.Solver(n, n, n, mu_eff=mu)
+    s = ns3d.Solver(n, n, n, mu_eff=mu, precision=PRECISIONS[prec])
     r_gpu = s.rhs(_gpu(u)).cpu().numpy().reshape(5, -1)
     s.close()
     rng = np.random.default_rng(0)
