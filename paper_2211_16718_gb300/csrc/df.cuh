@@ -53,6 +53,16 @@ __device__ __forceinline__ df df_add(df x, df y) {
   return fast_two_sum(s.hi, s.lo);
 }
 
+// Double-word addition with one TwoSum: absolute error ~2^-47 (|x| + |y|), i.e.
+// accurate relative to the inputs (not to the result under cancellation).  Used
+// where the result only ever enters through such absolute bounds (differences
+// feeding the smoothness indicators and the interface offsets).
+__device__ __forceinline__ df df_add_fast(df x, df y) {
+  df s = two_sum(x.hi, y.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+  return fast_two_sum(s.hi, s.lo);
+}
+
 // Addition of two non-negative double-words (no cancellation possible).
 __device__ __forceinline__ df df_add_pos(df x, df y) {
   df s = two_sum(x.hi, y.hi);
@@ -144,5 +154,26 @@ __device__ __forceinline__ float d2f_trunc(double x) { return d2df_bits(x).hi; }
 
 // Largest power of two not above |x| (x finite, nonzero, normal float).
 __device__ __forceinline__ int exponent_of(float x) { return (int)((__float_as_uint(x) >> 23) & 0xffu) - 127; }
+
+// ---- FP64 reciprocal and reciprocal square root by Newton-Raphson -------------
+// Seeds from the FP32 MUFU approximations (relative error ~2^-22 after the
+// truncating conversion); each Newton step squares the error, two steps reach
+// FP64 rounding.  For x in the normal float range (positive for rsqrt).
+__device__ __forceinline__ double rcp_newton(double x) {
+  double r = f2d_bits(__frcp_rn(d2f_trunc(x)));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
+__device__ __forceinline__ double rsqrt_newton(double x) {
+  double r = f2d_bits(rsqrtf(d2f_trunc(x)));
+  const double hx = 0.5 * x;
+  double e = fma(-hx * r, r, 0.5);  // (1 - x r^2)/2
+  r = fma(r, e, r);
+  e = fma(-hx * r, r, 0.5);
+  return fma(r, e, r);
+}
 
 }  // namespace ns3d

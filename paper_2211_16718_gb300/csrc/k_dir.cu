@@ -41,21 +41,23 @@ namespace {
 
 constexpr int W = 4;              // lines per tile
 constexpr int NQ = 9;             // reconstructed scalars
-constexpr int NTHREADS = 128;
+constexpr int MIN_CTAS_PER_SM = 3;
 
 template <int MODE>
 struct Plan {
-  static constexpr int TP = (MODE == 0) ? 32 : 28;  // points per tile along the pencil
+  static constexpr int TP = (MODE == 0) ? 32 : 24;  // points per tile along the pencil
+  static constexpr int THREADS = (MODE == 0) ? 128 : 256;  // MODE 1: 8 warps share the tile (latency hiding)
   static constexpr int NP = TP + 6;                 // points incl. 3-point halo each side
   static constexpr int NW = TP + 4;                 // 3-point windows centred at -2 .. TP+1
   static constexpr int NI = TP + 1;                 // interfaces -1/2 .. TP-1/2
-  // shared-memory plan (8-byte words)
-  static constexpr int OFF_Q = 0;                               // [NQ][NP*W] doubles
+  // shared-memory plan (8-byte words: doubles, or double-float pairs in MODE 1)
+  static constexpr int OFF_Q = 0;                               // [NQ][NP*W] point values
   static constexpr int OFF_ROE = OFF_Q + NQ * NP * W;           // [5][NP*W]: sqrt(rho), u, v, w, H
   static constexpr int OFF_FV = OFF_ROE + 5 * NP * W;           // [4][NP*W]
-  static constexpr int OFF_B = OFF_FV + 4 * NP * W;             // [NQ][3][NW*W] (double, or df pairs)
+  static constexpr int OFF_B = OFF_FV + 4 * NP * W;             // [NQ][3][NW*W] squared indicators
   static constexpr int OFF_S = OFF_B + NQ * 3 * NW * W;         // [NQ][NW*W] second differences (MODE 1)
-  static constexpr int OFF_R = OFF_S + (MODE == 1 ? NQ * NW * W : 0);  // [18][NI*W], later [5][NI*W]
+  static constexpr int OFF_G = OFF_S + (MODE == 1 ? NQ * NW * W : 0);  // [NQ][NP*W] first differences (MODE 1)
+  static constexpr int OFF_R = OFF_G + (MODE == 1 ? NQ * NP * W : 0);  // [18][NI*W], later [5][NI*W]
   static constexpr int WORDS = OFF_R + 18 * NI * W;
   static constexpr int BYTES = WORDS * 8;
 };
@@ -104,7 +106,7 @@ __device__ __forceinline__ void df_weights(df B1, df B2, df B3, df& w1, df& w3) 
 }
 
 template <int D, int MODE>
-__global__ void __launch_bounds__(NTHREADS) k_dir(const DirArgs a) {
+__global__ void __launch_bounds__(Plan<MODE>::THREADS, MIN_CTAS_PER_SM) k_dir(const DirArgs a) {
   using PL = Plan<MODE>;
   constexpr int TP = PL::TP, NP = PL::NP, NW = PL::NW, NI = PL::NI;
   extern __shared__ double sm[];
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(const DirArgs a) {
   };
 
   // ---- A: load --------------------------------------------------------------
-  for (int item = tid; item < NP * W; item += NTHREADS) {
+  for (int item = tid; item < NP * W; item += PL::THREADS) {
     int pos, line;
     split<D>(item, NP, pos, line);
     const int c = wrap_idx(s0 - 3 + pos, nD);
@@ -162,21 +164,36 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(const DirArgs a) {
   }
   __syncthreads();
 
+  // ---- A2 (MODE 1): first differences g_j = q_{j+1} - q_j in FP64, kept as double-float
+  if (MODE == 1) {
+    const double* q = sm + PL::OFF_Q;
+    float2* G = reinterpret_cast<float2*>(sm + PL::OFF_G);
+    for (int item = tid; item < NQ * (NP - 1) * W; item += PL::THREADS) {
+      const int m = item / ((NP - 1) * W);
+      int j, line;
+      split<D>(item - m * (NP - 1) * W, NP - 1, j, line);
+      const double* qm = q + m * NP * W;
+      const df g = d2df_bits(qm[sidx<D>(j + 1, line, NP)] - qm[sidx<D>(j, line, NP)]);
+      G[m * NP * W + sidx<D>(j, line, NP)] = make_float2(g.hi, g.lo);
+    }
+    __syncthreads();
+  }
+
   // ---- B: squared scaled smoothness indicators of every window ----------------
   {
     const double* q = sm + PL::OFF_Q;
     int range_bad = 0;
-    for (int item = tid; item < NQ * NW * W; item += NTHREADS) {
+    for (int item = tid; item < NQ * NW * W; item += PL::THREADS) {
       const int m = item / (NW * W);
       int w, line;
       split<D>(item - m * NW * W, NW, w, line);
-      const double* qm = q + m * NP * W;
-      const double x = qm[sidx<D>(w, line, NP)];
-      const double y = qm[sidx<D>(w + 1, line, NP)];
-      const double z = qm[sidx<D>(w + 2, line, NP)];
-      const double gm = y - x, gp = z - y, s = gp - gm;
       const int o = sidx<D>(w, line, NW);
       if (MODE == 0) {
+        const double* qm = q + m * NP * W;
+        const double x = qm[sidx<D>(w, line, NP)];
+        const double y = qm[sidx<D>(w + 1, line, NP)];
+        const double z = qm[sidx<D>(w + 2, line, NP)];
+        const double gm = y - x, gp = z - y, s = gp - gm;
         double* bw = sm + PL::OFF_B;
         const double aa = fma((13.0 / 3.0) * s, s, a.eps4);
         const double u1 = fma(3.0, gp, -gm);   // x - 4y + 3z
@@ -188,12 +205,15 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(const DirArgs a) {
         bw[(m * 3 + 2) * NW * W + o] = b3 * b3;
       } else {
         float2* bw = reinterpret_cast<float2*>(sm + PL::OFF_B);
-        (sm + PL::OFF_S)[m * NW * W + o] = s;
-        const df dgm = d2df_bits(gm), dgp = d2df_bits(gp), ds = d2df_bits(s);
+        const float2* G = reinterpret_cast<const float2*>(sm + PL::OFF_G) + m * NP * W;
+        const float2 g0 = G[sidx<D>(w, line, NP)], g1 = G[sidx<D>(w + 1, line, NP)];
+        const df dgm = df{g0.x, g0.y}, dgp = df{g1.x, g1.y};
+        const df ds = df_add_fast(dgp, df_neg(dgm));
+        reinterpret_cast<float2*>(sm + PL::OFF_S)[m * NW * W + o] = make_float2(ds.hi, ds.lo);
         const df aa = df_add_pos(df_mul(df_sqr(ds), df{a.c133_hi, a.c133_lo}), df{a.eps4_hi, a.eps4_lo});
-        const df u1 = df_add(df_mul_f(dgp, 3.0f), df_neg(dgm));
-        const df u2 = df_add(dgm, dgp);
-        const df u3 = df_add(dgp, df_neg(df_mul_f(dgm, 3.0f)));
+        const df u1 = df_add_fast(df_mul_f(dgp, 3.0f), df_neg(dgm));
+        const df u2 = df_add_fast(dgm, dgp);
+        const df u3 = df_add_fast(dgp, df_neg(df_mul_f(dgm, 3.0f)));
         const df B1 = df_sqr(df_add_pos(df_sqr(u1), aa));
         const df B2 = df_sqr(df_add_pos(df_sqr(u2), aa));
         const df B3 = df_sqr(df_add_pos(df_sqr(u3), aa));
@@ -213,7 +233,7 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(const DirArgs a) {
   {
     const double* q = sm + PL::OFF_Q;
     double* rec = sm + PL::OFF_R;
-    for (int item = tid; item < NQ * NI * W; item += NTHREADS) {
+    for (int item = tid; item < NQ * NI * W; item += PL::THREADS) {
       const int m = item / (NI * W);
       int f, line;
       split<D>(item - m * NI * W, NI, f, line);
@@ -239,12 +259,26 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(const DirArgs a) {
         vL = weno_combine(B1f, B2f1, B3f2, xR, eR, eL);
         vR = weno_combine(B3f3, B2f2, B1f1, xL, eL, eR);
       } else {
-        const double* sw = sm + PL::OFF_S + m * NW * W;
-        const double s0 = sw[sidx<D>(f, line, NW)], s1 = sw[sidx<D>(f + 1, line, NW)];
-        const double s2 = sw[sidx<D>(f + 2, line, NW)], s3 = sw[sidx<D>(f + 3, line, NW)];
-        // F1 - F2 (left) = (s0 - s1)/3, F3 - F2 (left) = (s1 - s2)/6 = -(F3 - F2) (right),
-        // F1 - F2 (right) = (s3 - s2)/3
-        const double d1L = s0 - s1, dC = s1 - s2, d1R = s3 - s2;
+        // fhat_L = P2 + dL, fhat_R = P3 + dR with the offsets (differences only)
+        //   dL =  (2 g2 + g1)/6 + w1 (s0 - s1) + w3 (s1 - s2)      [w1 = omega_1/3, w3 = omega_3/6]
+        //   dR = -(2 g2 + g3)/6 + v1 (s3 - s2) - v3 (s1 - s2)
+        // (candidate 2 minus the point value, and F1 - F2, F3 - F2 as third differences),
+        // evaluated in double-float; only the two final additions use the FP64 pipe.
+        (void)P1;
+        (void)P4;
+        const float2* S = reinterpret_cast<const float2*>(sm + PL::OFF_S) + m * NW * W;
+        const float2* G = reinterpret_cast<const float2*>(sm + PL::OFF_G) + m * NP * W;
+        auto ldS = [&](int w) {
+          const float2 v = S[sidx<D>(w, line, NW)];
+          return df{v.x, v.y};
+        };
+        auto ldG = [&](int j) {
+          const float2 v = G[sidx<D>(j, line, NP)];
+          return df{v.x, v.y};
+        };
+        const df s0 = ldS(f), s1 = ldS(f + 1), s2 = ldS(f + 2), s3 = ldS(f + 3);
+        const df t0 = df_add_fast(s0, df_neg(s1)), tC = df_add_fast(s1, df_neg(s2)), t2 = df_add_fast(s3, df_neg(s2));
+        const df g1 = ldG(f + 1), g2 = ldG(f + 2), g3 = ldG(f + 3);
         const float2* b = reinterpret_cast<const float2*>(sm + PL::OFF_B) + m * 3 * NW * W;
         auto ld = [&](int k, int w) {
           const float2 v = b[k * NW * W + sidx<D>(w, line, NW)];
@@ -253,13 +287,14 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(const DirArgs a) {
         df w1, w3, v1, v3;
         df_weights(ld(0, f), ld(1, f + 1), ld(2, f + 2), w1, w3);
         df_weights(ld(2, f + 3), ld(1, f + 2), ld(0, f + 1), v1, v3);
-        const float fd1L = d2f_trunc(d1L), fdC = d2f_trunc(dC), fd1R = d2f_trunc(d1R);
-        const float corrL = __fmaf_rn(w1.lo, fd1L, w3.lo * fdC);
-        const float corrR = __fmaf_rn(v1.lo, fd1R, -(v3.lo * fdC));
-        const double eRc = fma(1.0 / 3.0, P3, fma(5.0 / 6.0, P2, fma(-1.0 / 6.0, P1, f2d_bits(corrL))));
-        const double eLc = fma(-1.0 / 6.0, P4, fma(5.0 / 6.0, P3, fma(1.0 / 3.0, P2, f2d_bits(corrR))));
-        vL = fma(f2d_bits(w1.hi), d1L, fma(f2d_bits(w3.hi), dC, eRc));
-        vR = fma(f2d_bits(v1.hi), d1R, fma(-f2d_bits(v3.hi), dC, eLc));
+        const df sixth{a.sixth_hi, a.sixth_lo};
+        const df g22 = df_mul_f(g2, 2.0f);
+        const df eL0 = df_mul(df_add_fast(g22, g1), sixth);
+        const df eR0 = df_mul(df_add_fast(g22, g3), sixth);
+        const df dL = df_add_fast(eL0, df_add_fast(df_mul(w1, t0), df_mul(w3, tC)));
+        const df dR = df_add_fast(df_neg(eR0), df_add_fast(df_mul(v1, t2), df_neg(df_mul(v3, tC))));
+        vL = (P2 + f2d_bits(dL.hi)) + f2d_bits(dL.lo);
+        vR = (P3 + f2d_bits(dR.hi)) + f2d_bits(dR.lo);
       }
       const int o = sidx<D>(f, line, NI);
       rec[(2 * m) * NI * W + o] = vL;
@@ -273,8 +308,8 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(const DirArgs a) {
     const double gm1 = a.gamma - 1.0;
     const double* r = sm + PL::OFF_ROE;
     double* rec = sm + PL::OFF_R;
-    int bad = 0;
-    for (int item = tid; item < NI * W; item += NTHREADS) {
+    int bad = 0, range_bad = 0;
+    for (int item = tid; item < NI * W; item += PL::THREADS) {
       int f, line;
       split<D>(item, NI, f, line);
       const int o = sidx<D>(f, line, NI);
@@ -293,7 +328,10 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(const DirArgs a) {
       fR[0] = uR[1 + D];
       const int sa = sidx<D>(f + 2, line, NP), sb = sidx<D>(f + 3, line, NP);
       const double ra = r[sa], rb = r[sb];
-      const double rs = 1.0 / (ra + rb);
+      const double rsum = ra + rb;
+      // MODE 1: FP32-seeded Newton reciprocals (FP64 accurate, ~4 FP64 operations
+      // instead of ~9 for the IEEE division); MODE 0: IEEE division and square root
+      const double rs = (MODE == 1) ? rcp_newton(rsum) : 1.0 / rsum;
       const double wa = ra * rs, wb = rb * rs;
       double V[3];
 #pragma unroll
@@ -302,8 +340,16 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(const DirArgs a) {
       const double q2h = 0.5 * fma(V[0], V[0], fma(V[1], V[1], V[2] * V[2]));
       const double c2 = gm1 * (H - q2h);
       bad |= !(c2 > 0.0);
-      const double c = sqrt(c2);
-      const double rc = 1.0 / c;
+      double c, rc;
+      if (MODE == 1) {
+        // the float seeds need c^2 and sqrt(rho_a) + sqrt(rho_b) inside the float range
+        range_bad |= !(c2 > 1e-36 && c2 < 1e36 && rsum > 1e-36 && rsum < 1e36);
+        rc = rsqrt_newton(c2);
+        c = c2 * rc;
+      } else {
+        c = sqrt(c2);
+        rc = 1.0 / c;
+      }
       double du[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) du[v] = uR[v] - uL[v];
@@ -338,6 +384,7 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(const DirArgs a) {
       for (int v = 0; v < 5; ++v) rec[v * NI * W + o] = 0.5 * (fL[v] + fR[v] - diss[v]);
     }
     if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(a.status, ST_NONPHYS);
+    if (MODE == 1 && __any_sync(0xffffffffu, range_bad) && (tid & 31) == 0) atomicOr(a.status, ST_DF_RANGE);
   }
   __syncthreads();
 
@@ -347,7 +394,7 @@ __global__ void __launch_bounds__(NTHREADS) k_dir(const DirArgs a) {
     const double r12 = 1.0 / (12.0 * a.g.h[D]);
     const double* F = sm + PL::OFF_R;
     const double* fvs = sm + PL::OFF_FV;
-    for (int item = tid; item < TP * W; item += NTHREADS) {
+    for (int item = tid; item < TP * W; item += PL::THREADS) {
       int pp, line;
       split<D>(item, TP, pp, line);
       if (s0 + pp >= nD || a0 + line >= na) continue;
@@ -435,7 +482,7 @@ cudaError_t launch_d(const DirArgs& a, cudaStream_t s) {
   constexpr int AX = (D == 0) ? 1 : 0;
   constexpr int BX = (D == 2) ? 1 : 2;
   dim3 grid((a.g.n[D] + PL::TP - 1) / PL::TP, (a.g.n[AX] + W - 1) / W, a.g.n[BX]);
-  k_dir<D, MODE><<<grid, NTHREADS, PL::BYTES, s>>>(a);
+  k_dir<D, MODE><<<grid, PL::THREADS, PL::BYTES, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -54,6 +54,7 @@ struct DirArgs {
   int mode;          // 0: all-FP64 weights; 1: double-float weights
   float c133_hi, c133_lo;  // 13/3 as a double-float
   float eps4_hi, eps4_lo;  // 4 * weno_eps as a double-float
+  float sixth_hi, sixth_lo;  // 1/6 as a double-float
 };
 
 // Launchers (return cudaGetLastError() of the launch).

@@ -119,6 +119,21 @@ def isentropic_vortex(nx: int, ny: int, nz: int, t: float = 0.0, length: float =
     return to_conserved(rho, u, v, w, p, gamma)
 
 
+def shock_tube(nx: int, ny: int, nz: int, axis: int = 0, gamma: float = GAMMA) -> np.ndarray:
+    """Periodic Sod-type shock tube along `axis`: (rho, p) = (1, 1/gamma) on the first half
+    and (0.125, 0.1/gamma) on the second, at rest (two discontinuities through the wrap)."""
+    shp = (nz, ny, nx)
+    n = shp[2 - axis]
+    left = (np.arange(n) < n // 2)
+    sl = [None, None, None]
+    sl[2 - axis] = slice(None)
+    mask = np.broadcast_to(left[tuple(sl)], shp)
+    rho = np.where(mask, 1.0, 0.125)
+    p = np.where(mask, 1.0 / gamma, 0.1 / gamma)
+    zero = np.zeros(shp)
+    return to_conserved(rho, zero, zero, zero, p, gamma)
+
+
 # ---- decaying isotropic turbulence (Sec. 2.3) --------------------------------
 def hit_spectrum(k, u0: float = 0.3, k0: float = 4.0):
     """Model spectrum E(k) = 16 sqrt(2/pi) u0^2/k0 (k/k0)^4 exp(-2 (k/k0)^2)."""

@@ -69,6 +69,9 @@ CASES = [
     ("hit64", lambda: I.isotropic_turbulence(64, seed=1), dict(mu_eff=I.hit_mu_eff())),
     ("near_sonic_harten_active", lambda: I.random_smooth(24, 20, 16, seed=6, amp=0.1, mach=1.1), dict(mu_eff=1e-3)),
     ("vortex_2d", lambda: I.isentropic_vortex(64, 64, 1, length=16.0), dict(lx=16.0, ly=16.0, lz=1.0)),
+    ("shock_tube_y", lambda: I.shock_tube(12, 40, 10, axis=1), dict(mu_eff=1e-3)),
+    ("shock_plus_noise", lambda: I.shock_tube(36, 20, 16, axis=0) * (1.0 + 0.01 * np.sin(
+        np.arange(36 * 20 * 16).reshape(16, 20, 36) * 0.37)), dict(mu_eff=0.0)),
 ]
 
 
