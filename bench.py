@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-strict", action="store_true", help="skip the all-FP64 comparison run")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk comparison run")
+    ap.add_argument("--study", choices=["fp32"], default=None,
+                    help="fp32: FP64 vs FP32-bulk over --steps steps at --n^3 (KE/enstrophy every step)")
     return ap.parse_args()
 
 
@@ -330,6 +333,7 @@ def run_ours(args, world, rank, local):
            "d2h_bytes_per_step": state_bytes + 8 * ns3d.NS3D_STATS_NDOUBLE,
            "call": "ns3d_step_host (pinned host state in, 1 RK4 step + statistics, state out)"}
 
+    u64_final = ud.clone()
     solver.close()
     del ud
 
@@ -344,6 +348,24 @@ def run_ours(args, world, rank, local):
         v2 = sum_over_ranks(float(n ** 3 * RK_STAGES * Ks), world) / (ms2 * 1e-3) / 1e9
         modes["fp64_strict"] = {"value": v2, "ms_per_step": ms2 / Ks, "steps": Ks, "weights": "FP64",
                                 "roofline": roofline_of(kt2, FLOPS_DIR)}
+    if not args.no_fp32:
+        # FP32-bulk: same W + K steps from the same state; error against the FP64 path
+        s3, u3, _, ms3, kt3, st3, _ = timed_loop(ns3d.NS3D_FP32_BULK, K, W, False)
+        s3.close()
+        v3 = sum_over_ranks(float(n ** 3 * RK_STAGES * K), world) / (ms3 * 1e-3) / 1e9
+        dmax = float((u3 - u64_final).abs().max().item())
+        umax = float(u64_final.abs().max().item())
+        modes["fp32_bulk"] = {
+            "value": v3, "ms_per_step": ms3 / K, "speedup_vs_fp64": v3 / value,
+            "arithmetic": "FP32 indicators, weights, interface values, Roe flux; FP64 state, difference, "
+                          "viscous terms, RK, reductions",
+            "error_vs_fp64_after_steps": W + K,
+            "ke_rel_err": float(abs(st3[-1, 5] - st[-1, 5]) / abs(st[-1, 5])),
+            "enstrophy_rel_err": float(abs(st3[-1, 6] - st[-1, 6]) / abs(st[-1, 6])),
+            "field_maxnorm_rel_err": dmax / umax,
+            "dir_kernel_ms": sum(kt3[k][0] for k in ("dir_x", "dir_y", "dir_z")) / K}
+        del u3
+    del u64_final
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -363,8 +385,65 @@ def run_ours(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_study_fp32(args, local):
+    """FP64 path vs FP32-bulk mode on the decaying-turbulence workload: same initial state
+    and dt, --steps RK4 steps each, KE and enstrophy logged every step on the device."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_2211_16718_gb300 import build as B
+    B.build()
+    from paper_2211_16718_gb300 import ns3d
+
+    n, K = args.n, args.steps
+    u0, mu = hit_state(n)
+    res, finals, dt = {}, {}, None
+    for name, prec in (("fp64", ns3d.NS3D_FP64), ("fp32_bulk", ns3d.NS3D_FP32_BULK)):
+        s = ns3d.Solver(n, n, n, mu_eff=mu, precision=prec)
+        ud = torch.from_numpy(u0.copy()).cuda()
+        if dt is None:
+            dt = s.dt_from_cfl(ud, args.cfl)
+        log = torch.zeros((K + 1, ns3d.NS3D_STATS_NDOUBLE), dtype=torch.float64, device="cuda")
+        s.stats_async(ud, log[0])
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(K):
+            s.rk_step(ud, dt, 1)
+            s.stats_async(ud, log[i + 1])
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res[name] = {"ms_per_step": ms / K, "gpts": n ** 3 * RK_STAGES * K / (ms * 1e-3) / 1e9,
+                     "log": log.cpu().numpy()}
+        s.close()
+        finals[name] = ud.cpu().numpy()
+        del ud
+    a, b = res["fp64"]["log"], res["fp32_bulk"]["log"]
+    diff = np.abs(finals["fp32_bulk"] - finals["fp64"]).reshape(5, -1).max(axis=1)
+    scale = np.abs(finals["fp64"]).reshape(5, -1).max(axis=1)
+    out = {"study": "fp32_bulk vs fp64", "workload": f"decaying isotropic turbulence {n}^3, seed 0, CFL {args.cfl}",
+           "steps": K, "dt": dt,
+           "fp64": {k: res["fp64"][k] for k in ("ms_per_step", "gpts")},
+           "fp32_bulk": {k: res["fp32_bulk"][k] for k in ("ms_per_step", "gpts")},
+           "speedup": res["fp64"]["ms_per_step"] / res["fp32_bulk"]["ms_per_step"],
+           "ke_rel_err_max_over_steps": float((np.abs(b[:, 5] - a[:, 5]) / np.abs(a[:, 5])).max()),
+           "enstrophy_rel_err_max_over_steps": float((np.abs(b[:, 6] - a[:, 6]) / np.abs(a[:, 6])).max()),
+           "ke_final": [float(a[-1, 5]), float(b[-1, 5])], "enstrophy_final": [float(a[-1, 6]), float(b[-1, 6])],
+           "field_maxnorm_rel_err_final": float(diff.max() / scale.max()),
+           "field_maxnorm_rel_err_per_variable": (diff / scale).tolist(),
+           "conservation_mass_rel_drift_fp32": float(abs(b[-1, 0] - b[0, 0]) / b[0, 0]),
+           "conservation_energy_rel_drift_fp32": float(abs(b[-1, 4] - b[0, 4]) / b[0, 4])}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.study == "fp32":
+        run_study_fp32(args, int(os.environ.get("LOCAL_RANK", "0")))
+        return
     if args.impl == "reference":
         # the oracle runs on the host of rank 0 only; other ranks exit without work
         run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))

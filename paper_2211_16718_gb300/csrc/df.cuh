@@ -149,6 +149,20 @@ __device__ __forceinline__ df d2df_bits(double x) {
   return df{hi, lo};
 }
 
+// Round-to-nearest FP64 -> FP32 by bit manipulation (finite values in the float
+// range; smaller magnitudes flush to zero, larger ones saturate to infinity).
+__device__ __forceinline__ float d2f_rn(double x) {
+  const uint32_t h = (uint32_t)__double2hiint(x);
+  const uint32_t l = (uint32_t)__double2loint(x);
+  const uint32_t sign = h & 0x80000000u;
+  const int e8 = (int)((h >> 20) & 0x7ffu) - 896;
+  if (e8 <= 0) return __uint_as_float(sign);
+  if (e8 >= 255) return __uint_as_float(sign | 0x7f800000u);
+  uint32_t bits = ((uint32_t)e8 << 23) | ((h & 0xfffffu) << 3) | (l >> 29);
+  bits += (l >> 28) & 1u;  // round half up on the first dropped bit (carry may bump the exponent)
+  return __uint_as_float(sign | bits);
+}
+
 // Nearest-float of a double (truncated to 24 bits; enough for correction terms).
 __device__ __forceinline__ float d2f_trunc(double x) { return d2df_bits(x).hi; }
 

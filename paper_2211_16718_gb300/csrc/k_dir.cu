@@ -33,6 +33,7 @@
 #include <math.h>
 
 #include "df.cuh"
+#include "k_dir_common.cuh"
 #include "ns3d_internal.cuh"
 
 namespace ns3d {
@@ -412,66 +413,7 @@ __global__ void __launch_bounds__(Plan<MODE>::THREADS, MIN_CTAS_PER_SM) k_dir(co
         }
       }
       const long long p = flat(s0 + pp, a0 + line);
-      switch (a.epi) {
-        case EPI_ACC_WRITE:
-#pragma unroll
-          for (int v = 0; v < 5; ++v) a.k[v * N + p] = cv[v];
-          break;
-        case EPI_ACC_ADD:
-#pragma unroll
-          for (int v = 0; v < 5; ++v) a.k[v * N + p] += cv[v];
-          break;
-        case EPI_RHS_OUT:
-#pragma unroll
-          for (int v = 0; v < 5; ++v) a.out[v * N + p] = a.k[v * N + p] + cv[v];
-          break;
-        case EPI_RK4_FIRST:
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            const double K = a.k[v * N + p] + cv[v];
-            a.out[v * N + p] = fma(a.a, K, a.un[v * N + p]);
-            a.acc[v * N + p] = K;
-          }
-          break;
-        case EPI_RK4_MID:
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            const double K = a.k[v * N + p] + cv[v];
-            a.out[v * N + p] = fma(a.a, K, a.un[v * N + p]);
-            a.acc[v * N + p] = fma(2.0, K, a.acc[v * N + p]);
-          }
-          break;
-        case EPI_RK4_LAST:
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            const double K = a.k[v * N + p] + cv[v];
-            a.out[v * N + p] = fma(a.a, a.acc[v * N + p] + K, a.un[v * N + p]);
-          }
-          break;
-        case EPI_SSP_1:
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            const double K = a.k[v * N + p] + cv[v];
-            a.out[v * N + p] = fma(a.a, K, a.un[v * N + p]);
-          }
-          break;
-        case EPI_SSP_2:
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            const double K = a.k[v * N + p] + cv[v];
-            a.out[v * N + p] = 0.75 * a.un[v * N + p] + 0.25 * fma(a.a, K, a.u[v * N + p]);
-          }
-          break;
-        case EPI_SSP_3:
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            const double K = a.k[v * N + p] + cv[v];
-            a.out[v * N + p] = (1.0 / 3.0) * a.un[v * N + p] + (2.0 / 3.0) * fma(a.a, K, a.u[v * N + p]);
-          }
-          break;
-        default:
-          break;
-      }
+      dir_epilogue(a, p, cv);
     }
   }
 }
@@ -501,10 +443,12 @@ cudaError_t set_attr() {
 cudaError_t prepare_dir_kernels() {
   cudaError_t e = set_attr<0>();
   if (e == cudaSuccess) e = set_attr<1>();
+  if (e == cudaSuccess) e = prepare_dir32_kernels();
   return e;
 }
 
 cudaError_t launch_dir(int d, const DirArgs& a, cudaStream_t s) {
+  if (a.mode == 2) return launch_dir32(d, a, s);
   if (a.mode == 1) {
     switch (d) {
       case 0: return launch_d<0, 1>(a, s);

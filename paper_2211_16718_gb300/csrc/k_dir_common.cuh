@@ -1,0 +1,106 @@
+// Pieces shared by the direction passes (k_dir.cu: FP64 modes, k_dir32.cu:
+// FP32-bulk mode): tile indexing and the accumulation / Runge-Kutta epilogue.
+#pragma once
+
+#include "ns3d_internal.cuh"
+
+namespace ns3d {
+
+constexpr int DIR_W = 4;  // lines per tile
+
+// Position-major for y/z lines (consecutive threads = consecutive x lines),
+// line-major for x lines (consecutive threads = consecutive x points).
+template <int D>
+__device__ __forceinline__ int tile_idx(int pos, int line, int npos) {
+  return D == 0 ? line * npos + pos : pos * DIR_W + line;
+}
+template <int D>
+__device__ __forceinline__ void tile_split(int item, int npos, int& pos, int& line) {
+  if (D == 0) {
+    pos = item % npos;
+    line = item / npos;
+  } else {
+    line = item % DIR_W;
+    pos = item / DIR_W;
+  }
+}
+
+// Flat grid index of pencil coordinate c on line la of the tile row bz.
+template <int D>
+__device__ __forceinline__ long long tile_flat(const Grid& g, int c, int la, int bz) {
+  constexpr int AX = (D == 0) ? 1 : 0;
+  constexpr int BX = (D == 2) ? 1 : 2;
+  int idx[3];
+  idx[D] = c;
+  idx[AX] = la;
+  idx[BX] = bz;
+  return ((long long)idx[2] * g.n[1] + idx[1]) * g.n[0] + idx[0];
+}
+
+// Accumulate this direction's contribution cv[5] at point p, or finish the RHS /
+// RK stage (last direction), according to a.epi.
+__device__ __forceinline__ void dir_epilogue(const DirArgs& a, long long p, const double cv[5]) {
+  const long long N = a.g.N;
+  switch (a.epi) {
+    case EPI_ACC_WRITE:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) a.k[v * N + p] = cv[v];
+      break;
+    case EPI_ACC_ADD:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) a.k[v * N + p] += cv[v];
+      break;
+    case EPI_RHS_OUT:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) a.out[v * N + p] = a.k[v * N + p] + cv[v];
+      break;
+    case EPI_RK4_FIRST:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K = a.k[v * N + p] + cv[v];
+        a.out[v * N + p] = fma(a.a, K, a.un[v * N + p]);
+        a.acc[v * N + p] = K;
+      }
+      break;
+    case EPI_RK4_MID:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K = a.k[v * N + p] + cv[v];
+        a.out[v * N + p] = fma(a.a, K, a.un[v * N + p]);
+        a.acc[v * N + p] = fma(2.0, K, a.acc[v * N + p]);
+      }
+      break;
+    case EPI_RK4_LAST:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K = a.k[v * N + p] + cv[v];
+        a.out[v * N + p] = fma(a.a, a.acc[v * N + p] + K, a.un[v * N + p]);
+      }
+      break;
+    case EPI_SSP_1:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K = a.k[v * N + p] + cv[v];
+        a.out[v * N + p] = fma(a.a, K, a.un[v * N + p]);
+      }
+      break;
+    case EPI_SSP_2:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K = a.k[v * N + p] + cv[v];
+        a.out[v * N + p] = 0.75 * a.un[v * N + p] + 0.25 * fma(a.a, K, a.u[v * N + p]);
+      }
+      break;
+    case EPI_SSP_3:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K = a.k[v * N + p] + cv[v];
+        a.out[v * N + p] = (1.0 / 3.0) * a.un[v * N + p] + (2.0 / 3.0) * fma(a.a, K, a.u[v * N + p]);
+      }
+      break;
+    default:
+      break;
+  }
+}
+
+}  // namespace ns3d

@@ -7,6 +7,7 @@
 //    partials).
 #include <math.h>
 
+#include "df.cuh"
 #include "ns3d_internal.cuh"
 
 namespace ns3d {
@@ -93,6 +94,78 @@ __global__ void __launch_bounds__(PW_THREADS) k_visc(const double* __restrict__ 
       fv[(long long)(4 * d + 1) * N + p] = tau[1];
       fv[(long long)(4 * d + 2) * N + p] = tau[2];
       fv[(long long)(4 * d + 3) * N + p] = en;
+    }
+  }
+}
+
+// ---- FP32-bulk variants: same formulas in FP32, results widened to FP64 -----------
+__global__ void __launch_bounds__(PW_THREADS) k_prim32(const double* __restrict__ u, double* __restrict__ pm,
+                                                       long long N, float gamma, int* __restrict__ status) {
+  int bad = 0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    const float rho = d2f_rn(u[p]), mx = d2f_rn(u[N + p]), my = d2f_rn(u[2 * N + p]);
+    const float mz = d2f_rn(u[3 * N + p]), e = d2f_rn(u[4 * N + p]);
+    const float ri = __frcp_rn(rho);
+    const float vx = mx * ri, vy = my * ri, vz = mz * ri;
+    const float ke = 0.5f * (mx * vx + my * vy + mz * vz);
+    const float pr = (gamma - 1.0f) * (e - ke);
+    pm[PM_U * N + p] = f2d_bits(vx);
+    pm[PM_V * N + p] = f2d_bits(vy);
+    pm[PM_W * N + p] = f2d_bits(vz);
+    pm[PM_P * N + p] = f2d_bits(pr);
+    pm[PM_T * N + p] = f2d_bits(gamma * pr * ri);
+    pm[PM_H * N + p] = f2d_bits((e + pr) * ri);
+    pm[PM_SR * N + p] = f2d_bits(__fsqrt_rn(rho));
+    bad |= !(rho > 0.0f) | !(pr > 0.0f) | !isfinite(e) | !isfinite(mx + my + mz);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONPHYS);
+}
+
+__device__ __forceinline__ float d4f(float qm2, float qm1, float qp1, float qp2, float r12h) {
+  return fmaf(8.0f, qp1 - qm1, -(qp2 - qm2)) * r12h;
+}
+
+__global__ void __launch_bounds__(PW_THREADS) k_visc32(const double* __restrict__ pm, double* __restrict__ fv,
+                                                       int nx, int ny, int nz, float r12hx, float r12hy,
+                                                       float r12hz, float mu, float kappa) {
+  const long long N = (long long)nx * ny * nz;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(p % nx);
+    const int j = (int)((p / nx) % ny);
+    const int k = (int)(p / ((long long)nx * ny));
+    float G[4][3];
+    const int n3[3] = {nx, ny, nz};
+    const float r12[3] = {r12hx, r12hy, r12hz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      long long nb[4];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const int off = (o < 2) ? (o - 2) : (o - 1);
+        int c[3] = {i, j, k};
+        c[d] = wrap_idx(c[d] + off, n3[d]);
+        nb[o] = flat3(c[0], c[1], c[2], nx, ny);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int plane = (q < 3) ? q : PM_T;
+        const double* A = pm + (long long)plane * N;
+        G[q][d] = d4f(d2f_rn(__ldg(A + nb[0])), d2f_rn(__ldg(A + nb[1])), d2f_rn(__ldg(A + nb[2])),
+                      d2f_rn(__ldg(A + nb[3])), r12[d]);
+      }
+    }
+    const float vel[3] = {d2f_rn(pm[PM_U * N + p]), d2f_rn(pm[PM_V * N + p]), d2f_rn(pm[PM_W * N + p])};
+    const float tdiv = (2.0f / 3.0f) * (G[0][0] + G[1][1] + G[2][2]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float tau[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) tau[m] = (m == d) ? mu * fmaf(2.0f, G[d][d], -tdiv) : mu * (G[m][d] + G[d][m]);
+      const float en = fmaf(vel[0], tau[0], fmaf(vel[1], tau[1], fmaf(vel[2], tau[2], kappa * G[3][d])));
+      fv[(long long)(4 * d + 0) * N + p] = f2d_bits(tau[0]);
+      fv[(long long)(4 * d + 1) * N + p] = f2d_bits(tau[1]);
+      fv[(long long)(4 * d + 2) * N + p] = f2d_bits(tau[2]);
+      fv[(long long)(4 * d + 3) * N + p] = f2d_bits(en);
     }
   }
 }
@@ -269,6 +342,18 @@ cudaError_t launch_prim(const Grid& g, const double* u, double* pm, double gamma
 cudaError_t launch_visc(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s) {
   k_visc<<<grid_for(g.N, PW_THREADS), PW_THREADS, 0, s>>>(pm, fv, g.n[0], g.n[1], g.n[2], 1.0 / (12.0 * g.h[0]),
                                                           1.0 / (12.0 * g.h[1]), 1.0 / (12.0 * g.h[2]), mu, kappa);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prim32(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s) {
+  k_prim32<<<grid_for(g.N, PW_THREADS), PW_THREADS, 0, s>>>(u, pm, g.N, (float)gamma, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_visc32(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s) {
+  k_visc32<<<grid_for(g.N, PW_THREADS), PW_THREADS, 0, s>>>(
+      pm, fv, g.n[0], g.n[1], g.n[2], (float)(1.0 / (12.0 * g.h[0])), (float)(1.0 / (12.0 * g.h[1])),
+      (float)(1.0 / (12.0 * g.h[2])), (float)mu, (float)kappa);
   return cudaGetLastError();
 }
 

@@ -112,7 +112,7 @@ DirArgs base_args(ns3d_ctx* c, const double* u) {
   a.eps4 = 4.0 * c->p.weno_eps;
   a.hdelta = c->p.harten_delta;
   a.status = c->status;
-  a.mode = (c->p.precision == NS3D_FP64_STRICT) ? 0 : 1;
+  a.mode = (c->p.precision == NS3D_FP64_STRICT) ? 0 : (c->p.precision == NS3D_FP32_BULK) ? 2 : 1;
   const double c133 = 13.0 / 3.0, eps4 = 4.0 * c->p.weno_eps;
   a.c133_hi = (float)c133;
   a.c133_lo = (float)(c133 - (double)a.c133_hi);
@@ -134,13 +134,18 @@ int status_code(int word) {
 // One full right-hand-side evaluation of state u: primitives, viscous fluxes,
 // x and y passes accumulating into k, z pass with the given epilogue.
 int rhs_pass(ns3d_ctx* c, const double* u, int epi, double* out, const double* un, double coef) {
-  int rc = timed(c, NS3D_K_PRIM, [&] { return launch_prim(c->g, u, c->pm, c->p.gamma, c->status, c->stream); },
-                 "primitive kernel");
+  const bool f32 = (c->p.precision == NS3D_FP32_BULK);
+  int rc = timed(c, NS3D_K_PRIM, [&] {
+    return f32 ? launch_prim32(c->g, u, c->pm, c->p.gamma, c->status, c->stream)
+               : launch_prim(c->g, u, c->pm, c->p.gamma, c->status, c->stream);
+  }, "primitive kernel");
   if (rc) return rc;
   if (c->p.mu_eff > 0.0) {
     const double kappa = c->p.mu_eff / ((c->p.gamma - 1.0) * c->p.prandtl);
-    rc = timed(c, NS3D_K_VISC, [&] { return launch_visc(c->g, c->pm, c->fv, c->p.mu_eff, kappa, c->stream); },
-               "viscous-flux kernel");
+    rc = timed(c, NS3D_K_VISC, [&] {
+      return f32 ? launch_visc32(c->g, c->pm, c->fv, c->p.mu_eff, kappa, c->stream)
+                 : launch_visc(c->g, c->pm, c->fv, c->p.mu_eff, kappa, c->stream);
+    }, "viscous-flux kernel");
     if (rc) return rc;
   }
   DirArgs a = base_args(c, u);
@@ -213,7 +218,7 @@ int validate(const ns3d_params* p, char* msg, size_t n) {
   if (!(p->harten_delta >= 0.0) || !isfinite(p->harten_delta))
     return snprintf(msg, n, "harten_delta must be >= 0"), NS3D_EINVAL;
   if (p->rk != NS3D_RK4 && p->rk != NS3D_SSPRK3) return snprintf(msg, n, "unknown rk scheme"), NS3D_EINVAL;
-  if (p->precision != NS3D_FP64 && p->precision != NS3D_FP64_STRICT)
+  if (p->precision != NS3D_FP64 && p->precision != NS3D_FP64_STRICT && p->precision != NS3D_FP32_BULK)
     return snprintf(msg, n, "unsupported precision mode"), NS3D_EINVAL;
   if (p->precision == NS3D_FP64 && !(p->weno_eps >= 1e-15))
     return snprintf(msg, n, "weno_eps below 1e-15 needs NS3D_FP64_STRICT"), NS3D_EINVAL;

@@ -51,7 +51,7 @@ struct DirArgs {
   double eps4;       // 4 * weno_eps (smoothness indicators are scaled by 4)
   double hdelta;     // Harten entropy-fix fraction
   int* status;
-  int mode;          // 0: all-FP64 weights; 1: double-float weights
+  int mode;          // 0: all FP64; 1: FP64 values, double-float weights/offsets; 2: FP32 bulk
   float c133_hi, c133_lo;  // 13/3 as a double-float
   float eps4_hi, eps4_lo;  // 4 * weno_eps as a double-float
   float sixth_hi, sixth_lo;  // 1/6 as a double-float
@@ -60,8 +60,13 @@ struct DirArgs {
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_prim(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s);
 cudaError_t launch_visc(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s);
+// FP32-bulk variants (FP32 arithmetic, results widened to FP64)
+cudaError_t launch_prim32(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s);
+cudaError_t launch_visc32(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s);
 cudaError_t prepare_dir_kernels();  // per device, before the first launch
-cudaError_t launch_dir(int d, const DirArgs& a, cudaStream_t s);
+cudaError_t launch_dir(int d, const DirArgs& a, cudaStream_t s);  // dispatches on a.mode
+cudaError_t prepare_dir32_kernels();
+cudaError_t launch_dir32(int d, const DirArgs& a, cudaStream_t s);  // FP32-bulk (a.mode == 2)
 int stats_num_blocks(const Grid& g);
 cudaError_t launch_stats(const Grid& g, const double* u, const double* pm, double gamma, double* partials,
                          cudaStream_t s);
