@@ -61,8 +61,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-strict", action="store_true", help="skip the all-FP64 comparison run")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk comparison run")
-    ap.add_argument("--study", choices=["fp32"], default=None,
-                    help="fp32: FP64 vs FP32-bulk over --steps steps at --n^3 (KE/enstrophy every step)")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 48-instance ensemble measurement")
+    ap.add_argument("--study", choices=["fp32", "ensemble"], default=None,
+                    help="fp32: FP64 vs FP32-bulk over --steps steps at --n^3 (KE/enstrophy every step); "
+                         "ensemble: 48 uneven realisations, --steps steps per schedule")
     return ap.parse_args()
 
 
@@ -154,14 +156,24 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def ncu_traffic_per_point(kernel: str, source: str):
+KDIR_SOURCES = ("k_dir.cu", "k_dir_impl.cuh", "k_dir_common.cuh", "k_point_impl.cuh", "df.cuh")
+
+
+def kernel_source_sha(names=KDIR_SOURCES) -> str:
+    """sha256 prefix over the sources that make up the direction-pass kernel."""
+    import hashlib
+    h = hashlib.sha256()
+    for nm in names:
+        h.update(open(os.path.join(ROOT, "paper_2211_16718_gb300", "csrc", nm), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic_per_point(kernel: str, sha: str):
     """DRAM bytes per grid point of one launch (dram__bytes_read.sum + dram__bytes_write.sum
-    from a committed ncu summary under profiles/), or None if the kernel source has changed
+    from a committed ncu summary under profiles/), or None if the kernel sources have changed
     since the counters were taken."""
     import glob
-    import hashlib
     import re
-    sha = hashlib.sha256(open(source, "rb").read()).hexdigest()[:16]
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         for line in open(path):
             m = re.match(rf"TRAFFIC {kernel} bytes_per_point=([0-9.]+) grid=(\d+) \S+ source_sha256=(\w+)", line)
@@ -309,7 +321,7 @@ def run_ours(args, world, rank, local):
     roofline["fp32_work_note"] = ("the double-float weights add ~3.6k FP32-pipe instructions per point and "
                                   "direction (FP32 runs 63x the FP64 rate), not counted in achieved")
     avg_launch_s = roofline["avg_launch_ms"] * 1e-3
-    tr = ncu_traffic_per_point("k_dir", os.path.join(ROOT, "paper_2211_16718_gb300", "csrc", "k_dir.cu"))
+    tr = ncu_traffic_per_point("k_dir", kernel_source_sha())
     if tr is not None:
         bpp, src, grid = tr
         roofline["traffic"] = bpp * n ** 3
@@ -366,6 +378,11 @@ def run_ours(args, world, rank, local):
             "dir_kernel_ms": sum(kt3[k][0] for k in ("dir_x", "dir_y", "dir_z")) / K}
         del u3
     del u64_final
+
+    if not args.no_ensemble:
+        # batched ensemble of uneven grids (10 steps per schedule; the full 50-step run is
+        # bench.py --study ensemble --steps 50)
+        modes["ensemble_48"] = run_ensemble(10, args.cfl)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -439,8 +456,76 @@ def run_study_fp32(args, local):
     print(json.dumps(out), flush=True)
 
 
+ENSEMBLE_SIZES = (32, 48, 64, 96, 128)
+
+
+def run_ensemble(steps: int, cfl: float, count: int = 48, cache_path=None, sizes_cycle=ENSEMBLE_SIZES) -> dict:
+    """Ensemble of `count` decaying-turbulence realisations (seed i, grid sizes_cycle[i % len]^3,
+    dt_i from CFL `cfl` of its own initial state): `steps` RK4 steps in each schedule (from
+    the same initial states), after the autotuner has picked the tile shape."""
+    import numpy as np
+    import torch
+    from paper_2211_16718_gb300 import inputs as I
+    from paper_2211_16718_gb300 import ns3d
+
+    sizes = [sizes_cycle[i % len(sizes_cycle)] for i in range(count)]
+    host = [I.isotropic_turbulence(n, seed=i) for i, n in enumerate(sizes)]
+    params = [ns3d.default_params(n, n, n, mu_eff=I.hit_mu_eff()) for n in sizes]
+    pts = sum(n ** 3 for n in sizes)
+    b = ns3d.Batch(params)
+    states = [torch.from_numpy(h.copy()).cuda() for h in host]
+    b.set_states(states)
+    b.set_dt([1.0] * count)
+    ws = b.stats().cpu().numpy()[:, 9]
+    dts = [cfl / w for w in ws]
+    b.set_dt(dts)
+    variant, tune_ms = b.autotune(cache_path)
+    out = {"instances": count, "sizes": f"seed i: {tuple(sizes_cycle)}[i % {len(sizes_cycle)}]^3", "points": pts,
+           "steps": steps,
+           "autotuned_variant": variant, "autotune_ms_per_step": tune_ms,
+           "tile_shapes": {"0": "24x4", "1": "16x4", "2": "40x2"}}
+    finals = {}
+    for schedule in ("sequential", "graph", "persistent"):
+        for s, h in zip(states, host):
+            s.copy_(torch.from_numpy(h))
+        b.step(1, schedule)  # warm-up (and graph capture for this step count)
+        for s, h in zip(states, host):
+            s.copy_(torch.from_numpy(h))
+        if schedule != "sequential":
+            b.step(steps, schedule)  # capture the full-length graph once, untimed
+            for s, h in zip(states, host):
+                s.copy_(torch.from_numpy(h))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.step(steps, schedule)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[schedule] = {"ms": ms, "gpts": pts * RK_STAGES * steps / (ms * 1e-3) / 1e9}
+        finals[schedule] = [s.cpu().numpy() for s in states[:3]]
+    b.check()
+    out["persistent_in_graph"] = b.info()["persistent_in_graph"]
+    out["persistent_ctas_per_sm"] = b.info()["persistent_ctas_per_sm"]
+    out["schedules_bitwise_equal"] = all(np.array_equal(a, c) for k in ("graph", "persistent")
+                                         for a, c in zip(finals[k], finals["sequential"]))
+    out["speedup_persistent_vs_sequential"] = out["persistent"]["gpts"] / out["sequential"]["gpts"]
+    out["speedup_graph_vs_sequential"] = out["graph"]["gpts"] / out["sequential"]["gpts"]
+    b.close()
+    return out
+
+
 def main():
     args = parse()
+    if args.study == "ensemble":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        from paper_2211_16718_gb300 import build as B
+        B.build()
+        print(json.dumps({"study": "ensemble", "config5": run_ensemble(args.steps, args.cfl),
+                          "small_instances": run_ensemble(args.steps, args.cfl, count=256,
+                                                          sizes_cycle=(12, 16, 20, 24))}), flush=True)
+        return
     if args.study == "fp32":
         run_study_fp32(args, int(os.environ.get("LOCAL_RANK", "0")))
         return

@@ -175,6 +175,54 @@ const char *ns3d_strerror(int code);
 /* Message of the last failure of ctx (empty if none). */
 const char *ns3d_last_error(const ns3d_ctx *ctx);
 
+/* ---- ensembles of independent grids of uneven sizes ---------------------------
+ * Many independent realisations (e.g. the decaying-turbulence problem of Sec. 2.3
+ * with different seeds and grid sizes) advanced together on one GPU.  Each
+ * instance has its own parameters (grid, box, mu_eff, ...; all instances share
+ * precision, which must be NS3D_FP64 or NS3D_FP64_STRICT, and rk), its own
+ * caller-owned state and its own dt.  The schedules compute bitwise identical
+ * results:
+ *  NS3D_BATCH_SEQUENTIAL  per-instance launches (5 per RK stage per instance);
+ *  NS3D_BATCH_GRAPH       one launch per phase for all instances over a flattened
+ *                         (instance, tile) work list, the whole nsteps loop captured
+ *                         once in a CUDA graph and replayed with one graph launch;
+ *  NS3D_BATCH_PERSISTENT  one cooperative kernel for all steps, stages, phases and
+ *                         instances, phases separated by grid-wide barriers
+ *                         (captured in a CUDA graph when the runtime allows it). */
+enum { NS3D_BATCH_SEQUENTIAL = 0, NS3D_BATCH_GRAPH = 1, NS3D_BATCH_PERSISTENT = 2 };
+typedef struct ns3d_batch ns3d_batch;
+
+/* params[count] (count 1..4096, each grid <= 2^31 points); allocates the
+ * per-instance scratch (~39 doubles per point).  NS3D_EINVAL / NS3D_ENOMEM. */
+int ns3d_batch_init(const ns3d_params *params, int count, void *cuda_stream, ns3d_batch **out);
+void ns3d_batch_free(ns3d_batch *b);
+/* u_dev[count]: host array of caller-owned device states (layout as above). */
+int ns3d_batch_set_states(ns3d_batch *b, double *const *u_dev);
+/* dt[count]: host array of per-instance time steps. */
+int ns3d_batch_set_dt(ns3d_batch *b, const double *dt);
+/* Advance every instance by nsteps steps with the given schedule (no host sync). */
+int ns3d_batch_step(ns3d_batch *b, int nsteps, int schedule);
+/* Statistics of every instance into out_dev[count * NS3D_STATS_NDOUBLE] (no sync). */
+int ns3d_batch_stats(ns3d_batch *b, double *out_dev);
+/* Read and clear the batch's sticky status word (synchronises). */
+int ns3d_batch_check(ns3d_batch *b);
+/* Tile shape of the direction passes: variant 0 (24 x 4), 1 (16 x 4), 2 (40 x 2)
+ * points x lines; results do not depend on it. */
+int ns3d_batch_set_variant(ns3d_batch *b, int variant);
+/* Autotuner: times one graph-scheduled step of every tile variant on copies of the
+ * current states (which are not advanced), selects the fastest and appends
+ * {"key": ..., "variant": ..., "ms_per_step": [...]} to the JSON-lines file
+ * cache_path (NULL: no cache); a key already in the cache is used without timing.
+ * ms_out[3] (may be NULL) receives the timings (-1 when taken from the cache). */
+int ns3d_batch_autotune(ns3d_batch *b, const char *cache_path, double *ms_out);
+/* Current variant, CTAs per SM of the persistent kernel (0 before its first use)
+ * and whether it runs captured in a graph (1), as a direct launch (0) or not yet (-1). */
+int ns3d_batch_info(const ns3d_batch *b, int *variant, int *persistent_ctas_per_sm, int *persistent_in_graph);
+const char *ns3d_batch_last_error(const ns3d_batch *b);
+
+/* Tile shape of the direction passes of a single context (see ns3d_batch_set_variant). */
+int ns3d_set_variant(ns3d_ctx *ctx, int variant);
+
 /* ---- measurement support (no counterpart in the paper) -------------------- */
 /* Kernel identifiers used by the timing calls. */
 enum {

@@ -18,7 +18,7 @@ namespace ns3d {
 
 namespace {
 
-constexpr int W = DIR_W;
+constexpr int W = 4;
 constexpr int NQ = 9;
 constexpr int TP = 32;
 constexpr int NP = TP + 6, NW = TP + 4, NI = TP + 1;
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(THREADS) k_dir32(const DirArgs a) {
   // ---- A: load, convert, point fluxes in FP32 ---------------------------------
   for (int item = tid; item < NP * W; item += THREADS) {
     int pos, line;
-    tile_split<D>(item, NP, pos, line);
+    tile_split<D, W>(item, NP, pos, line);
     const int c = wrap_idx(s0 - 3 + pos, nD);
     const int la = min(a0 + line, na - 1);
     const long long p = tile_flat<D>(a.g, c, la, bz);
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(THREADS) k_dir32(const DirArgs a) {
     const float vx = d2f_rn(__ldg(a.pm + PM_U * N + p)), vy = d2f_rn(__ldg(a.pm + PM_V * N + p));
     const float vz = d2f_rn(__ldg(a.pm + PM_W * N + p)), pr = d2f_rn(__ldg(a.pm + PM_P * N + p));
     const float un = (D == 0) ? vx : (D == 1) ? vy : vz;
-    const int s = tile_idx<D>(pos, line, NP);
+    const int s = tile_idx<D, W>(pos, line, NP);
     float* q = smf + OFF_Q;
 #pragma unroll
     for (int v = 0; v < 5; ++v) q[v * NP * W + s] = U[v];
@@ -104,16 +104,16 @@ __global__ void __launch_bounds__(THREADS) k_dir32(const DirArgs a) {
     for (int item = tid; item < NQ * NW * W; item += THREADS) {
       const int m = item / (NW * W);
       int w, line;
-      tile_split<D>(item - m * NW * W, NW, w, line);
+      tile_split<D, W>(item - m * NW * W, NW, w, line);
       const float* qm = q + m * NP * W;
-      const float x = qm[tile_idx<D>(w, line, NP)];
-      const float y = qm[tile_idx<D>(w + 1, line, NP)];
-      const float z = qm[tile_idx<D>(w + 2, line, NP)];
+      const float x = qm[tile_idx<D, W>(w, line, NP)];
+      const float y = qm[tile_idx<D, W>(w + 1, line, NP)];
+      const float z = qm[tile_idx<D, W>(w + 2, line, NP)];
       const float gm = y - x, gp = z - y, sd = gp - gm;
       const float aa = fmaf((13.0f / 3.0f) * sd, sd, eps4);
       const float u1 = fmaf(3.0f, gp, -gm), u2 = gm + gp, u3 = fmaf(-3.0f, gm, gp);
       const float b1 = fmaf(u1, u1, aa), b2 = fmaf(u2, u2, aa), b3 = fmaf(u3, u3, aa);
-      const int o = tile_idx<D>(w, line, NW);
+      const int o = tile_idx<D, W>(w, line, NW);
       bw[(m * 3 + 0) * NW * W + o] = b1 * b1;
       bw[(m * 3 + 1) * NW * W + o] = b2 * b2;
       bw[(m * 3 + 2) * NW * W + o] = b3 * b3;
@@ -129,21 +129,21 @@ __global__ void __launch_bounds__(THREADS) k_dir32(const DirArgs a) {
     for (int item = tid; item < NQ * NI * W; item += THREADS) {
       const int m = item / (NI * W);
       int f, line;
-      tile_split<D>(item - m * NI * W, NI, f, line);
+      tile_split<D, W>(item - m * NI * W, NI, f, line);
       const float* qm = q + m * NP * W;
-      const float P0 = qm[tile_idx<D>(f, line, NP)], P1 = qm[tile_idx<D>(f + 1, line, NP)];
-      const float P2 = qm[tile_idx<D>(f + 2, line, NP)], P3 = qm[tile_idx<D>(f + 3, line, NP)];
-      const float P4 = qm[tile_idx<D>(f + 4, line, NP)], P5 = qm[tile_idx<D>(f + 5, line, NP)];
+      const float P0 = qm[tile_idx<D, W>(f, line, NP)], P1 = qm[tile_idx<D, W>(f + 1, line, NP)];
+      const float P2 = qm[tile_idx<D, W>(f + 2, line, NP)], P3 = qm[tile_idx<D, W>(f + 3, line, NP)];
+      const float P4 = qm[tile_idx<D, W>(f + 4, line, NP)], P5 = qm[tile_idx<D, W>(f + 5, line, NP)];
       const float xR = fmaf(11.0f / 6.0f, P2, fmaf(-7.0f / 6.0f, P1, (1.0f / 3.0f) * P0));
       const float eR = fmaf(1.0f / 3.0f, P3, fmaf(5.0f / 6.0f, P2, (-1.0f / 6.0f) * P1));
       const float eL = fmaf(-1.0f / 6.0f, P4, fmaf(5.0f / 6.0f, P3, (1.0f / 3.0f) * P2));
       const float xL = fmaf(1.0f / 3.0f, P5, fmaf(-7.0f / 6.0f, P4, (11.0f / 6.0f) * P3));
       const float* b = bw + m * 3 * NW * W;
-      const float vL = weno_combine32(b[0 * NW * W + tile_idx<D>(f, line, NW)], b[1 * NW * W + tile_idx<D>(f + 1, line, NW)],
-                                      b[2 * NW * W + tile_idx<D>(f + 2, line, NW)], xR, eR, eL);
-      const float vR = weno_combine32(b[2 * NW * W + tile_idx<D>(f + 3, line, NW)], b[1 * NW * W + tile_idx<D>(f + 2, line, NW)],
-                                      b[0 * NW * W + tile_idx<D>(f + 1, line, NW)], xL, eL, eR);
-      const int o = tile_idx<D>(f, line, NI);
+      const float vL = weno_combine32(b[0 * NW * W + tile_idx<D, W>(f, line, NW)], b[1 * NW * W + tile_idx<D, W>(f + 1, line, NW)],
+                                      b[2 * NW * W + tile_idx<D, W>(f + 2, line, NW)], xR, eR, eL);
+      const float vR = weno_combine32(b[2 * NW * W + tile_idx<D, W>(f + 3, line, NW)], b[1 * NW * W + tile_idx<D, W>(f + 2, line, NW)],
+                                      b[0 * NW * W + tile_idx<D, W>(f + 1, line, NW)], xL, eL, eR);
+      const int o = tile_idx<D, W>(f, line, NI);
       rec[(2 * m) * NI * W + o] = vL;
       rec[(2 * m + 1) * NI * W + o] = vR;
     }
@@ -160,8 +160,8 @@ __global__ void __launch_bounds__(THREADS) k_dir32(const DirArgs a) {
     int bad = 0;
     for (int item = tid; item < NI * W; item += THREADS) {
       int f, line;
-      tile_split<D>(item, NI, f, line);
-      const int o = tile_idx<D>(f, line, NI);
+      tile_split<D, W>(item, NI, f, line);
+      const int o = tile_idx<D, W>(f, line, NI);
       float uL[5], uR[5], fL[5], fR[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(THREADS) k_dir32(const DirArgs a) {
       }
       fL[0] = uL[1 + D];
       fR[0] = uR[1 + D];
-      const int sa = tile_idx<D>(f + 2, line, NP), sb = tile_idx<D>(f + 3, line, NP);
+      const int sa = tile_idx<D, W>(f + 2, line, NP), sb = tile_idx<D, W>(f + 3, line, NP);
       const float ra = r[sa], rb = r[sb];
       const float rs = __frcp_rn(ra + rb);
       const float wa = ra * rs, wb = rb * rs;
@@ -233,18 +233,18 @@ __global__ void __launch_bounds__(THREADS) k_dir32(const DirArgs a) {
     const double* fvs = smd + OFF_FV / 2;
     for (int item = tid; item < TP * W; item += THREADS) {
       int pp, line;
-      tile_split<D>(item, TP, pp, line);
+      tile_split<D, W>(item, TP, pp, line);
       if (s0 + pp >= nD || a0 + line >= na) continue;
       double cv[5];
-      const int op = tile_idx<D>(pp + 1, line, NI), om = tile_idx<D>(pp, line, NI);
+      const int op = tile_idx<D, W>(pp + 1, line, NI), om = tile_idx<D, W>(pp, line, NI);
 #pragma unroll
       for (int v = 0; v < 5; ++v) cv[v] = (F[v * NI * W + om] - F[v * NI * W + op]) * rdx;
       if (a.fv != nullptr) {
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
           const double* fc = fvs + cc * NP * W;
-          const double d1 = fc[tile_idx<D>(pp + 4, line, NP)] - fc[tile_idx<D>(pp + 2, line, NP)];
-          const double d2 = fc[tile_idx<D>(pp + 5, line, NP)] - fc[tile_idx<D>(pp + 1, line, NP)];
+          const double d1 = fc[tile_idx<D, W>(pp + 4, line, NP)] - fc[tile_idx<D, W>(pp + 2, line, NP)];
+          const double d2 = fc[tile_idx<D, W>(pp + 5, line, NP)] - fc[tile_idx<D, W>(pp + 1, line, NP)];
           cv[1 + cc] = fma(fma(8.0, d1, -d2), r12, cv[1 + cc]);
         }
       }

@@ -6,22 +6,21 @@
 
 namespace ns3d {
 
-constexpr int DIR_W = 4;  // lines per tile
-
-// Position-major for y/z lines (consecutive threads = consecutive x lines),
+// Shared-memory index of (position along the pencil, line) in a tile of W lines:
+// position-major for y/z lines (consecutive threads = consecutive x lines),
 // line-major for x lines (consecutive threads = consecutive x points).
-template <int D>
+template <int D, int W>
 __device__ __forceinline__ int tile_idx(int pos, int line, int npos) {
-  return D == 0 ? line * npos + pos : pos * DIR_W + line;
+  return D == 0 ? line * npos + pos : pos * W + line;
 }
-template <int D>
+template <int D, int W>
 __device__ __forceinline__ void tile_split(int item, int npos, int& pos, int& line) {
   if (D == 0) {
     pos = item % npos;
     line = item / npos;
   } else {
-    line = item % DIR_W;
-    pos = item / DIR_W;
+    line = item % W;
+    pos = item / W;
   }
 }
 

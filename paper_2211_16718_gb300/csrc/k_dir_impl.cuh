@@ -1,0 +1,410 @@
+// Fused per-direction pass of the right-hand side (arXiv 2211.16718, Sec. 2.2):
+// for every grid line along direction D, component-wise WENO5 reconstruction of
+// u and f_D (left- and right-biased, Jiang-Shu weights), Roe flux with Harten's
+// entropy fix at every interface, conservative difference of the interface
+// fluxes, 4th-order central divergence of the viscous flux along D, and the
+// accumulation / Runge-Kutta stage epilogue.
+//
+// One CTA owns a tile of TP points along D times W lines (periodic halo of 3
+// points each side, fetched with wrapped indices).  Everything is staged in
+// shared memory and computed in five phases separated by barriers:
+//   A  load state, primitives, viscous flux; point fluxes f_D        [NP x W]
+//   B  smoothness indicators of every 3-point window for the 9
+//      reconstructed scalars (u_0..u_4, f_1..f_4)                      [9 x NW x W]
+//   C  left/right WENO5 values of the 9 scalars at every interface     [9 x NI x W]
+//   D  Roe flux at every interface                                     [NI x W]
+//   E  flux difference + viscous divergence + epilogue, global writes  [TP x W]
+// The mass flux f_0 = (rho u_D) is the momentum component u_{1+D} itself, so its
+// reconstructions are those of u_{1+D}.
+//
+// With b_k = 4(eps + beta_k) and B_k = b_k^2, the weights are
+// omega_k = (c_k/B_k) / sum_j (c_j/B_j) = c_k prod_{m!=k} B_m / sum_j c_j prod_{m!=j} B_m.
+// The three squared indicators of a window serve the left-biased reconstruction
+// at one interface and the right-biased one at another, so each is computed once.
+//
+// MODE 0 (all FP64): fhat = sum_k omega_k F_k with one FP64 division.
+// MODE 1 (FP64 values, double-float weights): since sum omega = 1,
+//   fhat = F_2 + omega_1 (F_1 - F_2) + omega_3 (F_3 - F_2),
+// where F_1 - F_2 and F_3 - F_2 are third differences of the data (FP64, from the
+// window second differences s) and the weights, which only multiply these small
+// differences, are evaluated in double-float arithmetic (~48 bits) on the FP32
+// pipe.  The FP64 work per interface and scalar drops from ~60 to ~16
+// instructions; the result agrees with the all-FP64 evaluation to rounding.
+#include <math.h>
+
+#pragma once
+
+#include "df.cuh"
+#include "k_dir_common.cuh"
+#include "k_point_impl.cuh"
+#include "ns3d_internal.cuh"
+
+namespace ns3d {
+
+constexpr int NQ = 9;             // reconstructed scalars
+constexpr int MIN_CTAS_PER_SM = 3;
+
+// Tile plan of a direction pass: TP points along the pencil times W lines.
+template <int MODE, int TP_, int W_>
+struct Plan {
+  static constexpr int TP = TP_;                    // points per tile along the pencil
+  static constexpr int W = W_;                      // lines per tile
+  static constexpr int THREADS = (MODE == 0) ? 128 : 256;  // MODE 1: 8 warps share the tile (latency hiding)
+  static constexpr int NP = TP + 6;                 // points incl. 3-point halo each side
+  static constexpr int NW = TP + 4;                 // 3-point windows centred at -2 .. TP+1
+  static constexpr int NI = TP + 1;                 // interfaces -1/2 .. TP-1/2
+  // shared-memory plan (8-byte words: doubles, or double-float pairs in MODE 1)
+  static constexpr int OFF_Q = 0;                               // [NQ][NP*W] point values
+  static constexpr int OFF_ROE = OFF_Q + NQ * NP * W;           // [5][NP*W]: sqrt(rho), u, v, w, H
+  static constexpr int OFF_FV = OFF_ROE + 5 * NP * W;           // [4][NP*W]
+  static constexpr int OFF_B = OFF_FV + 4 * NP * W;             // [NQ][3][NW*W] squared indicators
+  static constexpr int OFF_S = OFF_B + NQ * 3 * NW * W;         // [NQ][NW*W] second differences (MODE 1)
+  static constexpr int OFF_G = OFF_S + (MODE == 1 ? NQ * NW * W : 0);  // [NQ][NP*W] first differences (MODE 1)
+  static constexpr int OFF_R = OFF_G + (MODE == 1 ? NQ * NP * W : 0);  // [18][NI*W], later [5][NI*W]
+  static constexpr int WORDS = OFF_R + 18 * NI * W;
+  static constexpr int BYTES = WORDS * 8;
+};
+
+__device__ __forceinline__ double weno_combine(double B1, double B2, double B3, double F1, double F2, double F3) {
+  const double p23 = B2 * B3;
+  const double t13 = 6.0 * (B1 * B3);
+  const double t12 = 3.0 * (B1 * B2);
+  const double num = fma(p23, F1, fma(t13, F2, t12 * F3));
+  const double den = p23 + t13 + t12;
+  return num / den;
+}
+
+// Double-float weights of one reconstruction from its three squared, scaled
+// indicators (candidate order 1, 2, 3): w1 = omega_1/3, w3 = omega_3/6.
+__device__ __forceinline__ void df_weights(df B1, df B2, df B3, df& w1, df& w3) {
+  // common power-of-two scaling keeps the products in range (omega is scale-free)
+  const int E = max(exponent_of(B1.hi), max(exponent_of(B2.hi), exponent_of(B3.hi)));
+  const float sc = pow2f(-E);
+  B1 = df{B1.hi * sc, B1.lo * sc};
+  B2 = df{B2.hi * sc, B2.lo * sc};
+  B3 = df{B3.hi * sc, B3.lo * sc};
+  const df p23 = df_mul(B2, B3);
+  const df p13 = df_mul(B1, B3);
+  const df p12 = df_mul(B1, B2);
+  const df den = df_add_pos(p23, df_add_pos(df_mul_f(p13, 6.0f), df_mul_f(p12, 3.0f)));
+  w1 = df_div(p23, df_mul_f(den, 3.0f));
+  w3 = df_div(p12, df_mul_f(den, 2.0f));
+}
+
+// One tile (tx, ty, tz) of the direction-D pass, executed by the whole CTA on the
+// shared memory sm (PL::BYTES).  Used by the standalone kernels (one tile per CTA),
+// the batched kernels and the persistent ensemble kernel (many tiles per CTA,
+// with a barrier between tiles).  NC selects read-only-cache loads, valid only when
+// the inputs are not written during the kernel (false in the persistent kernel).
+template <int D, int MODE, int TP_, int W_, bool NC = true>
+__device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, int ty, int tz) {
+  using PL = Plan<MODE, TP_, W_>;
+  constexpr int TP = PL::TP, NP = PL::NP, NW = PL::NW, NI = PL::NI, W = PL::W;
+  const int nD = a.g.n[D];
+  constexpr int AX = (D == 0) ? 1 : 0;   // axis of the W lines
+  constexpr int BX = (D == 2) ? 1 : 2;   // axis of blockIdx.z
+  const int na = a.g.n[AX];
+  const int nx = a.g.n[0], ny = a.g.n[1];
+  const long long N = a.g.N;
+  const int s0 = tx * TP;
+  const int a0 = ty * W;
+  const int bz = tz;
+  const int tid = threadIdx.x;
+
+  auto flat = [&](int c, int la) -> long long {
+    int idx[3];
+    idx[D] = c;
+    idx[AX] = la;
+    idx[BX] = bz;
+    return ((long long)idx[2] * ny + idx[1]) * nx + idx[0];
+  };
+
+  // ---- A: load --------------------------------------------------------------
+  for (int item = tid; item < NP * W; item += PL::THREADS) {
+    int pos, line;
+    tile_split<D, W>(item, NP, pos, line);
+    const int c = wrap_idx(s0 - 3 + pos, nD);
+    const int la = min(a0 + line, na - 1);
+    const long long p = flat(c, la);
+    double U[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) U[v] = ldx<NC>(a.u + v * N + p);
+    const double vx = ldx<NC>(a.pm + PM_U * N + p), vy = ldx<NC>(a.pm + PM_V * N + p), vz = ldx<NC>(a.pm + PM_W * N + p);
+    const double pr = ldx<NC>(a.pm + PM_P * N + p);
+    const double un = (D == 0) ? vx : (D == 1) ? vy : vz;
+    const int s = tile_idx<D, W>(pos, line, NP);
+    double* q = sm + PL::OFF_Q;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) q[v * NP * W + s] = U[v];
+    q[5 * NP * W + s] = (D == 0) ? fma(U[1], un, pr) : U[1] * un;
+    q[6 * NP * W + s] = (D == 1) ? fma(U[2], un, pr) : U[2] * un;
+    q[7 * NP * W + s] = (D == 2) ? fma(U[3], un, pr) : U[3] * un;
+    q[8 * NP * W + s] = (U[4] + pr) * un;
+    double* r = sm + PL::OFF_ROE;
+    r[0 * NP * W + s] = ldx<NC>(a.pm + PM_SR * N + p);
+    r[1 * NP * W + s] = vx;
+    r[2 * NP * W + s] = vy;
+    r[3 * NP * W + s] = vz;
+    r[4 * NP * W + s] = ldx<NC>(a.pm + PM_H * N + p);
+    if (a.fv != nullptr) {
+      double* f = sm + PL::OFF_FV;
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) f[cc * NP * W + s] = ldx<NC>(a.fv + (long long)(4 * D + cc) * N + p);
+    }
+  }
+  __syncthreads();
+
+  // ---- A2 (MODE 1): first differences g_j = q_{j+1} - q_j in FP64, kept as double-float
+  if (MODE == 1) {
+    const double* q = sm + PL::OFF_Q;
+    float2* G = reinterpret_cast<float2*>(sm + PL::OFF_G);
+    for (int item = tid; item < NQ * (NP - 1) * W; item += PL::THREADS) {
+      const int m = item / ((NP - 1) * W);
+      int j, line;
+      tile_split<D, W>(item - m * (NP - 1) * W, NP - 1, j, line);
+      const double* qm = q + m * NP * W;
+      const df g = d2df_bits(qm[tile_idx<D, W>(j + 1, line, NP)] - qm[tile_idx<D, W>(j, line, NP)]);
+      G[m * NP * W + tile_idx<D, W>(j, line, NP)] = make_float2(g.hi, g.lo);
+    }
+    __syncthreads();
+  }
+
+  // ---- B: squared scaled smoothness indicators of every window ----------------
+  {
+    const double* q = sm + PL::OFF_Q;
+    int range_bad = 0;
+    for (int item = tid; item < NQ * NW * W; item += PL::THREADS) {
+      const int m = item / (NW * W);
+      int w, line;
+      tile_split<D, W>(item - m * NW * W, NW, w, line);
+      const int o = tile_idx<D, W>(w, line, NW);
+      if (MODE == 0) {
+        const double* qm = q + m * NP * W;
+        const double x = qm[tile_idx<D, W>(w, line, NP)];
+        const double y = qm[tile_idx<D, W>(w + 1, line, NP)];
+        const double z = qm[tile_idx<D, W>(w + 2, line, NP)];
+        const double gm = y - x, gp = z - y, s = gp - gm;
+        double* bw = sm + PL::OFF_B;
+        const double aa = fma((13.0 / 3.0) * s, s, a.eps4);
+        const double u1 = fma(3.0, gp, -gm);   // x - 4y + 3z
+        const double u2 = gm + gp;             // z - x
+        const double u3 = fma(-3.0, gm, gp);   // 3x - 4y + z
+        const double b1 = fma(u1, u1, aa), b2 = fma(u2, u2, aa), b3 = fma(u3, u3, aa);
+        bw[(m * 3 + 0) * NW * W + o] = b1 * b1;
+        bw[(m * 3 + 1) * NW * W + o] = b2 * b2;
+        bw[(m * 3 + 2) * NW * W + o] = b3 * b3;
+      } else {
+        float2* bw = reinterpret_cast<float2*>(sm + PL::OFF_B);
+        const float2* G = reinterpret_cast<const float2*>(sm + PL::OFF_G) + m * NP * W;
+        const float2 g0 = G[tile_idx<D, W>(w, line, NP)], g1 = G[tile_idx<D, W>(w + 1, line, NP)];
+        const df dgm = df{g0.x, g0.y}, dgp = df{g1.x, g1.y};
+        const df ds = df_add_fast(dgp, df_neg(dgm));
+        reinterpret_cast<float2*>(sm + PL::OFF_S)[m * NW * W + o] = make_float2(ds.hi, ds.lo);
+        const df aa = df_add_pos(df_mul(df_sqr(ds), df{a.c133_hi, a.c133_lo}), df{a.eps4_hi, a.eps4_lo});
+        const df u1 = df_add_fast(df_mul_f(dgp, 3.0f), df_neg(dgm));
+        const df u2 = df_add_fast(dgm, dgp);
+        const df u3 = df_add_fast(dgp, df_neg(df_mul_f(dgm, 3.0f)));
+        const df B1 = df_sqr(df_add_pos(df_sqr(u1), aa));
+        const df B2 = df_sqr(df_add_pos(df_sqr(u2), aa));
+        const df B3 = df_sqr(df_add_pos(df_sqr(u3), aa));
+        bw[(m * 3 + 0) * NW * W + o] = make_float2(B1.hi, B1.lo);
+        bw[(m * 3 + 1) * NW * W + o] = make_float2(B2.hi, B2.lo);
+        bw[(m * 3 + 2) * NW * W + o] = make_float2(B3.hi, B3.lo);
+        // the float exponent range bounds the indicators (differences of the data
+        // up to ~1e9); beyond it the host reports NS3D_ERANGE instead of a NaN
+        range_bad |= !(fmaxf(B1.hi, fmaxf(B2.hi, B3.hi)) < 1e36f);
+      }
+    }
+    if (MODE == 1 && __any_sync(0xffffffffu, range_bad) && (tid & 31) == 0) atomicOr(a.status, ST_DF_RANGE);
+  }
+  __syncthreads();
+
+  // ---- C: left/right WENO5 values at every interface --------------------------
+  {
+    const double* q = sm + PL::OFF_Q;
+    double* rec = sm + PL::OFF_R;
+    for (int item = tid; item < NQ * NI * W; item += PL::THREADS) {
+      const int m = item / (NI * W);
+      int f, line;
+      tile_split<D, W>(item - m * NI * W, NI, f, line);
+      const double* qm = q + m * NP * W;
+      const double P1 = qm[tile_idx<D, W>(f + 1, line, NP)];
+      const double P2 = qm[tile_idx<D, W>(f + 2, line, NP)], P3 = qm[tile_idx<D, W>(f + 3, line, NP)];
+      const double P4 = qm[tile_idx<D, W>(f + 4, line, NP)];
+      double vL, vR;
+      if (MODE == 0) {
+        const double P0 = qm[tile_idx<D, W>(f, line, NP)], P5 = qm[tile_idx<D, W>(f + 5, line, NP)];
+        // third-order candidates at the interface between P2 and P3
+        const double xR = fma(11.0 / 6.0, P2, fma(-7.0 / 6.0, P1, (1.0 / 3.0) * P0));
+        const double eR = fma(1.0 / 3.0, P3, fma(5.0 / 6.0, P2, (-1.0 / 6.0) * P1));
+        const double eL = fma(-1.0 / 6.0, P4, fma(5.0 / 6.0, P3, (1.0 / 3.0) * P2));
+        const double xL = fma(1.0 / 3.0, P5, fma(-7.0 / 6.0, P4, (11.0 / 6.0) * P3));
+        const double* b = sm + PL::OFF_B + m * 3 * NW * W;
+        const double B1f = b[0 * NW * W + tile_idx<D, W>(f, line, NW)];
+        const double B2f1 = b[1 * NW * W + tile_idx<D, W>(f + 1, line, NW)];
+        const double B3f2 = b[2 * NW * W + tile_idx<D, W>(f + 2, line, NW)];
+        const double B3f3 = b[2 * NW * W + tile_idx<D, W>(f + 3, line, NW)];
+        const double B2f2 = b[1 * NW * W + tile_idx<D, W>(f + 2, line, NW)];
+        const double B1f1 = b[0 * NW * W + tile_idx<D, W>(f + 1, line, NW)];
+        vL = weno_combine(B1f, B2f1, B3f2, xR, eR, eL);
+        vR = weno_combine(B3f3, B2f2, B1f1, xL, eL, eR);
+      } else {
+        // fhat_L = P2 + dL, fhat_R = P3 + dR with the offsets (differences only)
+        //   dL =  (2 g2 + g1)/6 + w1 (s0 - s1) + w3 (s1 - s2)      [w1 = omega_1/3, w3 = omega_3/6]
+        //   dR = -(2 g2 + g3)/6 + v1 (s3 - s2) - v3 (s1 - s2)
+        // (candidate 2 minus the point value, and F1 - F2, F3 - F2 as third differences),
+        // evaluated in double-float; only the two final additions use the FP64 pipe.
+        (void)P1;
+        (void)P4;
+        const float2* S = reinterpret_cast<const float2*>(sm + PL::OFF_S) + m * NW * W;
+        const float2* G = reinterpret_cast<const float2*>(sm + PL::OFF_G) + m * NP * W;
+        auto ldS = [&](int w) {
+          const float2 v = S[tile_idx<D, W>(w, line, NW)];
+          return df{v.x, v.y};
+        };
+        auto ldG = [&](int j) {
+          const float2 v = G[tile_idx<D, W>(j, line, NP)];
+          return df{v.x, v.y};
+        };
+        const df s0 = ldS(f), s1 = ldS(f + 1), s2 = ldS(f + 2), s3 = ldS(f + 3);
+        const df t0 = df_add_fast(s0, df_neg(s1)), tC = df_add_fast(s1, df_neg(s2)), t2 = df_add_fast(s3, df_neg(s2));
+        const df g1 = ldG(f + 1), g2 = ldG(f + 2), g3 = ldG(f + 3);
+        const float2* b = reinterpret_cast<const float2*>(sm + PL::OFF_B) + m * 3 * NW * W;
+        auto ld = [&](int k, int w) {
+          const float2 v = b[k * NW * W + tile_idx<D, W>(w, line, NW)];
+          return df{v.x, v.y};
+        };
+        df w1, w3, v1, v3;
+        df_weights(ld(0, f), ld(1, f + 1), ld(2, f + 2), w1, w3);
+        df_weights(ld(2, f + 3), ld(1, f + 2), ld(0, f + 1), v1, v3);
+        const df sixth{a.sixth_hi, a.sixth_lo};
+        const df g22 = df_mul_f(g2, 2.0f);
+        const df eL0 = df_mul(df_add_fast(g22, g1), sixth);
+        const df eR0 = df_mul(df_add_fast(g22, g3), sixth);
+        const df dL = df_add_fast(eL0, df_add_fast(df_mul(w1, t0), df_mul(w3, tC)));
+        const df dR = df_add_fast(df_neg(eR0), df_add_fast(df_mul(v1, t2), df_neg(df_mul(v3, tC))));
+        vL = (P2 + f2d_bits(dL.hi)) + f2d_bits(dL.lo);
+        vR = (P3 + f2d_bits(dR.hi)) + f2d_bits(dR.lo);
+      }
+      const int o = tile_idx<D, W>(f, line, NI);
+      rec[(2 * m) * NI * W + o] = vL;
+      rec[(2 * m + 1) * NI * W + o] = vR;
+    }
+  }
+  __syncthreads();
+
+  // ---- D: Roe flux at every interface -------------------------------------------
+  {
+    const double gm1 = a.gamma - 1.0;
+    const double* r = sm + PL::OFF_ROE;
+    double* rec = sm + PL::OFF_R;
+    int bad = 0, range_bad = 0;
+    for (int item = tid; item < NI * W; item += PL::THREADS) {
+      int f, line;
+      tile_split<D, W>(item, NI, f, line);
+      const int o = tile_idx<D, W>(f, line, NI);
+      double uL[5], uR[5], fL[5], fR[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        uL[v] = rec[(2 * v) * NI * W + o];
+        uR[v] = rec[(2 * v + 1) * NI * W + o];
+      }
+#pragma unroll
+      for (int v = 1; v < 5; ++v) {
+        fL[v] = rec[(2 * (4 + v)) * NI * W + o];
+        fR[v] = rec[(2 * (4 + v) + 1) * NI * W + o];
+      }
+      fL[0] = uL[1 + D];
+      fR[0] = uR[1 + D];
+      const int sa = tile_idx<D, W>(f + 2, line, NP), sb = tile_idx<D, W>(f + 3, line, NP);
+      const double ra = r[sa], rb = r[sb];
+      const double rsum = ra + rb;
+      // MODE 1: FP32-seeded Newton reciprocals (FP64 accurate, ~4 FP64 operations
+      // instead of ~9 for the IEEE division); MODE 0: IEEE division and square root
+      const double rs = (MODE == 1) ? rcp_newton(rsum) : 1.0 / rsum;
+      const double wa = ra * rs, wb = rb * rs;
+      double V[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) V[m] = fma(wa, r[(1 + m) * NP * W + sa], wb * r[(1 + m) * NP * W + sb]);
+      const double H = fma(wa, r[4 * NP * W + sa], wb * r[4 * NP * W + sb]);
+      const double q2h = 0.5 * fma(V[0], V[0], fma(V[1], V[1], V[2] * V[2]));
+      const double c2 = gm1 * (H - q2h);
+      bad |= !(c2 > 0.0);
+      double c, rc;
+      if (MODE == 1) {
+        // the float seeds need c^2 and sqrt(rho_a) + sqrt(rho_b) inside the float range
+        range_bad |= !(c2 > 1e-36 && c2 < 1e36 && rsum > 1e-36 && rsum < 1e36);
+        rc = rsqrt_newton(c2);
+        c = c2 * rc;
+      } else {
+        c = sqrt(c2);
+        rc = 1.0 / c;
+      }
+      double du[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) du[v] = uR[v] - uL[v];
+      constexpr int T1 = (D == 0) ? 1 : 0;
+      constexpr int T2 = (D == 2) ? 1 : 2;
+      const double un = V[D], vt1 = V[T1], vt2 = V[T2];
+      const double b1 = gm1 * (rc * rc);
+      const double vdm = fma(V[0], du[1], fma(V[1], du[2], V[2] * du[3]));
+      const double phi = b1 * (fma(q2h, du[0], du[4]) - vdm);
+      const double a2 = du[0] - phi;
+      const double a3 = fma(-vt1, du[0], du[1 + T1]);
+      const double a4 = fma(-vt2, du[0], du[1 + T2]);
+      const double ach = 0.5 * (fma(un, du[0], -du[1 + D]) * rc);
+      const double ph = 0.5 * phi;
+      const double a1 = ph + ach, a5 = ph - ach;
+      double l1 = fabs(un - c), l5 = fabs(un + c);
+      const double l2 = fabs(un);
+      const double delta = a.hdelta * c;
+      if (l1 < delta) l1 = (l1 * l1 + delta * delta) / (2.0 * delta);
+      if (l5 < delta) l5 = (l5 * l5 + delta * delta) / (2.0 * delta);
+      const double A1 = l1 * a1, A2 = l2 * a2, A3 = l2 * a3, A4 = l2 * a4, A5 = l5 * a5;
+      const double S = A1 + A5;
+      const double d0 = S + A2;
+      const double cD = c * (A5 - A1);
+      double diss[5];
+      diss[0] = d0;
+      diss[1 + D] = fma(d0, un, cD);
+      diss[1 + T1] = fma(d0, vt1, A3);
+      diss[1 + T2] = fma(d0, vt2, A4);
+      diss[4] = fma(S, H, fma(cD, un, fma(A2, q2h, fma(A3, vt1, A4 * vt2))));
+#pragma unroll
+      for (int v = 0; v < 5; ++v) rec[v * NI * W + o] = 0.5 * (fL[v] + fR[v] - diss[v]);
+    }
+    if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(a.status, ST_NONPHYS);
+    if (MODE == 1 && __any_sync(0xffffffffu, range_bad) && (tid & 31) == 0) atomicOr(a.status, ST_DF_RANGE);
+  }
+  __syncthreads();
+
+  // ---- E: conservative difference + viscous divergence + epilogue ----------------
+  {
+    const double rdx = 1.0 / a.g.h[D];
+    const double r12 = 1.0 / (12.0 * a.g.h[D]);
+    const double* F = sm + PL::OFF_R;
+    const double* fvs = sm + PL::OFF_FV;
+    for (int item = tid; item < TP * W; item += PL::THREADS) {
+      int pp, line;
+      tile_split<D, W>(item, TP, pp, line);
+      if (s0 + pp >= nD || a0 + line >= na) continue;
+      double cv[5];
+      const int op = tile_idx<D, W>(pp + 1, line, NI), om = tile_idx<D, W>(pp, line, NI);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) cv[v] = (F[v * NI * W + om] - F[v * NI * W + op]) * rdx;
+      if (a.fv != nullptr) {
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          const double* fc = fvs + cc * NP * W;
+          const double d1 = fc[tile_idx<D, W>(pp + 4, line, NP)] - fc[tile_idx<D, W>(pp + 2, line, NP)];
+          const double d2 = fc[tile_idx<D, W>(pp + 5, line, NP)] - fc[tile_idx<D, W>(pp + 1, line, NP)];
+          cv[1 + cc] = fma(fma(8.0, d1, -d2), r12, cv[1 + cc]);
+        }
+      }
+      const long long p = flat(s0 + pp, a0 + line);
+      dir_epilogue(a, p, cv);
+    }
+  }
+}
+
+}  // namespace ns3d

@@ -1,0 +1,91 @@
+// Per-point bodies of the primitive-variable and viscous-flux passes (FP64),
+// shared by the standalone kernels (k_pointwise.cu) and the batched / persistent
+// ensemble kernels (ns3d_batch.cu).
+#pragma once
+
+#include <math.h>
+
+#include "ns3d_internal.cuh"
+
+namespace ns3d {
+
+// Global load through the read-only cache (NC) or a plain coherent load.
+template <bool NC>
+__device__ __forceinline__ double ldx(const double* p) {
+  if (NC) return __ldg(p);
+  return *p;
+}
+
+// Primitive variables of point p (Sec. 2.1 equation of state): u, v, w, p,
+// T = gamma p / rho, H = (e + p)/rho, sqrt(rho).  Returns 1 if non-physical.
+__device__ __forceinline__ int prim_point(const double* __restrict__ u, double* __restrict__ pm, long long N,
+                                          long long p, double gamma) {
+  const double rho = u[p], mx = u[N + p], my = u[2 * N + p], mz = u[3 * N + p], e = u[4 * N + p];
+  const double ri = 1.0 / rho;
+  const double vx = mx * ri, vy = my * ri, vz = mz * ri;
+  const double ke = 0.5 * (mx * vx + my * vy + mz * vz);
+  const double pr = (gamma - 1.0) * (e - ke);
+  pm[PM_U * N + p] = vx;
+  pm[PM_V * N + p] = vy;
+  pm[PM_W * N + p] = vz;
+  pm[PM_P * N + p] = pr;
+  pm[PM_T * N + p] = gamma * pr * ri;
+  pm[PM_H * N + p] = (e + pr) * ri;
+  pm[PM_SR * N + p] = sqrt(rho);
+  return !(rho > 0.0) | !(pr > 0.0) | !isfinite(e) | !isfinite(mx + my + mz);
+}
+
+__device__ __forceinline__ long long flat3(int i, int j, int k, int nx, int ny) {
+  return ((long long)k * ny + j) * nx + i;
+}
+
+// 4th-order central first derivative, difference form, times 1/(12 h).
+__device__ __forceinline__ double d4(double qm2, double qm1, double qp1, double qp2, double r12h) {
+  return fma(8.0, qp1 - qm1, -(qp2 - qm2)) * r12h;
+}
+
+// Gradients of (u, v, w, T) at point p, then the three viscous flux vectors
+// f^v, g^v, h^v (Sec. 2.1 stresses with the symmetric strain rate, heat flux
+// q = -kappa grad T), written to fv[(4 d + c) N + p].
+template <bool NC = true>
+__device__ __forceinline__ void visc_point(const double* __restrict__ pm, double* __restrict__ fv, int nx, int ny,
+                                           int nz, long long p, const double r12[3], double mu, double kappa) {
+  const long long N = (long long)nx * ny * nz;
+  const int i = (int)(p % nx);
+  const int j = (int)((p / nx) % ny);
+  const int k = (int)(p / ((long long)nx * ny));
+  double G[4][3];
+  const int n3[3] = {nx, ny, nz};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    long long nb[4];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      const int off = (o < 2) ? (o - 2) : (o - 1);  // -2, -1, +1, +2
+      int c[3] = {i, j, k};
+      c[d] = wrap_idx(c[d] + off, n3[d]);
+      nb[o] = flat3(c[0], c[1], c[2], nx, ny);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int plane = (q < 3) ? q : PM_T;
+      const double* A = pm + (long long)plane * N;
+      G[q][d] = d4(ldx<NC>(A + nb[0]), ldx<NC>(A + nb[1]), ldx<NC>(A + nb[2]), ldx<NC>(A + nb[3]), r12[d]);
+    }
+  }
+  const double vel[3] = {pm[PM_U * N + p], pm[PM_V * N + p], pm[PM_W * N + p]};
+  const double tdiv = (2.0 / 3.0) * (G[0][0] + G[1][1] + G[2][2]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double tau[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) tau[m] = (m == d) ? mu * fma(2.0, G[d][d], -tdiv) : mu * (G[m][d] + G[d][m]);
+    const double en = fma(vel[0], tau[0], fma(vel[1], tau[1], fma(vel[2], tau[2], kappa * G[3][d])));
+    fv[(long long)(4 * d + 0) * N + p] = tau[0];
+    fv[(long long)(4 * d + 1) * N + p] = tau[1];
+    fv[(long long)(4 * d + 2) * N + p] = tau[2];
+    fv[(long long)(4 * d + 3) * N + p] = en;
+  }
+}
+
+}  // namespace ns3d

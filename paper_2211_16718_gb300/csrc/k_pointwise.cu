@@ -8,6 +8,7 @@
 #include <math.h>
 
 #include "df.cuh"
+#include "k_point_impl.cuh"
 #include "ns3d_internal.cuh"
 
 namespace ns3d {
@@ -22,80 +23,23 @@ int grid_for(long long n, int threads) {
   return (int)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
-// Primitive variables of one point: u, v, w, p, T = gamma p / rho, H = (e + p)/rho, sqrt(rho).
+// Primitive variables of every point (body: prim_point).
 __global__ void __launch_bounds__(PW_THREADS) k_prim(const double* __restrict__ u, double* __restrict__ pm,
                                                      long long N, double gamma, int* __restrict__ status) {
   int bad = 0;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-    const double rho = u[p], mx = u[N + p], my = u[2 * N + p], mz = u[3 * N + p], e = u[4 * N + p];
-    const double ri = 1.0 / rho;
-    const double vx = mx * ri, vy = my * ri, vz = mz * ri;
-    const double ke = 0.5 * (mx * vx + my * vy + mz * vz);
-    const double pr = (gamma - 1.0) * (e - ke);
-    pm[PM_U * N + p] = vx;
-    pm[PM_V * N + p] = vy;
-    pm[PM_W * N + p] = vz;
-    pm[PM_P * N + p] = pr;
-    pm[PM_T * N + p] = gamma * pr * ri;
-    pm[PM_H * N + p] = (e + pr) * ri;
-    pm[PM_SR * N + p] = sqrt(rho);
-    bad |= !(rho > 0.0) | !(pr > 0.0) | !isfinite(e) | !isfinite(mx + my + mz);
-  }
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x)
+    bad |= prim_point(u, pm, N, p, gamma);
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONPHYS);
 }
 
-__device__ __forceinline__ long long flat3(int i, int j, int k, int nx, int ny) {
-  return ((long long)k * ny + j) * nx + i;
-}
-
-// 4th-order central first derivative, difference form, times 1/(12 h).
-__device__ __forceinline__ double d4(double qm2, double qm1, double qp1, double qp2, double r12h) {
-  return fma(8.0, qp1 - qm1, -(qp2 - qm2)) * r12h;
-}
-
-// Gradients of (u, v, w, T) at every point, then the three viscous flux vectors.
+// Gradients of (u, v, w, T) at every point, then the three viscous flux vectors (body: visc_point).
 __global__ void __launch_bounds__(PW_THREADS) k_visc(const double* __restrict__ pm, double* __restrict__ fv,
                                                      int nx, int ny, int nz, double r12hx, double r12hy,
                                                      double r12hz, double mu, double kappa) {
   const long long N = (long long)nx * ny * nz;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(p % nx);
-    const int j = (int)((p / nx) % ny);
-    const int k = (int)(p / ((long long)nx * ny));
-    double G[4][3];
-    const int n3[3] = {nx, ny, nz};
-    const double r12[3] = {r12hx, r12hy, r12hz};
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      long long nb[4];
-#pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        const int off = (o < 2) ? (o - 2) : (o - 1);  // -2, -1, +1, +2
-        int c[3] = {i, j, k};
-        c[d] = wrap_idx(c[d] + off, n3[d]);
-        nb[o] = flat3(c[0], c[1], c[2], nx, ny);
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int plane = (q < 3) ? q : PM_T;
-        const double* A = pm + (long long)plane * N;
-        G[q][d] = d4(__ldg(A + nb[0]), __ldg(A + nb[1]), __ldg(A + nb[2]), __ldg(A + nb[3]), r12[d]);
-      }
-    }
-    const double vel[3] = {pm[PM_U * N + p], pm[PM_V * N + p], pm[PM_W * N + p]};
-    const double tdiv = (2.0 / 3.0) * (G[0][0] + G[1][1] + G[2][2]);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      double tau[3];
-#pragma unroll
-      for (int m = 0; m < 3; ++m) tau[m] = (m == d) ? mu * fma(2.0, G[d][d], -tdiv) : mu * (G[m][d] + G[d][m]);
-      const double en = fma(vel[0], tau[0], fma(vel[1], tau[1], fma(vel[2], tau[2], kappa * G[3][d])));
-      fv[(long long)(4 * d + 0) * N + p] = tau[0];
-      fv[(long long)(4 * d + 1) * N + p] = tau[1];
-      fv[(long long)(4 * d + 2) * N + p] = tau[2];
-      fv[(long long)(4 * d + 3) * N + p] = en;
-    }
-  }
+  const double r12[3] = {r12hx, r12hy, r12hz};
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x)
+    visc_point(pm, fv, nx, ny, nz, p, r12, mu, kappa);
 }
 
 // ---- FP32-bulk variants: same formulas in FP32, results widened to FP64 -----------

@@ -35,6 +35,7 @@ struct ns3d_ctx {
   double* uhost_dev = nullptr; // device state for ns3d_step_host (lazy)
   double* stats_host = nullptr;// pinned [NS3D_STATS_NDOUBLE]
   int nstat_blocks = 0;
+  int variant = 0;             // tile-shape variant of the direction passes
   char err[512] = {0};
   // timing
   bool timing = false;
@@ -113,6 +114,7 @@ DirArgs base_args(ns3d_ctx* c, const double* u) {
   a.hdelta = c->p.harten_delta;
   a.status = c->status;
   a.mode = (c->p.precision == NS3D_FP64_STRICT) ? 0 : (c->p.precision == NS3D_FP32_BULK) ? 2 : 1;
+  a.variant = c->variant;
   const double c133 = 13.0 / 3.0, eps4 = 4.0 * c->p.weno_eps;
   a.c133_hi = (float)c133;
   a.c133_lo = (float)(c133 - (double)a.c133_hi);
@@ -477,6 +479,12 @@ int ns3d_timing_read(ns3d_ctx* c, double* ms_out, long long* launches_out, int n
     if (ms_out) ms_out[k] = c->ms[k];
     if (launches_out) launches_out[k] = c->launches[k];
   }
+  return NS3D_OK;
+}
+
+int ns3d_set_variant(ns3d_ctx* c, int variant) {
+  if (!c || variant < 0 || variant >= DIR_VARIANTS) return NS3D_EINVAL;
+  c->variant = variant;
   return NS3D_OK;
 }
 

@@ -1,0 +1,735 @@
+// Batched ensembles of independent grids of uneven sizes (e.g. many turbulence
+// realisations), advanced together.  Three schedules of the same arithmetic
+// (bitwise identical results):
+//   SEQUENTIAL  every instance with its own launches (5 per RK stage per instance);
+//   GRAPH       one batched launch per phase for all instances, over a flattened
+//               (instance, tile) work list, the whole multi-step loop captured in
+//               one CUDA graph and replayed with a single graph launch;
+//   PERSISTENT  one cooperative kernel for all steps, stages, phases and
+//               instances; phases are separated by grid-wide barriers
+//               (cooperative groups), so co-residency of all CTAs is guaranteed by
+//               the cooperative launch and there is no hand-written spin-wait.
+// The tile shape of the direction passes is chosen by ns3d_batch_autotune, which
+// times the candidate shapes on the actual ensemble and caches the choice in a
+// JSON-lines file keyed by device and ensemble.
+#include <cooperative_groups.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "k_dir_impl.cuh"
+#include "k_point_impl.cuh"
+#include "ns3d_internal.cuh"
+
+namespace cg = cooperative_groups;
+using namespace ns3d;
+
+namespace {
+
+constexpr int MAX_STAGES = 4;
+constexpr int BT = 256;  // threads of the pointwise batched kernels
+
+struct Inst {
+  Grid g;
+  double gamma, mu, kappa;
+  double r12[3];
+  const double* uin[MAX_STAGES];  // stage input states
+  double* pm;
+  double* fv;                     // nullptr if inviscid
+  DirArgs dir[MAX_STAGES][3];
+  int ntile[3][2];                // tiles along the pencil, along the lines (per direction)
+};
+
+struct BatchView {
+  int count, nstages;
+  const Inst* inst;
+  const long long* pt_off;    // [count + 1] prefix sums of points
+  const long long* tile_off;  // [3][count + 1] prefix sums of tiles per direction
+  int* status;
+};
+
+// Largest i with off[i] <= x (off[0] = 0 <= x < off[count]).
+__device__ __forceinline__ int find_inst(const long long* off, int count, long long x) {
+  int lo = 0, hi = count;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void phase_prim(const BatchView& b, int s, long long t0, long long stride, int& bad) {
+  const long long tot = b.pt_off[b.count];
+  for (long long x = t0; x < tot; x += stride) {
+    const int i = find_inst(b.pt_off, b.count, x);
+    const Inst& in = b.inst[i];
+    bad |= prim_point(in.uin[s], in.pm, in.g.N, x - b.pt_off[i], in.gamma);
+  }
+}
+
+template <bool NC>
+__device__ __forceinline__ void phase_visc(const BatchView& b, long long t0, long long stride) {
+  const long long tot = b.pt_off[b.count];
+  for (long long x = t0; x < tot; x += stride) {
+    const int i = find_inst(b.pt_off, b.count, x);
+    const Inst& in = b.inst[i];
+    if (in.fv == nullptr) continue;
+    visc_point<NC>(in.pm, in.fv, in.g.n[0], in.g.n[1], in.g.n[2], x - b.pt_off[i], in.r12, in.mu, in.kappa);
+  }
+}
+
+template <int D, int MODE, int TP, int W, bool NC>
+__device__ __forceinline__ void phase_dir(const BatchView& b, int s, double* sm, long long t0, long long stride) {
+  const long long* off = b.tile_off + D * (b.count + 1);
+  const long long tot = off[b.count];
+  for (long long t = t0; t < tot; t += stride) {
+    const int i = find_inst(off, b.count, t);
+    const Inst& in = b.inst[i];
+    const long long lt = t - off[i];
+    const int ntx = in.ntile[D][0], nty = in.ntile[D][1];
+    const int tx = (int)(lt % ntx);
+    const long long r = lt / ntx;
+    const int ty = (int)(r % nty);
+    const int tz = (int)(r / nty);
+    dir_tile<D, MODE, TP, W, NC>(in.dir[s][D], sm, tx, ty, tz);
+    __syncthreads();  // the next tile reuses the shared memory
+  }
+}
+
+// ---- batched kernels (one launch per phase for all instances) ------------------------
+__global__ void __launch_bounds__(BT) kb_prim(BatchView b, int s) {
+  int bad = 0;
+  phase_prim(b, s, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x, bad);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(b.status, ST_NONPHYS);
+}
+
+__global__ void __launch_bounds__(BT) kb_visc(BatchView b) {
+  phase_visc<true>(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+}
+
+template <int D, int MODE, int TP, int W>
+__global__ void __launch_bounds__(Plan<MODE, TP, W>::THREADS, MIN_CTAS_PER_SM) kb_dir(BatchView b, int s) {
+  extern __shared__ double sm[];
+  phase_dir<D, MODE, TP, W, true>(b, s, sm, blockIdx.x, gridDim.x);
+}
+
+// ---- persistent kernel: every step, stage, phase and instance in one launch ---------
+template <int MODE, int TP, int W>
+__global__ void __launch_bounds__(Plan<MODE, TP, W>::THREADS, MIN_CTAS_PER_SM) kb_persistent(BatchView b,
+                                                                                           int nsteps) {
+  extern __shared__ double sm[];
+  cg::grid_group grid = cg::this_grid();
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  int bad = 0;
+  for (int step = 0; step < nsteps; ++step) {
+    for (int s = 0; s < b.nstages; ++s) {
+      phase_prim(b, s, t0, stride, bad);
+      grid.sync();
+      phase_visc<false>(b, t0, stride);
+      grid.sync();
+      phase_dir<0, MODE, TP, W, false>(b, s, sm, blockIdx.x, gridDim.x);
+      grid.sync();
+      phase_dir<1, MODE, TP, W, false>(b, s, sm, blockIdx.x, gridDim.x);
+      grid.sync();
+      phase_dir<2, MODE, TP, W, false>(b, s, sm, blockIdx.x, gridDim.x);
+      grid.sync();
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(b.status, ST_NONPHYS);
+}
+
+template <int MODE, int TP, int W>
+struct Kernels {
+  static cudaError_t set_attr() {
+    const int bytes = Plan<MODE, TP, W>::BYTES;
+    cudaError_t e = cudaFuncSetAttribute(kb_dir<0, MODE, TP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kb_dir<1, MODE, TP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kb_dir<2, MODE, TP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kb_persistent<MODE, TP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+  }
+  static cudaError_t dir(int d, const BatchView& v, int s, long long tiles, cudaStream_t st) {
+    const int bytes = Plan<MODE, TP, W>::BYTES, th = Plan<MODE, TP, W>::THREADS;
+    const unsigned grid = (unsigned)(tiles > 0 ? tiles : 1);
+    if (d == 0) kb_dir<0, MODE, TP, W><<<grid, th, bytes, st>>>(v, s);
+    else if (d == 1) kb_dir<1, MODE, TP, W><<<grid, th, bytes, st>>>(v, s);
+    else kb_dir<2, MODE, TP, W><<<grid, th, bytes, st>>>(v, s);
+    return cudaGetLastError();
+  }
+  static cudaError_t persistent(const BatchView& v, int nsteps, int ctas_per_sm, int sms, cudaStream_t st) {
+    const int bytes = Plan<MODE, TP, W>::BYTES, th = Plan<MODE, TP, W>::THREADS;
+    BatchView vv = v;
+    int ns = nsteps;
+    void* args[] = {&vv, &ns};
+    return cudaLaunchCooperativeKernel((const void*)kb_persistent<MODE, TP, W>, dim3(ctas_per_sm * sms), dim3(th),
+                                       args, bytes, st);
+  }
+  static int max_ctas_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kb_persistent<MODE, TP, W>, Plan<MODE, TP, W>::THREADS,
+                                                      Plan<MODE, TP, W>::BYTES) != cudaSuccess)
+      return 0;
+    return n;
+  }
+};
+
+// Dispatch on (mode, variant) to the template instantiation.
+template <typename F>
+cudaError_t with_kernels(int mode, int variant, F&& f) {
+  if (mode == 0) return f(Kernels<0, 32, 4>());
+  if (variant == 1) return f(Kernels<1, 16, 4>());
+  if (variant == 2) return f(Kernels<1, 40, 2>());
+  return f(Kernels<1, 24, 4>());
+}
+
+std::mutex g_attr_mutex;
+bool g_attr_done[64] = {false};
+
+cudaError_t prepare_batch_kernels() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(g_attr_mutex);
+  if (dev >= 0 && dev < 64 && g_attr_done[dev]) return cudaSuccess;
+  cudaError_t e = Kernels<0, 32, 4>::set_attr();
+  if (e == cudaSuccess) e = Kernels<1, 24, 4>::set_attr();
+  if (e == cudaSuccess) e = Kernels<1, 16, 4>::set_attr();
+  if (e == cudaSuccess) e = Kernels<1, 40, 2>::set_attr();
+  if (e == cudaSuccess) e = prepare_dir_kernels();
+  if (e == cudaSuccess && dev >= 0 && dev < 64) g_attr_done[dev] = true;
+  return e;
+}
+
+}  // namespace
+
+struct ns3d_batch {
+  int count = 0;
+  std::vector<ns3d_params> p;
+  cudaStream_t stream = nullptr;      // caller's stream: every launch runs here
+  cudaStream_t cap_stream = nullptr;  // private stream that graph captures record on
+  int mode = 1, variant = 0, nstages = 4, sms = 0;
+  std::vector<Inst> inst;
+  std::vector<double*> bufs;  // per-instance scratch allocations
+  std::vector<double*> u;
+  std::vector<double> dt;
+  std::vector<long long> pt_off, tile_off;
+  Inst* d_inst = nullptr;
+  long long* d_pt_off = nullptr;
+  long long* d_tile_off = nullptr;
+  int* d_status = nullptr;
+  double* partials = nullptr;
+  int nstat_blocks = 0;
+  bool ready = false;
+  cudaGraphExec_t gexec = nullptr;
+  int g_nsteps = -1;
+  cudaGraphExec_t pexec = nullptr;
+  int p_nsteps = -1;
+  int persistent_graph = -1;  // 1: captured in a graph, 0: direct cooperative launch, -1: not yet
+  int pers_ctas = 0;
+  char err[256] = {0};
+};
+
+namespace {
+
+int berr(ns3d_batch* b, int code, const char* msg) {
+  if (b) snprintf(b->err, sizeof(b->err), "%s", msg);
+  return code;
+}
+
+void drop_graphs(ns3d_batch* b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->pexec) cudaGraphExecDestroy(b->pexec);
+  b->gexec = nullptr;
+  b->pexec = nullptr;
+  b->g_nsteps = b->p_nsteps = -1;
+}
+
+BatchView view_of(const ns3d_batch* b) {
+  BatchView v;
+  v.count = b->count;
+  v.nstages = b->nstages;
+  v.inst = b->d_inst;
+  v.pt_off = b->d_pt_off;
+  v.tile_off = b->d_tile_off;
+  v.status = b->d_status;
+  return v;
+}
+
+// Fill the per-instance launch descriptors for the current states, dt and variant
+// and upload them.
+int rebuild(ns3d_batch* b) {
+  if (b->u.empty() || b->dt.empty()) return NS3D_OK;
+  int tp = 0, w = 0;
+  dir_tile_shape(b->mode, b->variant, &tp, &w);
+  b->tile_off.assign(3 * (b->count + 1), 0);
+  for (int i = 0; i < b->count; ++i) {
+    Inst& in = b->inst[i];
+    double* u = b->u[i];
+    double* ua = b->bufs[6 * i + 2];
+    double* ub = b->bufs[6 * i + 3];
+    double* acc = b->bufs[6 * i + 4];
+    double* k = b->bufs[6 * i + 5];
+    const double dt = b->dt[i];
+    const double* uin4[4] = {u, ua, ub, ua};
+    double* out4[4] = {ua, ub, ua, u};
+    const int epi4[4] = {EPI_RK4_FIRST, EPI_RK4_MID, EPI_RK4_MID, EPI_RK4_LAST};
+    const double coef4[4] = {0.5 * dt, 0.5 * dt, dt, dt / 6.0};
+    const double* uin3[3] = {u, ua, ub};
+    double* out3[3] = {ua, ub, u};
+    const int epi3[3] = {EPI_SSP_1, EPI_SSP_2, EPI_SSP_3};
+    for (int s = 0; s < b->nstages; ++s) {
+      in.uin[s] = (b->nstages == 4) ? uin4[s] : uin3[s];
+      for (int d = 0; d < 3; ++d) {
+        DirArgs& a = in.dir[s][d];
+        memset(&a, 0, sizeof(a));
+        a.g = in.g;
+        a.u = in.uin[s];
+        a.pm = in.pm;
+        a.fv = in.fv;
+        a.k = k;
+        a.acc = acc;
+        a.gamma = in.gamma;
+        a.eps4 = 4.0 * b->p[i].weno_eps;
+        a.hdelta = b->p[i].harten_delta;
+        a.status = b->d_status;
+        a.mode = b->mode;
+        a.variant = b->variant;
+        const double c133 = 13.0 / 3.0, eps4 = 4.0 * b->p[i].weno_eps, sixth = 1.0 / 6.0;
+        a.c133_hi = (float)c133;
+        a.c133_lo = (float)(c133 - (double)a.c133_hi);
+        a.eps4_hi = (float)eps4;
+        a.eps4_lo = (float)(eps4 - (double)a.eps4_hi);
+        a.sixth_hi = (float)sixth;
+        a.sixth_lo = (float)(sixth - (double)a.sixth_hi);
+        if (d == 0) {
+          a.epi = EPI_ACC_WRITE;
+        } else if (d == 1) {
+          a.epi = EPI_ACC_ADD;
+        } else {
+          a.epi = (b->nstages == 4) ? epi4[s] : epi3[s];
+          a.out = (b->nstages == 4) ? out4[s] : out3[s];
+          a.un = u;
+          a.a = (b->nstages == 4) ? coef4[s] : dt;
+        }
+      }
+    }
+    for (int d = 0; d < 3; ++d) {
+      const int ax = (d == 0) ? 1 : 0, bx = (d == 2) ? 1 : 2;
+      in.ntile[d][0] = (in.g.n[d] + tp - 1) / tp;
+      in.ntile[d][1] = (in.g.n[ax] + w - 1) / w;
+      const long long tiles = (long long)in.ntile[d][0] * in.ntile[d][1] * in.g.n[bx];
+      b->tile_off[d * (b->count + 1) + i + 1] = b->tile_off[d * (b->count + 1) + i] + tiles;
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(Inst) * b->count, cudaMemcpyHostToDevice,
+                                  b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_tile_off, b->tile_off.data(), sizeof(long long) * b->tile_off.size(),
+                        cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return berr(b, NS3D_ECUDA, cudaGetErrorString(e));
+  drop_graphs(b);
+  b->ready = true;
+  return NS3D_OK;
+}
+
+// One step of every instance with per-instance launches.
+int step_sequential(ns3d_batch* b) {
+  for (int i = 0; i < b->count; ++i) {
+    const Inst& in = b->inst[i];
+    for (int s = 0; s < b->nstages; ++s) {
+      cudaError_t e = launch_prim(in.g, in.uin[s], in.pm, in.gamma, b->d_status, b->stream);
+      if (e == cudaSuccess && in.fv) e = launch_visc(in.g, in.pm, in.fv, in.mu, in.kappa, b->stream);
+      for (int d = 0; d < 3 && e == cudaSuccess; ++d) e = launch_dir(d, in.dir[s][d], b->stream);
+      if (e != cudaSuccess) return berr(b, NS3D_ECUDA, cudaGetErrorString(e));
+    }
+  }
+  return NS3D_OK;
+}
+
+// Enqueue nsteps steps of batched launches on stream st (graph capture body).
+cudaError_t enqueue_batched(ns3d_batch* b, int nsteps, cudaStream_t st) {
+  const BatchView v = view_of(b);
+  const long long pts = b->pt_off[b->count];
+  long long blocks = (pts + BT - 1) / BT;
+  const unsigned pgrid = (unsigned)(blocks < 152LL * 16 ? (blocks > 0 ? blocks : 1) : 152LL * 16);
+  bool visc = false;
+  for (const Inst& in : b->inst) visc |= (in.fv != nullptr);
+  cudaError_t e = cudaSuccess;
+  for (int step = 0; step < nsteps && e == cudaSuccess; ++step) {
+    for (int s = 0; s < b->nstages && e == cudaSuccess; ++s) {
+      kb_prim<<<pgrid, BT, 0, st>>>(v, s);
+      e = cudaGetLastError();
+      if (e == cudaSuccess && visc) {
+        kb_visc<<<pgrid, BT, 0, st>>>(v);
+        e = cudaGetLastError();
+      }
+      for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
+        const long long tiles = b->tile_off[d * (b->count + 1) + b->count];
+        e = with_kernels(b->mode, b->variant, [&](auto K) { return decltype(K)::dir(d, v, s, tiles, st); });
+      }
+    }
+  }
+  return e;
+}
+
+int step_graph(ns3d_batch* b, int nsteps) {
+  if (!b->gexec || b->g_nsteps != nsteps) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return berr(b, NS3D_ECUDA, cudaGetErrorString(e));
+    cudaError_t eq = enqueue_batched(b, nsteps, b->cap_stream);
+    e = cudaStreamEndCapture(b->cap_stream, &g);
+    if (eq != cudaSuccess || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return berr(b, NS3D_ECUDA, cudaGetErrorString(eq != cudaSuccess ? eq : e));
+    }
+    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return berr(b, NS3D_ECUDA, cudaGetErrorString(e));
+    b->g_nsteps = nsteps;
+  }
+  cudaError_t e = cudaGraphLaunch(b->gexec, b->stream);
+  if (e != cudaSuccess) return berr(b, NS3D_ECUDA, cudaGetErrorString(e));
+  return NS3D_OK;
+}
+
+int step_persistent(ns3d_batch* b, int nsteps) {
+  if (b->pers_ctas <= 0) {
+    if (b->mode == 0) b->pers_ctas = Kernels<0, 32, 4>::max_ctas_per_sm();
+    else if (b->variant == 1) b->pers_ctas = Kernels<1, 16, 4>::max_ctas_per_sm();
+    else if (b->variant == 2) b->pers_ctas = Kernels<1, 40, 2>::max_ctas_per_sm();
+    else b->pers_ctas = Kernels<1, 24, 4>::max_ctas_per_sm();
+    if (b->pers_ctas <= 0) return berr(b, NS3D_ECUDA, "persistent kernel does not fit on an SM");
+  }
+  const BatchView v = view_of(b);
+  // Try once to capture the cooperative launch in a graph; fall back to a direct launch.
+  if (b->persistent_graph != 0 && (!b->pexec || b->p_nsteps != nsteps)) {
+    if (b->pexec) cudaGraphExecDestroy(b->pexec);
+    b->pexec = nullptr;
+    cudaGraph_t g = nullptr;
+    bool ok = (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess);
+    cudaError_t el = cudaSuccess;
+    if (ok) el = with_kernels(b->mode, b->variant, [&](auto K) {
+      return decltype(K)::persistent(v, nsteps, b->pers_ctas, b->sms, b->cap_stream);
+    });
+    cudaError_t ee = ok ? cudaStreamEndCapture(b->cap_stream, &g) : cudaErrorUnknown;
+    ok = ok && el == cudaSuccess && ee == cudaSuccess && g != nullptr &&
+         cudaGraphInstantiate(&b->pexec, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();  // clear any capture error
+    b->persistent_graph = ok ? 1 : 0;
+    if (ok) b->p_nsteps = nsteps;
+  }
+  cudaError_t e;
+  if (b->persistent_graph == 1) {
+    e = cudaGraphLaunch(b->pexec, b->stream);
+  } else {
+    e = with_kernels(b->mode, b->variant, [&](auto K) {
+      return decltype(K)::persistent(v, nsteps, b->pers_ctas, b->sms, b->stream);
+    });
+  }
+  if (e != cudaSuccess) return berr(b, NS3D_ECUDA, cudaGetErrorString(e));
+  return NS3D_OK;
+}
+
+std::string device_name() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "unknown";
+  return prop.name;
+}
+
+std::string tune_key(const ns3d_batch* b) {
+  std::string k = device_name() + "|batch|mode" + std::to_string(b->mode) + "|stages" + std::to_string(b->nstages) +
+                  "|";
+  for (int i = 0; i < b->count; ++i) {
+    k += std::to_string(b->p[i].nx) + "x" + std::to_string(b->p[i].ny) + "x" + std::to_string(b->p[i].nz);
+    k += (b->p[i].mu_eff > 0.0) ? "v" : "e";
+    if (i + 1 < b->count) k += ",";
+  }
+  return k;
+}
+
+// Look the key up in a JSON-lines cache ({"key": "...", "variant": N, ...} per line).
+int cache_lookup(const char* path, const std::string& key) {
+  if (!path) return -1;
+  FILE* f = fopen(path, "r");
+  if (!f) return -1;
+  const std::string needle = "\"key\": \"" + key + "\"";
+  std::vector<char> line(1 << 16);
+  int found = -1;
+  while (fgets(line.data(), (int)line.size(), f)) {
+    if (strstr(line.data(), needle.c_str())) {
+      const char* v = strstr(line.data(), "\"variant\": ");
+      if (v) found = atoi(v + 11);
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ns3d_batch_init(const ns3d_params* params, int count, void* cuda_stream, ns3d_batch** out) {
+  if (!out || !params || count < 1 || count > 4096) return NS3D_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    const ns3d_params& p = params[i];
+    if (p.nx < 1 || p.ny < 1 || p.nz < 1 || (long long)p.nx * p.ny * p.nz > (1LL << 31)) return NS3D_EINVAL;
+    if (p.nx > 65535 * 2 || p.ny > 65535 || p.nz > 65535) return NS3D_EINVAL;
+    if (!(p.lx > 0) || !(p.ly > 0) || !(p.lz > 0) || !(p.gamma > 1.0) || !(p.mu_eff >= 0.0)) return NS3D_EINVAL;
+    if (p.mu_eff > 0.0 && !(p.prandtl > 0.0)) return NS3D_EINVAL;
+    if (!(p.weno_eps >= 1e-15) || p.weno_p != 2 || !(p.harten_delta >= 0.0)) return NS3D_EINVAL;
+    if (p.precision != params[0].precision || p.rk != params[0].rk) return NS3D_EINVAL;
+  }
+  if (params[0].precision != NS3D_FP64 && params[0].precision != NS3D_FP64_STRICT) return NS3D_EINVAL;
+  if (params[0].rk != NS3D_RK4 && params[0].rk != NS3D_SSPRK3) return NS3D_EINVAL;
+  ns3d_batch* b = new ns3d_batch();
+  b->count = count;
+  b->p.assign(params, params + count);
+  b->stream = (cudaStream_t)cuda_stream;
+  b->mode = (params[0].precision == NS3D_FP64_STRICT) ? 0 : 1;
+  b->nstages = (params[0].rk == NS3D_RK4) ? 4 : 3;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (prepare_batch_kernels() != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return NS3D_ECUDA;
+  }
+  b->inst.resize(count);
+  b->pt_off.assign(count + 1, 0);
+  long long maxN = 0;
+  for (int i = 0; i < count; ++i) {
+    const ns3d_params& p = params[i];
+    Inst& in = b->inst[i];
+    memset(&in, 0, sizeof(in));
+    in.g.n[0] = p.nx;
+    in.g.n[1] = p.ny;
+    in.g.n[2] = p.nz;
+    in.g.N = (long long)p.nx * p.ny * p.nz;
+    in.g.h[0] = p.lx / p.nx;
+    in.g.h[1] = p.ly / p.ny;
+    in.g.h[2] = p.lz / p.nz;
+    in.gamma = p.gamma;
+    in.mu = p.mu_eff;
+    in.kappa = (p.mu_eff > 0.0) ? p.mu_eff / ((p.gamma - 1.0) * p.prandtl) : 0.0;
+    for (int d = 0; d < 3; ++d) in.r12[d] = 1.0 / (12.0 * in.g.h[d]);
+    b->pt_off[i + 1] = b->pt_off[i] + in.g.N;
+    if (in.g.N > maxN) maxN = in.g.N;
+    // scratch: primitives, viscous fluxes, two stage states, RK accumulator, RHS accumulator
+    const size_t sizes[6] = {7, 12, 5, 5, 5, 5};
+    for (int a = 0; a < 6; ++a) {
+      double* ptr = nullptr;
+      if (a == 1 && p.mu_eff == 0.0) {
+        b->bufs.push_back(nullptr);
+        continue;
+      }
+      if (cudaMalloc(&ptr, sizeof(double) * sizes[a] * (size_t)in.g.N) != cudaSuccess) {
+        cudaGetLastError();
+        ns3d_batch_free(b);
+        return NS3D_ENOMEM;
+      }
+      b->bufs.push_back(ptr);
+    }
+    in.pm = b->bufs[6 * i + 0];
+    in.fv = b->bufs[6 * i + 1];
+  }
+  Grid gmax;
+  gmax.N = maxN;
+  b->nstat_blocks = stats_num_blocks(gmax);
+  bool ok = cudaMalloc(&b->d_inst, sizeof(Inst) * count) == cudaSuccess &&
+            cudaMalloc(&b->d_pt_off, sizeof(long long) * (count + 1)) == cudaSuccess &&
+            cudaMalloc(&b->d_tile_off, sizeof(long long) * 3 * (count + 1)) == cudaSuccess &&
+            cudaMalloc(&b->d_status, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&b->partials, sizeof(double) * 16 * (size_t)b->nstat_blocks) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    ns3d_batch_free(b);
+    return NS3D_ENOMEM;
+  }
+  cudaError_t e = cudaMemcpyAsync(b->d_pt_off, b->pt_off.data(), sizeof(long long) * (count + 1),
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    ns3d_batch_free(b);
+    return NS3D_ECUDA;
+  }
+  *out = b;
+  return NS3D_OK;
+}
+
+void ns3d_batch_free(ns3d_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  drop_graphs(b);
+  for (double* p : b->bufs) cudaFree(p);
+  cudaFree(b->d_inst);
+  cudaFree(b->d_pt_off);
+  cudaFree(b->d_tile_off);
+  cudaFree(b->d_status);
+  cudaFree(b->partials);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+}
+
+int ns3d_batch_set_states(ns3d_batch* b, double* const* u_dev) {
+  if (!b || !u_dev) return NS3D_EINVAL;
+  for (int i = 0; i < b->count; ++i)
+    if (!u_dev[i]) return berr(b, NS3D_EINVAL, "null state pointer");
+  b->u.assign(u_dev, u_dev + b->count);
+  return rebuild(b);
+}
+
+int ns3d_batch_set_dt(ns3d_batch* b, const double* dt) {
+  if (!b || !dt) return NS3D_EINVAL;
+  for (int i = 0; i < b->count; ++i)
+    if (!isfinite(dt[i])) return berr(b, NS3D_EINVAL, "dt must be finite");
+  b->dt.assign(dt, dt + b->count);
+  return rebuild(b);
+}
+
+int ns3d_batch_set_variant(ns3d_batch* b, int variant) {
+  if (!b || variant < 0 || variant >= DIR_VARIANTS) return NS3D_EINVAL;
+  if (b->mode == 0 && variant != 0) return NS3D_EINVAL;
+  b->variant = variant;
+  b->pers_ctas = 0;
+  b->persistent_graph = -1;
+  return rebuild(b);
+}
+
+int ns3d_batch_step(ns3d_batch* b, int nsteps, int schedule) {
+  if (!b || nsteps < 0) return NS3D_EINVAL;
+  if (!b->ready) return berr(b, NS3D_EINVAL, "set states and dt first");
+  if (nsteps == 0) return NS3D_OK;
+  if (schedule == NS3D_BATCH_SEQUENTIAL) {
+    for (int s = 0; s < nsteps; ++s) {
+      int rc = step_sequential(b);
+      if (rc) return rc;
+    }
+    return NS3D_OK;
+  }
+  if (schedule == NS3D_BATCH_GRAPH) return step_graph(b, nsteps);
+  if (schedule == NS3D_BATCH_PERSISTENT) return step_persistent(b, nsteps);
+  return berr(b, NS3D_EINVAL, "unknown schedule");
+}
+
+int ns3d_batch_stats(ns3d_batch* b, double* out_dev) {
+  if (!b || !out_dev) return NS3D_EINVAL;
+  if (!b->ready) return berr(b, NS3D_EINVAL, "set states and dt first");
+  for (int i = 0; i < b->count; ++i) {
+    const Inst& in = b->inst[i];
+    cudaError_t e = launch_prim(in.g, b->u[i], in.pm, in.gamma, b->d_status, b->stream);
+    if (e == cudaSuccess) e = launch_stats(in.g, b->u[i], in.pm, in.gamma, b->partials, b->stream);
+    if (e == cudaSuccess)
+      e = launch_stats_final(in.g, b->partials, stats_num_blocks(in.g), b->d_status,
+                             out_dev + (size_t)i * NS3D_STATS_NDOUBLE, b->stream);
+    if (e != cudaSuccess) return berr(b, NS3D_ECUDA, cudaGetErrorString(e));
+  }
+  return NS3D_OK;
+}
+
+int ns3d_batch_check(ns3d_batch* b) {
+  if (!b) return NS3D_EINVAL;
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return berr(b, NS3D_ECUDA, cudaGetErrorString(e));
+  if (h & ST_NONPHYS) return NS3D_ENONPHYSICAL;
+  if (h & ST_DF_RANGE) return NS3D_ERANGE;
+  return NS3D_OK;
+}
+
+int ns3d_batch_autotune(ns3d_batch* b, const char* cache_path, double* ms_out) {
+  if (!b) return NS3D_EINVAL;
+  if (!b->ready) return berr(b, NS3D_EINVAL, "set states and dt first");
+  if (b->mode == 0) return NS3D_OK;  // a single tile shape
+  const std::string key = tune_key(b);
+  const int cached = cache_lookup(cache_path, key);
+  if (cached >= 0 && cached < DIR_VARIANTS) {
+    if (ms_out)
+      for (int v = 0; v < DIR_VARIANTS; ++v) ms_out[v] = -1.0;
+    return ns3d_batch_set_variant(b, cached);
+  }
+  // time the candidates on copies of the states (the caller's states are not advanced)
+  std::vector<double*> saved = b->u, tmp(b->count, nullptr);
+  int rc = NS3D_OK;
+  for (int i = 0; i < b->count && rc == NS3D_OK; ++i) {
+    const size_t bytes = sizeof(double) * 5 * (size_t)b->inst[i].g.N;
+    if (cudaMalloc(&tmp[i], bytes) != cudaSuccess) rc = NS3D_ENOMEM;
+    else if (cudaMemcpyAsync(tmp[i], saved[i], bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
+      rc = NS3D_ECUDA;
+  }
+  double ms[DIR_VARIANTS] = {0};
+  int best = 0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  if (rc == NS3D_OK) {
+    b->u = tmp;
+    for (int v = 0; v < DIR_VARIANTS && rc == NS3D_OK; ++v) {
+      rc = ns3d_batch_set_variant(b, v);
+      if (rc == NS3D_OK) rc = ns3d_batch_step(b, 1, NS3D_BATCH_GRAPH);  // warm-up + capture
+      if (rc == NS3D_OK) {
+        cudaEventRecord(e0, b->stream);
+        rc = ns3d_batch_step(b, 1, NS3D_BATCH_GRAPH);
+        cudaEventRecord(e1, b->stream);
+        float t = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+          rc = NS3D_ECUDA;
+        ms[v] = t;
+        if (t < ms[best]) best = v;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(b->stream);
+  for (double* p : tmp) cudaFree(p);
+  b->u = saved;
+  ns3d_batch_check(b);  // the timing runs may have flagged the copies; clear the word
+  if (rc != NS3D_OK) {
+    rebuild(b);
+    return rc;
+  }
+  if (ms_out)
+    for (int v = 0; v < DIR_VARIANTS; ++v) ms_out[v] = ms[v];
+  if (cache_path) {
+    FILE* f = fopen(cache_path, "a");
+    if (f) {
+      fprintf(f, "{\"key\": \"%s\", \"variant\": %d, \"ms_per_step\": [%.4f, %.4f, %.4f]}\n", key.c_str(), best, ms[0],
+              ms[1], ms[2]);
+      fclose(f);
+    }
+  }
+  return ns3d_batch_set_variant(b, best);
+}
+
+int ns3d_batch_info(const ns3d_batch* b, int* variant, int* persistent_ctas_per_sm, int* persistent_in_graph) {
+  if (!b) return NS3D_EINVAL;
+  if (variant) *variant = b->variant;
+  if (persistent_ctas_per_sm) *persistent_ctas_per_sm = b->pers_ctas;
+  if (persistent_in_graph) *persistent_in_graph = b->persistent_graph;
+  return NS3D_OK;
+}
+
+const char* ns3d_batch_last_error(const ns3d_batch* b) { return b ? b->err : "batch is NULL"; }
+
+}  // extern "C"

@@ -52,6 +52,7 @@ struct DirArgs {
   double hdelta;     // Harten entropy-fix fraction
   int* status;
   int mode;          // 0: all FP64; 1: FP64 values, double-float weights/offsets; 2: FP32 bulk
+  int variant;       // tile-shape variant of MODE 1 (see dir_tile_shape)
   float c133_hi, c133_lo;  // 13/3 as a double-float
   float eps4_hi, eps4_lo;  // 4 * weno_eps as a double-float
   float sixth_hi, sixth_lo;  // 1/6 as a double-float
@@ -64,7 +65,9 @@ cudaError_t launch_visc(const Grid& g, const double* pm, double* fv, double mu, 
 cudaError_t launch_prim32(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s);
 cudaError_t launch_visc32(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s);
 cudaError_t prepare_dir_kernels();  // per device, before the first launch
-cudaError_t launch_dir(int d, const DirArgs& a, cudaStream_t s);  // dispatches on a.mode
+cudaError_t launch_dir(int d, const DirArgs& a, cudaStream_t s);  // dispatches on a.mode, a.variant
+void dir_tile_shape(int mode, int variant, int* tp, int* w);      // points x lines of a tile
+constexpr int DIR_VARIANTS = 3;                                   // tile variants of MODE 1
 cudaError_t prepare_dir32_kernels();
 cudaError_t launch_dir32(int d, const DirArgs& a, cudaStream_t s);  // FP32-bulk (a.mode == 2)
 int stats_num_blocks(const Grid& g);

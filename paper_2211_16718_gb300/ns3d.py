@@ -244,3 +244,101 @@ def stats_noalloc(params: CParams, u, out):
     if rc != NS3D_OK:
         raise Ns3dError(rc, lib().ns3d_strerror(rc).decode())
     return out
+
+
+# ---- ensembles of independent grids -------------------------------------------------
+NS3D_BATCH_SEQUENTIAL, NS3D_BATCH_GRAPH, NS3D_BATCH_PERSISTENT = 0, 1, 2
+SCHEDULES = {"sequential": NS3D_BATCH_SEQUENTIAL, "graph": NS3D_BATCH_GRAPH, "persistent": NS3D_BATCH_PERSISTENT}
+
+
+def _batch_fn(name, res, args):
+    fn = getattr(lib(), name)
+    fn.restype = res
+    fn.argtypes = args
+    return fn
+
+
+class Batch:
+    """An ensemble of independent grids (ns3d_batch_*): per-instance parameters, states
+    (caller-owned CUDA float64 tensors) and time steps; three schedules of the same
+    arithmetic: "sequential", "graph" (batched launches in one CUDA graph) and
+    "persistent" (one cooperative kernel for all steps)."""
+
+    def __init__(self, params: list):
+        P = ctypes.c_void_p
+        self.count = len(params)
+        arr = (CParams * self.count)(*params)
+        self.params = list(params)
+        self._b = ctypes.c_void_p()
+        rc = _batch_fn("ns3d_batch_init", ctypes.c_int, [ctypes.POINTER(CParams), ctypes.c_int, P, ctypes.POINTER(P)])(
+            arr, self.count, _stream_handle(), ctypes.byref(self._b))
+        if rc != NS3D_OK:
+            raise Ns3dError(rc, lib().ns3d_strerror(rc).decode())
+        self._states = None
+
+    def _err(self, rc):
+        if rc == NS3D_OK:
+            return
+        msg = _batch_fn("ns3d_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p])(self._b).decode()
+        if rc == NS3D_ENONPHYSICAL:
+            raise NonPhysicalError(rc, msg or "non-physical state")
+        raise Ns3dError(rc, msg or lib().ns3d_strerror(rc).decode())
+
+    def set_states(self, tensors):
+        if len(tensors) != self.count:
+            raise ValueError("one state per instance")
+        ptrs = (ctypes.c_void_p * self.count)()
+        for i, (t, p) in enumerate(zip(tensors, self.params)):
+            ptrs[i] = _dptr(t, 5 * p.nx * p.ny * p.nz).value
+        self._states = list(tensors)
+        self._err(_batch_fn("ns3d_batch_set_states", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p])(self._b, ptrs))
+
+    def set_dt(self, dts):
+        arr = (ctypes.c_double * self.count)(*[float(d) for d in dts])
+        self._err(_batch_fn("ns3d_batch_set_dt", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p])(self._b, arr))
+
+    def set_variant(self, v: int):
+        self._err(_batch_fn("ns3d_batch_set_variant", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int])(self._b, int(v)))
+
+    def step(self, nsteps: int = 1, schedule: str = "graph"):
+        self._err(_batch_fn("ns3d_batch_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int])(
+            self._b, int(nsteps), SCHEDULES[schedule]))
+
+    def stats(self):
+        import torch
+        out = torch.zeros((self.count, NS3D_STATS_NDOUBLE), dtype=torch.float64, device="cuda")
+        self._err(_batch_fn("ns3d_batch_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p])(
+            self._b, ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def check(self):
+        self._err(_batch_fn("ns3d_batch_check", ctypes.c_int, [ctypes.c_void_p])(self._b))
+
+    def autotune(self, cache_path=None):
+        ms = (ctypes.c_double * 3)()
+        path = cache_path.encode() if cache_path else None
+        self._err(_batch_fn("ns3d_batch_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_void_p])(
+            self._b, path, ms))
+        return self.info()["variant"], list(ms)
+
+    def info(self) -> dict:
+        v, c, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._err(_batch_fn("ns3d_batch_info", ctypes.c_int, [ctypes.c_void_p] * 4)(
+            self._b, ctypes.byref(v), ctypes.byref(c), ctypes.byref(g)))
+        return {"variant": v.value, "persistent_ctas_per_sm": c.value, "persistent_in_graph": g.value}
+
+    def close(self):
+        if self._b:
+            _batch_fn("ns3d_batch_free", None, [ctypes.c_void_p])(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def set_solver_variant(solver: Solver, v: int):
+    rc = _batch_fn("ns3d_set_variant", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int])(solver._ctx, int(v))
+    solver._check(rc)
