@@ -223,6 +223,46 @@ const char *ns3d_batch_last_error(const ns3d_batch *b);
 /* Tile shape of the direction passes of a single context (see ns3d_batch_set_variant). */
 int ns3d_set_variant(ns3d_ctx *ctx, int variant);
 
+/* ---- adjoint (vector-Jacobian products) -----------------------------------------
+ * Exact discrete adjoints of the operators above (the paper has none; they serve
+ * gradients of statistics of the flow with respect to its initial state), all in
+ * FP64 for NS3D_FP64 and NS3D_FP64_STRICT contexts (NS3D_FP32_BULK: NS3D_EINVAL).
+ * Derivatives follow the discretisation as written: the WENO5 weights (smooth,
+ * eps > 0), the Roe average, Harten's quadratic branch, and |lambda| with the
+ * subgradient sign(0) = 0 at its kink.  The first adjoint call of a context
+ * allocates 46*N doubles of library-owned device scratch (NS3D_ENOMEM); the
+ * trajectory calls allocate their checkpoints.  No call synchronises except
+ * ns3d_functional with value_host != NULL. */
+enum { NS3D_FUNC_KE = 0, NS3D_FUNC_ENSTROPHY = 1 };
+
+/* out_dev = J(u_dev)^T lam_dev, J = dR/du of ns3d_rhs at u_dev.  5*N doubles each;
+ * out_dev must not overlap u_dev or lam_dev. */
+int ns3d_rhs_vjp(ns3d_ctx *ctx, const double *u_dev, const double *lam_dev, double *out_dev);
+
+/* Reverse of one step of the context's integrator from the state u_dev (the state
+ * at the start of the step, unchanged): on entry ubar_dev is the adjoint of the
+ * state after the step, on return the adjoint of u_dev.  The stage states are
+ * recomputed from u_dev with the forward step's own launches. */
+int ns3d_rk_step_vjp(ns3d_ctx *ctx, const double *u_dev, double *ubar_dev, double dt);
+
+/* Functional of a state: NS3D_FUNC_KE = mean of rho |v|^2 / 2, NS3D_FUNC_ENSTROPHY =
+ * mean of rho |omega|^2 / 2 (as in ns3d_stats).  value_host (may be NULL) receives
+ * its value (synchronises); grad_dev (may be NULL; 5*N doubles, not overlapping
+ * u_dev) receives its gradient with respect to u_dev. */
+int ns3d_functional(ns3d_ctx *ctx, const double *u_dev, int which, double *value_host, double *grad_dev);
+
+/* Advance u_dev in place by nsteps steps (as ns3d_rk_step) and record the states
+ * at steps 0, every, 2*every, ... (ceil(nsteps/every) checkpoints of 5*N doubles,
+ * library-owned, kept until the next call or ns3d_free). */
+int ns3d_traj_forward(ns3d_ctx *ctx, double *u_dev, double dt, int nsteps, int every);
+
+/* Reverse sweep over the trajectory recorded by the last ns3d_traj_forward: on
+ * entry ubar_dev is the adjoint of the final state, on return the adjoint of the
+ * initial state.  Each segment of `every` steps is recomputed from its checkpoint
+ * (allocating `every` states once), then reversed step by step with
+ * ns3d_rk_step_vjp.  NS3D_EINVAL if no trajectory has been recorded. */
+int ns3d_traj_vjp(ns3d_ctx *ctx, double *ubar_dev);
+
 /* ---- measurement support (no counterpart in the paper) -------------------- */
 /* Kernel identifiers used by the timing calls. */
 enum {
@@ -233,7 +273,10 @@ enum {
   NS3D_K_DIR_Z = 4,      /* ... z, with the RK stage update fused in */
   NS3D_K_STATS = 5,      /* statistics partial reductions */
   NS3D_K_STATS_FINAL = 6,
-  NS3D_K_COUNT = 7
+  NS3D_K_ADJ_VISC = 7,   /* adjoint of the viscous terms and of the primitive variables */
+  NS3D_K_ADJ_DIR = 8,    /* adjoint of the fused direction passes (x, y, z) */
+  NS3D_K_ADJ_MISC = 9,   /* functional seeds and adjoint copies */
+  NS3D_K_COUNT = 10
 };
 
 /* on != 0: record CUDA events around every kernel launch of ctx (on its stream)

@@ -1,0 +1,764 @@
+// Hand-written adjoint (vector-Jacobian product g = J(u)^T lambda) of the
+// right-hand side of arXiv 2211.16718, Sec. 2.1-2.2, all in FP64.
+//
+// Hyperbolic part, per direction D: R_i -= (Fhat_{i+1/2} - Fhat_{i-1/2})/h, so the
+// adjoint of the interface flux is Lhat_{i+1/2} = (lambda_{i+1} - lambda_i)/h.  With
+//   Fhat = (f^L + f^R)/2 - X |Lambda| X^{-1} (u^R - u^L)/2   (Roe average of U_i, U_{i+1}),
+// the adjoint flows into the 18 reconstructions of the interface (u^L, u^R of the five
+// conserved variables with the mass flux f_0 = rho u_D folded into u_{1+D}, f^L, f^R of
+// f_1..f_4) and into the Roe-averaged state.  Each WENO5 reconstruction
+//   q = sum_k omega_k q_k,   omega_k = (c_k/b_k^2) / sum_j (c_j/b_j^2),   b_k = 4(eps + beta_k)
+// has the exact derivative dq/dq_t = sum_k omega_k dq_k/dq_t
+//   + sum_k (-2 omega_k (q_k - q)/b_k) db_k/dq_t,
+// b_k = 4 eps + (13/3) s_k^2 + v_k^2 with s_k the second difference and v_k the first-
+// derivative combination of window k.  |lambda| has the subgradient sign(0) = 0 at its
+// kink; Harten's quadratic branch is differentiated as written (Sec. 2.2).
+//
+// One CTA owns TP points along D times W lines; every interface whose stencil touches
+// one of the tile's points (TP + 5 of them per line, halo of 5 points each side) is
+// processed, and each point then gathers its contributions in a fixed order, so the
+// result is deterministic and independent of the tiling.  Phases:
+//   A  load u, primitives, point fluxes f_1..f_4, lambda                   [NP x W]
+//   C  left/right WENO5 values and weights of the 9 scalars               [9 x NI x W]
+//   D  Roe flux adjoint: adjoint of du = u^R - u^L and of the two states  [NI x W]
+//   E  WENO5 adjoints -> six stencil contributions per scalar, interface [9 x NI x W]
+//   F  gather, point-flux adjoint (f_1..f_4 of U), epilogue                [TP x W]
+//
+// Viscous part: G[q][e] = D_e W_q (W = u, v, w, T), viscous fluxes built from G and the
+// velocities at each point, R_{1+c} += D_d Fv_d[c]; D_d^T = -D_d for the periodic
+// 4th-order central difference.  Two point kernels: (1) adjoint of Fv -> adjoint of G
+// and of the velocities, (2) -sum_e D_e of the G adjoint plus the velocity adjoint ->
+// adjoint of u through u_k = m_k/rho, T = gamma (gamma - 1)(e/rho - |m|^2/(2 rho^2)).
+#include <math.h>
+
+#include "k_dir_common.cuh"
+#include "k_point_impl.cuh"
+#include "ns3d_internal.cuh"
+
+namespace ns3d {
+
+namespace {
+
+template <int TP_, int W_>
+struct AdjPlan {
+  static constexpr int TP = TP_;
+  static constexpr int W = W_;
+  static constexpr int THREADS = 256;
+  static constexpr int NP = TP + 10;  // points incl. a halo of 5 each side
+  static constexpr int NI = TP + 5;   // interfaces i+1/2, i = s0-3 .. s0+TP+1
+  static constexpr int OFF_Q = 0;                       // [9][NP*W] u_0..u_4, f_1..f_4
+  static constexpr int OFF_RI = OFF_Q + 9 * NP * W;     // [6][NP*W] sqrt(rho), u, v, w, H, p
+  static constexpr int OFF_L = OFF_RI + 6 * NP * W;     // [5][NP*W] lambda
+  static constexpr int OFF_REC = OFF_L + 5 * NP * W;    // [18][NI*W] left/right values
+  static constexpr int OFF_RD = OFF_REC + 18 * NI * W;  // [15][NI*W] adjoint of du; Roe-state adjoints a, b
+  static constexpr int OFF_WC = OFF_RD + 15 * NI * W;   // [9][6][NI*W] weights, then contributions
+  static constexpr int WORDS = OFF_WC + 54 * NI * W;
+  static constexpr int BYTES = WORDS * 8;
+};
+
+constexpr int ADJ_TP = 16, ADJ_W = 4;
+using APL = AdjPlan<ADJ_TP, ADJ_W>;
+
+// Smoothness terms of the three windows of a left-biased stencil q0..q4:
+// s_k (second difference), v_k (first-derivative combination), b_k = 4 eps + 13/3 s^2 + v^2.
+struct Windows {
+  double s[3], v[3], b[3];
+};
+
+__device__ __forceinline__ Windows windows(double q0, double q1, double q2, double q3, double q4, double eps4) {
+  Windows w;
+  const double g0 = q1 - q0, g1 = q2 - q1, g2 = q3 - q2, g3 = q4 - q3;
+  w.s[0] = g1 - g0;
+  w.s[1] = g2 - g1;
+  w.s[2] = g3 - g2;
+  w.v[0] = fma(3.0, g1, -g0);  // q0 - 4 q1 + 3 q2
+  w.v[1] = g1 + g2;            // q3 - q1
+  w.v[2] = fma(-3.0, g2, g3);  // 3 q2 - 4 q3 + q4
+#pragma unroll
+  for (int k = 0; k < 3; ++k) w.b[k] = fma(w.v[k], w.v[k], fma((13.0 / 3.0) * w.s[k], w.s[k], eps4));
+  return w;
+}
+
+__device__ __forceinline__ void candidates(double q0, double q1, double q2, double q3, double q4, double c[3]) {
+  c[0] = fma(11.0 / 6.0, q2, fma(-7.0 / 6.0, q1, (1.0 / 3.0) * q0));
+  c[1] = fma(1.0 / 3.0, q3, fma(5.0 / 6.0, q2, (-1.0 / 6.0) * q1));
+  c[2] = fma(-1.0 / 6.0, q4, fma(5.0 / 6.0, q3, (1.0 / 3.0) * q2));
+}
+
+// WENO5 value and weights of the stencil q0..q4 (value at the interface right of q2).
+__device__ __forceinline__ double weno_value(double q0, double q1, double q2, double q3, double q4, double eps4,
+                                             double om[3]) {
+  const Windows w = windows(q0, q1, q2, q3, q4, eps4);
+  double c[3];
+  candidates(q0, q1, q2, q3, q4, c);
+  const double B0 = w.b[0] * w.b[0], B1 = w.b[1] * w.b[1], B2 = w.b[2] * w.b[2];
+  const double a0 = B1 * B2, a1 = 6.0 * (B0 * B2), a2 = 3.0 * (B0 * B1);
+  const double r = 1.0 / (a0 + a1 + a2);
+  om[0] = a0 * r;
+  om[1] = a1 * r;
+  om[2] = a2 * r;
+  return fma(om[0], c[0], fma(om[1], c[1], om[2] * c[2]));
+}
+
+// Adjoint of one reconstruction: out[t] = y * d(value)/d(q_t), t = 0..4.
+__device__ __forceinline__ void weno_adjoint(double q0, double q1, double q2, double q3, double q4, double eps4,
+                                             const double om[3], double val, double y, double out[5]) {
+  const Windows w = windows(q0, q1, q2, q3, q4, eps4);
+  double c[3];
+  candidates(q0, q1, q2, q3, q4, c);
+  const double y0 = y * om[0], y1 = y * om[1], y2 = y * om[2];
+  out[0] = (1.0 / 3.0) * y0;
+  out[1] = fma(-7.0 / 6.0, y0, (-1.0 / 6.0) * y1);
+  out[2] = fma(11.0 / 6.0, y0, fma(5.0 / 6.0, y1, (1.0 / 3.0) * y2));
+  out[3] = fma(1.0 / 3.0, y1, (5.0 / 6.0) * y2);
+  out[4] = (-1.0 / 6.0) * y2;
+  // adjoint of b_k: -2 y omega_k (q_k - val) / b_k, with one division for the three
+  const double rb = 1.0 / (w.b[0] * w.b[1] * w.b[2]);
+  const double ib0 = (w.b[1] * w.b[2]) * rb, ib1 = (w.b[0] * w.b[2]) * rb, ib2 = (w.b[0] * w.b[1]) * rb;
+  const double k0 = -2.0 * y0 * (c[0] - val) * ib0;
+  const double k1 = -2.0 * y1 * (c[1] - val) * ib1;
+  const double k2 = -2.0 * y2 * (c[2] - val) * ib2;
+  // db/d(x, y, z) of a window = 26/3 s (1, -2, 1) + 2 v dv/d(x, y, z)
+  double t = (26.0 / 3.0) * w.s[0] * k0, r = 2.0 * w.v[0] * k0;  // dv = (1, -4, 3)
+  out[0] += t + r;
+  out[1] += fma(-2.0, t, -4.0 * r);
+  out[2] += fma(3.0, r, t);
+  t = (26.0 / 3.0) * w.s[1] * k1;
+  r = 2.0 * w.v[1] * k1;  // dv = (-1, 0, 1)
+  out[1] += t - r;
+  out[2] += -2.0 * t;
+  out[3] += t + r;
+  t = (26.0 / 3.0) * w.s[2] * k2;
+  r = 2.0 * w.v[2] * k2;  // dv = (3, -4, 1)
+  out[2] += fma(3.0, r, t);
+  out[3] += fma(-2.0, t, -4.0 * r);
+  out[4] += t + r;
+}
+
+// |lambda| with Harten's fix (acoustic fields): value and derivatives d/dlambda, d/ddelta.
+__device__ __forceinline__ double harten(double lam, double delta, double& dl, double& dd) {
+  const double a = fabs(lam);
+  if (a < delta) {
+    const double rd = 1.0 / delta;
+    dl = lam * rd;
+    dd = 0.5 - 0.5 * (lam * rd) * (lam * rd);
+    return 0.5 * (lam * lam + delta * delta) * rd;
+  }
+  dl = (lam > 0.0) ? 1.0 : (lam < 0.0 ? -1.0 : 0.0);
+  dd = 0.0;
+  return a;
+}
+
+__device__ __forceinline__ void adj_epilogue(const AdjArgs& a, long long p, const double cv[5]) {
+  const long long N = a.g.N;
+  switch (a.epi) {
+    case AEPI_WRITE:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) a.k[v * N + p] = cv[v];
+      break;
+    case AEPI_ADD:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) a.k[v * N + p] += cv[v];
+      break;
+    case AEPI_OUT:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) a.gout[v * N + p] = a.k[v * N + p] + cv[v];
+      break;
+    case AEPI_RK4_4:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K = a.k[v * N + p] + cv[v], ub = a.ubs[v * N + p];
+        a.gout[v * N + p] = ub + K;
+        a.lnext[v * N + p] = fma(a.c1, ub, a.c2 * K);
+      }
+      break;
+    case AEPI_RK4_M:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K = a.k[v * N + p] + cv[v], ub = a.ubs[v * N + p];
+        a.gout[v * N + p] += K;
+        a.lnext[v * N + p] = fma(a.c1, ub, a.c2 * K);
+      }
+      break;
+    case AEPI_ACC:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) a.gout[v * N + p] += a.k[v * N + p] + cv[v];
+      break;
+    case AEPI_SSP_3:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K = a.k[v * N + p] + cv[v], ub = a.ubs[v * N + p];
+        const double s = fma(2.0 / 3.0, ub, K);
+        a.gout[v * N + p] = fma(1.0 / 3.0, ub, 0.75 * s);
+        a.lnext[v * N + p] = (0.25 * a.c2) * s;
+        a.sb[v * N + p] = 0.25 * s;
+      }
+      break;
+    case AEPI_SSP_2:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K = a.k[v * N + p] + cv[v];
+        const double s = a.sb[v * N + p] + K;
+        a.gout[v * N + p] += s;
+        a.lnext[v * N + p] = a.c2 * s;
+      }
+      break;
+    default:
+      break;
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(APL::THREADS, 2) k_adj_dir(const AdjArgs a) {
+  extern __shared__ double sm[];
+  constexpr int TP = APL::TP, NP = APL::NP, NI = APL::NI, W = APL::W;
+  constexpr int AX = (D == 0) ? 1 : 0;
+  constexpr int T1 = (D == 0) ? 1 : 0;
+  constexpr int T2 = (D == 2) ? 1 : 2;
+  const int nD = a.g.n[D];
+  const int na = a.g.n[AX];
+  const long long N = a.g.N;
+  const int s0 = blockIdx.x * TP;
+  const int a0 = blockIdx.y * W;
+  const int bz = blockIdx.z;
+  const int tid = threadIdx.x;
+  const double rdx = 1.0 / a.g.h[D];
+  const double gm1 = a.gamma - 1.0;
+  double* q = sm + APL::OFF_Q;
+  double* ri = sm + APL::OFF_RI;
+  double* lm = sm + APL::OFF_L;
+  double* rec = sm + APL::OFF_REC;
+  double* rd = sm + APL::OFF_RD;
+  double* wc = sm + APL::OFF_WC;
+
+  // ---- A: load -------------------------------------------------------------------
+  for (int item = tid; item < NP * W; item += APL::THREADS) {
+    int pos, line;
+    tile_split<D, W>(item, NP, pos, line);
+    const int c = wrap_idx(s0 - 5 + pos, nD);
+    const int la = min(a0 + line, na - 1);
+    const long long p = tile_flat<D>(a.g, c, la, bz);
+    double U[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) U[v] = __ldg(a.u + v * N + p);
+    const double vx = __ldg(a.pm + PM_U * N + p), vy = __ldg(a.pm + PM_V * N + p), vz = __ldg(a.pm + PM_W * N + p);
+    const double pr = __ldg(a.pm + PM_P * N + p);
+    const double un = (D == 0) ? vx : (D == 1) ? vy : vz;
+    const int s = tile_idx<D, W>(pos, line, NP);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) q[v * NP * W + s] = U[v];
+    q[5 * NP * W + s] = (D == 0) ? fma(U[1], un, pr) : U[1] * un;
+    q[6 * NP * W + s] = (D == 1) ? fma(U[2], un, pr) : U[2] * un;
+    q[7 * NP * W + s] = (D == 2) ? fma(U[3], un, pr) : U[3] * un;
+    q[8 * NP * W + s] = (U[4] + pr) * un;
+    ri[0 * NP * W + s] = __ldg(a.pm + PM_SR * N + p);
+    ri[1 * NP * W + s] = vx;
+    ri[2 * NP * W + s] = vy;
+    ri[3 * NP * W + s] = vz;
+    ri[4 * NP * W + s] = __ldg(a.pm + PM_H * N + p);
+    ri[5 * NP * W + s] = pr;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) lm[v * NP * W + s] = a.lam_scale * __ldg(a.lam + v * N + p);
+  }
+  __syncthreads();
+
+  // ---- C: values and weights of the left/right reconstructions -----------------------
+  for (int item = tid; item < 9 * NI * W; item += APL::THREADS) {
+    const int m = item / (NI * W);
+    int f, line;
+    tile_split<D, W>(item - m * NI * W, NI, f, line);
+    const double* qm = q + m * NP * W;
+    double P[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) P[j] = qm[tile_idx<D, W>(f + j, line, NP)];
+    double wL[3], wR[3];
+    const double vL = weno_value(P[0], P[1], P[2], P[3], P[4], a.eps4, wL);
+    const double vR = weno_value(P[5], P[4], P[3], P[2], P[1], a.eps4, wR);
+    const int o = tile_idx<D, W>(f, line, NI);
+    rec[(2 * m) * NI * W + o] = vL;
+    rec[(2 * m + 1) * NI * W + o] = vR;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      wc[(m * 6 + k) * NI * W + o] = wL[k];
+      wc[(m * 6 + 3 + k) * NI * W + o] = wR[k];
+    }
+  }
+  __syncthreads();
+
+  // ---- D: adjoint of the Roe flux at every interface --------------------------------------
+  {
+    int bad = 0;
+    for (int item = tid; item < NI * W; item += APL::THREADS) {
+      int f, line;
+      tile_split<D, W>(item, NI, f, line);
+      const int o = tile_idx<D, W>(f, line, NI);
+      const int sa = tile_idx<D, W>(f + 2, line, NP), sb = tile_idx<D, W>(f + 3, line, NP);
+      double du[5], Lh[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        du[v] = rec[(2 * v + 1) * NI * W + o] - rec[(2 * v) * NI * W + o];
+        Lh[v] = (lm[v * NP * W + sb] - lm[v * NP * W + sa]) * rdx;
+      }
+      // forward: Roe average of the two point states, eigen-decomposition of the dissipation
+      const double ra = ri[sa], rb = ri[sb];
+      const double rsum = ra + rb;
+      const double rs = 1.0 / rsum;
+      const double wa = ra * rs, wb = rb * rs;
+      double Va[3], Vb[3], V[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        Va[m] = ri[(1 + m) * NP * W + sa];
+        Vb[m] = ri[(1 + m) * NP * W + sb];
+        V[m] = fma(wa, Va[m], wb * Vb[m]);
+      }
+      const double Ha = ri[4 * NP * W + sa], Hb = ri[4 * NP * W + sb];
+      const double H = fma(wa, Ha, wb * Hb);
+      const double q2h = 0.5 * fma(V[0], V[0], fma(V[1], V[1], V[2] * V[2]));
+      const double c2 = gm1 * (H - q2h);
+      bad |= !(c2 > 0.0);
+      const double c = sqrt(c2);
+      const double rc = 1.0 / c;
+      const double un = V[D], vt1 = V[T1], vt2 = V[T2];
+      const double b1 = gm1 * (rc * rc);
+      const double vdm = fma(V[0], du[1], fma(V[1], du[2], V[2] * du[3]));
+      const double Y = fma(q2h, du[0], du[4]) - vdm;
+      const double phi = b1 * Y;
+      const double X = fma(un, du[0], -du[1 + D]);
+      const double ach = 0.5 * (X * rc);
+      const double a2 = du[0] - phi;
+      const double a3 = fma(-vt1, du[0], du[1 + T1]);
+      const double a4 = fma(-vt2, du[0], du[1 + T2]);
+      const double a1 = 0.5 * phi + ach, a5 = 0.5 * phi - ach;
+      const double delta = a.hdelta * c;
+      double dl1, dd1, dl5, dd5;
+      const double l1 = harten(un - c, delta, dl1, dd1);
+      const double l5 = harten(un + c, delta, dl5, dd5);
+      const double l2 = fabs(un);
+      const double sg2 = (un > 0.0) ? 1.0 : (un < 0.0 ? -1.0 : 0.0);
+      const double A1 = l1 * a1, A2 = l2 * a2, A3 = l2 * a3, A4 = l2 * a4, A5 = l5 * a5;
+      const double S = A1 + A5, d0 = S + A2, cD = c * (A5 - A1);
+      // backward: Dbar = adjoint of the dissipation vector = -Lhat/2
+      double Db[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Db[v] = -0.5 * Lh[v];
+      const double d0b = fma(Db[1 + D], un, fma(Db[1 + T1], vt1, fma(Db[1 + T2], vt2, Db[0])));
+      const double cDb = fma(Db[4], un, Db[1 + D]);
+      const double Sb = fma(Db[4], H, d0b);
+      const double A2b = fma(Db[4], q2h, d0b);
+      const double A3b = fma(Db[4], vt1, Db[1 + T1]);
+      const double A4b = fma(Db[4], vt2, Db[1 + T2]);
+      const double A1b = fma(-c, cDb, Sb), A5b = fma(c, cDb, Sb);
+      double unb = fma(Db[1 + D], d0, Db[4] * cD);
+      double vt1b = fma(Db[1 + T1], d0, Db[4] * A3);
+      double vt2b = fma(Db[1 + T2], d0, Db[4] * A4);
+      double Hbar = Db[4] * S;
+      double q2hb = Db[4] * A2;
+      double cb = cDb * (A5 - A1);
+      // A_k = l_k a_k
+      const double a1b = A1b * l1, a2b = A2b * l2, a3b = A3b * l2, a4b = A4b * l2, a5b = A5b * l5;
+      const double l1b = A1b * a1, l5b = A5b * a5;
+      const double l2b = fma(A2b, a2, fma(A3b, a3, A4b * a4));
+      unb = fma(dl1, l1b, fma(dl5, l5b, fma(sg2, l2b, unb)));
+      cb = fma(-dl1, l1b, fma(dl5, l5b, fma(a.hdelta, fma(dd1, l1b, dd5 * l5b), cb)));
+      // wave strengths
+      const double phib = fma(0.5, a1b + a5b, -a2b);
+      const double achb = a1b - a5b;
+      double dub[5];
+      dub[0] = fma(-vt1, a3b, fma(-vt2, a4b, a2b));
+      dub[1 + T1] = a3b;
+      dub[1 + T2] = a4b;
+      dub[1 + D] = 0.0;
+      dub[4] = 0.0;
+      vt1b = fma(-a3b, du[0], vt1b);
+      vt2b = fma(-a4b, du[0], vt2b);
+      const double Xb = 0.5 * rc * achb;
+      double rcb = 0.5 * X * achb;
+      unb = fma(Xb, du[0], unb);
+      dub[0] = fma(Xb, un, dub[0]);
+      dub[1 + D] -= Xb;
+      const double b1b = phib * Y;
+      const double Yb = phib * b1;
+      q2hb = fma(Yb, du[0], q2hb);
+      dub[0] = fma(Yb, q2h, dub[0]);
+      dub[4] += Yb;
+      double Vbar[3];
+      Vbar[D] = unb;
+      Vbar[T1] = vt1b;
+      Vbar[T2] = vt2b;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        Vbar[m] = fma(-Yb, du[1 + m], Vbar[m]);  // vdm = V . du_m
+        dub[1 + m] = fma(-Yb, V[m], dub[1 + m]);
+      }
+      rcb = fma(b1b, 2.0 * gm1 * rc, rcb);
+      cb = fma(-rcb, rc * rc, cb);
+      // c = sqrt(gm1 (H - q2h))
+      const double c2b = 0.5 * cb * rc;
+      Hbar = fma(gm1, c2b, Hbar);
+      q2hb = fma(-gm1, c2b, q2hb);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) Vbar[m] = fma(q2hb, V[m], Vbar[m]);
+      // Roe average of the point states a, b
+      double rab = Hbar * (Ha - H), rbb = Hbar * (Hb - H);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        rab = fma(Vbar[m], Va[m] - V[m], rab);
+        rbb = fma(Vbar[m], Vb[m] - V[m], rbb);
+      }
+      rab *= rs;
+      rbb *= rs;
+      // point primitives: V = m/rho, H = gamma e/rho - gm1 |V|^2/2, sqrt(rho)
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const int sp = side ? sb : sa;
+        const double wgt = side ? wb : wa;
+        const double* Vp = side ? Vb : Va;
+        const double rho = q[sp], e = q[4 * NP * W + sp];
+        const double rr = 1.0 / rho;
+        const double Hb_ = wgt * Hbar;
+        const double srb = side ? rbb : rab;
+        double Vt[3], vdot = 0.0;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          Vt[m] = fma(-Hb_ * gm1, Vp[m], wgt * Vbar[m]);
+          vdot = fma(Vt[m], Vp[m], vdot);
+        }
+        const double eb = Hb_ * a.gamma * rr;
+        const double rhob = fma(0.5, srb / ri[sp], -fma(Hb_ * a.gamma, e * rr, vdot) * rr);
+        const int base = side ? 10 : 5;
+        rd[(base + 0) * NI * W + o] = rhob;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) rd[(base + 1 + m) * NI * W + o] = Vt[m] * rr;
+        rd[(base + 4) * NI * W + o] = eb;
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) rd[v * NI * W + o] = dub[v];
+    }
+    if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(a.status, ST_NONPHYS);
+  }
+  __syncthreads();
+
+  // ---- E: adjoints of the reconstructions -> stencil contributions --------------------
+  for (int item = tid; item < 9 * NI * W; item += APL::THREADS) {
+    const int m = item / (NI * W);
+    int f, line;
+    tile_split<D, W>(item - m * NI * W, NI, f, line);
+    const int o = tile_idx<D, W>(f, line, NI);
+    const int sa = tile_idx<D, W>(f + 2, line, NP), sb = tile_idx<D, W>(f + 3, line, NP);
+    double yL, yR;
+    if (m < 5) {
+      const double g = rd[m * NI * W + o];
+      yL = -g;
+      yR = g;
+      if (m == 1 + D) {  // mass flux f_0 = u_{1+D}: (f^L + f^R)/2 part
+        const double h0 = 0.5 * ((lm[sb] - lm[sa]) * rdx);
+        yL += h0;
+        yR += h0;
+      }
+    } else {
+      const double hm = 0.5 * ((lm[(m - 4) * NP * W + sb] - lm[(m - 4) * NP * W + sa]) * rdx);
+      yL = hm;
+      yR = hm;
+    }
+    const double* qm = q + m * NP * W;
+    double P[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) P[j] = qm[tile_idx<D, W>(f + j, line, NP)];
+    double wL[3], wR[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      wL[k] = wc[(m * 6 + k) * NI * W + o];
+      wR[k] = wc[(m * 6 + 3 + k) * NI * W + o];
+    }
+    const double vL = rec[(2 * m) * NI * W + o], vR = rec[(2 * m + 1) * NI * W + o];
+    double cL[5], cR[5];
+    weno_adjoint(P[0], P[1], P[2], P[3], P[4], a.eps4, wL, vL, yL, cL);
+    weno_adjoint(P[5], P[4], P[3], P[2], P[1], a.eps4, wR, vR, yR, cR);
+    // position f + j: left stencil index j, right stencil index 5 - j
+    wc[(m * 6 + 0) * NI * W + o] = cL[0];
+#pragma unroll
+    for (int j = 1; j < 5; ++j) wc[(m * 6 + j) * NI * W + o] = cL[j] + cR[5 - j];
+    wc[(m * 6 + 5) * NI * W + o] = cR[0];
+  }
+  __syncthreads();
+
+  // ---- F: gather, adjoint of the point fluxes, epilogue ----------------------------------
+  for (int item = tid; item < TP * W; item += APL::THREADS) {
+    int pp, line;
+    tile_split<D, W>(item, TP, pp, line);
+    if (s0 + pp >= nD || a0 + line >= na) continue;
+    const int pos = pp + 5;
+    double g[9];
+#pragma unroll
+    for (int m = 0; m < 9; ++m) {
+      double acc = 0.0;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) acc += wc[(m * 6 + j) * NI * W + tile_idx<D, W>(pos - j, line, NI)];
+      g[m] = acc;
+    }
+    const int oa = tile_idx<D, W>(pos - 2, line, NI), ob = tile_idx<D, W>(pos - 3, line, NI);
+    double cv[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) cv[v] = g[v] + (rd[(5 + v) * NI * W + oa] + rd[(10 + v) * NI * W + ob]);
+    // f_{1+k} = m_k u_D + [k = D] p, f_4 = (e + p) u_D
+    const int s = tile_idx<D, W>(pos, line, NP);
+    const double rho = q[s], e = q[4 * NP * W + s], pr = ri[5 * NP * W + s];
+    const double V[3] = {ri[1 * NP * W + s], ri[2 * NP * W + s], ri[3 * NP * W + s]};
+    const double un = V[D];
+    const double Fb1 = g[5], Fb2 = g[6], Fb3 = g[7], Fb4 = g[8];
+    const double Fbm[3] = {Fb1, Fb2, Fb3};
+    const double pb = fma(Fb4, un, Fbm[D]);
+    double unb = Fb4 * (e + pr);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      unb = fma(Fbm[k], q[(1 + k) * NP * W + s], unb);
+      cv[1 + k] = fma(Fbm[k], un, cv[1 + k]);
+    }
+    cv[4] = fma(Fb4, un, cv[4]);
+    const double rr = 1.0 / rho;
+    cv[1 + D] = fma(unb, rr, cv[1 + D]);
+    cv[0] = fma(-unb * un, rr, cv[0]);
+    const double gp = gm1 * pb;
+    cv[4] += gp;
+    double v2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      cv[1 + k] = fma(-gp, V[k], cv[1 + k]);
+      v2 = fma(V[k], V[k], v2);
+    }
+    cv[0] = fma(0.5 * gp, v2, cv[0]);
+    const long long p = tile_flat<D>(a.g, s0 + pp, a0 + line, bz);
+    adj_epilogue(a, p, cv);
+  }
+}
+
+__device__ __forceinline__ void point_ijk(long long p, int nx, int ny, int& i, int& j, int& k) {
+  i = (int)(p % nx);
+  j = (int)((p / nx) % ny);
+  k = (int)(p / ((long long)nx * ny));
+}
+
+// Neighbour flat indices at offsets -2, -1, +1, +2 along direction d.
+__device__ __forceinline__ void neighbours(int i, int j, int k, int d, const Grid& g, long long nb[4]) {
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    const int off = (o < 2) ? (o - 2) : (o - 1);
+    int c[3] = {i, j, k};
+    c[d] = wrap_idx(c[d] + off, g.n[d]);
+    nb[o] = flat3(c[0], c[1], c[2], g.n[0], g.n[1]);
+  }
+}
+
+// Gradients G[q][e] of (u, v, w, T) at point p (the same stencil as the viscous fluxes).
+__device__ __forceinline__ void point_gradients(const Grid& g, const double* pm, int i, int j, int k, double G[4][3]) {
+  const long long N = g.N;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    long long nb[4];
+    neighbours(i, j, k, d, g, nb);
+    const double r12 = 1.0 / (12.0 * g.h[d]);
+#pragma unroll
+    for (int qv = 0; qv < 4; ++qv) {
+      const int plane = (qv < 3) ? qv : PM_T;
+      const double* A = pm + (long long)plane * N;
+      G[qv][d] = d4(__ldg(A + nb[0]), __ldg(A + nb[1]), __ldg(A + nb[2]), __ldg(A + nb[3]), r12);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_visc_adj1(const Grid g, const double* __restrict__ pm,
+                                                   const double* __restrict__ lam, double lam_scale,
+                                                   double* __restrict__ sc, double mu, double kappa) {
+  const long long N = g.N;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    point_ijk(p, g.n[0], g.n[1], i, j, k);
+    double G[4][3];
+    point_gradients(g, pm, i, j, k, G);
+    const double vel[3] = {pm[PM_U * N + p], pm[PM_V * N + p], pm[PM_W * N + p]};
+    const double tdiv = (2.0 / 3.0) * (G[0][0] + G[1][1] + G[2][2]);
+    double Gb[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    double vb[3] = {0, 0, 0};
+    double divb = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      long long nb[4];
+      neighbours(i, j, k, d, g, nb);
+      const double r12 = 1.0 / (12.0 * g.h[d]);
+      double Fb[4];  // adjoint of the viscous flux along d: -D_d lambda_{1+c}
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        const double* L = lam + (long long)(1 + cc) * N;
+        Fb[cc] = -lam_scale * d4(__ldg(L + nb[0]), __ldg(L + nb[1]), __ldg(L + nb[2]), __ldg(L + nb[3]), r12);
+      }
+      Gb[3][d] = fma(kappa, Fb[3], Gb[3][d]);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const double tau = (m == d) ? mu * fma(2.0, G[d][d], -tdiv) : mu * (G[m][d] + G[d][m]);
+        const double tb = fma(Fb[3], vel[m], Fb[m]);
+        vb[m] = fma(Fb[3], tau, vb[m]);
+        if (m == d) {
+          Gb[d][d] = fma(2.0 * mu, tb, Gb[d][d]);
+          divb = fma(-(2.0 / 3.0) * mu, tb, divb);
+        } else {
+          Gb[m][d] = fma(mu, tb, Gb[m][d]);
+          Gb[d][m] = fma(mu, tb, Gb[d][m]);
+        }
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) Gb[d][d] += divb;
+#pragma unroll
+    for (int qv = 0; qv < 4; ++qv)
+#pragma unroll
+      for (int e = 0; e < 3; ++e) sc[(long long)(qv * 3 + e) * N + p] = Gb[qv][e];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) sc[(long long)(12 + m) * N + p] = vb[m];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_visc_adj2(const Grid g, const double* __restrict__ u,
+                                                   const double* __restrict__ sc, double gamma,
+                                                   double* __restrict__ out, int accumulate, int with_rho) {
+  const long long N = g.N;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    point_ijk(p, g.n[0], g.n[1], i, j, k);
+    double Wb[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      long long nb[4];
+      neighbours(i, j, k, e, g, nb);
+      const double r12 = 1.0 / (12.0 * g.h[e]);
+#pragma unroll
+      for (int qv = 0; qv < 4; ++qv) {
+        const double* A = sc + (long long)(qv * 3 + e) * N;
+        Wb[qv] -= d4(__ldg(A + nb[0]), __ldg(A + nb[1]), __ldg(A + nb[2]), __ldg(A + nb[3]), r12);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 3; ++m) Wb[m] += sc[(long long)(12 + m) * N + p];
+    const double rho = u[p], e = u[4 * N + p];
+    const double rr = 1.0 / rho;
+    const double V[3] = {u[N + p] * rr, u[2 * N + p] * rr, u[3 * N + p] * rr};
+    const double gg = gamma * (gamma - 1.0);
+    const double Tb = gg * Wb[3];
+    double ub[5];
+    ub[4] = Tb * rr;
+    double v2 = 0.0, wv = 0.0;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      ub[1 + m] = fma(-Tb, V[m], Wb[m]) * rr;
+      v2 = fma(V[m], V[m], v2);
+      wv = fma(Wb[m], V[m], wv);
+    }
+    ub[0] = fma(Tb, v2 - e * rr, -wv) * rr;
+    if (with_rho) ub[0] += sc[15 * N + p];
+    if (accumulate) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) out[v * N + p] += ub[v];
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) out[v * N + p] = ub[v];
+    }
+  }
+}
+
+// d(mean of rho |v|^2/2)/du: (-|V|^2/2, V) / N, 0 for the energy.
+__global__ void __launch_bounds__(256) k_ke_seed(const Grid g, const double* __restrict__ u,
+                                                 double* __restrict__ out) {
+  const long long N = g.N;
+  const double rn = 1.0 / (double)N;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    const double rr = 1.0 / u[p];
+    double v2 = 0.0;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const double V = u[(1 + m) * N + p] * rr;
+      out[(1 + m) * N + p] = V * rn;
+      v2 = fma(V, V, v2);
+    }
+    out[p] = -0.5 * v2 * rn;
+    out[4 * N + p] = 0.0;
+  }
+}
+
+// Enstrophy mean of rho |omega|^2/2: adjoint of the velocity gradients (rho omega / N on
+// the antisymmetric pairs), zero velocity adjoint, direct density term |omega|^2/(2N).
+__global__ void __launch_bounds__(256) k_ens_seed(const Grid g, const double* __restrict__ u,
+                                                  const double* __restrict__ pm, double* __restrict__ sc) {
+  const long long N = g.N;
+  const double rn = 1.0 / (double)N;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    point_ijk(p, g.n[0], g.n[1], i, j, k);
+    double G[4][3];
+    point_gradients(g, pm, i, j, k, G);
+    const double wx = G[2][1] - G[1][2], wy = G[0][2] - G[2][0], wz = G[1][0] - G[0][1];
+    const double rw = u[p] * rn;
+    double Gb[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    Gb[2][1] = rw * wx;
+    Gb[1][2] = -rw * wx;
+    Gb[0][2] = rw * wy;
+    Gb[2][0] = -rw * wy;
+    Gb[1][0] = rw * wz;
+    Gb[0][1] = -rw * wz;
+#pragma unroll
+    for (int qv = 0; qv < 4; ++qv)
+#pragma unroll
+      for (int e = 0; e < 3; ++e) sc[(long long)(qv * 3 + e) * N + p] = Gb[qv][e];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) sc[(long long)(12 + m) * N + p] = 0.0;
+    sc[15 * N + p] = 0.5 * rn * fma(wx, wx, fma(wy, wy, wz * wz));
+  }
+}
+
+int point_blocks(const Grid& g) {
+  const long long b = (g.N + 255) / 256;
+  return (int)(b < 152LL * 16 ? b : 152LL * 16);
+}
+
+}  // namespace
+
+cudaError_t prepare_adj_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(k_adj_dir<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, APL::BYTES);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_dir<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, APL::BYTES);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_dir<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, APL::BYTES);
+  return e;
+}
+
+cudaError_t launch_adj_dir(int d, const AdjArgs& a, cudaStream_t s) {
+  const int AXd = (d == 0) ? 1 : 0;
+  const int BXd = (d == 2) ? 1 : 2;
+  dim3 grid((a.g.n[d] + APL::TP - 1) / APL::TP, (a.g.n[AXd] + APL::W - 1) / APL::W, a.g.n[BXd]);
+  switch (d) {
+    case 0: k_adj_dir<0><<<grid, APL::THREADS, APL::BYTES, s>>>(a); break;
+    case 1: k_adj_dir<1><<<grid, APL::THREADS, APL::BYTES, s>>>(a); break;
+    default: k_adj_dir<2><<<grid, APL::THREADS, APL::BYTES, s>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_visc_adj1(const Grid& g, const double* pm, const double* lam, double lam_scale, double* scratch,
+                             double mu, double kappa, cudaStream_t s) {
+  k_visc_adj1<<<point_blocks(g), 256, 0, s>>>(g, pm, lam, lam_scale, scratch, mu, kappa);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_visc_adj2(const Grid& g, const double* u, const double* scratch, double gamma, double* out,
+                             int accumulate, int with_rho, cudaStream_t s) {
+  k_visc_adj2<<<point_blocks(g), 256, 0, s>>>(g, u, scratch, gamma, out, accumulate, with_rho);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ke_seed(const Grid& g, const double* u, double* grad, cudaStream_t s) {
+  k_ke_seed<<<point_blocks(g), 256, 0, s>>>(g, u, grad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ens_seed(const Grid& g, const double* u, const double* pm, double* scratch, cudaStream_t s) {
+  k_ens_seed<<<point_blocks(g), 256, 0, s>>>(g, u, pm, scratch);
+  return cudaGetLastError();
+}
+
+}  // namespace ns3d

@@ -9,87 +9,11 @@
 #include <new>
 #include <vector>
 
-#include "ns3d_internal.cuh"
+#include "ns3d_ctx.cuh"
 
 using namespace ns3d;
 
-struct TimedLaunch {
-  int kid;
-  cudaEvent_t e0, e1;
-};
-
-struct ns3d_ctx {
-  ns3d_params p;
-  Grid g;
-  cudaStream_t stream;
-  int device;
-  double* pm = nullptr;        // [NPRIM][N]
-  double* fv = nullptr;        // [NVISC][N] (viscous only)
-  double* k = nullptr;         // [5][N] RHS accumulator
-  double* ua = nullptr;        // [5][N] stage state
-  double* ub = nullptr;        // [5][N] stage state
-  double* acc = nullptr;       // [5][N] RK4 accumulator
-  double* partials = nullptr;  // [stats blocks][10]
-  double* stats_dev = nullptr; // [NS3D_STATS_NDOUBLE]
-  int* status = nullptr;       // sticky status word
-  double* uhost_dev = nullptr; // device state for ns3d_step_host (lazy)
-  double* stats_host = nullptr;// pinned [NS3D_STATS_NDOUBLE]
-  int nstat_blocks = 0;
-  int variant = 0;             // tile-shape variant of the direction passes
-  char err[512] = {0};
-  // timing
-  bool timing = false;
-  std::vector<TimedLaunch> pending;
-  std::vector<cudaEvent_t> pool;
-  double ms[NS3D_K_COUNT] = {0};
-  long long launches[NS3D_K_COUNT] = {0};
-};
-
 namespace {
-
-int set_err(ns3d_ctx* c, int code, const char* fmt, ...) {
-  if (c) {
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(c->err, sizeof(c->err), fmt, ap);
-    va_end(ap);
-  }
-  return code;
-}
-
-int cuda_fail(ns3d_ctx* c, cudaError_t e, const char* what) {
-  return set_err(c, NS3D_ECUDA, "%s: %s", what, cudaGetErrorString(e));
-}
-
-cudaEvent_t pool_get(ns3d_ctx* c) {
-  if (!c->pool.empty()) {
-    cudaEvent_t e = c->pool.back();
-    c->pool.pop_back();
-    return e;
-  }
-  cudaEvent_t e = nullptr;
-  cudaEventCreate(&e);
-  return e;
-}
-
-// Launch wrapper: records events around the launch when timing is on.
-template <typename F>
-int timed(ns3d_ctx* c, int kid, F&& fn, const char* what) {
-  TimedLaunch t{kid, nullptr, nullptr};
-  if (c->timing) {
-    t.e0 = pool_get(c);
-    t.e1 = pool_get(c);
-    cudaEventRecord(t.e0, c->stream);
-  }
-  cudaError_t e = fn();
-  if (c->timing) {
-    cudaEventRecord(t.e1, c->stream);
-    c->pending.push_back(t);
-  }
-  c->launches[kid] += 1;
-  if (e != cudaSuccess) return cuda_fail(c, e, what);
-  return NS3D_OK;
-}
 
 bool overlaps(const void* a, const void* b, size_t bytes) {
   const char* x = (const char*)a;
@@ -132,6 +56,10 @@ int status_code(int word) {
   if (word & ST_DF_RANGE) return NS3D_ERANGE;
   return NS3D_OK;
 }
+
+}  // namespace
+
+namespace ns3d {
 
 // One full right-hand-side evaluation of state u: primitives, viscous fluxes,
 // x and y passes accumulating into k, z pass with the given epilogue.
@@ -188,6 +116,10 @@ int rk_one_step(ns3d_ctx* c, double* u, double dt) {
   if ((rc = rhs_pass(c, c->ua, EPI_SSP_2, c->ub, u, dt))) return rc;
   return rhs_pass(c, c->ub, EPI_SSP_3, u, u, dt);
 }
+
+}  // namespace ns3d
+
+namespace {
 
 int collect_timing(ns3d_ctx* c) {
   for (auto& t : c->pending) {
@@ -347,6 +279,7 @@ void ns3d_free(ns3d_ctx* c) {
   cudaFree(c->stats_dev);
   cudaFree(c->status);
   cudaFree(c->uhost_dev);
+  adjoint_free(c);
   if (c->stats_host) cudaFreeHost(c->stats_host);
   delete c;
 }

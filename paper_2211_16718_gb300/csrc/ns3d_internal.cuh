@@ -77,6 +77,51 @@ cudaError_t launch_stats_final(const Grid& g, const double* partials, int nblock
                                double* out, cudaStream_t s);
 int alu_probe(double out[5]);
 
+// ---- adjoint (vector-Jacobian product) of the right-hand side --------------------
+// Epilogue of the last adjoint direction pass; K = k + contribution = J(u)^T lambda.
+enum AdjEpi {
+  AEPI_WRITE = 0,  // k = contribution
+  AEPI_ADD = 1,    // k += contribution
+  AEPI_OUT = 2,    // gout = K
+  AEPI_RK4_4 = 3,  // gout = ubs + K;  lnext = c1 ubs + c2 K     (RK4, stage 4 in reverse)
+  AEPI_RK4_M = 4,  // gout += K;       lnext = c1 ubs + c2 K     (stages 3, 2)
+  AEPI_ACC = 5,    // gout += K                                  (RK4 and SSP-RK3, stage 1)
+  AEPI_SSP_3 = 6,  // s = 2/3 ubs + K; gout = 1/3 ubs + 3/4 s; lnext = c2 s/4; sb = s/4
+  AEPI_SSP_2 = 7   // s = sb + K;      gout += s;  lnext = c2 s  (sb and lnext may alias)
+};
+
+struct AdjArgs {
+  Grid g;
+  const double* u;    // state at which the Jacobian is taken [5][N]
+  const double* pm;   // its primitives [NPRIM][N]
+  const double* lam;  // adjoint input [5][N]; lambda = lam_scale * lam
+  double lam_scale;
+  double* k;          // accumulator [5][N]
+  int epi;            // AdjEpi
+  double* gout;       // AEPI_OUT / RK modes: adjoint of the step's initial state
+  const double* ubs;  // incoming adjoint of the step's final state
+  double* lnext;      // adjoint input of the next (earlier) stage
+  double* sb;         // SSP stage adjoint
+  double c1, c2;
+  double gamma, eps4, hdelta;
+  int* status;
+};
+
+constexpr int ADJ_SCRATCH_PLANES = 16;  // viscous-adjoint scratch: grad adjoint 12, velocity 3, rho 1
+cudaError_t prepare_adj_kernels();
+cudaError_t launch_adj_dir(int d, const AdjArgs& a, cudaStream_t s);
+// scratch = adjoint of the velocity/temperature gradients and of the velocities
+cudaError_t launch_visc_adj1(const Grid& g, const double* pm, const double* lam, double lam_scale, double* scratch,
+                             double mu, double kappa, cudaStream_t s);
+// out (= or +=) adjoint of u through the primitives, from the scratch planes;
+// with_rho adds the direct density plane (scratch plane 15)
+cudaError_t launch_visc_adj2(const Grid& g, const double* u, const double* scratch, double gamma, double* out,
+                             int accumulate, int with_rho, cudaStream_t s);
+// gradient of the mean kinetic energy with respect to u
+cudaError_t launch_ke_seed(const Grid& g, const double* u, double* grad, cudaStream_t s);
+// scratch planes of the enstrophy gradient (finished by launch_visc_adj2 with with_rho)
+cudaError_t launch_ens_seed(const Grid& g, const double* u, const double* pm, double* scratch, cudaStream_t s);
+
 // Periodic wrap of an index that may be off by less than a few periods.
 __host__ __device__ inline int wrap_idx(int i, int n) {
   int r = i % n;

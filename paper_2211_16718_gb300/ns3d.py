@@ -20,10 +20,13 @@ NS3D_ERANGE = -6
 NS3D_RK4, NS3D_SSPRK3 = 0, 1
 NS3D_FP64, NS3D_FP32_BULK, NS3D_FP64_STRICT = 0, 1, 2
 NS3D_STATS_NDOUBLE = 12
-KERNELS = ("prim", "visc", "dir_x", "dir_y", "dir_z", "stats", "stats_final")
+KERNELS = ("prim", "visc", "dir_x", "dir_y", "dir_z", "stats", "stats_final", "adj_visc", "adj_dir", "adj_misc")
+NS3D_FUNC_KE, NS3D_FUNC_ENSTROPHY = 0, 1
+FUNCTIONALS = {"ke": NS3D_FUNC_KE, "enstrophy": NS3D_FUNC_ENSTROPHY}
 EXPORTS = ("ns3d_default_params", "ns3d_init", "ns3d_free", "ns3d_set_stream", "ns3d_rhs", "ns3d_rk_step",
            "ns3d_stats", "ns3d_stats_async", "ns3d_step_host", "ns3d_check", "ns3d_strerror", "ns3d_last_error",
-           "ns3d_timing_enable", "ns3d_timing_read", "ns3d_alu_probe")
+           "ns3d_timing_enable", "ns3d_timing_read", "ns3d_alu_probe", "ns3d_rhs_vjp", "ns3d_rk_step_vjp",
+           "ns3d_functional", "ns3d_traj_forward", "ns3d_traj_vjp")
 
 
 class Ns3dError(RuntimeError):
@@ -85,6 +88,11 @@ def lib():
                 "ns3d_timing_enable": (I, [P, I]),
                 "ns3d_timing_read": (I, [P, P, P, I]),
                 "ns3d_alu_probe": (I, [P]),
+                "ns3d_rhs_vjp": (I, [P, P, P, P]),
+                "ns3d_rk_step_vjp": (I, [P, P, P, D]),
+                "ns3d_functional": (I, [P, P, I, P, P]),
+                "ns3d_traj_forward": (I, [P, P, D, I, I]),
+                "ns3d_traj_vjp": (I, [P, P]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -189,6 +197,48 @@ class Solver:
     def check(self):
         self._sync_stream()
         self._check(lib().ns3d_check(self._ctx))
+
+    # ---- adjoint -----------------------------------------------------------------
+    def rhs_vjp(self, u, lam, out=None):
+        """out = J(u)^T lam with J = dR/du (ns3d_rhs_vjp)."""
+        import torch
+        if out is None:
+            out = torch.empty_like(u)
+        self._sync_stream()
+        self._check(lib().ns3d_rhs_vjp(self._ctx, _dptr(u, 5 * self.N), _dptr(lam, 5 * self.N),
+                                       _dptr(out, 5 * self.N)))
+        return out
+
+    def rk_step_vjp(self, u, ubar, dt: float):
+        """ubar <- (d step(u)/du)^T ubar for one step from u (ns3d_rk_step_vjp); u is unchanged."""
+        self._sync_stream()
+        self._check(lib().ns3d_rk_step_vjp(self._ctx, _dptr(u, 5 * self.N), _dptr(ubar, 5 * self.N), float(dt)))
+        return ubar
+
+    def functional(self, u, which: str = "ke", grad=None, value: bool = True):
+        """(value, grad) of the mean kinetic energy ("ke") or enstrophy ("enstrophy") of u;
+        grad: a tensor like u to receive the gradient, True to allocate one, or None."""
+        import torch
+        if grad is True:
+            grad = torch.empty_like(u)
+        v = ctypes.c_double()
+        self._sync_stream()
+        self._check(lib().ns3d_functional(self._ctx, _dptr(u, 5 * self.N), FUNCTIONALS[which],
+                                          ctypes.byref(v) if value else None,
+                                          _dptr(grad, 5 * self.N) if grad is not None else None))
+        return (v.value if value else None), grad
+
+    def traj_forward(self, u, dt: float, nsteps: int, every: int = 16):
+        """Advance u by nsteps steps, recording checkpoints every `every` steps (ns3d_traj_forward)."""
+        self._sync_stream()
+        self._check(lib().ns3d_traj_forward(self._ctx, _dptr(u, 5 * self.N), float(dt), int(nsteps), int(every)))
+        return u
+
+    def traj_vjp(self, ubar):
+        """ubar (adjoint of the final state) <- adjoint of the initial state (ns3d_traj_vjp)."""
+        self._sync_stream()
+        self._check(lib().ns3d_traj_vjp(self._ctx, _dptr(ubar, 5 * self.N)))
+        return ubar
 
     def timing_enable(self, on: bool = True):
         self._check(lib().ns3d_timing_enable(self._ctx, int(bool(on))))

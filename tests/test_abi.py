@@ -71,6 +71,11 @@ def test_null_arguments(lib):
     assert lib.ns3d_rhs(None, None, None) == ns3d.NS3D_EINVAL
     assert lib.ns3d_rk_step(None, None, 0.1, 1) == ns3d.NS3D_EINVAL
     assert lib.ns3d_stats(None, None, None) == ns3d.NS3D_EINVAL
+    assert lib.ns3d_rhs_vjp(None, None, None, None) == ns3d.NS3D_EINVAL
+    assert lib.ns3d_rk_step_vjp(None, None, None, 0.1) == ns3d.NS3D_EINVAL
+    assert lib.ns3d_functional(None, None, 0, None, None) == ns3d.NS3D_EINVAL
+    assert lib.ns3d_traj_forward(None, None, 0.1, 1, 1) == ns3d.NS3D_EINVAL
+    assert lib.ns3d_traj_vjp(None, None) == ns3d.NS3D_EINVAL
     lib.ns3d_free(None)
 
 
