@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--no-strict", action="store_true", help="skip the all-FP64 comparison run")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk comparison run")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 48-instance ensemble measurement")
-    ap.add_argument("--study", choices=["fp32", "ensemble"], default=None,
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (Taylor-Green 64^3) measurement")
+    ap.add_argument("--study", choices=["fp32", "ensemble", "adjoint", "vjp"], default=None,
                     help="fp32: FP64 vs FP32-bulk over --steps steps at --n^3 (KE/enstrophy every step); "
                          "ensemble: 48 uneven realisations, --steps steps per schedule")
     return ap.parse_args()
@@ -379,6 +380,9 @@ def run_ours(args, world, rank, local):
         del u3
     del u64_final
 
+    if not args.no_adjoint:
+        modes["adjoint"] = run_adjoint()
+
     if not args.no_ensemble:
         # batched ensemble of uneven grids (10 steps per schedule; the full 50-step run is
         # bench.py --study ensemble --steps 50)
@@ -400,6 +404,134 @@ def run_ours(args, world, rank, local):
                 "kernel_ms": {k: v[0] for k, v in ktimes.items()}, "clocks": clk, "modes": modes,
                 "final_stats": {"ke": float(st[-1, 5]), "enstrophy": float(st[-1, 6]), "status_ok": status_ok}}
         print(json.dumps(line), flush=True)
+
+
+ADJ_N, ADJ_STEPS, ADJ_EVERY, ADJ_MU, ADJ_CFL, ADJ_FD_DIRS, ADJ_FD_EPS = 64, 256, 16, 2.5e-4, 0.5, 8, 1e-6
+
+
+def fd_direction(u, seed: int):
+    """Seeded Gaussian direction, each field scaled to that field's RMS (the three momentum
+    components share the RMS of |rho v|, so that the zero w-momentum of the vortex is
+    perturbed too)."""
+    import numpy as np
+    g = np.random.default_rng(seed).normal(size=u.shape)
+    rms = lambda a: float(np.sqrt(np.mean(a * a)))
+    s_m = float(np.sqrt(np.mean(u[1] ** 2 + u[2] ** 2 + u[3] ** 2)))
+    scales = [rms(u[0]), s_m, s_m, s_m, rms(u[4])]
+    for v in range(5):
+        g[v] *= scales[v] / rms(g[v])
+    return g
+
+
+def run_adjoint(n: int = ADJ_N, nsteps: int = ADJ_STEPS, every: int = ADJ_EVERY, n_fd: int = ADJ_FD_DIRS,
+                oracle_steps: int = 16, kernel_sizes=(ADJ_N,)) -> dict:
+    """Gradient of the mean kinetic energy at step nsteps with respect to the initial
+    state of a Taylor-Green vortex (Re = 400: mu_eff = 2.5e-4 at Mach 0.1), by the
+    checkpointed reverse sweep; its cost against the forward path, central differences
+    of the GPU forward path along seeded directions, and the oracle's forward-mode
+    derivative over the first oracle_steps steps."""
+    import numpy as np
+    import torch
+    from oracle import dual_oracle as DO
+    from oracle import oracle as O
+    from paper_2211_16718_gb300 import inputs as I
+    from paper_2211_16718_gb300 import ns3d
+
+    u0 = I.taylor_green(n, v0=0.1)
+    s = ns3d.Solver(n, n, n, mu_eff=ADJ_MU)
+    ud = torch.from_numpy(u0.copy()).cuda()
+    dt = s.dt_from_cfl(ud, ADJ_CFL)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    # warm-up (kernels, adjoint buffers, checkpoints)
+    x = ud.clone()
+    s.traj_forward(x, dt, 4, 2)
+    g = torch.empty_like(x)
+    s.functional(x, "ke", grad=g, value=False)
+    s.traj_vjp(g)
+    torch.cuda.synchronize()
+
+    x = ud.clone()
+    ms_fwd = timed(lambda: s.rk_step(x, dt, nsteps))
+    x = ud.clone()
+    ms_rec = timed(lambda: s.traj_forward(x, dt, nsteps, every))
+    J, g = s.functional(x, "ke", grad=True)
+    ms_adj = timed(lambda: s.traj_vjp(g))
+    s.check()
+    grad = g.cpu().numpy()
+
+    def J_of(y):
+        xd = torch.from_numpy(y).cuda()
+        s.rk_step(xd, dt, nsteps)
+        return s.functional(xd, "ke")[0]
+
+    fd = []
+    for seed in range(n_fd):
+        w = fd_direction(u0, seed)
+        d_fd = (J_of(u0 + ADJ_FD_EPS * w) - J_of(u0 - ADJ_FD_EPS * w)) / (2 * ADJ_FD_EPS)
+        d_ad = float((grad * w).sum())
+        fd.append({"seed": seed, "fd": d_fd, "adjoint": d_ad, "rel_diff": abs(d_fd - d_ad) / abs(d_ad)})
+
+    # the oracle's forward-mode derivative of KE after oracle_steps steps along direction 0
+    w0 = fd_direction(u0, 0)
+    x = ud.clone()
+    s.traj_forward(x, dt, oracle_steps, every)
+    _, g2 = s.functional(x, "ke", grad=True)
+    s.traj_vjp(g2)
+    d_gpu = float((g2.cpu().numpy() * w0).sum())
+    DO.build()
+    DO.set_threads(os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    xN, dN = DO.rk_step_jvp(O.Params(n, n, n, mu_eff=ADJ_MU), u0, w0, dt, oracle_steps, "rk4")
+    d_or = float(DO.stats_jvp(O.Params(n, n, n, mu_eff=ADJ_MU), xN, dN)[1][5])
+    t_or = time.perf_counter() - t0
+
+    # kernel level: one RHS against one RHS vector-Jacobian product
+    kern = {}
+    for m in kernel_sizes:
+        um, mu_m = (I.taylor_green(m, v0=0.1), ADJ_MU) if m == n else hit_state(m)
+        sm = ns3d.Solver(m, m, m, mu_eff=mu_m)
+        a = torch.from_numpy(um).cuda()
+        lam = a.flip(1)  # any non-constant field (J^T applied to a constant is zero)
+        out = torch.empty_like(a)
+        for _ in range(3):
+            sm.rhs(a, out)
+            sm.rhs_vjp(a, lam, out)
+        reps = 10
+        ms_r = timed(lambda: [sm.rhs(a, out) for _ in range(reps)]) / reps
+        ms_v = timed(lambda: [sm.rhs_vjp(a, lam, out) for _ in range(reps)]) / reps
+        sm.timing_enable(True)
+        sm.rhs_vjp(a, lam, out)
+        kt = sm.timing_read()
+        sm.timing_enable(False)
+        kern[f"{m}^3"] = {"rhs_ms": ms_r, "rhs_vjp_ms": ms_v, "vjp_over_rhs": ms_v / ms_r,
+                          "rhs_vjp_gpts": m ** 3 / (ms_v * 1e-3) / 1e9,
+                          "vjp_kernel_ms": {k: v[0] for k, v in kt.items() if v[1] > 0}}
+        sm.close()
+        del a, lam, out
+    s.close()
+    errs = [f["rel_diff"] for f in fd]
+    return {"workload": f"Taylor-Green vortex {n}^3, Mach 0.1, mu_eff {ADJ_MU} (Re 400), RK4, dt at CFL "
+                        f"{ADJ_CFL}; J = mean kinetic energy at step {nsteps}; gradient w.r.t. the 5 initial fields",
+            "dt": dt, "steps": nsteps, "checkpoint_every": every, "J": J,
+            "forward_ms": ms_fwd, "forward_recorded_ms": ms_rec, "adjoint_ms": ms_adj,
+            "adjoint_over_forward": ms_adj / ms_fwd,
+            "adjoint_ms_per_step": ms_adj / nsteps, "forward_ms_per_step": ms_fwd / nsteps,
+            "fd_check": {"directions": n_fd, "eps": ADJ_FD_EPS,
+                         "direction": "seeded Gaussian, each field scaled to its RMS (momenta: RMS of |rho v|)",
+                         "max_rel_diff": max(errs), "median_rel_diff": statistics.median(errs), "per_direction": fd},
+            "oracle_check": {"steps": oracle_steps, "direction_seed": 0, "adjoint": d_gpu, "oracle_forward_mode": d_or,
+                             "rel_diff": abs(d_gpu - d_or) / abs(d_or), "oracle_seconds": t_or},
+            "kernels": kern}
 
 
 def run_study_fp32(args, local):
@@ -528,6 +660,34 @@ def main():
         return
     if args.study == "fp32":
         run_study_fp32(args, int(os.environ.get("LOCAL_RANK", "0")))
+        return
+    if args.study == "vjp":
+        # --steps K right-hand-side vector-Jacobian products of the --n^3 turbulence state
+        # (a small, fixed launch sequence for profilers)
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        from paper_2211_16718_gb300 import build as B
+        B.build()
+        from paper_2211_16718_gb300 import ns3d
+        u, mu = hit_state(args.n)
+        sv = ns3d.Solver(args.n, args.n, args.n, mu_eff=mu)
+        a = torch.from_numpy(u).cuda()
+        lam = a.flip(1)  # any non-constant field (J^T applied to a constant is zero)
+        out = torch.empty_like(a)
+        for _ in range(args.steps):
+            sv.rhs_vjp(a, lam, out)
+        sv.check()
+        torch.cuda.synchronize()
+        print(json.dumps({"study": "vjp", "n": args.n, "calls": args.steps,
+                          "out_maxabs": float(out.abs().max().item())}), flush=True)
+        sv.close()
+        return
+    if args.study == "adjoint":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        from paper_2211_16718_gb300 import build as B
+        B.build()
+        print(json.dumps({"study": "adjoint", "config4": run_adjoint(kernel_sizes=(ADJ_N, 256))}), flush=True)
         return
     if args.impl == "reference":
         # the oracle runs on the host of rank 0 only; other ranks exit without work
