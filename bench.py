@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk comparison run")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 48-instance ensemble measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (Taylor-Green 64^3) measurement")
-    ap.add_argument("--study", choices=["fp32", "ensemble", "adjoint", "vjp"], default=None,
+    ap.add_argument("--study", choices=["fp32", "ensemble", "adjoint", "vjp", "big"], default=None,
                     help="fp32: FP64 vs FP32-bulk over --steps steps at --n^3 (KE/enstrophy every step); "
                          "ensemble: 48 uneven realisations, --steps steps per schedule")
     return ap.parse_args()
@@ -534,6 +534,92 @@ def run_adjoint(n: int = ADJ_N, nsteps: int = ADJ_STEPS, every: int = ADJ_EVERY,
             "kernels": kern}
 
 
+def window_oracle_check(u_dev, rhs_dev, mu: float, n_sample: int, seed: int = 0) -> dict:
+    """Compare the GPU right-hand side at sampled points of an n^3 grid with the oracle
+    evaluated on the 11^3 periodic window centred on each point: the RHS at a point
+    reads the state within 4 points of it along the axes, so the window's own
+    periodic wrap never reaches the centre's stencil and the oracle's value is exact."""
+    import numpy as np
+    import torch
+    from oracle import oracle as O
+    n = u_dev.shape[-1]
+    r, w = 5, 11
+    h = 2 * math.pi / n
+    P = O.Params(w, w, w, lx=w * h, ly=w * h, lz=w * h, mu_eff=mu)
+    scale = float(rhs_dev.abs().max().item())
+    pts = np.random.default_rng(seed).integers(0, n, size=(n_sample, 3))
+    off = torch.arange(-r, r + 1, device=u_dev.device)
+    worst = 0.0
+    for i, j, k in pts:
+        iz, iy, ix = (off + int(k)) % n, (off + int(j)) % n, (off + int(i)) % n
+        win = u_dev[:, iz][:, :, iy][:, :, :, ix].cpu().numpy()
+        ref = O.rhs_points(P, win, [(r * w + r) * w + r])[0]
+        got = rhs_dev[:, int(k), int(j), int(i)].cpu().numpy()
+        worst = max(worst, float(np.abs(got - ref).max()) / scale)
+    return {"points": n_sample, "window": "11^3 periodic, centred", "max_rel_err": worst,
+            "normalisation": "max |R| over the whole grid (all 5 variables)"}
+
+
+def run_big(n: int, steps: int, cfl: float, n_sample: int = 24) -> dict:
+    """The decaying-turbulence problem on an n^3 grid (1024^3: 43 GB per state) with
+    SSP-RK3: storage chosen automatically (viscous fluxes one direction at a time when
+    the full scratch would not fit), one RHS checked against the oracle on sampled
+    windows, then timed steps with statistics every step."""
+    import numpy as np
+    import torch
+    from paper_2211_16718_gb300 import inputs as I
+    from paper_2211_16718_gb300 import ns3d
+    t0 = time.perf_counter()
+    u = I.isotropic_turbulence_device(n, seed=0)
+    torch.cuda.synchronize()
+    t_ic = time.perf_counter() - t0
+    torch.cuda.empty_cache()
+    mu = I.hit_mu_eff()
+    s = ns3d.Solver(n, n, n, mu_eff=mu, rk=ns3d.NS3D_SSPRK3)
+    info0 = s.storage_info()
+    rhs = torch.empty_like(u)
+    s.rhs(u, rhs)
+    s.check()
+    parity = window_oracle_check(u, rhs, mu, n_sample)
+    del rhs
+    torch.cuda.empty_cache()
+    dt = s.dt_from_cfl(u, cfl)
+    st0 = s.stats(u)
+    s.rk_step(u, dt, 1)  # allocates the stage states
+    torch.cuda.synchronize()
+    stats_buf = torch.zeros((steps, ns3d.NS3D_STATS_NDOUBLE), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    e0.record(stream)
+    for i in range(steps):
+        s.rk_step(u, dt, 1)
+        s.stats_async(u, stats_buf[i])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    st = stats_buf.cpu().numpy()
+    st1 = s.stats(u)
+    info1 = s.storage_info()
+    free_b, total_b = torch.cuda.mem_get_info()
+    s.close()
+    drift = {k: abs(st1[k] - st0[k]) / max(abs(st0[k]), 1e-300) for k in ("mass", "energy")}
+    drift["momentum_abs"] = max(abs(st1[k] - st0[k]) for k in ("momx", "momy", "momz"))
+    return {"workload": f"decaying isotropic turbulence {n}^3, FP64, SSP-RK3, dt at CFL {cfl}",
+            "grid": n, "steps": steps, "dt": dt, "gpts": n ** 3 * 3 * steps / (ms * 1e-3) / 1e9,
+            "ms_per_step": ms / steps, "rhs_per_step": 3,
+            "storage": "lean" if info1["storage"] == ns3d.NS3D_STORAGE_LEAN else "full",
+            "library_bytes_after_init": info0["device_bytes"], "library_bytes": info1["device_bytes"],
+            "state_bytes": 5 * 8 * n ** 3, "device_free_bytes": free_b, "device_total_bytes": total_b,
+            "ic_seconds": t_ic, "ic": "hit_velocity(64, seed 0) spectrally interpolated on the device",
+            "parity_rhs_sampled": parity, "conservation_drift": drift,
+            "ke": [float(st0["ke"])] + [float(x) for x in st[:, 5]],
+            "enstrophy": [float(st0["enstrophy"])] + [float(x) for x in st[:, 6]],
+            "status_ok": bool(np.all(st[:, 10] == 0)), "clocks": clk}
+
+
 def run_study_fp32(args, local):
     """FP64 path vs FP32-bulk mode on the decaying-turbulence workload: same initial state
     and dt, --steps RK4 steps each, KE and enstrophy logged every step on the device."""
@@ -660,6 +746,14 @@ def main():
         return
     if args.study == "fp32":
         run_study_fp32(args, int(os.environ.get("LOCAL_RANK", "0")))
+        return
+    if args.study == "big":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        from paper_2211_16718_gb300 import build as B
+        B.build()
+        n = args.n if args.n != 256 else 1024
+        print(json.dumps({"study": "big", "result": run_big(n, args.steps, args.cfl)}), flush=True)
         return
     if args.study == "vjp":
         # --steps K right-hand-side vector-Jacobian products of the --n^3 turbulence state

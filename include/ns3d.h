@@ -67,6 +67,14 @@ enum { NS3D_RK4 = 0, NS3D_SSPRK3 = 1 };           /* time integrators (Sec. 2.2)
  *                   FP32; state, RK accumulation and reductions in FP64.
  *  NS3D_FP64_STRICT every operation in FP64 (one FP64 division per reconstruction). */
 enum { NS3D_FP64 = 0, NS3D_FP32_BULK = 1, NS3D_FP64_STRICT = 2 };
+/* Storage of the viscous flux vectors (same results, bitwise, in every mode):
+ *  NS3D_STORAGE_FULL  all three directions' fluxes at once, 12*N doubles;
+ *  NS3D_STORAGE_LEAN  the flux of one direction before each direction pass, 4*N
+ *                     doubles (the gradients are evaluated three times): lets a
+ *                     1024^3 grid with SSP-RK3 fit in one GB300's HBM;
+ *  NS3D_STORAGE_AUTO  FULL if its scratch fits in the free device memory at
+ *                     ns3d_init with a 4 GB margin, else LEAN. */
+enum { NS3D_STORAGE_AUTO = 0, NS3D_STORAGE_FULL = 1, NS3D_STORAGE_LEAN = 2 };
 
 typedef struct ns3d_ctx ns3d_ctx;                 /* opaque; owned by the library */
 
@@ -81,6 +89,7 @@ typedef struct {
   double prandtl;       /* Prandtl number, default 0.72 (Sec. 2.1) */
   double weno_eps;      /* epsilon of the WENO weights, default 1e-6 (Sec. 2.2) */
   double harten_delta;  /* entropy-fix width as a fraction of the Roe sound speed, >= 0 */
+  int storage;          /* NS3D_STORAGE_AUTO (default), _FULL or _LEAN */
 } ns3d_params;
 
 /* Statistics of a state (all FP64 reductions over the grid). */
@@ -99,13 +108,15 @@ typedef struct {
 #define NS3D_STATS_NDOUBLE 12
 
 /* Fill *p with the paper's defaults for an nx x ny x nz grid on [0, 2pi)^3:
- * gamma 1.4, Pr 0.72, eps 1e-6, p = 2, harten_delta 0.1, mu_eff 0, RK4, FP64. */
+ * gamma 1.4, Pr 0.72, eps 1e-6, p = 2, harten_delta 0.1, mu_eff 0, RK4, FP64,
+ * NS3D_STORAGE_AUTO. */
 void ns3d_default_params(ns3d_params *p, int nx, int ny, int nz);
 
 /* Create a context: validates *p (NS3D_EINVAL), allocates the library-owned
  * device scratch (NS3D_ENOMEM): primitive variables 7*N, viscous fluxes 12*N
- * (only if mu_eff > 0), RHS accumulator 5*N, two RK stage states 10*N, RK
- * accumulator 5*N doubles, reduction partials and a status word.
+ * (4*N with NS3D_STORAGE_LEAN; none if mu_eff = 0), RHS accumulator 5*N doubles,
+ * reduction partials and a status word.  The first Runge-Kutta step allocates
+ * two stage states 10*N (and for RK4 an accumulator 5*N) doubles.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream). */
 int ns3d_init(const ns3d_params *p, void *cuda_stream, ns3d_ctx **out);
 
@@ -120,7 +131,8 @@ int ns3d_set_stream(ns3d_ctx *ctx, void *cuda_stream);
 int ns3d_rhs(ns3d_ctx *ctx, const double *u_dev, double *rhs_dev);
 
 /* Advance u_dev in place by nsteps (>= 0) steps of size dt (finite) with the
- * context's integrator (Sec. 2.2).  No host synchronisation. */
+ * context's integrator (Sec. 2.2).  No host synchronisation (except the first
+ * call, which allocates the stage buffers; NS3D_ENOMEM if they do not fit). */
 int ns3d_rk_step(ns3d_ctx *ctx, double *u_dev, double dt, int nsteps);
 
 /* Statistics of u_dev copied into *out_host; synchronises the stream.  Returns
@@ -222,6 +234,10 @@ const char *ns3d_batch_last_error(const ns3d_batch *b);
 
 /* Tile shape of the direction passes of a single context (see ns3d_batch_set_variant). */
 int ns3d_set_variant(ns3d_ctx *ctx, int variant);
+
+/* Storage chosen by ns3d_init (NS3D_STORAGE_FULL or NS3D_STORAGE_LEAN) and the
+ * library-owned device bytes the context holds now. */
+int ns3d_storage_info(const ns3d_ctx *ctx, int *storage, size_t *device_bytes);
 
 /* ---- adjoint (vector-Jacobian products) -----------------------------------------
  * Exact discrete adjoints of the operators above (the paper has none; they serve

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(THREADS) k_dir32(const DirArgs a) {
     if (a.fv != nullptr) {
       double* f = smd + OFF_FV / 2;
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) f[cc * NP * W + s] = __ldg(a.fv + (long long)(4 * D + cc) * N + p);
+      for (int cc = 0; cc < 4; ++cc) f[cc * NP * W + s] = __ldg(a.fv + (long long)(a.fv_dstride * D + cc) * N + p);
     }
   }
   __syncthreads();

@@ -149,7 +149,7 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
     if (a.fv != nullptr) {
       double* f = sm + PL::OFF_FV;
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) f[cc * NP * W + s] = ldx<NC>(a.fv + (long long)(4 * D + cc) * N + p);
+      for (int cc = 0; cc < 4; ++cc) f[cc * NP * W + s] = ldx<NC>(a.fv + (long long)(a.fv_dstride * D + cc) * N + p);
     }
   }
   __syncthreads();

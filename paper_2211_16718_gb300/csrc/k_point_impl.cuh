@@ -46,10 +46,12 @@ __device__ __forceinline__ double d4(double qm2, double qm1, double qp1, double 
 
 // Gradients of (u, v, w, T) at point p, then the three viscous flux vectors
 // f^v, g^v, h^v (Sec. 2.1 stresses with the symmetric strain rate, heat flux
-// q = -kappa grad T), written to fv[(4 d + c) N + p].
+// q = -kappa grad T), written to fv[(4 d + c) N + p]; with only_d >= 0 just the
+// flux along only_d, written to fv[c N + p] (same arithmetic, so the same bits).
 template <bool NC = true>
 __device__ __forceinline__ void visc_point(const double* __restrict__ pm, double* __restrict__ fv, int nx, int ny,
-                                           int nz, long long p, const double r12[3], double mu, double kappa) {
+                                           int nz, long long p, const double r12[3], double mu, double kappa,
+                                           int only_d = -1) {
   const long long N = (long long)nx * ny * nz;
   const int i = (int)(p % nx);
   const int j = (int)((p / nx) % ny);
@@ -77,14 +79,16 @@ __device__ __forceinline__ void visc_point(const double* __restrict__ pm, double
   const double tdiv = (2.0 / 3.0) * (G[0][0] + G[1][1] + G[2][2]);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
+    if (only_d >= 0 && d != only_d) continue;
+    const int b = (only_d >= 0) ? 0 : 4 * d;
     double tau[3];
 #pragma unroll
     for (int m = 0; m < 3; ++m) tau[m] = (m == d) ? mu * fma(2.0, G[d][d], -tdiv) : mu * (G[m][d] + G[d][m]);
     const double en = fma(vel[0], tau[0], fma(vel[1], tau[1], fma(vel[2], tau[2], kappa * G[3][d])));
-    fv[(long long)(4 * d + 0) * N + p] = tau[0];
-    fv[(long long)(4 * d + 1) * N + p] = tau[1];
-    fv[(long long)(4 * d + 2) * N + p] = tau[2];
-    fv[(long long)(4 * d + 3) * N + p] = en;
+    fv[(long long)(b + 0) * N + p] = tau[0];
+    fv[(long long)(b + 1) * N + p] = tau[1];
+    fv[(long long)(b + 2) * N + p] = tau[2];
+    fv[(long long)(b + 3) * N + p] = en;
   }
 }
 

@@ -35,11 +35,11 @@ __global__ void __launch_bounds__(PW_THREADS) k_prim(const double* __restrict__ 
 // Gradients of (u, v, w, T) at every point, then the three viscous flux vectors (body: visc_point).
 __global__ void __launch_bounds__(PW_THREADS) k_visc(const double* __restrict__ pm, double* __restrict__ fv,
                                                      int nx, int ny, int nz, double r12hx, double r12hy,
-                                                     double r12hz, double mu, double kappa) {
+                                                     double r12hz, double mu, double kappa, int only_d) {
   const long long N = (long long)nx * ny * nz;
   const double r12[3] = {r12hx, r12hy, r12hz};
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x)
-    visc_point(pm, fv, nx, ny, nz, p, r12, mu, kappa);
+    visc_point(pm, fv, nx, ny, nz, p, r12, mu, kappa, only_d);
 }
 
 // ---- FP32-bulk variants: same formulas in FP32, results widened to FP64 -----------
@@ -71,7 +71,7 @@ __device__ __forceinline__ float d4f(float qm2, float qm1, float qp1, float qp2,
 
 __global__ void __launch_bounds__(PW_THREADS) k_visc32(const double* __restrict__ pm, double* __restrict__ fv,
                                                        int nx, int ny, int nz, float r12hx, float r12hy,
-                                                       float r12hz, float mu, float kappa) {
+                                                       float r12hz, float mu, float kappa, int only_d) {
   const long long N = (long long)nx * ny * nz;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(p % nx);
@@ -102,14 +102,16 @@ __global__ void __launch_bounds__(PW_THREADS) k_visc32(const double* __restrict_
     const float tdiv = (2.0f / 3.0f) * (G[0][0] + G[1][1] + G[2][2]);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
+      if (only_d >= 0 && d != only_d) continue;
+      const int b = (only_d >= 0) ? 0 : 4 * d;
       float tau[3];
 #pragma unroll
       for (int m = 0; m < 3; ++m) tau[m] = (m == d) ? mu * fmaf(2.0f, G[d][d], -tdiv) : mu * (G[m][d] + G[d][m]);
       const float en = fmaf(vel[0], tau[0], fmaf(vel[1], tau[1], fmaf(vel[2], tau[2], kappa * G[3][d])));
-      fv[(long long)(4 * d + 0) * N + p] = f2d_bits(tau[0]);
-      fv[(long long)(4 * d + 1) * N + p] = f2d_bits(tau[1]);
-      fv[(long long)(4 * d + 2) * N + p] = f2d_bits(tau[2]);
-      fv[(long long)(4 * d + 3) * N + p] = f2d_bits(en);
+      fv[(long long)(b + 0) * N + p] = f2d_bits(tau[0]);
+      fv[(long long)(b + 1) * N + p] = f2d_bits(tau[1]);
+      fv[(long long)(b + 2) * N + p] = f2d_bits(tau[2]);
+      fv[(long long)(b + 3) * N + p] = f2d_bits(en);
     }
   }
 }
@@ -283,9 +285,11 @@ cudaError_t launch_prim(const Grid& g, const double* u, double* pm, double gamma
   return cudaGetLastError();
 }
 
-cudaError_t launch_visc(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s) {
+cudaError_t launch_visc(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s,
+                        int only_d) {
   k_visc<<<grid_for(g.N, PW_THREADS), PW_THREADS, 0, s>>>(pm, fv, g.n[0], g.n[1], g.n[2], 1.0 / (12.0 * g.h[0]),
-                                                          1.0 / (12.0 * g.h[1]), 1.0 / (12.0 * g.h[2]), mu, kappa);
+                                                          1.0 / (12.0 * g.h[1]), 1.0 / (12.0 * g.h[2]), mu, kappa,
+                                                          only_d);
   return cudaGetLastError();
 }
 
@@ -294,10 +298,11 @@ cudaError_t launch_prim32(const Grid& g, const double* u, double* pm, double gam
   return cudaGetLastError();
 }
 
-cudaError_t launch_visc32(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s) {
+cudaError_t launch_visc32(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s,
+                          int only_d) {
   k_visc32<<<grid_for(g.N, PW_THREADS), PW_THREADS, 0, s>>>(
       pm, fv, g.n[0], g.n[1], g.n[2], (float)(1.0 / (12.0 * g.h[0])), (float)(1.0 / (12.0 * g.h[1])),
-      (float)(1.0 / (12.0 * g.h[2])), (float)mu, (float)kappa);
+      (float)(1.0 / (12.0 * g.h[2])), (float)mu, (float)kappa, only_d);
   return cudaGetLastError();
 }
 

@@ -25,11 +25,8 @@ int adj_ready(ns3d_ctx* c) {
   const size_t words = ((size_t)AB_STATES * 5 + ADJ_SCRATCH_PLANES) * (size_t)c->g.N;
   cudaError_t e = prepare_adj_kernels();
   if (e != cudaSuccess) return cuda_fail(c, e, "adjoint kernel attributes");
-  if (cudaMalloc((void**)&c->adj, words * sizeof(double)) != cudaSuccess) {
-    cudaGetLastError();
-    c->adj = nullptr;
+  if (!dev_alloc(c, (void**)&c->adj, words * sizeof(double)))
     return set_err(c, NS3D_ENOMEM, "adjoint buffers (%zu bytes)", words * sizeof(double));
-  }
   return NS3D_OK;
 }
 
@@ -101,13 +98,14 @@ AdjArgs epi_args(int epi, double* gout, const double* ubs, double* lnext, double
 
 // ubar <- (d step(u0)/d u0)^T ubar for one step of the context's integrator.
 int rk_vjp_step(ns3d_ctx* c, const double* u0, double* ubar, double dt) {
+  int rc = ensure_stage_buffers(c);  // the RK4 stage epilogues also update the accumulator
+  if (rc) return rc;
   double* S2 = adj_buf(c, AB_S2);
   double* S3 = adj_buf(c, AB_S3);
   double* S4 = adj_buf(c, AB_S4);
   double* ubs = adj_buf(c, AB_UBS);
   double* La = adj_buf(c, AB_LA);
   double* Lb = adj_buf(c, AB_LB);
-  int rc;
   if (c->p.rk == NS3D_RK4) {
     // stage states, with the same launches (and so the same rounding) as the forward step
     if ((rc = rhs_pass(c, u0, EPI_RK4_FIRST, S2, u0, 0.5 * dt))) return rc;
@@ -132,14 +130,11 @@ int grow(ns3d_ctx* c, double** buf, int* cap, int states, const char* what) {
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "synchronise before reallocation");
   cudaFree(*buf);
+  c->bytes -= sizeof(double) * 5 * (size_t)c->g.N * (size_t)(*cap);
   *buf = nullptr;
   *cap = 0;
   const size_t bytes = sizeof(double) * 5 * (size_t)c->g.N * (size_t)states;
-  if (cudaMalloc((void**)buf, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    *buf = nullptr;
-    return set_err(c, NS3D_ENOMEM, "%s (%zu bytes)", what, bytes);
-  }
+  if (!dev_alloc(c, (void**)buf, bytes)) return set_err(c, NS3D_ENOMEM, "%s (%zu bytes)", what, bytes);
   *cap = states;
   return NS3D_OK;
 }

@@ -27,6 +27,7 @@ DirArgs base_args(ns3d_ctx* c, const double* u) {
   a.u = u;
   a.pm = c->pm;
   a.fv = (c->p.mu_eff > 0.0) ? c->fv : nullptr;
+  a.fv_dstride = c->lean ? 0 : 4;
   a.k = c->k;
   a.epi = EPI_ACC_WRITE;
   a.out = nullptr;
@@ -70,26 +71,31 @@ int rhs_pass(ns3d_ctx* c, const double* u, int epi, double* out, const double* u
                : launch_prim(c->g, u, c->pm, c->p.gamma, c->status, c->stream);
   }, "primitive kernel");
   if (rc) return rc;
-  if (c->p.mu_eff > 0.0) {
-    const double kappa = c->p.mu_eff / ((c->p.gamma - 1.0) * c->p.prandtl);
-    rc = timed(c, NS3D_K_VISC, [&] {
-      return f32 ? launch_visc32(c->g, c->pm, c->fv, c->p.mu_eff, kappa, c->stream)
-                 : launch_visc(c->g, c->pm, c->fv, c->p.mu_eff, kappa, c->stream);
+  const bool visc = c->p.mu_eff > 0.0;
+  const double kappa = visc ? c->p.mu_eff / ((c->p.gamma - 1.0) * c->p.prandtl) : 0.0;
+  // viscous fluxes of all directions (only_d < 0), or of direction only_d (lean storage)
+  auto visc_flux = [&](int only_d) {
+    return timed(c, NS3D_K_VISC, [&] {
+      return f32 ? launch_visc32(c->g, c->pm, c->fv, c->p.mu_eff, kappa, c->stream, only_d)
+                 : launch_visc(c->g, c->pm, c->fv, c->p.mu_eff, kappa, c->stream, only_d);
     }, "viscous-flux kernel");
+  };
+  if (visc && !c->lean && (rc = visc_flux(-1))) return rc;
+  DirArgs a = base_args(c, u);
+  static const int kid[3] = {NS3D_K_DIR_X, NS3D_K_DIR_Y, NS3D_K_DIR_Z};
+  static const char* what[3] = {"x-direction kernel", "y-direction kernel", "z-direction kernel"};
+  for (int d = 0; d < 3; ++d) {
+    if (visc && c->lean && (rc = visc_flux(d))) return rc;
+    a.epi = (d == 0) ? EPI_ACC_WRITE : (d == 1) ? EPI_ACC_ADD : epi;
+    if (d == 2) {
+      a.out = out;
+      a.un = un;
+      a.a = coef;
+    }
+    rc = timed(c, kid[d], [&] { return launch_dir(d, a, c->stream); }, what[d]);
     if (rc) return rc;
   }
-  DirArgs a = base_args(c, u);
-  a.epi = EPI_ACC_WRITE;
-  rc = timed(c, NS3D_K_DIR_X, [&] { return launch_dir(0, a, c->stream); }, "x-direction kernel");
-  if (rc) return rc;
-  a.epi = EPI_ACC_ADD;
-  rc = timed(c, NS3D_K_DIR_Y, [&] { return launch_dir(1, a, c->stream); }, "y-direction kernel");
-  if (rc) return rc;
-  a.epi = epi;
-  a.out = out;
-  a.un = un;
-  a.a = coef;
-  return timed(c, NS3D_K_DIR_Z, [&] { return launch_dir(2, a, c->stream); }, "z-direction kernel");
+  return NS3D_OK;
 }
 
 int stats_pass(ns3d_ctx* c, const double* u, double* out_dev) {
@@ -104,8 +110,18 @@ int stats_pass(ns3d_ctx* c, const double* u, double* out_dev) {
                "statistics final kernel");
 }
 
+int ensure_stage_buffers(ns3d_ctx* c) {
+  const size_t bytes = sizeof(double) * 5 * (size_t)c->g.N;
+  if (!c->ua && !dev_alloc(c, (void**)&c->ua, bytes)) return set_err(c, NS3D_ENOMEM, "RK stage state");
+  if (!c->ub && !dev_alloc(c, (void**)&c->ub, bytes)) return set_err(c, NS3D_ENOMEM, "RK stage state");
+  if (c->p.rk == NS3D_RK4 && !c->acc && !dev_alloc(c, (void**)&c->acc, bytes))
+    return set_err(c, NS3D_ENOMEM, "RK4 accumulator");
+  return NS3D_OK;
+}
+
 int rk_one_step(ns3d_ctx* c, double* u, double dt) {
-  int rc;
+  int rc = ensure_stage_buffers(c);
+  if (rc) return rc;
   if (c->p.rk == NS3D_RK4) {
     if ((rc = rhs_pass(c, u, EPI_RK4_FIRST, c->ua, u, 0.5 * dt))) return rc;
     if ((rc = rhs_pass(c, c->ua, EPI_RK4_MID, c->ub, u, 0.5 * dt))) return rc;
@@ -154,6 +170,8 @@ int validate(const ns3d_params* p, char* msg, size_t n) {
   if (p->rk != NS3D_RK4 && p->rk != NS3D_SSPRK3) return snprintf(msg, n, "unknown rk scheme"), NS3D_EINVAL;
   if (p->precision != NS3D_FP64 && p->precision != NS3D_FP64_STRICT && p->precision != NS3D_FP32_BULK)
     return snprintf(msg, n, "unsupported precision mode"), NS3D_EINVAL;
+  if (p->storage != NS3D_STORAGE_AUTO && p->storage != NS3D_STORAGE_FULL && p->storage != NS3D_STORAGE_LEAN)
+    return snprintf(msg, n, "unknown storage mode"), NS3D_EINVAL;
   if (p->precision == NS3D_FP64 && !(p->weno_eps >= 1e-15))
     return snprintf(msg, n, "weno_eps below 1e-15 needs NS3D_FP64_STRICT"), NS3D_EINVAL;
   return NS3D_OK;
@@ -221,28 +239,37 @@ int ns3d_init(const ns3d_params* p, void* cuda_stream, ns3d_ctx** out) {
     ns3d_free(c);
     return rc;
   }
+  const bool visc = p->mu_eff > 0.0;
+  if (p->storage == NS3D_STORAGE_LEAN) {
+    c->lean = 1;
+  } else if (p->storage == NS3D_STORAGE_AUTO && visc) {
+    // FULL unless its scratch (incl. stage states and accumulator) would not fit with a margin
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      cudaGetLastError();
+      free_b = 0;
+    }
+    const size_t full = sizeof(double) * N * (NPRIM + 5 + NVISC + 10 + (p->rk == NS3D_RK4 ? 5 : 0));
+    const size_t margin = (size_t)4 << 30;
+    c->lean = (free_b > 0 && full + margin > free_b) ? 1 : 0;
+  }
   struct {
     void** ptr;
     size_t bytes;
   } allocs[] = {
       {(void**)&c->pm, sizeof(double) * NPRIM * N},
       {(void**)&c->k, sizeof(double) * 5 * N},
-      {(void**)&c->ua, sizeof(double) * 5 * N},
-      {(void**)&c->ub, sizeof(double) * 5 * N},
-      {(void**)&c->acc, sizeof(double) * 5 * N},
       {(void**)&c->partials, sizeof(double) * 16 * (size_t)c->nstat_blocks},
       {(void**)&c->stats_dev, sizeof(double) * NS3D_STATS_NDOUBLE},
       {(void**)&c->status, sizeof(int)},
   };
   for (auto& a : allocs) {
-    if (cudaMalloc(a.ptr, a.bytes) != cudaSuccess) {
-      cudaGetLastError();
+    if (!dev_alloc(c, a.ptr, a.bytes)) {
       ns3d_free(c);
       return NS3D_ENOMEM;
     }
   }
-  if (p->mu_eff > 0.0 && cudaMalloc((void**)&c->fv, sizeof(double) * NVISC * N) != cudaSuccess) {
-    cudaGetLastError();
+  if (visc && !dev_alloc(c, (void**)&c->fv, sizeof(double) * (c->lean ? 4 : NVISC) * N)) {
     ns3d_free(c);
     return NS3D_ENOMEM;
   }
@@ -361,10 +388,8 @@ int ns3d_step_host(ns3d_ctx* c, double* u_host, double dt, int nsteps, ns3d_stat
   if (!u_host) return set_err(c, NS3D_EINVAL, "null host state");
   if (nsteps < 0 || !isfinite(dt)) return set_err(c, NS3D_EINVAL, "nsteps must be >= 0 and dt finite");
   const size_t bytes = sizeof(double) * 5 * (size_t)c->g.N;
-  if (!c->uhost_dev && cudaMalloc((void**)&c->uhost_dev, bytes) != cudaSuccess) {
-    cudaGetLastError();
+  if (!c->uhost_dev && !dev_alloc(c, (void**)&c->uhost_dev, bytes))
     return set_err(c, NS3D_ENOMEM, "device state for host stepping");
-  }
   cudaError_t e = cudaMemcpyAsync(c->uhost_dev, u_host, bytes, cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
   int rc = ns3d_rk_step(c, c->uhost_dev, dt, nsteps);
@@ -418,6 +443,13 @@ int ns3d_timing_read(ns3d_ctx* c, double* ms_out, long long* launches_out, int n
 int ns3d_set_variant(ns3d_ctx* c, int variant) {
   if (!c || variant < 0 || variant >= DIR_VARIANTS) return NS3D_EINVAL;
   c->variant = variant;
+  return NS3D_OK;
+}
+
+int ns3d_storage_info(const ns3d_ctx* c, int* storage, size_t* device_bytes) {
+  if (!c) return NS3D_EINVAL;
+  if (storage) *storage = c->lean ? NS3D_STORAGE_LEAN : NS3D_STORAGE_FULL;
+  if (device_bytes) *device_bytes = c->bytes;
   return NS3D_OK;
 }
 

@@ -294,6 +294,7 @@ int rebuild(ns3d_batch* b) {
         a.u = in.uin[s];
         a.pm = in.pm;
         a.fv = in.fv;
+        a.fv_dstride = 4;
         a.k = k;
         a.acc = acc;
         a.gamma = in.gamma;

@@ -32,6 +32,8 @@ struct ns3d_ctx {
   double* stats_host = nullptr;// pinned [NS3D_STATS_NDOUBLE]
   int nstat_blocks = 0;
   int variant = 0;             // tile-shape variant of the direction passes
+  int lean = 0;                // viscous fluxes one direction at a time ([4][N] instead of [12][N])
+  size_t bytes = 0;            // library-owned device bytes
   // adjoint (allocated on first use): RK stage states, incoming adjoint copy,
   // two stage-adjoint buffers, viscous-adjoint scratch [16][N]
   double* adj = nullptr;
@@ -96,6 +98,19 @@ int timed(ns3d_ctx* c, int kid, F&& fn, const char* what) {
   return NS3D_OK;
 }
 
+// cudaMalloc counted in c->bytes; false (and a cleared CUDA error) if it fails.
+inline bool dev_alloc(ns3d_ctx* c, void** p, size_t bytes) {
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return false;
+  }
+  c->bytes += bytes;
+  return true;
+}
+
+// Allocate the Runge-Kutta stage states (and the RK4 accumulator) on first use (ns3d_api.cu).
+int ensure_stage_buffers(ns3d_ctx* c);
 // One right-hand-side evaluation of u with the given z-pass epilogue (ns3d_api.cu).
 int rhs_pass(ns3d_ctx* c, const double* u, int epi, double* out, const double* un, double coef);
 // Statistics of u into out_dev[NS3D_STATS_NDOUBLE] (ns3d_api.cu).

@@ -41,6 +41,7 @@ struct DirArgs {
   const double* u;   // stage input state [5][N]
   const double* pm;  // primitives of u [NPRIM][N]
   const double* fv;  // viscous fluxes [NVISC][N] or nullptr (inviscid)
+  int fv_dstride;    // planes per direction in fv: 4 ([12][N], all directions) or 0 ([4][N], this direction)
   double* k;         // RHS accumulator [5][N]
   int epi;           // Epi
   double* out;       // EPI_RHS_OUT: destination; RK modes: next stage state
@@ -60,10 +61,13 @@ struct DirArgs {
 
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_prim(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s);
-cudaError_t launch_visc(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s);
+// only_d < 0: all three viscous flux vectors into fv[12][N]; only_d = d: the flux along d into fv[4][N]
+cudaError_t launch_visc(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s,
+                        int only_d = -1);
 // FP32-bulk variants (FP32 arithmetic, results widened to FP64)
 cudaError_t launch_prim32(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s);
-cudaError_t launch_visc32(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s);
+cudaError_t launch_visc32(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s,
+                          int only_d = -1);
 cudaError_t prepare_dir_kernels();  // per device, before the first launch
 cudaError_t launch_dir(int d, const DirArgs& a, cudaStream_t s);  // dispatches on a.mode, a.variant
 void dir_tile_shape(int mode, int variant, int* tp, int* w);      // points x lines of a tile

@@ -192,3 +192,40 @@ def isotropic_turbulence(n: int, seed: int, u0: float = 0.3, k0: float = 4.0,
 def hit_mu_eff(u0: float = 0.3, k0: float = 4.0, re_lambda: float = 50.0, rho: float = 1.0) -> float:
     """mu_eff = rho u0 lambda / Re_lambda with the Taylor microscale of E(k): lambda = 2/k0."""
     return rho * u0 * (2.0 / k0) / re_lambda
+
+
+def isotropic_turbulence_device(n: int, seed: int, nbase: int = 64, u0: float = 0.3, k0: float = 4.0,
+                                gamma: float = GAMMA, device: str = "cuda"):
+    """The decaying-turbulence initial state on an n^3 grid built directly in device
+    memory (a torch float64 tensor [5, n, n, n]), for grids whose host-side generation
+    would take too long or too much host memory (1024^3: 43 GB per state).
+
+    The velocity is hit_velocity(nbase, seed) interpolated spectrally to n^3: its
+    Fourier coefficients (all shells below nbase/2, Nyquist zero) are zero-padded and
+    inverse-transformed on the device, so the n^3 field is the same band-limited field
+    sampled more finely.  The spectrum E(k) of Sec. 2.3 carries a fraction below
+    exp(-2 (nbase/(2 k0))^2) (~1e-56 for nbase = 64, k0 = 4) of its energy beyond
+    shell nbase/2, so this is the n^3 realisation up to that truncation.  The RMS
+    normalisation of hit_velocity carries over exactly (Parseval on both grids).
+    torch (FFT on the device) is used for input generation only."""
+    import torch
+    if n < nbase:
+        raise ValueError("n must be >= nbase")
+    vel = hit_velocity(nbase, seed, u0, k0)
+    scale = (n / nbase) ** 3
+    h = nbase // 2
+    out = torch.empty((5, n, n, n), dtype=torch.float64, device=device)
+    out[0].fill_(1.0)
+    for c in range(3):
+        small = torch.fft.rfftn(torch.from_numpy(np.ascontiguousarray(vel[c])).to(device))  # [nb, nb, nb/2+1]
+        big = torch.zeros((n, n, n // 2 + 1), dtype=torch.complex128, device=device)
+        # fftfreq order: indices 0..h-1 are k = 0..h-1, h..nb-1 are k = -h..-1 (k = -h is Nyquist, zero)
+        for zs, zd in ((slice(0, h), slice(0, h)), (slice(h, nbase), slice(n - h, n))):
+            for ys, yd in ((slice(0, h), slice(0, h)), (slice(h, nbase), slice(n - h, n))):
+                big[zd, yd, : h + 1] = small[zs, ys, : h + 1] * scale
+        del small
+        out[1 + c] = torch.fft.irfftn(big, s=(n, n, n))
+        del big
+    p = 1.0 / gamma
+    out[4] = p / (gamma - 1.0) + 0.5 * (out[1] * out[1] + out[2] * out[2] + out[3] * out[3])
+    return out

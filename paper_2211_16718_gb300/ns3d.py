@@ -19,6 +19,7 @@ NS3D_OK, NS3D_EINVAL, NS3D_ENOMEM, NS3D_ECUDA, NS3D_ENONPHYSICAL, NS3D_ETIMEOUT 
 NS3D_ERANGE = -6
 NS3D_RK4, NS3D_SSPRK3 = 0, 1
 NS3D_FP64, NS3D_FP32_BULK, NS3D_FP64_STRICT = 0, 1, 2
+NS3D_STORAGE_AUTO, NS3D_STORAGE_FULL, NS3D_STORAGE_LEAN = 0, 1, 2
 NS3D_STATS_NDOUBLE = 12
 KERNELS = ("prim", "visc", "dir_x", "dir_y", "dir_z", "stats", "stats_final", "adj_visc", "adj_dir", "adj_misc")
 NS3D_FUNC_KE, NS3D_FUNC_ENSTROPHY = 0, 1
@@ -26,7 +27,7 @@ FUNCTIONALS = {"ke": NS3D_FUNC_KE, "enstrophy": NS3D_FUNC_ENSTROPHY}
 EXPORTS = ("ns3d_default_params", "ns3d_init", "ns3d_free", "ns3d_set_stream", "ns3d_rhs", "ns3d_rk_step",
            "ns3d_stats", "ns3d_stats_async", "ns3d_step_host", "ns3d_check", "ns3d_strerror", "ns3d_last_error",
            "ns3d_timing_enable", "ns3d_timing_read", "ns3d_alu_probe", "ns3d_rhs_vjp", "ns3d_rk_step_vjp",
-           "ns3d_functional", "ns3d_traj_forward", "ns3d_traj_vjp")
+           "ns3d_functional", "ns3d_traj_forward", "ns3d_traj_vjp", "ns3d_storage_info")
 
 
 class Ns3dError(RuntimeError):
@@ -46,6 +47,7 @@ class CParams(ctypes.Structure):
         ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
         ("gamma", ctypes.c_double), ("mu_eff", ctypes.c_double), ("prandtl", ctypes.c_double),
         ("weno_eps", ctypes.c_double), ("harten_delta", ctypes.c_double),
+        ("storage", ctypes.c_int),
     ]
 
 
@@ -93,6 +95,7 @@ def lib():
                 "ns3d_functional": (I, [P, P, I, P, P]),
                 "ns3d_traj_forward": (I, [P, P, D, I, I]),
                 "ns3d_traj_vjp": (I, [P, P]),
+                "ns3d_storage_info": (I, [P, P, P]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -239,6 +242,12 @@ class Solver:
         self._sync_stream()
         self._check(lib().ns3d_traj_vjp(self._ctx, _dptr(ubar, 5 * self.N)))
         return ubar
+
+    def storage_info(self) -> dict:
+        """{"storage": NS3D_STORAGE_FULL | NS3D_STORAGE_LEAN, "device_bytes": library-owned bytes}"""
+        st, nb = ctypes.c_int(), ctypes.c_size_t()
+        self._check(lib().ns3d_storage_info(self._ctx, ctypes.byref(st), ctypes.byref(nb)))
+        return {"storage": st.value, "device_bytes": nb.value}
 
     def timing_enable(self, on: bool = True):
         self._check(lib().ns3d_timing_enable(self._ctx, int(bool(on))))

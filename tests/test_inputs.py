@@ -91,3 +91,20 @@ def test_vortex_is_periodic_to_roundoff():
     edge = u[:, :, :, 0]
     free = I.uniform(1, 64, 1, rho=1.0, u=0.5, v=0.25)[:, :, :, 0]
     assert np.abs(edge - free).max() < 1e-13
+
+
+def test_device_turbulence_is_the_spectral_interpolant_of_the_base_grid():
+    """The n^3 field built on the device (here on the CPU) takes the base-grid field's values
+    at the coincident points and keeps its RMS and zero divergence."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    from paper_2211_16718_gb300 import inputs as I
+    u = I.isotropic_turbulence_device(48, seed=5, nbase=16, device="cpu").numpy()
+    base = I.isotropic_turbulence(16, seed=5)
+    assert np.abs(u[:, ::3, ::3, ::3] - base).max() <= 1e-14
+    rms = np.sqrt((u[1] ** 2 + u[2] ** 2 + u[3] ** 2).mean() / 3)
+    assert abs(rms - 0.3) <= 1e-14
+    k = np.fft.fftfreq(48, d=1.0 / 48)
+    div = sum(np.fft.ifftn(1j * k.reshape(sh) * np.fft.fftn(u[1 + c])).real
+              for c, sh in enumerate([(1, 1, 48), (1, 48, 1), (48, 1, 1)]))
+    assert np.abs(div).max() <= 1e-12

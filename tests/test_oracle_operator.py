@@ -243,3 +243,25 @@ def test_cfl_reading_matches_paper_128_dt(oracle):
     st = oracle.stats(oracle.Params(n, n, n), u)
     cfl = 0.025 * st["max_wavespeed_over_dx"]
     assert 0.7 < cfl < 1.3
+
+
+def test_rhs_at_a_point_is_local_to_an_11_cube_window(oracle):
+    """The right-hand side at a point depends only on the state within 4 points along
+    the axes, so evaluating it on the 11^3 periodic window centred on the point gives the
+    full-grid value bitwise (the basis of the sampled parity checks on grids the oracle
+    cannot hold)."""
+    import numpy as np
+    from paper_2211_16718_gb300 import inputs as I
+    n = 20
+    u = I.isotropic_turbulence(n, seed=4)
+    mu = I.hit_mu_eff()
+    P = oracle.Params(n, n, n, mu_eff=mu)
+    full = oracle.rhs(P, u)
+    r, w = 5, 11
+    h = 2 * np.pi / n
+    Pw = oracle.Params(w, w, w, lx=w * h, ly=w * h, lz=w * h, mu_eff=mu)
+    for (i, j, k) in [(0, 0, 0), (3, 17, 9), (19, 5, 12)]:
+        iz, iy, ix = [(np.arange(-r, r + 1) + c) % n for c in (k, j, i)]
+        win = np.ascontiguousarray(u[:, iz][:, :, iy][:, :, :, ix])
+        got = oracle.rhs_points(Pw, win, [(r * w + r) * w + r])[0]
+        assert np.array_equal(got, full[:, k, j, i])
