@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-strict", action="store_true", help="skip the all-FP64 comparison run")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk comparison run")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 48-instance ensemble measurement")
+    ap.add_argument("--precision", choices=["fp64", "strict"], default="fp64",
+                    help="context precision of --study vjp (NS3D_FP64 or NS3D_FP64_STRICT)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (Taylor-Green 64^3) measurement")
     ap.add_argument("--study", choices=["fp32", "ensemble", "adjoint", "vjp", "big"], default=None,
                     help="fp32: FP64 vs FP32-bulk over --steps steps at --n^3 (KE/enstrophy every step); "
@@ -764,7 +766,8 @@ def main():
         B.build()
         from paper_2211_16718_gb300 import ns3d
         u, mu = hit_state(args.n)
-        sv = ns3d.Solver(args.n, args.n, args.n, mu_eff=mu)
+        prec = ns3d.NS3D_FP64_STRICT if args.precision == "strict" else ns3d.NS3D_FP64
+        sv = ns3d.Solver(args.n, args.n, args.n, mu_eff=mu, precision=prec)
         a = torch.from_numpy(u).cuda()
         lam = a.flip(1)  # any non-constant field (J^T applied to a constant is zero)
         out = torch.empty_like(a)

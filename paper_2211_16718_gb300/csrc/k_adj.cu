@@ -31,6 +31,7 @@
 // adjoint of u through u_k = m_k/rho, T = gamma (gamma - 1)(e/rho - |m|^2/(2 rho^2)).
 #include <math.h>
 
+#include "df.cuh"
 #include "k_dir_common.cuh"
 #include "k_point_impl.cuh"
 #include "ns3d_internal.cuh"
@@ -136,10 +137,11 @@ __device__ __forceinline__ void weno_adjoint(double q0, double q1, double q2, do
 }
 
 // |lambda| with Harten's fix (acoustic fields): value and derivatives d/dlambda, d/ddelta.
+template <bool FAST>
 __device__ __forceinline__ double harten(double lam, double delta, double& dl, double& dd) {
   const double a = fabs(lam);
   if (a < delta) {
-    const double rd = 1.0 / delta;
+    const double rd = FAST ? rcp_newton(delta) : 1.0 / delta;
     dl = lam * rd;
     dd = 0.5 - 0.5 * (lam * rd) * (lam * rd);
     return 0.5 * (lam * lam + delta * delta) * rd;
@@ -147,6 +149,155 @@ __device__ __forceinline__ double harten(double lam, double delta, double& dl, d
   dl = (lam > 0.0) ? 1.0 : (lam < 0.0 ? -1.0 : 0.0);
   dd = 0.0;
   return a;
+}
+
+// Adjoint of the Roe flux at one interface (Sec. 2.2, Eq. Roe, with the wave-strength
+// algebra of the forward pass): given du = u^R - u^L, Lh = adjoint of the interface flux,
+// and the two point states a = i, b = i+1 (sqrt(rho), velocity, H, rho, e), returns
+// dub = adjoint of du and ga, gb = adjoint of the conserved states a, b through the Roe
+// average.  FAST: FP32-seeded Newton reciprocals instead of IEEE division and square
+// root (FP64-accurate).  Returns 1 for a non-physical Roe state, 2 for values outside the
+// range of the Newton seeds.
+template <int D, bool FAST>
+__device__ __forceinline__ int roe_adjoint(const double du[5], const double Lh[5], double ra, double rb,
+                                           const double Va[3], const double Vb[3], double Ha, double Hb,
+                                           double rho_a, double e_a, double rho_b, double e_b, double gamma,
+                                           double hdelta, double dub[5], double ga[5], double gb[5]) {
+  constexpr int T1 = (D == 0) ? 1 : 0;
+  constexpr int T2 = (D == 2) ? 1 : 2;
+  const double gm1 = gamma - 1.0;
+  const double rsum = ra + rb;
+  const double rs = FAST ? rcp_newton(rsum) : 1.0 / rsum;
+  const double wa = ra * rs, wb = rb * rs;
+  double V[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) V[m] = fma(wa, Va[m], wb * Vb[m]);
+  const double H = fma(wa, Ha, wb * Hb);
+  const double q2h = 0.5 * fma(V[0], V[0], fma(V[1], V[1], V[2] * V[2]));
+  const double c2 = gm1 * (H - q2h);
+  int flags = !(c2 > 0.0) ? 1 : 0;
+  double c, rc;
+  if (FAST) {
+    // the float seeds of the Newton reciprocals need these inside the float range
+    flags |= (c2 > 1e-36 && c2 < 1e36 && rsum > 1e-36 && rsum < 1e36 && rho_a > 1e-36 && rho_a < 1e36 &&
+              rho_b > 1e-36 && rho_b < 1e36) ? 0 : 2;
+    rc = rsqrt_newton(c2);
+    c = c2 * rc;
+  } else {
+    c = sqrt(c2);
+    rc = 1.0 / c;
+  }
+  const double un = V[D], vt1 = V[T1], vt2 = V[T2];
+  const double b1 = gm1 * (rc * rc);
+  const double vdm = fma(V[0], du[1], fma(V[1], du[2], V[2] * du[3]));
+  const double Y = fma(q2h, du[0], du[4]) - vdm;
+  const double phi = b1 * Y;
+  const double X = fma(un, du[0], -du[1 + D]);
+  const double ach = 0.5 * (X * rc);
+  const double a2 = du[0] - phi;
+  const double a3 = fma(-vt1, du[0], du[1 + T1]);
+  const double a4 = fma(-vt2, du[0], du[1 + T2]);
+  const double a1 = 0.5 * phi + ach, a5 = 0.5 * phi - ach;
+  const double delta = hdelta * c;
+  double dl1, dd1, dl5, dd5;
+  const double l1 = harten<FAST>(un - c, delta, dl1, dd1);
+  const double l5 = harten<FAST>(un + c, delta, dl5, dd5);
+  const double l2 = fabs(un);
+  const double sg2 = (un > 0.0) ? 1.0 : (un < 0.0 ? -1.0 : 0.0);
+  const double A1 = l1 * a1, A2 = l2 * a2, A3 = l2 * a3, A4 = l2 * a4, A5 = l5 * a5;
+  const double S = A1 + A5, d0 = S + A2, cD = c * (A5 - A1);
+  // backward: Dbar = adjoint of the dissipation vector = -Lhat/2
+  double Db[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Db[v] = -0.5 * Lh[v];
+  const double d0b = fma(Db[1 + D], un, fma(Db[1 + T1], vt1, fma(Db[1 + T2], vt2, Db[0])));
+  const double cDb = fma(Db[4], un, Db[1 + D]);
+  const double Sb = fma(Db[4], H, d0b);
+  const double A2b = fma(Db[4], q2h, d0b);
+  const double A3b = fma(Db[4], vt1, Db[1 + T1]);
+  const double A4b = fma(Db[4], vt2, Db[1 + T2]);
+  const double A1b = fma(-c, cDb, Sb), A5b = fma(c, cDb, Sb);
+  double unb = fma(Db[1 + D], d0, Db[4] * cD);
+  double vt1b = fma(Db[1 + T1], d0, Db[4] * A3);
+  double vt2b = fma(Db[1 + T2], d0, Db[4] * A4);
+  double Hbar = Db[4] * S;
+  double q2hb = Db[4] * A2;
+  double cb = cDb * (A5 - A1);
+  // A_k = l_k a_k
+  const double a1b = A1b * l1, a2b = A2b * l2, a3b = A3b * l2, a4b = A4b * l2, a5b = A5b * l5;
+  const double l1b = A1b * a1, l5b = A5b * a5;
+  const double l2b = fma(A2b, a2, fma(A3b, a3, A4b * a4));
+  unb = fma(dl1, l1b, fma(dl5, l5b, fma(sg2, l2b, unb)));
+  cb = fma(-dl1, l1b, fma(dl5, l5b, fma(hdelta, fma(dd1, l1b, dd5 * l5b), cb)));
+  // wave strengths
+  const double phib = fma(0.5, a1b + a5b, -a2b);
+  const double achb = a1b - a5b;
+  dub[0] = fma(-vt1, a3b, fma(-vt2, a4b, a2b));
+  dub[1 + T1] = a3b;
+  dub[1 + T2] = a4b;
+  dub[1 + D] = 0.0;
+  dub[4] = 0.0;
+  vt1b = fma(-a3b, du[0], vt1b);
+  vt2b = fma(-a4b, du[0], vt2b);
+  const double Xb = 0.5 * rc * achb;
+  double rcb = 0.5 * X * achb;
+  unb = fma(Xb, du[0], unb);
+  dub[0] = fma(Xb, un, dub[0]);
+  dub[1 + D] -= Xb;
+  const double b1b = phib * Y;
+  const double Yb = phib * b1;
+  q2hb = fma(Yb, du[0], q2hb);
+  dub[0] = fma(Yb, q2h, dub[0]);
+  dub[4] += Yb;
+  double Vbar[3];
+  Vbar[D] = unb;
+  Vbar[T1] = vt1b;
+  Vbar[T2] = vt2b;
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    Vbar[m] = fma(-Yb, du[1 + m], Vbar[m]);  // vdm = V . du_m
+    dub[1 + m] = fma(-Yb, V[m], dub[1 + m]);
+  }
+  rcb = fma(b1b, 2.0 * gm1 * rc, rcb);
+  cb = fma(-rcb, rc * rc, cb);
+  // c = sqrt(gm1 (H - q2h))
+  const double c2b = 0.5 * cb * rc;
+  Hbar = fma(gm1, c2b, Hbar);
+  q2hb = fma(-gm1, c2b, q2hb);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) Vbar[m] = fma(q2hb, V[m], Vbar[m]);
+  // Roe average of the point states a, b
+  double rab = Hbar * (Ha - H), rbb = Hbar * (Hb - H);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    rab = fma(Vbar[m], Va[m] - V[m], rab);
+    rbb = fma(Vbar[m], Vb[m] - V[m], rbb);
+  }
+  rab *= rs;
+  rbb *= rs;
+  // point primitives: V = m/rho, H = gamma e/rho - gm1 |V|^2/2, sqrt(rho)
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const double wgt = side ? wb : wa;
+    const double* Vp = side ? Vb : Va;
+    const double rho = side ? rho_b : rho_a, e = side ? e_b : e_a, sr = side ? rb : ra;
+    const double rr = FAST ? rcp_newton(rho) : 1.0 / rho;
+    const double Hb_ = wgt * Hbar;
+    const double srb = side ? rbb : rab;
+    double Vt[3], vdot = 0.0;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      Vt[m] = fma(-Hb_ * gm1, Vp[m], wgt * Vbar[m]);
+      vdot = fma(Vt[m], Vp[m], vdot);
+    }
+    double* gs = side ? gb : ga;
+    gs[4] = Hb_ * gamma * rr;
+    // d sqrt(rho)/d rho = 1/(2 sqrt(rho)) = sqrt(rho) / (2 rho)
+    gs[0] = fma(0.5 * srb, sr * rr, -fma(Hb_ * gamma, e * rr, vdot) * rr);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) gs[1 + m] = Vt[m] * rr;
+  }
+  return flags;
 }
 
 __device__ __forceinline__ void adj_epilogue(const AdjArgs& a, long long p, const double cv[5]) {
@@ -213,8 +364,6 @@ __global__ void __launch_bounds__(APL::THREADS, 2) k_adj_dir(const AdjArgs a) {
   extern __shared__ double sm[];
   constexpr int TP = APL::TP, NP = APL::NP, NI = APL::NI, W = APL::W;
   constexpr int AX = (D == 0) ? 1 : 0;
-  constexpr int T1 = (D == 0) ? 1 : 0;
-  constexpr int T2 = (D == 2) ? 1 : 2;
   const int nD = a.g.n[D];
   const int na = a.g.n[AX];
   const long long N = a.g.N;
@@ -299,142 +448,24 @@ __global__ void __launch_bounds__(APL::THREADS, 2) k_adj_dir(const AdjArgs a) {
         du[v] = rec[(2 * v + 1) * NI * W + o] - rec[(2 * v) * NI * W + o];
         Lh[v] = (lm[v * NP * W + sb] - lm[v * NP * W + sa]) * rdx;
       }
-      // forward: Roe average of the two point states, eigen-decomposition of the dissipation
-      const double ra = ri[sa], rb = ri[sb];
-      const double rsum = ra + rb;
-      const double rs = 1.0 / rsum;
-      const double wa = ra * rs, wb = rb * rs;
-      double Va[3], Vb[3], V[3];
+      double Va[3], Vb[3];
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
         Va[m] = ri[(1 + m) * NP * W + sa];
         Vb[m] = ri[(1 + m) * NP * W + sb];
-        V[m] = fma(wa, Va[m], wb * Vb[m]);
       }
-      const double Ha = ri[4 * NP * W + sa], Hb = ri[4 * NP * W + sb];
-      const double H = fma(wa, Ha, wb * Hb);
-      const double q2h = 0.5 * fma(V[0], V[0], fma(V[1], V[1], V[2] * V[2]));
-      const double c2 = gm1 * (H - q2h);
-      bad |= !(c2 > 0.0);
-      const double c = sqrt(c2);
-      const double rc = 1.0 / c;
-      const double un = V[D], vt1 = V[T1], vt2 = V[T2];
-      const double b1 = gm1 * (rc * rc);
-      const double vdm = fma(V[0], du[1], fma(V[1], du[2], V[2] * du[3]));
-      const double Y = fma(q2h, du[0], du[4]) - vdm;
-      const double phi = b1 * Y;
-      const double X = fma(un, du[0], -du[1 + D]);
-      const double ach = 0.5 * (X * rc);
-      const double a2 = du[0] - phi;
-      const double a3 = fma(-vt1, du[0], du[1 + T1]);
-      const double a4 = fma(-vt2, du[0], du[1 + T2]);
-      const double a1 = 0.5 * phi + ach, a5 = 0.5 * phi - ach;
-      const double delta = a.hdelta * c;
-      double dl1, dd1, dl5, dd5;
-      const double l1 = harten(un - c, delta, dl1, dd1);
-      const double l5 = harten(un + c, delta, dl5, dd5);
-      const double l2 = fabs(un);
-      const double sg2 = (un > 0.0) ? 1.0 : (un < 0.0 ? -1.0 : 0.0);
-      const double A1 = l1 * a1, A2 = l2 * a2, A3 = l2 * a3, A4 = l2 * a4, A5 = l5 * a5;
-      const double S = A1 + A5, d0 = S + A2, cD = c * (A5 - A1);
-      // backward: Dbar = adjoint of the dissipation vector = -Lhat/2
-      double Db[5];
+      double dub[5], ga[5], gb[5];
+      bad |= roe_adjoint<D, false>(du, Lh, ri[sa], ri[sb], Va, Vb, ri[4 * NP * W + sa], ri[4 * NP * W + sb], q[sa],
+                                   q[4 * NP * W + sa], q[sb], q[4 * NP * W + sb], a.gamma, a.hdelta, dub, ga, gb);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) Db[v] = -0.5 * Lh[v];
-      const double d0b = fma(Db[1 + D], un, fma(Db[1 + T1], vt1, fma(Db[1 + T2], vt2, Db[0])));
-      const double cDb = fma(Db[4], un, Db[1 + D]);
-      const double Sb = fma(Db[4], H, d0b);
-      const double A2b = fma(Db[4], q2h, d0b);
-      const double A3b = fma(Db[4], vt1, Db[1 + T1]);
-      const double A4b = fma(Db[4], vt2, Db[1 + T2]);
-      const double A1b = fma(-c, cDb, Sb), A5b = fma(c, cDb, Sb);
-      double unb = fma(Db[1 + D], d0, Db[4] * cD);
-      double vt1b = fma(Db[1 + T1], d0, Db[4] * A3);
-      double vt2b = fma(Db[1 + T2], d0, Db[4] * A4);
-      double Hbar = Db[4] * S;
-      double q2hb = Db[4] * A2;
-      double cb = cDb * (A5 - A1);
-      // A_k = l_k a_k
-      const double a1b = A1b * l1, a2b = A2b * l2, a3b = A3b * l2, a4b = A4b * l2, a5b = A5b * l5;
-      const double l1b = A1b * a1, l5b = A5b * a5;
-      const double l2b = fma(A2b, a2, fma(A3b, a3, A4b * a4));
-      unb = fma(dl1, l1b, fma(dl5, l5b, fma(sg2, l2b, unb)));
-      cb = fma(-dl1, l1b, fma(dl5, l5b, fma(a.hdelta, fma(dd1, l1b, dd5 * l5b), cb)));
-      // wave strengths
-      const double phib = fma(0.5, a1b + a5b, -a2b);
-      const double achb = a1b - a5b;
-      double dub[5];
-      dub[0] = fma(-vt1, a3b, fma(-vt2, a4b, a2b));
-      dub[1 + T1] = a3b;
-      dub[1 + T2] = a4b;
-      dub[1 + D] = 0.0;
-      dub[4] = 0.0;
-      vt1b = fma(-a3b, du[0], vt1b);
-      vt2b = fma(-a4b, du[0], vt2b);
-      const double Xb = 0.5 * rc * achb;
-      double rcb = 0.5 * X * achb;
-      unb = fma(Xb, du[0], unb);
-      dub[0] = fma(Xb, un, dub[0]);
-      dub[1 + D] -= Xb;
-      const double b1b = phib * Y;
-      const double Yb = phib * b1;
-      q2hb = fma(Yb, du[0], q2hb);
-      dub[0] = fma(Yb, q2h, dub[0]);
-      dub[4] += Yb;
-      double Vbar[3];
-      Vbar[D] = unb;
-      Vbar[T1] = vt1b;
-      Vbar[T2] = vt2b;
-#pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        Vbar[m] = fma(-Yb, du[1 + m], Vbar[m]);  // vdm = V . du_m
-        dub[1 + m] = fma(-Yb, V[m], dub[1 + m]);
-      }
-      rcb = fma(b1b, 2.0 * gm1 * rc, rcb);
-      cb = fma(-rcb, rc * rc, cb);
-      // c = sqrt(gm1 (H - q2h))
-      const double c2b = 0.5 * cb * rc;
-      Hbar = fma(gm1, c2b, Hbar);
-      q2hb = fma(-gm1, c2b, q2hb);
-#pragma unroll
-      for (int m = 0; m < 3; ++m) Vbar[m] = fma(q2hb, V[m], Vbar[m]);
-      // Roe average of the point states a, b
-      double rab = Hbar * (Ha - H), rbb = Hbar * (Hb - H);
-#pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        rab = fma(Vbar[m], Va[m] - V[m], rab);
-        rbb = fma(Vbar[m], Vb[m] - V[m], rbb);
-      }
-      rab *= rs;
-      rbb *= rs;
-      // point primitives: V = m/rho, H = gamma e/rho - gm1 |V|^2/2, sqrt(rho)
-#pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        const int sp = side ? sb : sa;
-        const double wgt = side ? wb : wa;
-        const double* Vp = side ? Vb : Va;
-        const double rho = q[sp], e = q[4 * NP * W + sp];
-        const double rr = 1.0 / rho;
-        const double Hb_ = wgt * Hbar;
-        const double srb = side ? rbb : rab;
-        double Vt[3], vdot = 0.0;
-#pragma unroll
-        for (int m = 0; m < 3; ++m) {
-          Vt[m] = fma(-Hb_ * gm1, Vp[m], wgt * Vbar[m]);
-          vdot = fma(Vt[m], Vp[m], vdot);
-        }
-        const double eb = Hb_ * a.gamma * rr;
-        const double rhob = fma(0.5, srb / ri[sp], -fma(Hb_ * a.gamma, e * rr, vdot) * rr);
-        const int base = side ? 10 : 5;
-        rd[(base + 0) * NI * W + o] = rhob;
-#pragma unroll
-        for (int m = 0; m < 3; ++m) rd[(base + 1 + m) * NI * W + o] = Vt[m] * rr;
-        rd[(base + 4) * NI * W + o] = eb;
+      for (int v = 0; v < 5; ++v) {
+        rd[(5 + v) * NI * W + o] = ga[v];
+        rd[(10 + v) * NI * W + o] = gb[v];
       }
 #pragma unroll
       for (int v = 0; v < 5; ++v) rd[v * NI * W + o] = dub[v];
     }
-    if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(a.status, ST_NONPHYS);
+    if (__any_sync(0xffffffffu, bad & 1) && (tid & 31) == 0) atomicOr(a.status, ST_NONPHYS);
   }
   __syncthreads();
 
@@ -527,6 +558,395 @@ __global__ void __launch_bounds__(APL::THREADS, 2) k_adj_dir(const AdjArgs a) {
       v2 = fma(V[k], V[k], v2);
     }
     cv[0] = fma(0.5 * gp, v2, cv[0]);
+    const long long p = tile_flat<D>(a.g, s0 + pp, a0 + line, bz);
+    adj_epilogue(a, p, cv);
+  }
+}
+
+
+// ============================================================================================
+// NS3D_FP64 form: the reconstruction adjoints in double-float arithmetic on the FP32 pipe.
+// Everything the WENO5 derivative needs is a function of the first differences g_j of the
+// data: s_k (second differences), v_k, b_k = 4 eps + 13/3 s_k^2 + v_k^2, the weights, the
+// candidate differences q_0 - q_1 = (s_0 - s_1)/3 and q_2 - q_1 = (s_1 - s_2)/6, and
+// q_k - q = (q_k - q_1) - M with M = omega_0 (q_0 - q_1) + omega_2 (q_2 - q_1).  The value
+// itself is q = P_c + (2 g_2 + g_1)/6 + M (P_c the stencil centre), the same offset form as
+// the forward pass.  The interface fluxes' adjoints and the Roe adjoint stay in FP64 (Newton
+// reciprocals); the per-point sums of the reconstruction contributions are converted back
+// to FP64 once.  To keep double-float values inside the float range whatever the scale of
+// the adjoint input, each tile divides lambda by the power of two of its largest magnitude
+// and multiplies its results back (exact).
+// ============================================================================================
+template <int TP_, int W_>
+struct AdjPlanDF {
+  static constexpr int TP = TP_;
+  static constexpr int W = W_;
+  static constexpr int THREADS = 256;
+  static constexpr int NP = TP + 10;  // points incl. a halo of 5 each side
+  static constexpr int NI = TP + 5;   // interfaces
+  static constexpr int NW = TP + 8;   // 3-point windows starting at 0 .. NW-1
+  static constexpr int OFF_Q = 0;                        // [9][NP*W] doubles
+  static constexpr int OFF_RI = OFF_Q + 9 * NP * W;      // [6][NP*W]
+  static constexpr int OFF_L = OFF_RI + 6 * NP * W;      // [5][NP*W] lambda / 2^E
+  static constexpr int OFF_G = OFF_L + 5 * NP * W;       // [9][NP*W] float2 first differences
+  static constexpr int OFF_B = OFF_G + 9 * NP * W;       // [9][3][NW*W] float2 b_k of every window
+  static constexpr int OFF_REC = OFF_B + 27 * NW * W;    // [10][NI*W] doubles: u^L, u^R of u_0..u_4
+  static constexpr int OFF_RD = OFF_REC + 10 * NI * W;   // [15][NI*W] doubles: Roe adjoints
+  static constexpr int OFF_WC = OFF_RD + 15 * NI * W;    // [9][6][NI*W] float2 stencil contributions
+  static constexpr int WORDS = OFF_WC + 54 * NI * W;
+  static constexpr int BYTES = WORDS * 8;
+};
+using APF = AdjPlanDF<16, 4>;
+
+__device__ __forceinline__ df df_sub(df x, df y) { return df_add_fast(x, df_neg(y)); }
+__device__ __forceinline__ df df_twice(df x) { return df{2.0f * x.hi, 2.0f * x.lo}; }
+__device__ __forceinline__ float2 df_pack(df x) { return make_float2(x.hi, x.lo); }
+__device__ __forceinline__ df df_unpack(float2 v) { return df{v.x, v.y}; }
+
+// The three weights of one reconstruction from its b_k (candidate order 0, 1, 2; optimal
+// weights 1, 6, 3 over 10), with a common power-of-two scaling (omega is scale-free).
+__device__ __forceinline__ void df_omega(df b0, df b1, df b2, df om[3]) {
+  df B0 = df_sqr(b0), B1 = df_sqr(b1), B2 = df_sqr(b2);
+  const int E = max(exponent_of(B0.hi), max(exponent_of(B1.hi), exponent_of(B2.hi)));
+  const float sc = pow2f(-E);
+  B0 = df{B0.hi * sc, B0.lo * sc};
+  B1 = df{B1.hi * sc, B1.lo * sc};
+  B2 = df{B2.hi * sc, B2.lo * sc};
+  const df a0 = df_mul(B1, B2);
+  const df a1 = df_mul_f(df_mul(B0, B2), 6.0f);
+  const df a2 = df_mul_f(df_mul(B0, B1), 3.0f);
+  const df r = df_div(df{1.0f, 0.0f}, df_add_pos(a0, df_add_pos(a1, a2)));
+  om[0] = df_mul(a0, r);
+  om[1] = df_mul(a1, r);
+  om[2] = df_mul(a2, r);
+}
+
+struct DFConst {
+  df third, sixth, c263;  // 1/3, 1/6, 26/3
+};
+
+// Offset M of the reconstruction from its candidate 1, and the candidate differences.
+__device__ __forceinline__ df df_offset(df g0, df g1, df g2, df g3, const df om[3], const DFConst& k, df& E0, df& E2,
+                                        df s[3]) {
+  s[0] = df_sub(g1, g0);
+  s[1] = df_sub(g2, g1);
+  s[2] = df_sub(g3, g2);
+  E0 = df_mul(df_sub(s[0], s[1]), k.third);
+  E2 = df_mul(df_sub(s[1], s[2]), k.sixth);
+  return df_add_fast(df_mul(om[0], E0), df_mul(om[2], E2));
+}
+
+// FP64 value of the reconstruction with centre value pc: pc + (2 g2 + g1)/6 + M.
+__device__ __forceinline__ double df_value(double pc, df g1, df g2, df M, const DFConst& k) {
+  const df d = df_add_fast(df_mul(df_add_fast(df_twice(g2), g1), k.sixth), M);
+  return (pc + f2d_bits(d.hi)) + f2d_bits(d.lo);
+}
+
+// y * d(value)/d(q_t), t = 0..4, of the reconstruction of stencil differences g0..g3 with
+// window terms b0..b2 (as weno_adjoint, in double-float).
+__device__ __forceinline__ void df_recon_adjoint(df g0, df g1, df g2, df g3, df b0, df b1, df b2, df y,
+                                                 const DFConst& k, df out[5]) {
+  df om[3], s[3], E0, E2;
+  df_omega(b0, b1, b2, om);
+  const df M = df_offset(g0, g1, g2, g3, om, k, E0, E2, s);
+  const df v0 = df_sub(df_mul_f(g1, 3.0f), g0);
+  const df v1 = df_add_fast(g1, g2);
+  const df v2 = df_sub(g3, df_mul_f(g2, 3.0f));
+  const df y0 = df_mul(y, om[0]), y1 = df_mul(y, om[1]), y2 = df_mul(y, om[2]);
+  // adjoints of b_k: -2 y_k (q_k - q) / b_k with q_0 - q = E0 - M, q_1 - q = -M, q_2 - q = E2 - M
+  const df k0 = df_twice(df_div(df_mul(y0, df_sub(M, E0)), b0));
+  const df k1 = df_twice(df_div(df_mul(y1, M), b1));
+  const df k2 = df_twice(df_div(df_mul(y2, df_sub(M, E2)), b2));
+  // direct term sum_k y_k dq_k/dq_t
+  out[0] = df_mul(y0, k.third);
+  out[1] = df_neg(df_mul(df_add_fast(df_mul_f(y0, 7.0f), y1), k.sixth));
+  out[2] = df_mul(df_add_fast(df_mul_f(y0, 11.0f), df_add_fast(df_mul_f(y1, 5.0f), df_twice(y2))), k.sixth);
+  out[3] = df_mul(df_add_fast(df_twice(y1), df_mul_f(y2, 5.0f)), k.sixth);
+  out[4] = df_neg(df_mul(y2, k.sixth));
+  // db/d(x, y, z) of a window = 26/3 s (1, -2, 1) + 2 v dv/d(x, y, z)
+  df t = df_mul(df_mul(s[0], k0), k.c263), r = df_twice(df_mul(v0, k0));  // dv = (1, -4, 3)
+  out[0] = df_add_fast(out[0], df_add_fast(t, r));
+  out[1] = df_sub(out[1], df_add_fast(df_twice(t), df_twice(df_twice(r))));
+  out[2] = df_add_fast(out[2], df_add_fast(t, df_mul_f(r, 3.0f)));
+  t = df_mul(df_mul(s[1], k1), k.c263);
+  r = df_twice(df_mul(v1, k1));  // dv = (-1, 0, 1)
+  out[1] = df_add_fast(out[1], df_sub(t, r));
+  out[2] = df_sub(out[2], df_twice(t));
+  out[3] = df_add_fast(out[3], df_add_fast(t, r));
+  t = df_mul(df_mul(s[2], k2), k.c263);
+  r = df_twice(df_mul(v2, k2));  // dv = (3, -4, 1)
+  out[2] = df_add_fast(out[2], df_add_fast(t, df_mul_f(r, 3.0f)));
+  out[3] = df_sub(out[3], df_add_fast(df_twice(t), df_twice(df_twice(r))));
+  out[4] = df_add_fast(out[4], df_add_fast(t, r));
+}
+
+__device__ __forceinline__ double pow2d(int k) { return __hiloint2double((k + 1023) << 20, 0); }
+
+template <int D>
+__global__ void __launch_bounds__(APF::THREADS, 2) k_adj_dir_df(const AdjArgs a) {
+  extern __shared__ double sm[];
+  __shared__ int s_emax;
+  constexpr int TP = APF::TP, NP = APF::NP, NI = APF::NI, NW = APF::NW, W = APF::W;
+  constexpr int AX = (D == 0) ? 1 : 0;
+  const int nD = a.g.n[D];
+  const int na = a.g.n[AX];
+  const long long N = a.g.N;
+  const int s0 = blockIdx.x * TP;
+  const int a0 = blockIdx.y * W;
+  const int bz = blockIdx.z;
+  const int tid = threadIdx.x;
+  const double rdx = 1.0 / a.g.h[D];
+  double* q = sm + APF::OFF_Q;
+  double* ri = sm + APF::OFF_RI;
+  double* lm = sm + APF::OFF_L;
+  float2* G = reinterpret_cast<float2*>(sm + APF::OFF_G);
+  float2* Bw = reinterpret_cast<float2*>(sm + APF::OFF_B);
+  double* rec = sm + APF::OFF_REC;
+  double* rd = sm + APF::OFF_RD;
+  float2* wc = reinterpret_cast<float2*>(sm + APF::OFF_WC);
+  DFConst kc;
+  {
+    const double third = 1.0 / 3.0, sixth = 1.0 / 6.0, c263 = 26.0 / 3.0;
+    kc.third = df{(float)third, (float)(third - (double)(float)third)};
+    kc.sixth = df{(float)sixth, (float)(sixth - (double)(float)sixth)};
+    kc.c263 = df{(float)c263, (float)(c263 - (double)(float)c263)};
+  }
+  const df eps4{(float)a.eps4, (float)(a.eps4 - (double)(float)a.eps4)};
+  const df c133{(float)(13.0 / 3.0), (float)(13.0 / 3.0 - (double)(float)(13.0 / 3.0))};
+  if (tid == 0) s_emax = -2000;
+  __syncthreads();
+
+  // ---- A: load; largest binary exponent of lambda in the tile ----------------------------
+  int emax = -2000;
+  for (int item = tid; item < NP * W; item += APF::THREADS) {
+    int pos, line;
+    tile_split<D, W>(item, NP, pos, line);
+    const int c = wrap_idx(s0 - 5 + pos, nD);
+    const int la = min(a0 + line, na - 1);
+    const long long p = tile_flat<D>(a.g, c, la, bz);
+    double U[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) U[v] = __ldg(a.u + v * N + p);
+    const double vx = __ldg(a.pm + PM_U * N + p), vy = __ldg(a.pm + PM_V * N + p), vz = __ldg(a.pm + PM_W * N + p);
+    const double pr = __ldg(a.pm + PM_P * N + p);
+    const double un = (D == 0) ? vx : (D == 1) ? vy : vz;
+    const int s = tile_idx<D, W>(pos, line, NP);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) q[v * NP * W + s] = U[v];
+    q[5 * NP * W + s] = (D == 0) ? fma(U[1], un, pr) : U[1] * un;
+    q[6 * NP * W + s] = (D == 1) ? fma(U[2], un, pr) : U[2] * un;
+    q[7 * NP * W + s] = (D == 2) ? fma(U[3], un, pr) : U[3] * un;
+    q[8 * NP * W + s] = (U[4] + pr) * un;
+    ri[0 * NP * W + s] = __ldg(a.pm + PM_SR * N + p);
+    ri[1 * NP * W + s] = vx;
+    ri[2 * NP * W + s] = vy;
+    ri[3 * NP * W + s] = vz;
+    ri[4 * NP * W + s] = __ldg(a.pm + PM_H * N + p);
+    ri[5 * NP * W + s] = pr;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const double l = a.lam_scale * __ldg(a.lam + v * N + p);
+      lm[v * NP * W + s] = l;
+      const int e = ((__double2hiint(l) >> 20) & 0x7ff) - 1023;
+      if (l != 0.0 && e > emax) emax = e;
+    }
+  }
+  emax = __reduce_max_sync(0xffffffffu, emax);
+  if ((tid & 31) == 0) atomicMax(&s_emax, emax);
+  __syncthreads();
+  // E = exponent of the largest |lambda| (0 if lambda vanishes on the tile); lambda / 2^E
+  const int E = (s_emax == -2000) ? 0 : max(-1000, min(1000, s_emax));
+  const double down = pow2d(-E);
+  int range_bad = 0;
+  for (int item = tid; item < NP * W; item += APF::THREADS) {
+    int pos, line;
+    tile_split<D, W>(item, NP, pos, line);
+    const int s = tile_idx<D, W>(pos, line, NP);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) lm[v * NP * W + s] *= down;
+  }
+  // first differences of the 9 scalars, FP64, kept as double-float
+  for (int item = tid; item < 9 * (NP - 1) * W; item += APF::THREADS) {
+    const int m = item / ((NP - 1) * W);
+    int j, line;
+    tile_split<D, W>(item - m * (NP - 1) * W, NP - 1, j, line);
+    const double* qm = q + m * NP * W;
+    const double d = qm[tile_idx<D, W>(j + 1, line, NP)] - qm[tile_idx<D, W>(j, line, NP)];
+    G[m * NP * W + tile_idx<D, W>(j, line, NP)] = df_pack(d2df_bits(d));
+  }
+  __syncthreads();
+
+  // ---- B: b_k of every window ------------------------------------------------------------
+  for (int item = tid; item < 9 * NW * W; item += APF::THREADS) {
+    const int m = item / (NW * W);
+    int w, line;
+    tile_split<D, W>(item - m * NW * W, NW, w, line);
+    const float2* Gm = G + m * NP * W;
+    const df g0 = df_unpack(Gm[tile_idx<D, W>(w, line, NP)]), g1 = df_unpack(Gm[tile_idx<D, W>(w + 1, line, NP)]);
+    const df sw = df_sub(g1, g0);
+    const df aa = df_add_pos(df_mul(df_sqr(sw), c133), eps4);
+    const df b0 = df_add_pos(df_sqr(df_sub(df_mul_f(g1, 3.0f), g0)), aa);
+    const df b1 = df_add_pos(df_sqr(df_add_fast(g0, g1)), aa);
+    const df b2 = df_add_pos(df_sqr(df_sub(g1, df_mul_f(g0, 3.0f))), aa);
+    const int o = tile_idx<D, W>(w, line, NW);
+    Bw[(m * 3 + 0) * NW * W + o] = df_pack(b0);
+    Bw[(m * 3 + 1) * NW * W + o] = df_pack(b1);
+    Bw[(m * 3 + 2) * NW * W + o] = df_pack(b2);
+    // b^2 must stay inside the float range (differences of the data up to ~1e9)
+    range_bad |= !(fmaxf(b0.hi, fmaxf(b1.hi, b2.hi)) < 1e18f);
+  }
+  __syncthreads();
+
+  // ---- C: values of the u reconstructions (for the Roe adjoint) --------------------------
+  for (int item = tid; item < 5 * NI * W; item += APF::THREADS) {
+    const int m = item / (NI * W);
+    int f, line;
+    tile_split<D, W>(item - m * NI * W, NI, f, line);
+    const float2* Gm = G + m * NP * W;
+    df g[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) g[j] = df_unpack(Gm[tile_idx<D, W>(f + j, line, NP)]);
+    const float2* B = Bw + m * 3 * NW * W;
+    auto ldb = [&](int k, int w) { return df_unpack(B[k * NW * W + tile_idx<D, W>(w, line, NW)]); };
+    const double* qm = q + m * NP * W;
+    df om[3], s[3], E0, E2;
+    df_omega(ldb(0, f), ldb(1, f + 1), ldb(2, f + 2), om);
+    const df ML = df_offset(g[0], g[1], g[2], g[3], om, kc, E0, E2, s);
+    const double vL = df_value(qm[tile_idx<D, W>(f + 2, line, NP)], g[1], g[2], ML, kc);
+    df_omega(ldb(2, f + 3), ldb(1, f + 2), ldb(0, f + 1), om);
+    const df MR = df_offset(df_neg(g[4]), df_neg(g[3]), df_neg(g[2]), df_neg(g[1]), om, kc, E0, E2, s);
+    const double vR = df_value(qm[tile_idx<D, W>(f + 3, line, NP)], df_neg(g[3]), df_neg(g[2]), MR, kc);
+    const int o = tile_idx<D, W>(f, line, NI);
+    rec[(2 * m) * NI * W + o] = vL;
+    rec[(2 * m + 1) * NI * W + o] = vR;
+  }
+  __syncthreads();
+
+  // ---- D: adjoint of the Roe flux -----------------------------------------------------------
+  {
+    int bad = 0;
+    for (int item = tid; item < NI * W; item += APF::THREADS) {
+      int f, line;
+      tile_split<D, W>(item, NI, f, line);
+      const int o = tile_idx<D, W>(f, line, NI);
+      const int sa = tile_idx<D, W>(f + 2, line, NP), sb = tile_idx<D, W>(f + 3, line, NP);
+      double du[5], Lh[5], Va[3], Vb[3];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        du[v] = rec[(2 * v + 1) * NI * W + o] - rec[(2 * v) * NI * W + o];
+        Lh[v] = (lm[v * NP * W + sb] - lm[v * NP * W + sa]) * rdx;
+      }
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        Va[m] = ri[(1 + m) * NP * W + sa];
+        Vb[m] = ri[(1 + m) * NP * W + sb];
+      }
+      double dub[5], ga[5], gb[5];
+      bad |= roe_adjoint<D, true>(du, Lh, ri[sa], ri[sb], Va, Vb, ri[4 * NP * W + sa], ri[4 * NP * W + sb], q[sa],
+                                  q[4 * NP * W + sa], q[sb], q[4 * NP * W + sb], a.gamma, a.hdelta, dub, ga, gb);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        rd[v * NI * W + o] = dub[v];
+        rd[(5 + v) * NI * W + o] = ga[v];
+        rd[(10 + v) * NI * W + o] = gb[v];
+      }
+    }
+    if (__any_sync(0xffffffffu, bad & 1) && (tid & 31) == 0) atomicOr(a.status, ST_NONPHYS);
+    range_bad |= bad & 2;
+  }
+  __syncthreads();
+
+  // ---- E: reconstruction adjoints -> six stencil contributions per scalar and interface -----
+  for (int item = tid; item < 9 * NI * W; item += APF::THREADS) {
+    const int m = item / (NI * W);
+    int f, line;
+    tile_split<D, W>(item - m * NI * W, NI, f, line);
+    const int o = tile_idx<D, W>(f, line, NI);
+    const int sa = tile_idx<D, W>(f + 2, line, NP), sb = tile_idx<D, W>(f + 3, line, NP);
+    double yL, yR;
+    if (m < 5) {
+      const double gdu = rd[m * NI * W + o];
+      yL = -gdu;
+      yR = gdu;
+      if (m == 1 + D) {  // mass flux f_0 = u_{1+D}: (f^L + f^R)/2 part
+        const double h0 = 0.5 * ((lm[sb] - lm[sa]) * rdx);
+        yL += h0;
+        yR += h0;
+      }
+    } else {
+      const double hm = 0.5 * ((lm[(m - 4) * NP * W + sb] - lm[(m - 4) * NP * W + sa]) * rdx);
+      yL = hm;
+      yR = hm;
+    }
+    range_bad |= !(fabs(yL) < 1e30 && fabs(yR) < 1e30);
+    const float2* Gm = G + m * NP * W;
+    df g[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) g[j] = df_unpack(Gm[tile_idx<D, W>(f + j, line, NP)]);
+    const float2* B = Bw + m * 3 * NW * W;
+    auto ldb = [&](int k, int w) { return df_unpack(B[k * NW * W + tile_idx<D, W>(w, line, NW)]); };
+    df cL[5], cR[5];
+    df_recon_adjoint(g[0], g[1], g[2], g[3], ldb(0, f), ldb(1, f + 1), ldb(2, f + 2), d2df_bits(yL), kc, cL);
+    df_recon_adjoint(df_neg(g[4]), df_neg(g[3]), df_neg(g[2]), df_neg(g[1]), ldb(2, f + 3), ldb(1, f + 2),
+                     ldb(0, f + 1), d2df_bits(yR), kc, cR);
+    float2* wm = wc + m * 6 * NI * W;
+    wm[0 * NI * W + o] = df_pack(cL[0]);
+#pragma unroll
+    for (int j = 1; j < 5; ++j) wm[j * NI * W + o] = df_pack(df_add_fast(cL[j], cR[5 - j]));
+    wm[5 * NI * W + o] = df_pack(cR[0]);
+  }
+  if (__any_sync(0xffffffffu, range_bad) && (tid & 31) == 0) atomicOr(a.status, ST_DF_RANGE);
+  __syncthreads();
+
+  // ---- F: gather, adjoint of the point fluxes, scale back, epilogue ----------------------------
+  const double up = pow2d(E);
+  const double gm1 = a.gamma - 1.0;
+  for (int item = tid; item < TP * W; item += APF::THREADS) {
+    int pp, line;
+    tile_split<D, W>(item, TP, pp, line);
+    if (s0 + pp >= nD || a0 + line >= na) continue;
+    const int pos = pp + 5;
+    double gsum[9];
+#pragma unroll
+    for (int m = 0; m < 9; ++m) {
+      const float2* wm = wc + m * 6 * NI * W;
+      df acc = df_unpack(wm[tile_idx<D, W>(pos, line, NI)]);
+#pragma unroll
+      for (int j = 1; j < 6; ++j) acc = df_add_fast(acc, df_unpack(wm[j * NI * W + tile_idx<D, W>(pos - j, line, NI)]));
+      gsum[m] = f2d_bits(acc.hi) + f2d_bits(acc.lo);
+    }
+    const int oa = tile_idx<D, W>(pos - 2, line, NI), ob = tile_idx<D, W>(pos - 3, line, NI);
+    double cv[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) cv[v] = gsum[v] + (rd[(5 + v) * NI * W + oa] + rd[(10 + v) * NI * W + ob]);
+    const int s = tile_idx<D, W>(pos, line, NP);
+    const double rho = q[s], e = q[4 * NP * W + s], pr = ri[5 * NP * W + s];
+    const double V[3] = {ri[1 * NP * W + s], ri[2 * NP * W + s], ri[3 * NP * W + s]};
+    const double un = V[D];
+    const double Fbm[3] = {gsum[5], gsum[6], gsum[7]};
+    const double Fb4 = gsum[8];
+    const double pb = fma(Fb4, un, Fbm[D]);
+    double unb = Fb4 * (e + pr);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      unb = fma(Fbm[k], q[(1 + k) * NP * W + s], unb);
+      cv[1 + k] = fma(Fbm[k], un, cv[1 + k]);
+    }
+    cv[4] = fma(Fb4, un, cv[4]);
+    const double rr = rcp_newton(rho);
+    cv[1 + D] = fma(unb, rr, cv[1 + D]);
+    cv[0] = fma(-unb * un, rr, cv[0]);
+    const double gp = gm1 * pb;
+    cv[4] += gp;
+    double v2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      cv[1 + k] = fma(-gp, V[k], cv[1 + k]);
+      v2 = fma(V[k], V[k], v2);
+    }
+    cv[0] = fma(0.5 * gp, v2, cv[0]);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) cv[v] *= up;
     const long long p = tile_flat<D>(a.g, s0 + pp, a0 + line, bz);
     adj_epilogue(a, p, cv);
   }
@@ -724,12 +1144,27 @@ cudaError_t prepare_adj_kernels() {
   cudaError_t e = cudaFuncSetAttribute(k_adj_dir<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, APL::BYTES);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_dir<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, APL::BYTES);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_dir<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, APL::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adj_dir_df<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, APF::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adj_dir_df<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, APF::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adj_dir_df<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, APF::BYTES);
   return e;
 }
 
 cudaError_t launch_adj_dir(int d, const AdjArgs& a, cudaStream_t s) {
   const int AXd = (d == 0) ? 1 : 0;
   const int BXd = (d == 2) ? 1 : 2;
+  if (a.mode == 1) {
+    dim3 grid((a.g.n[d] + APF::TP - 1) / APF::TP, (a.g.n[AXd] + APF::W - 1) / APF::W, a.g.n[BXd]);
+    switch (d) {
+      case 0: k_adj_dir_df<0><<<grid, APF::THREADS, APF::BYTES, s>>>(a); break;
+      case 1: k_adj_dir_df<1><<<grid, APF::THREADS, APF::BYTES, s>>>(a); break;
+      default: k_adj_dir_df<2><<<grid, APF::THREADS, APF::BYTES, s>>>(a); break;
+    }
+    return cudaGetLastError();
+  }
   dim3 grid((a.g.n[d] + APL::TP - 1) / APL::TP, (a.g.n[AXd] + APL::W - 1) / APL::W, a.g.n[BXd]);
   switch (d) {
     case 0: k_adj_dir<0><<<grid, APL::THREADS, APL::BYTES, s>>>(a); break;

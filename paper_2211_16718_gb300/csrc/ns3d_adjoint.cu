@@ -73,6 +73,7 @@ int vjp_pass(ns3d_ctx* c, const double* u, const double* lam, double scale, AdjA
   a.eps4 = 4.0 * c->p.weno_eps;
   a.hdelta = c->p.harten_delta;
   a.status = c->status;
+  a.mode = (c->p.precision == NS3D_FP64_STRICT) ? 0 : 1;
   a.epi = visc ? AEPI_ADD : AEPI_WRITE;
   rc = timed(c, NS3D_K_ADJ_DIR, [&] { return launch_adj_dir(0, a, c->stream); }, "x-direction adjoint kernel");
   if (rc) return rc;

@@ -109,6 +109,7 @@ struct AdjArgs {
   double c1, c2;
   double gamma, eps4, hdelta;
   int* status;
+  int mode;           // 0: all FP64; 1: reconstruction adjoints in double-float (NS3D_FP64)
 };
 
 constexpr int ADJ_SCRATCH_PLANES = 16;  // viscous-adjoint scratch: grad adjoint 12, velocity 3, rho 1
