@@ -106,6 +106,22 @@ __device__ __forceinline__ df df_div(df x, df y) {
   return fast_two_sum(q1, q2);
 }
 
+// Square root of a positive double-word: float seed, one correction with the exact
+// square of the seed (Dekker's method).
+__device__ __forceinline__ df df_sqrt(df x) {
+  const float r = __fsqrt_rn(x.hi);
+  const df p = two_prod(r, r);
+  float d = __fsub_rn(x.hi, p.hi);
+  d = __fsub_rn(d, p.lo);
+  d = __fadd_rn(d, x.lo);
+  return fast_two_sum(r, __fdiv_rn(d, __fadd_rn(r, r)));
+}
+
+__device__ __forceinline__ df df_abs(df x) { return (x.hi < 0.0f) ? df_neg(x) : x; }
+
+// x < y for double-words in canonical form (|lo| <= ulp(hi)/2).
+__device__ __forceinline__ bool df_lt(df x, df y) { return x.hi < y.hi || (x.hi == y.hi && x.lo < y.lo); }
+
 // ---- conversions by bit manipulation (no FP64 instructions) -----------------
 // float -> double, exact for normal floats; zero and subnormals map to signed 0.
 __device__ __forceinline__ double f2d_bits(float f) {

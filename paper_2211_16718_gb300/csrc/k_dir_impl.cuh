@@ -140,12 +140,23 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
     q[6 * NP * W + s] = (D == 1) ? fma(U[2], un, pr) : U[2] * un;
     q[7 * NP * W + s] = (D == 2) ? fma(U[3], un, pr) : U[3] * un;
     q[8 * NP * W + s] = (U[4] + pr) * un;
-    double* r = sm + PL::OFF_ROE;
-    r[0 * NP * W + s] = ldx<NC>(a.pm + PM_SR * N + p);
-    r[1 * NP * W + s] = vx;
-    r[2 * NP * W + s] = vy;
-    r[3 * NP * W + s] = vz;
-    r[4 * NP * W + s] = ldx<NC>(a.pm + PM_H * N + p);
+    if (MODE == 1) {  // Roe inputs as double-float (the Roe flux runs on the FP32 pipe)
+      float2* r = reinterpret_cast<float2*>(sm + PL::OFF_ROE);
+      const df sr = d2df_bits(ldx<NC>(a.pm + PM_SR * N + p)), hh = d2df_bits(ldx<NC>(a.pm + PM_H * N + p));
+      const df dvx = d2df_bits(vx), dvy = d2df_bits(vy), dvz = d2df_bits(vz);
+      r[0 * NP * W + s] = make_float2(sr.hi, sr.lo);
+      r[1 * NP * W + s] = make_float2(dvx.hi, dvx.lo);
+      r[2 * NP * W + s] = make_float2(dvy.hi, dvy.lo);
+      r[3 * NP * W + s] = make_float2(dvz.hi, dvz.lo);
+      r[4 * NP * W + s] = make_float2(hh.hi, hh.lo);
+    } else {
+      double* r = sm + PL::OFF_ROE;
+      r[0 * NP * W + s] = ldx<NC>(a.pm + PM_SR * N + p);
+      r[1 * NP * W + s] = vx;
+      r[2 * NP * W + s] = vy;
+      r[3 * NP * W + s] = vz;
+      r[4 * NP * W + s] = ldx<NC>(a.pm + PM_H * N + p);
+    }
     if (a.fv != nullptr) {
       double* f = sm + PL::OFF_FV;
 #pragma unroll
@@ -317,6 +328,64 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
       fL[0] = uL[1 + D];
       fR[0] = uR[1 + D];
       const int sa = tile_idx<D, W>(f + 2, line, NP), sb = tile_idx<D, W>(f + 3, line, NP);
+      if (MODE == 1) {
+        // Roe dissipation X|Lambda|X^{-1} du in double-float; only du and the final
+        // combination 0.5 (f^L + f^R - diss) use the FP64 pipe
+        const float2* rf = reinterpret_cast<const float2*>(sm + PL::OFF_ROE);
+        auto ldr = [&](int k, int sp) { const float2 v = rf[k * NP * W + sp]; return df{v.x, v.y}; };
+        df du[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) du[v] = d2df_bits(uR[v] - uL[v]);
+        const df ra = ldr(0, sa), rb = ldr(0, sb);
+        const df rsum = df_add_pos(ra, rb);
+        const df rs = df_div(df{1.0f, 0.0f}, rsum);
+        const df wa = df_mul(ra, rs), wb = df_mul(rb, rs);
+        df V[3];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) V[m] = df_add_fast(df_mul(wa, ldr(1 + m, sa)), df_mul(wb, ldr(1 + m, sb)));
+        const df H = df_add_pos(df_mul(wa, ldr(4, sa)), df_mul(wb, ldr(4, sb)));
+        const df q2 = df_add_pos(df_sqr(V[0]), df_add_pos(df_sqr(V[1]), df_sqr(V[2])));
+        const df q2h = df{0.5f * q2.hi, 0.5f * q2.lo};
+        const df c2 = df_mul(df_add_fast(H, df_neg(q2h)), df{a.gm1_hi, a.gm1_lo});
+        bad |= !(c2.hi > 0.0f);
+        range_bad |= !(c2.hi > 1e-30f && c2.hi < 1e30f && rsum.hi > 1e-30f && rsum.hi < 1e30f);
+        const df c = df_sqrt(c2);
+        const df rc = df_div(df{1.0f, 0.0f}, c);
+        constexpr int T1 = (D == 0) ? 1 : 0;
+        constexpr int T2 = (D == 2) ? 1 : 2;
+        const df un = V[D], vt1 = V[T1], vt2 = V[T2];
+        const df b1 = df_mul(df{a.gm1_hi, a.gm1_lo}, df_sqr(rc));
+        const df vdm = df_add_fast(df_mul(V[0], du[1]), df_add_fast(df_mul(V[1], du[2]), df_mul(V[2], du[3])));
+        const df phi = df_mul(b1, df_add_fast(df_add_fast(df_mul(q2h, du[0]), du[4]), df_neg(vdm)));
+        const df a2 = df_add_fast(du[0], df_neg(phi));
+        const df a3 = df_add_fast(du[1 + T1], df_neg(df_mul(vt1, du[0])));
+        const df a4 = df_add_fast(du[1 + T2], df_neg(df_mul(vt2, du[0])));
+        const df ach0 = df_mul(df_add_fast(df_mul(un, du[0]), df_neg(du[1 + D])), rc);
+        const df ach = df{0.5f * ach0.hi, 0.5f * ach0.lo};
+        const df ph = df{0.5f * phi.hi, 0.5f * phi.lo};
+        const df a1 = df_add_fast(ph, ach), a5 = df_add_fast(ph, df_neg(ach));
+        df l1 = df_abs(df_add_fast(un, df_neg(c))), l5 = df_abs(df_add_fast(un, c));
+        const df l2 = df_abs(un);
+        const df delta = df_mul(c, df{a.hd_hi, a.hd_lo});
+        if (df_lt(l1, delta)) l1 = df_div(df_add_pos(df_sqr(l1), df_sqr(delta)), df{2.0f * delta.hi, 2.0f * delta.lo});
+        if (df_lt(l5, delta)) l5 = df_div(df_add_pos(df_sqr(l5), df_sqr(delta)), df{2.0f * delta.hi, 2.0f * delta.lo});
+        const df A1 = df_mul(l1, a1), A2 = df_mul(l2, a2), A3 = df_mul(l2, a3), A4 = df_mul(l2, a4);
+        const df A5 = df_mul(l5, a5);
+        const df S = df_add_fast(A1, A5);
+        const df d0 = df_add_fast(S, A2);
+        const df cD = df_mul(c, df_add_fast(A5, df_neg(A1)));
+        df diss[5];
+        diss[0] = d0;
+        diss[1 + D] = df_add_fast(df_mul(d0, un), cD);
+        diss[1 + T1] = df_add_fast(df_mul(d0, vt1), A3);
+        diss[1 + T2] = df_add_fast(df_mul(d0, vt2), A4);
+        diss[4] = df_add_fast(df_add_fast(df_mul(S, H), df_mul(cD, un)),
+                              df_add_fast(df_mul(A2, q2h), df_add_fast(df_mul(A3, vt1), df_mul(A4, vt2))));
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+          rec[v * NI * W + o] = 0.5 * ((fL[v] + fR[v]) - (f2d_bits(diss[v].hi) + f2d_bits(diss[v].lo)));
+        continue;
+      }
       const double ra = r[sa], rb = r[sb];
       const double rsum = ra + rb;
       // MODE 1: FP32-seeded Newton reciprocals (FP64 accurate, ~4 FP64 operations

@@ -48,6 +48,11 @@ DirArgs base_args(ns3d_ctx* c, const double* u) {
   const double sixth = 1.0 / 6.0;
   a.sixth_hi = (float)sixth;
   a.sixth_lo = (float)(sixth - (double)a.sixth_hi);
+  const double gm1 = c->p.gamma - 1.0;
+  a.gm1_hi = (float)gm1;
+  a.gm1_lo = (float)(gm1 - (double)a.gm1_hi);
+  a.hd_hi = (float)c->p.harten_delta;
+  a.hd_lo = (float)(c->p.harten_delta - (double)a.hd_hi);
   return a;
 }
 

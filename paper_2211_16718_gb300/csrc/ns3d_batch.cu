@@ -310,6 +310,11 @@ int rebuild(ns3d_batch* b) {
         a.eps4_lo = (float)(eps4 - (double)a.eps4_hi);
         a.sixth_hi = (float)sixth;
         a.sixth_lo = (float)(sixth - (double)a.sixth_hi);
+        const double gm1 = in.gamma - 1.0, hd = b->p[i].harten_delta;
+        a.gm1_hi = (float)gm1;
+        a.gm1_lo = (float)(gm1 - (double)a.gm1_hi);
+        a.hd_hi = (float)hd;
+        a.hd_lo = (float)(hd - (double)a.hd_hi);
         if (d == 0) {
           a.epi = EPI_ACC_WRITE;
         } else if (d == 1) {

@@ -57,6 +57,8 @@ struct DirArgs {
   float c133_hi, c133_lo;  // 13/3 as a double-float
   float eps4_hi, eps4_lo;  // 4 * weno_eps as a double-float
   float sixth_hi, sixth_lo;  // 1/6 as a double-float
+  float gm1_hi, gm1_lo;      // gamma - 1 as a double-float
+  float hd_hi, hd_lo;        // Harten fraction as a double-float
 };
 
 // Launchers (return cudaGetLastError() of the launch).
