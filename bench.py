@@ -33,20 +33,22 @@ if ROOT not in sys.path:
 METRIC = "grid-point RHS evals/sec (Gpts/s) and HBM roofline fraction; FP32-bulk/adjoint vs FP64"
 UNIT = "Gpts/s"
 RK_STAGES = 4
-# Algorithmic FP64 flops per grid point of one launch (FMA = 2, add/mul/div/sqrt = 1),
-# counted from the kernels' formulation without halo recomputation:
-#   direction pass: point fluxes 6, smoothness indicators 9 x 20, candidates +
-#   weighted combinations 9 x 46, Roe flux 96, difference + viscous divergence 34.
+# FP64 lane operations (FP64 instructions per thread, an FMA counting once) per grid point of
+# one direction pass, counted from each formulation without the halo's share:
+#  NS3D_FP64 (double-float weights, offsets and Roe dissipation): point fluxes 5, first
+#   differences 9, two additions per reconstruction 36, Roe du + 0.5(fL + fR - diss) 25,
+#   flux difference 10, viscous divergence 16.
+#  NS3D_FP64_STRICT: point fluxes 5, smoothness indicators 9 x 14, candidates and weighted sums
+#   (with the division sequence) 9 x 50, Roe flux ~100 (two divisions, a square root), 26.
+OPS_DIR_FP64 = 5 + 9 + 36 + 25 + 10 + 16
+OPS_DIR_STRICT = 5 + 9 * 14 + 9 * 50 + 100 + 26
+OPS_RK_EPI = 15            # RK4 stage update in the z pass (5 components x 3)
+# The method's FP64 flops per point and pass (FMA = 2) in its all-FP64 form, for context.
 FLOPS_DIR = 6 + 9 * 20 + 9 * 46 + 96 + 34
-# With the double-float weights (NS3D_FP64) the FP64 pipe executes per point and scalar:
-# window differences 3, third differences 3, two candidate chains 2 x 6, two weighted
-# sums 2 x 4; the weights themselves run on the FP32 pipe.
-FLOPS_DIR_DFW = 6 + 9 * (3 + 3 + 12 + 8) + 96 + 34
-FLOPS_RK_EPI = 15          # RK4 stage update in the z pass (5 components)
-FLOPS_PRIM = 17            # primitives (incl. 1 division, 1 square root)
-FLOPS_VISC = 111           # 12 gradients + 3 viscous flux vectors
-SMS, FP64_LANES_PER_SM, SM_MAX_MHZ = 152, 2, 2070.0
-FP64_PEAK_TFLOPS = SMS * FP64_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 1.2586
+SMS, FP64_LANES_PER_SM, SM_MAX_MHZ, ISSUE_PER_SM = 152, 2, 2070.0, 4
+FP64_LANEOPS_PEAK_T = SMS * FP64_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12          # 0.629 T lane-ops/s
+ISSUE_PEAK_G = SMS * ISSUE_PER_SM * SM_MAX_MHZ * 1e6 / 1e9                       # 1258.6 G warp-instr/s
+FP64_PEAK_TFLOPS = SMS * FP64_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 1.2586 (FMA = 2 flops)
 
 
 def parse():
@@ -185,6 +187,19 @@ def ncu_traffic_per_point(kernel: str, sha: str):
     return None
 
 
+def ncu_issue_per_point(kernel: str, sha: str):
+    """Warp instructions issued per grid point of one launch (smsp__inst_executed.sum from a
+    committed ncu summary), or None if the kernel sources have changed since."""
+    import glob
+    import re
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            m = re.match(rf"ISSUE {kernel} warp_instr_per_point=([0-9.]+) grid=(\d+) \S+ source_sha256=(\w+)", line)
+            if m and m.group(3) == sha:
+                return float(m.group(1)), os.path.basename(path), int(m.group(2))
+    return None
+
+
 def hit_state(n: int):
     from paper_2211_16718_gb300 import inputs as I
     return I.isotropic_turbulence(n, seed=0), I.hit_mu_eff()
@@ -302,35 +317,47 @@ def run_ours(args, world, rank, local):
     status_ok = bool(np.all(st[:, 10] == 0))
     launches = int(sum(c for _, c in ktimes.values()))
 
-    def roofline_of(kt, fp64_flops_dir):
+    def roofline_of(kt, ops_dir, form):
         # dominant kernel: the direction pass (x, y, z launches of the same kernel)
         dir_ms = sum(kt[k][0] for k in ("dir_x", "dir_y", "dir_z"))
         dir_launches = sum(kt[k][1] for k in ("dir_x", "dir_y", "dir_z"))
         avg_launch_s = dir_ms / dir_launches * 1e-3
-        flops_pt = fp64_flops_dir + FLOPS_RK_EPI / 3.0
-        achieved = flops_pt * n ** 3 / avg_launch_s / 1e12
+        ops_pt = ops_dir + OPS_RK_EPI / 3.0
+        achieved = ops_pt * n ** 3 / avg_launch_s / 1e12
         step_ms_total = sum(v[0] for v in kt.values())
-        return {"bound": "alu", "kernel": "k_dir (fused WENO5 + Roe + difference + viscous divergence)",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2070 MHz (unit counts and max clock)",
-                "fp64_flops_per_point": flops_pt, "avg_launch_ms": avg_launch_s * 1e3,
-                "method_equiv_tflops": (FLOPS_DIR + FLOPS_RK_EPI / 3.0) * n ** 3 / avg_launch_s / 1e12,
+        return {"bound": "alu", "kernel": f"k_dir ({form}: fused WENO5 + Roe + difference + viscous divergence)",
+                "achieved": achieved, "peak": FP64_LANEOPS_PEAK_T,
+                "unit": "T FP64 lane-ops/s (FP64 instructions per thread; FMA = 1)",
+                "frac": achieved / FP64_LANEOPS_PEAK_T, "traffic": None,
+                "peak_source": "152 SMs x 2 FP64 lanes/clk x 2070 MHz (unit counts, max clock; "
+                               "ns3d_alu_probe measures 626 G DFMA lane-ops/s)",
+                "fp64_ops_per_point": ops_pt, "avg_launch_ms": avg_launch_s * 1e3,
+                "method_fp64_flops_per_point": FLOPS_DIR + 5,
+                "method_equiv_tflops": (FLOPS_DIR + 5) * n ** 3 / avg_launch_s / 1e12,
                 "share_of_device_time": dir_ms / step_ms_total if step_ms_total > 0 else None,
                 "algorithmic_bytes_per_point": 8 * (5 + 6 + 4 + 5 + 5),
                 "hbm_gbs_algorithmic": 8 * (5 + 6 + 4 + 5 + 5) * n ** 3 / avg_launch_s / 1e9}
 
-    roofline = roofline_of(ktimes, FLOPS_DIR_DFW)
-    roofline["fp32_work_note"] = ("the double-float weights add ~3.6k FP32-pipe instructions per point and "
-                                  "direction (FP32 runs 63x the FP64 rate), not counted in achieved")
+    roofline = roofline_of(ktimes, OPS_DIR_FP64, "NS3D_FP64")
+    roofline["note"] = ("the double-float weights, offsets and Roe dissipation run ~5.9k FP32-pipe instructions "
+                        "per point and pass (FP32 runs 63x the FP64 rate), not counted in achieved; the pass is "
+                        "bound by instruction issue (see issue)")
     avg_launch_s = roofline["avg_launch_ms"] * 1e-3
     tr = ncu_traffic_per_point("k_dir", kernel_source_sha())
     if tr is not None:
         bpp, src, grid = tr
         roofline["traffic"] = bpp * n ** 3
-        roofline["traffic_note"] = (f"ncu dram read+write of one x-pass launch at {grid}^3 ({src}), "
+        roofline["traffic_note"] = (f"ncu dram read+write per launch at {grid}^3 ({src}), "
                                     f"{bpp:.1f} B/point scaled to {n}^3 (streaming kernel: traffic ~ points)")
         roofline["hbm_frac_measured"] = bpp * n ** 3 / avg_launch_s / 1e9 / 6713.6
+    iss = ncu_issue_per_point("k_dir", kernel_source_sha())
+    if iss is not None:
+        ipp, src, grid = iss
+        ach = ipp * n ** 3 / avg_launch_s / 1e9
+        roofline["issue"] = {"achieved": ach, "peak": ISSUE_PEAK_G, "unit": "G warp-instr/s", "frac": ach / ISSUE_PEAK_G,
+                             "warp_instr_per_point": ipp,
+                             "source": f"ncu smsp__inst_executed.sum per launch at {grid}^3 ({src})",
+                             "peak_source": "152 SMs x 4 schedulers x 1 issue/clk x 2070 MHz"}
 
     # end to end through the C ABI with host buffers (pinned): H2D state, RK4 step,
     # statistics, D2H state + statistics, every step
@@ -362,7 +389,7 @@ def run_ours(args, world, rank, local):
         del u2
         v2 = sum_over_ranks(float(n ** 3 * RK_STAGES * Ks), world) / (ms2 * 1e-3) / 1e9
         modes["fp64_strict"] = {"value": v2, "ms_per_step": ms2 / Ks, "steps": Ks, "weights": "FP64",
-                                "roofline": roofline_of(kt2, FLOPS_DIR)}
+                                "roofline": roofline_of(kt2, OPS_DIR_STRICT, "NS3D_FP64_STRICT")}
     if not args.no_fp32:
         # FP32-bulk: same W + K steps from the same state; error against the FP64 path
         s3, u3, _, ms3, kt3, st3, _ = timed_loop(ns3d.NS3D_FP32_BULK, K, W, False)
