@@ -5,6 +5,7 @@
 
 #include <math.h>
 
+#include "df.cuh"
 #include "ns3d_internal.cuh"
 
 namespace ns3d {
@@ -89,6 +90,64 @@ __device__ __forceinline__ void visc_point(const double* __restrict__ pm, double
     fv[(long long)(b + 1) * N + p] = tau[1];
     fv[(long long)(b + 2) * N + p] = tau[2];
     fv[(long long)(b + 3) * N + p] = en;
+  }
+}
+
+// visc_point in the NS3D_FP64 form: the stencil differences q_{+1} - q_{-1}, q_{+2} - q_{-2}
+// in FP64, everything after them (gradients, stresses, heat flux, work term) in double-float
+// on the FP32 pipe, and one FP64 addition per output (hi + lo).  The viscous fluxes are
+// ~mu |grad u| in size, so the double-float rounding (~1e-14 relative) stays far below the
+// FP64 rounding of the convective terms they are added to.
+template <bool NC = true>
+__device__ __forceinline__ void visc_point_df(const double* __restrict__ pm, double* __restrict__ fv, int nx, int ny,
+                                              int nz, long long p, const double r12[3], double mu, double kappa,
+                                              int only_d = -1) {
+  const long long N = (long long)nx * ny * nz;
+  const int i = (int)(p % nx);
+  const int j = (int)((p / nx) % ny);
+  const int k = (int)(p / ((long long)nx * ny));
+  df G[4][3];
+  const int n3[3] = {nx, ny, nz};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    long long nb[4];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      const int off = (o < 2) ? (o - 2) : (o - 1);  // -2, -1, +1, +2
+      int c[3] = {i, j, k};
+      c[d] = wrap_idx(c[d] + off, n3[d]);
+      nb[o] = flat3(c[0], c[1], c[2], nx, ny);
+    }
+    const df r = d2df_bits(r12[d]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int plane = (q < 3) ? q : PM_T;
+      const double* A = pm + (long long)plane * N;
+      const df d1 = d2df_bits(ldx<NC>(A + nb[2]) - ldx<NC>(A + nb[1]));
+      const df d2 = d2df_bits(ldx<NC>(A + nb[3]) - ldx<NC>(A + nb[0]));
+      G[q][d] = df_mul(df_add_fast(df_mul_f(d1, 8.0f), df_neg(d2)), r);
+    }
+  }
+  const df vel[3] = {d2df_bits(pm[PM_U * N + p]), d2df_bits(pm[PM_V * N + p]), d2df_bits(pm[PM_W * N + p])};
+  const df dmu = d2df_bits(mu), dkap = d2df_bits(kappa);
+  const double two3 = 2.0 / 3.0;
+  const df c23{(float)two3, (float)(two3 - (double)(float)two3)};
+  const df tdiv = df_mul(df_add_fast(G[0][0], df_add_fast(G[1][1], G[2][2])), c23);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (only_d >= 0 && d != only_d) continue;
+    const int b = (only_d >= 0) ? 0 : 4 * d;
+    df tau[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+      tau[m] = (m == d) ? df_mul(dmu, df_add_fast(df_mul_f(G[d][d], 2.0f), df_neg(tdiv)))
+                        : df_mul(dmu, df_add_fast(G[m][d], G[d][m]));
+    const df en = df_add_fast(df_add_fast(df_mul(vel[0], tau[0]), df_mul(vel[1], tau[1])),
+                              df_add_fast(df_mul(vel[2], tau[2]), df_mul(dkap, G[3][d])));
+    fv[(long long)(b + 0) * N + p] = f2d_bits(tau[0].hi) + f2d_bits(tau[0].lo);
+    fv[(long long)(b + 1) * N + p] = f2d_bits(tau[1].hi) + f2d_bits(tau[1].lo);
+    fv[(long long)(b + 2) * N + p] = f2d_bits(tau[2].hi) + f2d_bits(tau[2].lo);
+    fv[(long long)(b + 3) * N + p] = f2d_bits(en.hi) + f2d_bits(en.lo);
   }
 }
 

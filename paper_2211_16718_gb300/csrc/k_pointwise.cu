@@ -32,14 +32,18 @@ __global__ void __launch_bounds__(PW_THREADS) k_prim(const double* __restrict__ 
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONPHYS);
 }
 
-// Gradients of (u, v, w, T) at every point, then the three viscous flux vectors (body: visc_point).
+// Gradients of (u, v, w, T) at every point, then the three viscous flux vectors (body:
+// visc_point, or visc_point_df in the NS3D_FP64 form).
+template <bool DF>
 __global__ void __launch_bounds__(PW_THREADS) k_visc(const double* __restrict__ pm, double* __restrict__ fv,
                                                      int nx, int ny, int nz, double r12hx, double r12hy,
                                                      double r12hz, double mu, double kappa, int only_d) {
   const long long N = (long long)nx * ny * nz;
   const double r12[3] = {r12hx, r12hy, r12hz};
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x)
-    visc_point(pm, fv, nx, ny, nz, p, r12, mu, kappa, only_d);
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+    if (DF) visc_point_df(pm, fv, nx, ny, nz, p, r12, mu, kappa, only_d);
+    else visc_point(pm, fv, nx, ny, nz, p, r12, mu, kappa, only_d);
+  }
 }
 
 // ---- FP32-bulk variants: same formulas in FP32, results widened to FP64 -----------
@@ -286,10 +290,14 @@ cudaError_t launch_prim(const Grid& g, const double* u, double* pm, double gamma
 }
 
 cudaError_t launch_visc(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s,
-                        int only_d) {
-  k_visc<<<grid_for(g.N, PW_THREADS), PW_THREADS, 0, s>>>(pm, fv, g.n[0], g.n[1], g.n[2], 1.0 / (12.0 * g.h[0]),
-                                                          1.0 / (12.0 * g.h[1]), 1.0 / (12.0 * g.h[2]), mu, kappa,
-                                                          only_d);
+                        int only_d, int df) {
+  const double rx = 1.0 / (12.0 * g.h[0]), ry = 1.0 / (12.0 * g.h[1]), rz = 1.0 / (12.0 * g.h[2]);
+  if (df)
+    k_visc<true><<<grid_for(g.N, PW_THREADS), PW_THREADS, 0, s>>>(pm, fv, g.n[0], g.n[1], g.n[2], rx, ry, rz, mu,
+                                                                  kappa, only_d);
+  else
+    k_visc<false><<<grid_for(g.N, PW_THREADS), PW_THREADS, 0, s>>>(pm, fv, g.n[0], g.n[1], g.n[2], rx, ry, rz, mu,
+                                                                   kappa, only_d);
   return cudaGetLastError();
 }
 

@@ -82,7 +82,8 @@ int rhs_pass(ns3d_ctx* c, const double* u, int epi, double* out, const double* u
   auto visc_flux = [&](int only_d) {
     return timed(c, NS3D_K_VISC, [&] {
       return f32 ? launch_visc32(c->g, c->pm, c->fv, c->p.mu_eff, kappa, c->stream, only_d)
-                 : launch_visc(c->g, c->pm, c->fv, c->p.mu_eff, kappa, c->stream, only_d);
+                 : launch_visc(c->g, c->pm, c->fv, c->p.mu_eff, kappa, c->stream, only_d,
+                               c->p.precision == NS3D_FP64 ? 1 : 0);
     }, "viscous-flux kernel");
   };
   if (visc && !c->lean && (rc = visc_flux(-1))) return rc;

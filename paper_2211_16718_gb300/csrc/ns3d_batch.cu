@@ -46,6 +46,7 @@ struct Inst {
 
 struct BatchView {
   int count, nstages;
+  int df;                     // viscous fluxes in the NS3D_FP64 form (precision NS3D_FP64)
   const Inst* inst;
   const long long* pt_off;    // [count + 1] prefix sums of points
   const long long* tile_off;  // [3][count + 1] prefix sums of tiles per direction
@@ -79,7 +80,8 @@ __device__ __forceinline__ void phase_visc(const BatchView& b, long long t0, lon
     const int i = find_inst(b.pt_off, b.count, x);
     const Inst& in = b.inst[i];
     if (in.fv == nullptr) continue;
-    visc_point<NC>(in.pm, in.fv, in.g.n[0], in.g.n[1], in.g.n[2], x - b.pt_off[i], in.r12, in.mu, in.kappa);
+    if (b.df) visc_point_df<NC>(in.pm, in.fv, in.g.n[0], in.g.n[1], in.g.n[2], x - b.pt_off[i], in.r12, in.mu, in.kappa);
+    else visc_point<NC>(in.pm, in.fv, in.g.n[0], in.g.n[1], in.g.n[2], x - b.pt_off[i], in.r12, in.mu, in.kappa);
   }
 }
 
@@ -256,6 +258,7 @@ BatchView view_of(const ns3d_batch* b) {
   BatchView v;
   v.count = b->count;
   v.nstages = b->nstages;
+  v.df = (b->mode == 1) ? 1 : 0;
   v.inst = b->d_inst;
   v.pt_off = b->d_pt_off;
   v.tile_off = b->d_tile_off;
@@ -353,7 +356,7 @@ int step_sequential(ns3d_batch* b) {
     const Inst& in = b->inst[i];
     for (int s = 0; s < b->nstages; ++s) {
       cudaError_t e = launch_prim(in.g, in.uin[s], in.pm, in.gamma, b->d_status, b->stream);
-      if (e == cudaSuccess && in.fv) e = launch_visc(in.g, in.pm, in.fv, in.mu, in.kappa, b->stream);
+      if (e == cudaSuccess && in.fv) e = launch_visc(in.g, in.pm, in.fv, in.mu, in.kappa, b->stream, -1, b->mode);
       for (int d = 0; d < 3 && e == cudaSuccess; ++d) e = launch_dir(d, in.dir[s][d], b->stream);
       if (e != cudaSuccess) return berr(b, NS3D_ECUDA, cudaGetErrorString(e));
     }

@@ -63,9 +63,10 @@ struct DirArgs {
 
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_prim(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s);
-// only_d < 0: all three viscous flux vectors into fv[12][N]; only_d = d: the flux along d into fv[4][N]
+// only_d < 0: all three viscous flux vectors into fv[12][N]; only_d = d: the flux along d into fv[4][N];
+// df: the NS3D_FP64 form (double-float after the stencil differences)
 cudaError_t launch_visc(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s,
-                        int only_d = -1);
+                        int only_d = -1, int df = 0);
 // FP32-bulk variants (FP32 arithmetic, results widened to FP64)
 cudaError_t launch_prim32(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s);
 cudaError_t launch_visc32(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s,
