@@ -18,20 +18,27 @@ namespace ns3d {
 
 namespace {
 
-constexpr int W = 4;
 constexpr int NQ = 9;
-constexpr int TP = 32;
-constexpr int NP = TP + 6, NW = TP + 4, NI = TP + 1;
 constexpr int THREADS = 256;  // 8 warps per tile: latency hiding for the FP32 chains
-// shared-memory plan (4-byte words)
-constexpr int OFF_Q = 0;                          // float [NQ][NP*W]
-constexpr int OFF_ROE = OFF_Q + NQ * NP * W;      // float [5][NP*W]
-constexpr int OFF_B = OFF_ROE + 5 * NP * W;       // float [NQ][3][NW*W]
-constexpr int OFF_R = OFF_B + NQ * 3 * NW * W;    // float [18][NI*W]
-constexpr int OFF_FV = (OFF_R + 18 * NI * W + 1) & ~1;  // double [4][NP*W]
-constexpr int OFF_F = OFF_FV + 2 * 4 * NP * W;    // double [5][NI*W]
-constexpr int WORDS = OFF_F + 2 * 5 * NI * W;
-constexpr int BYTES = WORDS * 4;
+
+// Tile plan: TP points along the pencil x W lines (32 x 4 by default).  The y and z passes can
+// also run 16 x 8 or 8 x 16 tiles (W consecutive x-lines per row of loads); on GB300 at 256^3
+// these measured 7 % and 8 % slower than 32 x 4.  Every shape computes the same bits (the
+// per-interface arithmetic does not depend on the tiling).
+template <int TP_, int W_>
+struct P32 {
+  static constexpr int TP = TP_, W = W_;
+  static constexpr int NP = TP + 6, NW = TP + 4, NI = TP + 1;
+  // shared-memory plan (4-byte words)
+  static constexpr int OFF_Q = 0;                          // float [NQ][NP*W]
+  static constexpr int OFF_ROE = OFF_Q + NQ * NP * W;      // float [5][NP*W]
+  static constexpr int OFF_B = OFF_ROE + 5 * NP * W;       // float [NQ][3][NW*W]
+  static constexpr int OFF_R = OFF_B + NQ * 3 * NW * W;    // float [18][NI*W]
+  static constexpr int OFF_FV = (OFF_R + 18 * NI * W + 1) & ~1;  // double [4][NP*W]
+  static constexpr int OFF_F = OFF_FV + 2 * 4 * NP * W;    // double [5][NI*W]
+  static constexpr int WORDS = OFF_F + 2 * 5 * NI * W;
+  static constexpr int BYTES = WORDS * 4;
+};
 
 __device__ __forceinline__ float weno_combine32(float B1, float B2, float B3, float F1, float F2, float F3) {
   // common power-of-two scaling keeps the products in range (omega is scale-free)
@@ -48,8 +55,12 @@ __device__ __forceinline__ float weno_combine32(float B1, float B2, float B3, fl
   return __fdiv_rn(num, den);
 }
 
-template <int D>
+template <int D, int TP_, int W_>
 __global__ void __launch_bounds__(THREADS) k_dir32(const DirArgs a) {
+  using PL = P32<TP_, W_>;
+  constexpr int TP = PL::TP, W = PL::W, NP = PL::NP, NW = PL::NW, NI = PL::NI;
+  constexpr int OFF_Q = PL::OFF_Q, OFF_ROE = PL::OFF_ROE, OFF_B = PL::OFF_B, OFF_R = PL::OFF_R;
+  constexpr int OFF_FV = PL::OFF_FV, OFF_F = PL::OFF_F;
   extern __shared__ float smf[];
   double* smd = reinterpret_cast<double*>(smf);
   const int nD = a.g.n[D];
@@ -253,29 +264,47 @@ __global__ void __launch_bounds__(THREADS) k_dir32(const DirArgs a) {
   }
 }
 
-template <int D>
+template <int D, int TP, int W>
 cudaError_t launch32(const DirArgs& a, cudaStream_t s) {
   constexpr int AX = (D == 0) ? 1 : 0;
   constexpr int BX = (D == 2) ? 1 : 2;
   dim3 grid((a.g.n[D] + TP - 1) / TP, (a.g.n[AX] + W - 1) / W, a.g.n[BX]);
-  k_dir32<D><<<grid, THREADS, BYTES, s>>>(a);
+  k_dir32<D, TP, W><<<grid, THREADS, P32<TP, W>::BYTES, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int D, int TP, int W>
+cudaError_t attr32() {
+  return cudaFuncSetAttribute(k_dir32<D, TP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, P32<TP, W>::BYTES);
 }
 
 }  // namespace
 
 cudaError_t prepare_dir32_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(k_dir32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, BYTES);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dir32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, BYTES);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dir32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, BYTES);
+  cudaError_t e = attr32<0, 32, 4>();
+  if (e == cudaSuccess) e = attr32<1, 16, 8>();
+  if (e == cudaSuccess) e = attr32<2, 16, 8>();
+  if (e == cudaSuccess) e = attr32<1, 32, 4>();
+  if (e == cudaSuccess) e = attr32<2, 32, 4>();
+  if (e == cudaSuccess) e = attr32<1, 8, 16>();
+  if (e == cudaSuccess) e = attr32<2, 8, 16>();
   return e;
 }
 
+// x pass: 32 x 4; y and z passes by the context's variant: 0 -> 32 x 4, 1 -> 16 x 8, 2 -> 8 x 16.
 cudaError_t launch_dir32(int d, const DirArgs& a, cudaStream_t s) {
-  switch (d) {
-    case 0: return launch32<0>(a, s);
-    case 1: return launch32<1>(a, s);
-    default: return launch32<2>(a, s);
+  if (d == 0) return launch32<0, 32, 4>(a, s);
+  if (d == 1) {
+    switch (a.variant) {
+      case 1: return launch32<1, 16, 8>(a, s);
+      case 2: return launch32<1, 8, 16>(a, s);
+      default: return launch32<1, 32, 4>(a, s);
+    }
+  }
+  switch (a.variant) {
+    case 1: return launch32<2, 16, 8>(a, s);
+    case 2: return launch32<2, 8, 16>(a, s);
+    default: return launch32<2, 32, 4>(a, s);
   }
 }
 

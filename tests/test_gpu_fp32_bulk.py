@@ -111,3 +111,21 @@ def test_fp32_bulk_rk4_ten_steps(ns3d, orc):
     err = np.abs(ud.cpu().numpy() - orc.rk_step(P, u0, dt, 10)).max()
     bound = 10 * dt * FLUX_TOL * flux_scale(u0, (2 * math.pi,) * 3)
     assert err <= bound, (err, bound)
+
+
+def test_fp32_bulk_tile_variants_bitwise_identical(ns3d):
+    """The y and z passes' tile shapes (32 x 4, 16 x 8, 8 x 16) give the same bits."""
+    import torch
+    n = (20, 36, 18)
+    u = I.random_smooth(*n, seed=6, amp=0.1, mach=0.5)
+    outs = []
+    for v in range(3):
+        s = ns3d.Solver(*n, mu_eff=3e-3, precision=ns3d.NS3D_FP32_BULK)
+        ns3d.set_solver_variant(s, v)
+        ud = torch.from_numpy(u.copy()).cuda()
+        r = s.rhs(ud).cpu().numpy()
+        s.rk_step(ud, 0.01, 2)
+        outs.append((r, ud.cpu().numpy()))
+        s.close()
+    for v in (1, 2):
+        assert np.array_equal(outs[v][0], outs[0][0]) and np.array_equal(outs[v][1], outs[0][1])
