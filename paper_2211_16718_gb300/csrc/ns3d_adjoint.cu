@@ -97,33 +97,50 @@ AdjArgs epi_args(int epi, double* gout, const double* ubs, double* lnext, double
   return e;
 }
 
-// ubar <- (d step(u0)/d u0)^T ubar for one step of the context's integrator.
-int rk_vjp_step(ns3d_ctx* c, const double* u0, double* ubar, double dt) {
+// Stage states of one step from u0, with the launches (and so the rounding) of the
+// forward step: RK4 S2, S3, S4; SSP-RK3 S2, S3.  If next != nullptr the step is completed
+// into next (the forward step's last pass).
+int stage_states(ns3d_ctx* c, const double* u0, double* S2, double* S3, double* S4, double* next, double dt) {
   int rc = ensure_stage_buffers(c);  // the RK4 stage epilogues also update the accumulator
   if (rc) return rc;
-  double* S2 = adj_buf(c, AB_S2);
-  double* S3 = adj_buf(c, AB_S3);
-  double* S4 = adj_buf(c, AB_S4);
-  double* ubs = adj_buf(c, AB_UBS);
-  double* La = adj_buf(c, AB_LA);
-  double* Lb = adj_buf(c, AB_LB);
   if (c->p.rk == NS3D_RK4) {
-    // stage states, with the same launches (and so the same rounding) as the forward step
     if ((rc = rhs_pass(c, u0, EPI_RK4_FIRST, S2, u0, 0.5 * dt))) return rc;
     if ((rc = rhs_pass(c, S2, EPI_RK4_MID, S3, u0, 0.5 * dt))) return rc;
     if ((rc = rhs_pass(c, S3, EPI_RK4_MID, S4, u0, dt))) return rc;
-    if ((rc = copy_state(c, ubs, ubar, "adjoint copy"))) return rc;
+    return next ? rhs_pass(c, S4, EPI_RK4_LAST, next, u0, dt / 6.0) : NS3D_OK;
+  }
+  if ((rc = rhs_pass(c, u0, EPI_SSP_1, S2, u0, dt))) return rc;
+  if ((rc = rhs_pass(c, S2, EPI_SSP_2, S3, u0, dt))) return rc;
+  return next ? rhs_pass(c, S3, EPI_SSP_3, next, u0, dt) : NS3D_OK;
+}
+
+// ubar <- (d step(u0)/d u0)^T ubar, given the step's stage states (S4 unused for SSP-RK3).
+int rk_vjp_core(ns3d_ctx* c, const double* u0, const double* S2, const double* S3, const double* S4, double* ubar,
+                double dt) {
+  double* ubs = adj_buf(c, AB_UBS);
+  double* La = adj_buf(c, AB_LA);
+  double* Lb = adj_buf(c, AB_LB);
+  int rc;
+  if ((rc = copy_state(c, ubs, ubar, "adjoint copy"))) return rc;
+  if (c->p.rk == NS3D_RK4) {
     if ((rc = vjp_pass(c, S4, ubs, dt / 6.0, epi_args(AEPI_RK4_4, ubar, ubs, La, nullptr, dt / 3.0, dt)))) return rc;
     if ((rc = vjp_pass(c, S3, La, 1.0, epi_args(AEPI_RK4_M, ubar, ubs, Lb, nullptr, dt / 3.0, 0.5 * dt)))) return rc;
     if ((rc = vjp_pass(c, S2, Lb, 1.0, epi_args(AEPI_RK4_M, ubar, ubs, La, nullptr, dt / 6.0, 0.5 * dt)))) return rc;
     return vjp_pass(c, u0, La, 1.0, epi_args(AEPI_ACC, ubar, nullptr, nullptr, nullptr, 0.0, 0.0));
   }
-  if ((rc = rhs_pass(c, u0, EPI_SSP_1, S2, u0, dt))) return rc;
-  if ((rc = rhs_pass(c, S2, EPI_SSP_2, S3, u0, dt))) return rc;
-  if ((rc = copy_state(c, ubs, ubar, "adjoint copy"))) return rc;
   if ((rc = vjp_pass(c, S3, ubs, (2.0 / 3.0) * dt, epi_args(AEPI_SSP_3, ubar, ubs, Lb, La, 0.0, dt)))) return rc;
   if ((rc = vjp_pass(c, S2, Lb, 1.0, epi_args(AEPI_SSP_2, ubar, nullptr, La, La, 0.0, dt)))) return rc;
   return vjp_pass(c, u0, La, 1.0, epi_args(AEPI_ACC, ubar, nullptr, nullptr, nullptr, 0.0, 0.0));
+}
+
+// ubar <- (d step(u0)/d u0)^T ubar for one step of the context's integrator.
+int rk_vjp_step(ns3d_ctx* c, const double* u0, double* ubar, double dt) {
+  double* S2 = adj_buf(c, AB_S2);
+  double* S3 = adj_buf(c, AB_S3);
+  double* S4 = adj_buf(c, AB_S4);
+  int rc = stage_states(c, u0, S2, S3, S4, nullptr, dt);
+  if (rc) return rc;
+  return rk_vjp_core(c, u0, S2, S3, S4, ubar, dt);
 }
 
 int grow(ns3d_ctx* c, double** buf, int* cap, int states, const char* what) {
@@ -236,19 +253,26 @@ int ns3d_traj_vjp(ns3d_ctx* c, double* ubar) {
   if (rc) return rc;
   const int nsteps = c->traj_nsteps, every = c->traj_every;
   const double dt = c->traj_dt;
-  if ((rc = grow(c, &c->seg, &c->seg_cap, every, "trajectory segment"))) return rc;
+  // one segment: per step its state and stage states (RK4: 4 slots, SSP-RK3: 3), so the
+  // stages are computed once, by the same launches as the forward step
+  const int slots = (c->p.rk == NS3D_RK4) ? 4 : 3;
+  if ((rc = grow(c, &c->seg, &c->seg_cap, every * slots, "trajectory segment"))) return rc;
   const size_t S = 5 * (size_t)c->g.N;
+  auto slot = [&](int j, int k) { return c->seg + ((size_t)j * slots + k) * S; };
   const int nck = (nsteps + every - 1) / every;
   for (int sg = nck - 1; sg >= 0; --sg) {
     const int s0 = sg * every;
     const int len = (s0 + every <= nsteps) ? every : nsteps - s0;
-    if ((rc = copy_state(c, c->seg, c->ckpt + (size_t)sg * S, "segment copy"))) return rc;
-    for (int j = 1; j < len; ++j) {
-      if ((rc = copy_state(c, c->seg + (size_t)j * S, c->seg + (size_t)(j - 1) * S, "segment copy"))) return rc;
-      if ((rc = rk_one_step(c, c->seg + (size_t)j * S, dt))) return rc;
+    if ((rc = copy_state(c, slot(0, 0), c->ckpt + (size_t)sg * S, "segment copy"))) return rc;
+    for (int j = 0; j < len; ++j) {
+      double* S4 = (slots == 4) ? slot(j, 3) : nullptr;
+      if ((rc = stage_states(c, slot(j, 0), slot(j, 1), slot(j, 2), S4, j + 1 < len ? slot(j + 1, 0) : nullptr, dt)))
+        return rc;
     }
-    for (int j = len - 1; j >= 0; --j)
-      if ((rc = rk_vjp_step(c, c->seg + (size_t)j * S, ubar, dt))) return rc;
+    for (int j = len - 1; j >= 0; --j) {
+      const double* S4 = (slots == 4) ? slot(j, 3) : nullptr;
+      if ((rc = rk_vjp_core(c, slot(j, 0), slot(j, 1), slot(j, 2), S4, ubar, dt))) return rc;
+    }
   }
   return NS3D_OK;
 }
