@@ -241,8 +241,11 @@ int ns3d_storage_info(const ns3d_ctx *ctx, int *storage, size_t *device_bytes);
 
 /* ---- adjoint (vector-Jacobian products) -----------------------------------------
  * Exact discrete adjoints of the operators above (the paper has none; they serve
- * gradients of statistics of the flow with respect to its initial state), all in
- * FP64 for NS3D_FP64 and NS3D_FP64_STRICT contexts (NS3D_FP32_BULK: NS3D_EINVAL).
+ * gradients of statistics of the flow with respect to its initial state).
+ * NS3D_FP64_STRICT contexts evaluate them all in FP64; NS3D_FP64 contexts run the
+ * derivatives of the WENO5 reconstructions in double-float arithmetic (relative
+ * rounding ~1e-14, data range as for the forward weights, NS3D_ERANGE beyond it) and
+ * the rest in FP64; NS3D_FP32_BULK contexts return NS3D_EINVAL.
  * Derivatives follow the discretisation as written: the WENO5 weights (smooth,
  * eps > 0), the Roe average, Harten's quadratic branch, and |lambda| with the
  * subgradient sign(0) = 0 at its kink.  The first adjoint call of a context
