@@ -643,11 +643,10 @@ __device__ __forceinline__ double df_value(double pc, df g1, df g2, df M, const 
 }
 
 // y * d(value)/d(q_t), t = 0..4, of the reconstruction of stencil differences g0..g3 with
-// window terms b0..b2 (as weno_adjoint, in double-float).
-__device__ __forceinline__ void df_recon_adjoint(df g0, df g1, df g2, df g3, df b0, df b1, df b2, df y,
-                                                 const DFConst& k, df out[5]) {
-  df om[3], s[3], E0, E2;
-  df_omega(b0, b1, b2, om);
+// window terms b0..b2 and weights om (as weno_adjoint, in double-float).
+__device__ __forceinline__ void df_recon_adjoint(df g0, df g1, df g2, df g3, df b0, df b1, df b2, const df om[3],
+                                                 df y, const DFConst& k, df out[5]) {
+  df s[3], E0, E2;
   const df M = df_offset(g0, g1, g2, g3, om, k, E0, E2, s);
   const df v0 = df_sub(df_mul_f(g1, 3.0f), g0);
   const df v1 = df_add_fast(g1, g2);
@@ -809,16 +808,23 @@ __global__ void __launch_bounds__(APF::THREADS, 2) k_adj_dir_df(const AdjArgs a)
     const float2* B = Bw + m * 3 * NW * W;
     auto ldb = [&](int k, int w) { return df_unpack(B[k * NW * W + tile_idx<D, W>(w, line, NW)]); };
     const double* qm = q + m * NP * W;
-    df om[3], s[3], E0, E2;
-    df_omega(ldb(0, f), ldb(1, f + 1), ldb(2, f + 2), om);
-    const df ML = df_offset(g[0], g[1], g[2], g[3], om, kc, E0, E2, s);
+    df omL[3], omR[3], s[3], E0, E2;
+    df_omega(ldb(0, f), ldb(1, f + 1), ldb(2, f + 2), omL);
+    const df ML = df_offset(g[0], g[1], g[2], g[3], omL, kc, E0, E2, s);
     const double vL = df_value(qm[tile_idx<D, W>(f + 2, line, NP)], g[1], g[2], ML, kc);
-    df_omega(ldb(2, f + 3), ldb(1, f + 2), ldb(0, f + 1), om);
-    const df MR = df_offset(df_neg(g[4]), df_neg(g[3]), df_neg(g[2]), df_neg(g[1]), om, kc, E0, E2, s);
+    df_omega(ldb(2, f + 3), ldb(1, f + 2), ldb(0, f + 1), omR);
+    const df MR = df_offset(df_neg(g[4]), df_neg(g[3]), df_neg(g[2]), df_neg(g[1]), omR, kc, E0, E2, s);
     const double vR = df_value(qm[tile_idx<D, W>(f + 3, line, NP)], df_neg(g[3]), df_neg(g[2]), MR, kc);
     const int o = tile_idx<D, W>(f, line, NI);
     rec[(2 * m) * NI * W + o] = vL;
     rec[(2 * m + 1) * NI * W + o] = vR;
+    // the weights, for phase E (which overwrites these slots with its contributions)
+    float2* wm = wc + m * 6 * NI * W;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      wm[k * NI * W + o] = df_pack(omL[k]);
+      wm[(3 + k) * NI * W + o] = df_pack(omR[k]);
+    }
   }
   __syncthreads();
 
@@ -885,11 +891,22 @@ __global__ void __launch_bounds__(APF::THREADS, 2) k_adj_dir_df(const AdjArgs a)
     for (int j = 0; j < 5; ++j) g[j] = df_unpack(Gm[tile_idx<D, W>(f + j, line, NP)]);
     const float2* B = Bw + m * 3 * NW * W;
     auto ldb = [&](int k, int w) { return df_unpack(B[k * NW * W + tile_idx<D, W>(w, line, NW)]); };
-    df cL[5], cR[5];
-    df_recon_adjoint(g[0], g[1], g[2], g[3], ldb(0, f), ldb(1, f + 1), ldb(2, f + 2), d2df_bits(yL), kc, cL);
-    df_recon_adjoint(df_neg(g[4]), df_neg(g[3]), df_neg(g[2]), df_neg(g[1]), ldb(2, f + 3), ldb(1, f + 2),
-                     ldb(0, f + 1), d2df_bits(yR), kc, cR);
     float2* wm = wc + m * 6 * NI * W;
+    df omL[3], omR[3];
+    if (m < 5) {  // stored by phase C
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        omL[k] = df_unpack(wm[k * NI * W + o]);
+        omR[k] = df_unpack(wm[(3 + k) * NI * W + o]);
+      }
+    } else {
+      df_omega(ldb(0, f), ldb(1, f + 1), ldb(2, f + 2), omL);
+      df_omega(ldb(2, f + 3), ldb(1, f + 2), ldb(0, f + 1), omR);
+    }
+    df cL[5], cR[5];
+    df_recon_adjoint(g[0], g[1], g[2], g[3], ldb(0, f), ldb(1, f + 1), ldb(2, f + 2), omL, d2df_bits(yL), kc, cL);
+    df_recon_adjoint(df_neg(g[4]), df_neg(g[3]), df_neg(g[2]), df_neg(g[1]), ldb(2, f + 3), ldb(1, f + 2),
+                     ldb(0, f + 1), omR, d2df_bits(yR), kc, cR);
     wm[0 * NI * W + o] = df_pack(cL[0]);
 #pragma unroll
     for (int j = 1; j < 5; ++j) wm[j * NI * W + o] = df_pack(df_add_fast(cL[j], cR[5 - j]));
