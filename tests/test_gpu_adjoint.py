@@ -276,3 +276,53 @@ def test_trajectory_reversal_equals_stepwise_vjps_bitwise(ns3d, rk):
     s.traj_vjp(g2)
     assert torch.equal(g1, g2)
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_rhs_vjp_on_grids_smaller_than_the_stencil(ns3d, oracle, dual, precision):
+    """Dimensions of 1-3 points: every stencil wraps around the periodic box several times."""
+    n = (3, 2, 1)
+    u = I.random_smooth(*n, seed=14, amp=0.1, mach=0.5)
+    kw = dict(mu_eff=1e-2)
+    P = oracle.Params(*n, **kw)
+    lam = np.random.default_rng(8).normal(size=u.shape)
+    ref = dual.rhs_vjp_dense(P, u, lam)
+    s = ns3d.Solver(*n, precision=precision, **kw)
+    got = s.rhs_vjp(_dev(u), _dev(lam)).cpu().numpy()
+    s.check()
+    s.close()
+    assert np.abs(got - ref).max() <= TOL_DENSE * np.abs(ref).max()
+
+
+def test_adjoint_double_float_range_is_reported(ns3d):
+    """Data differences far beyond ~1e9 exceed the double-float range of the NS3D_FP64
+    adjoint: it reports NS3D_ERANGE; the strict form handles them.  Adjoint inputs of any
+    scale are fine (each tile works relative to the power of two of its largest |lambda|)."""
+    import torch
+    n = 16
+    x = I.grid(n)
+    shp = (n, n, n)
+    p = 1e25 * (1.0 + 0.1 * np.sin(x))[None, None, :] * np.ones(shp)
+    zero = np.zeros(shp)
+    u = _dev(I.to_conserved(np.ones(shp), zero, zero, zero, p))
+    lam = torch.ones_like(u) * torch.linspace(0.0, 1.0, n, dtype=torch.float64, device="cuda")
+    s = ns3d.Solver(n, n, n, precision=ns3d.NS3D_FP64_STRICT)
+    ref = s.rhs_vjp(u, lam)
+    s.check()
+    assert bool(torch.isfinite(ref).all())
+    s.close()
+    s = ns3d.Solver(n, n, n, precision=ns3d.NS3D_FP64)
+    s.rhs_vjp(u, lam)
+    with pytest.raises(ns3d.Ns3dError) as ei:
+        s.check()
+    assert ei.value.code == ns3d.NS3D_ERANGE
+    # ordinary data, adjoint scaled by 1e-200 and 1e+200: the same result scaled exactly
+    v = _dev(I.random_smooth(12, 12, 12, seed=3, amp=0.1))
+    lam = torch.from_numpy(np.random.default_rng(0).normal(size=(5, 12, 12, 12))).cuda()
+    s2 = ns3d.Solver(12, 12, 12, mu_eff=1e-3)
+    a = s2.rhs_vjp(v, lam)
+    for scale in (2.0 ** -660, 2.0 ** 660):
+        b = s2.rhs_vjp(v, lam * scale)
+        s2.check()
+        assert torch.equal(b, a * scale)
+    s2.close()
