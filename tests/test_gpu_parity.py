@@ -15,7 +15,7 @@ from tests._util import inc_rel_err, rel_err, rel_err_var
 
 pytestmark = pytest.mark.gpu
 
-RHS_TOL = 1e-12      # relative max-norm of the RHS vector (spec bound)
+RHS_TOL = 1e-12      # relative max-norm of the RHS vector after one evaluation
 # Mach-0.1 Taylor-Green: the FP64 evaluation itself is ~1.4e-12 (16^3) / 3.0e-12 (32^3) away
 # from the extended-precision one (tests/test_oracle_rounding.py), so two independent FP64
 # implementations cannot meet 1e-12 there; the bound is 1e-11 for those cases only.
