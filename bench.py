@@ -774,7 +774,7 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         from paper_2211_16718_gb300 import build as B
         B.build()
-        print(json.dumps({"study": "ensemble", "config5": run_ensemble(args.steps, args.cfl),
+        print(json.dumps({"study": "ensemble", "ensemble_48_uneven": run_ensemble(args.steps, args.cfl),
                           "small_instances": run_ensemble(args.steps, args.cfl, count=256,
                                                           sizes_cycle=(12, 16, 20, 24))}), flush=True)
         return
@@ -816,7 +816,8 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         from paper_2211_16718_gb300 import build as B
         B.build()
-        print(json.dumps({"study": "adjoint", "config4": run_adjoint(kernel_sizes=(ADJ_N, 256))}), flush=True)
+        print(json.dumps({"study": "adjoint", "taylor_green_64_ke_gradient": run_adjoint(kernel_sizes=(ADJ_N, 256))}),
+              flush=True)
         return
     if args.impl == "reference":
         # the oracle runs on the host of rank 0 only; other ranks exit without work
