@@ -21,10 +21,9 @@ namespace {
 constexpr int NQ = 9;
 constexpr int THREADS = 256;  // 8 warps per tile: latency hiding for the FP32 chains
 
-// Tile plan: TP points along the pencil x W lines (32 x 4 by default).  The y and z passes can
-// also run 16 x 8 or 8 x 16 tiles (W consecutive x-lines per row of loads); on GB300 at 256^3
-// these measured 7 % and 8 % slower than 32 x 4.  Every shape computes the same bits (the
-// per-interface arithmetic does not depend on the tiling).
+// Tile plan: TP points along the pencil x W lines.  The y and z passes can run 32 x 4 or
+// 16 x 8 tiles (W consecutive x-lines per row of loads).  Every shape computes the same bits
+// (the per-interface arithmetic does not depend on the tiling).
 template <int TP_, int W_>
 struct P32 {
   static constexpr int TP = TP_, W = W_;
@@ -161,6 +160,18 @@ __global__ void __launch_bounds__(THREADS) k_dir32(const DirArgs a) {
   }
   __syncthreads();
 
+  // ---- epilogue operands: fetched asynchronously into the (now unused) indicator space
+  //      while phase D runs; each thread later reads only its own point's slots
+  static_assert(TP * W <= THREADS, "one epilogue point per thread");
+  static_assert(30 * TP * W <= NQ * 3 * NW * W && OFF_B % 2 == 0, "prefetch slots fit the indicator space");
+  double* pre = smd + OFF_B / 2 + 15 * tid;
+  if (tid < TP * W) {
+    int pp, line;
+    tile_split<D, W>(tid, TP, pp, line);
+    if (s0 + pp < nD && a0 + line < na) epilogue_prefetch(a, tile_flat<D>(a.g, s0 + pp, a0 + line, bz), pre);
+  }
+  cp_async_commit();
+
   // ---- D: Roe flux (FP32), widened to FP64 -----------------------------------------
   {
     const float gm1 = (float)(a.gamma - 1.0);
@@ -237,6 +248,7 @@ __global__ void __launch_bounds__(THREADS) k_dir32(const DirArgs a) {
   __syncthreads();
 
   // ---- E: FP64 conservative difference + viscous divergence + epilogue -------------
+  cp_async_wait_all();
   {
     const double rdx = 1.0 / a.g.h[D];
     const double r12 = 1.0 / (12.0 * a.g.h[D]);
@@ -259,7 +271,7 @@ __global__ void __launch_bounds__(THREADS) k_dir32(const DirArgs a) {
           cv[1 + cc] = fma(fma(8.0, d1, -d2), r12, cv[1 + cc]);
         }
       }
-      dir_epilogue(a, tile_flat<D>(a.g, s0 + pp, a0 + line, bz), cv);
+      dir_epilogue_pre(a, tile_flat<D>(a.g, s0 + pp, a0 + line, bz), cv, pre);
     }
   }
 }
@@ -286,26 +298,15 @@ cudaError_t prepare_dir32_kernels() {
   if (e == cudaSuccess) e = attr32<2, 16, 8>();
   if (e == cudaSuccess) e = attr32<1, 32, 4>();
   if (e == cudaSuccess) e = attr32<2, 32, 4>();
-  if (e == cudaSuccess) e = attr32<1, 8, 16>();
-  if (e == cudaSuccess) e = attr32<2, 8, 16>();
   return e;
 }
 
-// x pass: 32 x 4; y and z passes by the context's variant: 0 -> 32 x 4, 1 -> 16 x 8, 2 -> 8 x 16.
+// x pass: 32 x 4.  y and z passes by the context's variant: 0 -> y 32 x 4, z 16 x 8 (the fastest
+// measured on GB300 at 256^3 with the epilogue prefetch); 1 -> y and z 32 x 4; 2 -> y and z 16 x 8.
 cudaError_t launch_dir32(int d, const DirArgs& a, cudaStream_t s) {
   if (d == 0) return launch32<0, 32, 4>(a, s);
-  if (d == 1) {
-    switch (a.variant) {
-      case 1: return launch32<1, 16, 8>(a, s);
-      case 2: return launch32<1, 8, 16>(a, s);
-      default: return launch32<1, 32, 4>(a, s);
-    }
-  }
-  switch (a.variant) {
-    case 1: return launch32<2, 16, 8>(a, s);
-    case 2: return launch32<2, 8, 16>(a, s);
-    default: return launch32<2, 32, 4>(a, s);
-  }
+  if (d == 1) return (a.variant == 2) ? launch32<1, 16, 8>(a, s) : launch32<1, 32, 4>(a, s);
+  return (a.variant == 1) ? launch32<2, 32, 4>(a, s) : launch32<2, 16, 8>(a, s);
 }
 
 }  // namespace ns3d

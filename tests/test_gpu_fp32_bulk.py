@@ -114,7 +114,7 @@ def test_fp32_bulk_rk4_ten_steps(ns3d, orc):
 
 
 def test_fp32_bulk_tile_variants_bitwise_identical(ns3d):
-    """The y and z passes' tile shapes (32 x 4, 16 x 8, 8 x 16) give the same bits."""
+    """The y and z passes' tile shapes (32 x 4, 16 x 8) give the same bits."""
     import torch
     n = (20, 36, 18)
     u = I.random_smooth(*n, seed=6, amp=0.1, mach=0.5)
