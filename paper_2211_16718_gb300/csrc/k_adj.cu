@@ -969,19 +969,13 @@ __global__ void __launch_bounds__(APF::THREADS, 2) k_adj_dir_df(const AdjArgs a)
   }
 }
 
-__device__ __forceinline__ void point_ijk(long long p, int nx, int ny, int& i, int& j, int& k) {
-  i = (int)(p % nx);
-  j = (int)((p / nx) % ny);
-  k = (int)(p / ((long long)nx * ny));
-}
-
 // Neighbour flat indices at offsets -2, -1, +1, +2 along direction d.
 __device__ __forceinline__ void neighbours(int i, int j, int k, int d, const Grid& g, long long nb[4]) {
 #pragma unroll
   for (int o = 0; o < 4; ++o) {
     const int off = (o < 2) ? (o - 2) : (o - 1);
     int c[3] = {i, j, k};
-    c[d] = wrap_idx(c[d] + off, g.n[d]);
+    c[d] = wrap_near(c[d], off, g.n[d]);
     nb[o] = flat3(c[0], c[1], c[2], g.n[0], g.n[1]);
   }
 }
@@ -1007,9 +1001,10 @@ __global__ void __launch_bounds__(256) k_visc_adj1(const Grid g, const double* _
                                                    const double* __restrict__ lam, double lam_scale,
                                                    double* __restrict__ sc, double mu, double kappa) {
   const long long N = g.N;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-    int i, j, k;
-    point_ijk(p, g.n[0], g.n[1], i, j, k);
+  // one thread per point of a 32 x 8 block of an x-y plane; blockIdx.z = the plane
+  const int i = blockIdx.x * 32 + threadIdx.x % 32, j = blockIdx.y * 8 + threadIdx.x / 32, k = blockIdx.z;
+  if (i < g.n[0] && j < g.n[1]) {
+    const long long p = flat3(i, j, k, g.n[0], g.n[1]);
     double G[4][3];
     point_gradients(g, pm, i, j, k, G);
     const double vel[3] = {pm[PM_U * N + p], pm[PM_V * N + p], pm[PM_W * N + p]};
@@ -1058,9 +1053,10 @@ __global__ void __launch_bounds__(256) k_visc_adj2(const Grid g, const double* _
                                                    const double* __restrict__ sc, double gamma,
                                                    double* __restrict__ out, int accumulate, int with_rho) {
   const long long N = g.N;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-    int i, j, k;
-    point_ijk(p, g.n[0], g.n[1], i, j, k);
+  // one thread per point of a 32 x 8 block of an x-y plane; blockIdx.z = the plane
+  const int i = blockIdx.x * 32 + threadIdx.x % 32, j = blockIdx.y * 8 + threadIdx.x / 32, k = blockIdx.z;
+  if (i < g.n[0] && j < g.n[1]) {
+    const long long p = flat3(i, j, k, g.n[0], g.n[1]);
     double Wb[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
@@ -1126,9 +1122,10 @@ __global__ void __launch_bounds__(256) k_ens_seed(const Grid g, const double* __
                                                   const double* __restrict__ pm, double* __restrict__ sc) {
   const long long N = g.N;
   const double rn = 1.0 / (double)N;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-    int i, j, k;
-    point_ijk(p, g.n[0], g.n[1], i, j, k);
+  // one thread per point of a 32 x 8 block of an x-y plane; blockIdx.z = the plane
+  const int i = blockIdx.x * 32 + threadIdx.x % 32, j = blockIdx.y * 8 + threadIdx.x / 32, k = blockIdx.z;
+  if (i < g.n[0] && j < g.n[1]) {
+    const long long p = flat3(i, j, k, g.n[0], g.n[1]);
     double G[4][3];
     point_gradients(g, pm, i, j, k, G);
     const double wx = G[2][1] - G[1][2], wy = G[0][2] - G[2][0], wz = G[1][0] - G[0][1];
@@ -1154,6 +1151,9 @@ int point_blocks(const Grid& g) {
   const long long b = (g.N + 255) / 256;
   return (int)(b < 152LL * 16 ? b : 152LL * 16);
 }
+
+// Launch geometry of the stencil point kernels: 32 x 8 x 1 blocks of 256 threads over (x, y, z).
+dim3 plane_blocks(const Grid& g) { return dim3((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, g.n[2]); }
 
 }  // namespace
 
@@ -1193,13 +1193,13 @@ cudaError_t launch_adj_dir(int d, const AdjArgs& a, cudaStream_t s) {
 
 cudaError_t launch_visc_adj1(const Grid& g, const double* pm, const double* lam, double lam_scale, double* scratch,
                              double mu, double kappa, cudaStream_t s) {
-  k_visc_adj1<<<point_blocks(g), 256, 0, s>>>(g, pm, lam, lam_scale, scratch, mu, kappa);
+  k_visc_adj1<<<plane_blocks(g), 256, 0, s>>>(g, pm, lam, lam_scale, scratch, mu, kappa);
   return cudaGetLastError();
 }
 
 cudaError_t launch_visc_adj2(const Grid& g, const double* u, const double* scratch, double gamma, double* out,
                              int accumulate, int with_rho, cudaStream_t s) {
-  k_visc_adj2<<<point_blocks(g), 256, 0, s>>>(g, u, scratch, gamma, out, accumulate, with_rho);
+  k_visc_adj2<<<plane_blocks(g), 256, 0, s>>>(g, u, scratch, gamma, out, accumulate, with_rho);
   return cudaGetLastError();
 }
 
@@ -1209,7 +1209,7 @@ cudaError_t launch_ke_seed(const Grid& g, const double* u, double* grad, cudaStr
 }
 
 cudaError_t launch_ens_seed(const Grid& g, const double* u, const double* pm, double* scratch, cudaStream_t s) {
-  k_ens_seed<<<point_blocks(g), 256, 0, s>>>(g, u, pm, scratch);
+  k_ens_seed<<<plane_blocks(g), 256, 0, s>>>(g, u, pm, scratch);
   return cudaGetLastError();
 }
 

@@ -24,7 +24,7 @@ __device__ __forceinline__ int prim_point(const double* __restrict__ u, double* 
   const double rho = u[p], mx = u[N + p], my = u[2 * N + p], mz = u[3 * N + p], e = u[4 * N + p];
   const double ri = 1.0 / rho;
   const double vx = mx * ri, vy = my * ri, vz = mz * ri;
-  const double ke = 0.5 * (mx * vx + my * vy + mz * vz);
+  const double ke = 0.5 * fma(mx, vx, fma(my, vy, mz * vz));  // explicit: the same bits in every kernel
   const double pr = (gamma - 1.0) * (e - ke);
   pm[PM_U * N + p] = vx;
   pm[PM_V * N + p] = vy;
@@ -40,9 +40,20 @@ __device__ __forceinline__ long long flat3(int i, int j, int k, int nx, int ny) 
   return ((long long)k * ny + j) * nx + i;
 }
 
-// 4th-order central first derivative, difference form, times 1/(12 h).
+// Periodic wrap of c + off for |off| <= 2: two compares instead of a division (any n >= 2),
+// the modulo only for a one-point dimension.
+__device__ __forceinline__ int wrap_near(int c, int off, int n) {
+  if (n < 2) return wrap_idx(c + off, n);
+  int r = c + off;
+  r = (r < 0) ? r + n : r;
+  return (r >= n) ? r - n : r;
+}
+
+// 4th-order central first derivative, difference form, times 1/(12 h).  The final product is
+// rounded on its own (__dmul_rn) so that no call site can fuse it into a following addition:
+// every kernel that evaluates a gradient then produces the same bits.
 __device__ __forceinline__ double d4(double qm2, double qm1, double qp1, double qp2, double r12h) {
-  return fma(8.0, qp1 - qm1, -(qp2 - qm2)) * r12h;
+  return __dmul_rn(fma(8.0, qp1 - qm1, -(qp2 - qm2)), r12h);
 }
 
 // Gradients of (u, v, w, T) at point p, then the three viscous flux vectors
@@ -50,13 +61,11 @@ __device__ __forceinline__ double d4(double qm2, double qm1, double qp1, double 
 // q = -kappa grad T), written to fv[(4 d + c) N + p]; with only_d >= 0 just the
 // flux along only_d, written to fv[c N + p] (same arithmetic, so the same bits).
 template <bool NC = true>
-__device__ __forceinline__ void visc_point(const double* __restrict__ pm, double* __restrict__ fv, int nx, int ny,
-                                           int nz, long long p, const double r12[3], double mu, double kappa,
-                                           int only_d = -1) {
+__device__ __forceinline__ void visc_point_ijk(const double* __restrict__ pm, double* __restrict__ fv, int nx, int ny,
+                                               int nz, int i, int j, int k, const double r12[3], double mu,
+                                               double kappa, int only_d = -1) {
   const long long N = (long long)nx * ny * nz;
-  const int i = (int)(p % nx);
-  const int j = (int)((p / nx) % ny);
-  const int k = (int)(p / ((long long)nx * ny));
+  const long long p = flat3(i, j, k, nx, ny);
   double G[4][3];
   const int n3[3] = {nx, ny, nz};
 #pragma unroll
@@ -66,7 +75,7 @@ __device__ __forceinline__ void visc_point(const double* __restrict__ pm, double
     for (int o = 0; o < 4; ++o) {
       const int off = (o < 2) ? (o - 2) : (o - 1);  // -2, -1, +1, +2
       int c[3] = {i, j, k};
-      c[d] = wrap_idx(c[d] + off, n3[d]);
+      c[d] = wrap_near(c[d], off, n3[d]);
       nb[o] = flat3(c[0], c[1], c[2], nx, ny);
     }
 #pragma unroll
@@ -99,13 +108,11 @@ __device__ __forceinline__ void visc_point(const double* __restrict__ pm, double
 // ~mu |grad u| in size, so the double-float rounding (~1e-14 relative) stays far below the
 // FP64 rounding of the convective terms they are added to.
 template <bool NC = true>
-__device__ __forceinline__ void visc_point_df(const double* __restrict__ pm, double* __restrict__ fv, int nx, int ny,
-                                              int nz, long long p, const double r12[3], double mu, double kappa,
-                                              int only_d = -1) {
+__device__ __forceinline__ void visc_point_df_ijk(const double* __restrict__ pm, double* __restrict__ fv, int nx,
+                                                  int ny, int nz, int i, int j, int k, const double r12[3], double mu,
+                                                  double kappa, int only_d = -1) {
   const long long N = (long long)nx * ny * nz;
-  const int i = (int)(p % nx);
-  const int j = (int)((p / nx) % ny);
-  const int k = (int)(p / ((long long)nx * ny));
+  const long long p = flat3(i, j, k, nx, ny);
   df G[4][3];
   const int n3[3] = {nx, ny, nz};
 #pragma unroll
@@ -115,7 +122,7 @@ __device__ __forceinline__ void visc_point_df(const double* __restrict__ pm, dou
     for (int o = 0; o < 4; ++o) {
       const int off = (o < 2) ? (o - 2) : (o - 1);  // -2, -1, +1, +2
       int c[3] = {i, j, k};
-      c[d] = wrap_idx(c[d] + off, n3[d]);
+      c[d] = wrap_near(c[d], off, n3[d]);
       nb[o] = flat3(c[0], c[1], c[2], nx, ny);
     }
     const df r = d2df_bits(r12[d]);
@@ -149,6 +156,22 @@ __device__ __forceinline__ void visc_point_df(const double* __restrict__ pm, dou
     fv[(long long)(b + 2) * N + p] = f2d_bits(tau[2].hi) + f2d_bits(tau[2].lo);
     fv[(long long)(b + 3) * N + p] = f2d_bits(en.hi) + f2d_bits(en.lo);
   }
+}
+
+// The per-point forms above, addressed by the flat point index p (batched kernels).
+template <bool NC = true>
+__device__ __forceinline__ void visc_point(const double* __restrict__ pm, double* __restrict__ fv, int nx, int ny,
+                                           int nz, long long p, const double r12[3], double mu, double kappa,
+                                           int only_d = -1) {
+  visc_point_ijk<NC>(pm, fv, nx, ny, nz, (int)(p % nx), (int)((p / nx) % ny), (int)(p / ((long long)nx * ny)), r12,
+                     mu, kappa, only_d);
+}
+template <bool NC = true>
+__device__ __forceinline__ void visc_point_df(const double* __restrict__ pm, double* __restrict__ fv, int nx, int ny,
+                                              int nz, long long p, const double r12[3], double mu, double kappa,
+                                              int only_d = -1) {
+  visc_point_df_ijk<NC>(pm, fv, nx, ny, nz, (int)(p % nx), (int)((p / nx) % ny), (int)(p / ((long long)nx * ny)),
+                        r12, mu, kappa, only_d);
 }
 
 }  // namespace ns3d

@@ -38,13 +38,16 @@ template <bool DF>
 __global__ void __launch_bounds__(PW_THREADS) k_visc(const double* __restrict__ pm, double* __restrict__ fv,
                                                      int nx, int ny, int nz, double r12hx, double r12hy,
                                                      double r12hz, double mu, double kappa, int only_d) {
-  const long long N = (long long)nx * ny * nz;
+  // one thread per point of a 32 x 8 block of an x-y plane; blockIdx.z = the plane
+  const int i = blockIdx.x * 32 + threadIdx.x % 32, j = blockIdx.y * 8 + threadIdx.x / 32, k = blockIdx.z;
+  if (i >= nx || j >= ny) return;
   const double r12[3] = {r12hx, r12hy, r12hz};
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-    if (DF) visc_point_df(pm, fv, nx, ny, nz, p, r12, mu, kappa, only_d);
-    else visc_point(pm, fv, nx, ny, nz, p, r12, mu, kappa, only_d);
-  }
+  if (DF) visc_point_df_ijk(pm, fv, nx, ny, nz, i, j, k, r12, mu, kappa, only_d);
+  else visc_point_ijk(pm, fv, nx, ny, nz, i, j, k, r12, mu, kappa, only_d);
 }
+
+// Launch geometry of the stencil point kernels: 32 x 8 x 1 blocks over (x, y, z).
+inline dim3 plane_grid(const Grid& g) { return dim3((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, g.n[2]); }
 
 // ---- FP32-bulk variants: same formulas in FP32, results widened to FP64 -----------
 __global__ void __launch_bounds__(PW_THREADS) k_prim32(const double* __restrict__ u, double* __restrict__ pm,
@@ -293,11 +296,9 @@ cudaError_t launch_visc(const Grid& g, const double* pm, double* fv, double mu, 
                         int only_d, int df) {
   const double rx = 1.0 / (12.0 * g.h[0]), ry = 1.0 / (12.0 * g.h[1]), rz = 1.0 / (12.0 * g.h[2]);
   if (df)
-    k_visc<true><<<grid_for(g.N, PW_THREADS), PW_THREADS, 0, s>>>(pm, fv, g.n[0], g.n[1], g.n[2], rx, ry, rz, mu,
-                                                                  kappa, only_d);
+    k_visc<true><<<plane_grid(g), PW_THREADS, 0, s>>>(pm, fv, g.n[0], g.n[1], g.n[2], rx, ry, rz, mu, kappa, only_d);
   else
-    k_visc<false><<<grid_for(g.N, PW_THREADS), PW_THREADS, 0, s>>>(pm, fv, g.n[0], g.n[1], g.n[2], rx, ry, rz, mu,
-                                                                   kappa, only_d);
+    k_visc<false><<<plane_grid(g), PW_THREADS, 0, s>>>(pm, fv, g.n[0], g.n[1], g.n[2], rx, ry, rz, mu, kappa, only_d);
   return cudaGetLastError();
 }
 
