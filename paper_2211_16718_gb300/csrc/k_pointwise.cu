@@ -80,10 +80,10 @@ __global__ void __launch_bounds__(PW_THREADS) k_visc32(const double* __restrict_
                                                        int nx, int ny, int nz, float r12hx, float r12hy,
                                                        float r12hz, float mu, float kappa, int only_d) {
   const long long N = (long long)nx * ny * nz;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(p % nx);
-    const int j = (int)((p / nx) % ny);
-    const int k = (int)(p / ((long long)nx * ny));
+  // one thread per point of a 32 x 8 block of an x-y plane; blockIdx.z = the plane
+  const int i = blockIdx.x * 32 + threadIdx.x % 32, j = blockIdx.y * 8 + threadIdx.x / 32, k = blockIdx.z;
+  if (i < nx && j < ny) {
+    const long long p = flat3(i, j, k, nx, ny);
     float G[4][3];
     const int n3[3] = {nx, ny, nz};
     const float r12[3] = {r12hx, r12hy, r12hz};
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(PW_THREADS) k_visc32(const double* __restrict_
       for (int o = 0; o < 4; ++o) {
         const int off = (o < 2) ? (o - 2) : (o - 1);
         int c[3] = {i, j, k};
-        c[d] = wrap_idx(c[d] + off, n3[d]);
+        c[d] = wrap_near(c[d], off, n3[d]);
         nb[o] = flat3(c[0], c[1], c[2], nx, ny);
       }
 #pragma unroll
@@ -309,7 +309,7 @@ cudaError_t launch_prim32(const Grid& g, const double* u, double* pm, double gam
 
 cudaError_t launch_visc32(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s,
                           int only_d) {
-  k_visc32<<<grid_for(g.N, PW_THREADS), PW_THREADS, 0, s>>>(
+  k_visc32<<<plane_grid(g), PW_THREADS, 0, s>>>(
       pm, fv, g.n[0], g.n[1], g.n[2], (float)(1.0 / (12.0 * g.h[0])), (float)(1.0 / (12.0 * g.h[1])),
       (float)(1.0 / (12.0 * g.h[2])), (float)mu, (float)kappa, only_d);
   return cudaGetLastError();
