@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--no-strict", action="store_true", help="skip the all-FP64 comparison run")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk comparison run")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 48-instance ensemble measurement")
+    ap.add_argument("--ens-count", type=int, default=0,
+                    help="--study ensemble: only this many instances (sizes --ens-sizes), e.g. for a profiler")
+    ap.add_argument("--ens-sizes", type=str, default="32,48", help="comma-separated grid sizes for --ens-count")
     ap.add_argument("--precision", choices=["fp64", "strict"], default="fp64",
                     help="context precision of --study vjp (NS3D_FP64 or NS3D_FP64_STRICT)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (Taylor-Green 64^3) measurement")
@@ -774,6 +777,11 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         from paper_2211_16718_gb300 import build as B
         B.build()
+        if args.ens_count > 0:
+            sizes = tuple(int(x) for x in args.ens_sizes.split(","))
+            print(json.dumps({"study": "ensemble", "custom": run_ensemble(args.steps, args.cfl, count=args.ens_count,
+                                                                           sizes_cycle=sizes)}), flush=True)
+            return
         print(json.dumps({"study": "ensemble", "ensemble_48_uneven": run_ensemble(args.steps, args.cfl),
                           "small_instances": run_ensemble(args.steps, args.cfl, count=256,
                                                           sizes_cycle=(12, 16, 20, 24))}), flush=True)

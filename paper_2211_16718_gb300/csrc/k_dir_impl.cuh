@@ -306,19 +306,18 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
 
   // ---- epilogue operands: fetched asynchronously into the (now unused) indicator
   //      space while phase D runs; each thread later reads only its own point's slots.
-  //      Only where the operands come from earlier launches (NC): in the persistent
-  //      kernel they are written by other CTAs of the same launch and read coherently.
+  //      cp.async.ca reads through L1 like a plain load, so in the persistent kernel (NC
+  //      false), where the operands were written by other CTAs before the last grid-wide
+  //      barrier, it sees them exactly as the plain loads it replaces would.
   static_assert(PL::TP * PL::W <= PL::THREADS, "one epilogue point per thread");
   static_assert(15 * PL::TP * PL::W <= NQ * 3 * PL::NW * PL::W, "prefetch slots fit the indicator space");
   double* pre = sm + PL::OFF_B + 15 * tid;
-  if (NC) {
-    if (tid < TP * W) {
-      int pp, line;
-      tile_split<D, W>(tid, TP, pp, line);
-      if (s0 + pp < nD && a0 + line < na) epilogue_prefetch(a, flat(s0 + pp, a0 + line), pre);
-    }
-    cp_async_commit();
+  if (tid < TP * W) {
+    int pp, line;
+    tile_split<D, W>(tid, TP, pp, line);
+    if (s0 + pp < nD && a0 + line < na) epilogue_prefetch(a, flat(s0 + pp, a0 + line), pre);
   }
+  cp_async_commit();
 
   // ---- D: Roe flux at every interface -------------------------------------------
   {
@@ -464,7 +463,7 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
   __syncthreads();
 
   // ---- E: conservative difference + viscous divergence + epilogue ----------------
-  if (NC) cp_async_wait_all();
+  cp_async_wait_all();
   {
     const double rdx = 1.0 / a.g.h[D];
     const double r12 = 1.0 / (12.0 * a.g.h[D]);
@@ -488,8 +487,7 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
         }
       }
       const long long p = flat(s0 + pp, a0 + line);
-      if (NC) dir_epilogue_pre(a, p, cv, pre);
-      else dir_epilogue(a, p, cv);
+      dir_epilogue_pre(a, p, cv, pre);
     }
   }
 }
