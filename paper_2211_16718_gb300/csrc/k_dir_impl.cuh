@@ -11,7 +11,8 @@
 //   A  load state, primitives, viscous flux; point fluxes f_D        [NP x W]
 //   B  smoothness indicators of every 3-point window for the 9
 //      reconstructed scalars (u_0..u_4, f_1..f_4)                      [9 x NW x W]
-//   C  left/right WENO5 values of the 9 scalars at every interface     [9 x NI x W]
+//   C  left/right WENO5 reconstructions of the 9 scalars at every
+//      interface (MODE 1: as their double-float sum and jump)          [9 x NI x W]
 //   D  Roe flux at every interface                                     [NI x W]
 //   E  flux difference + viscous divergence + epilogue, global writes  [TP x W]
 // The mass flux f_0 = (rho u_D) is the momentum component u_{1+D} itself, so its
@@ -28,9 +29,14 @@
 // where F_1 - F_2 and F_3 - F_2 are third differences of the data (FP64, from the
 // window second differences s) and the weights, which only multiply these small
 // differences, are evaluated in double-float arithmetic (~48 bits) on the FP32
-// pipe.  The FP64 work per interface and scalar drops from ~60 to ~16
-// instructions; the result agrees with the all-FP64 evaluation to rounding.
+// pipe.  The reconstructed values themselves are never formed: the Roe flux needs
+// fhat_L + fhat_R = P_i + P_{i+1} + (dL + dR) and the jump fhat_R - fhat_L =
+// (P_{i+1} - P_i) + dR - dL, both kept in double-float, so the FP64 pipe sees
+// only the first differences, the point sums and one combination per flux
+// component.  The result agrees with the all-FP64 evaluation to rounding.
 #include <math.h>
+
+#include <type_traits>
 
 #pragma once
 
@@ -74,15 +80,25 @@ __device__ __forceinline__ double weno_combine(double B1, double B2, double B3, 
   return num / den;
 }
 
+// Range of the squared indicators inside which df_weights needs no rescaling:
+// products of two stay below 2^120 (no overflow through the denominator and its
+// multiples) and above 2^-100 (their TwoProd error terms stay normal floats, so
+// the double-float products keep full precision).
+constexpr float DFW_LO = 0x1p-50f, DFW_HI = 0x1p60f;
+
 // Double-float weights of one reconstruction from its three squared, scaled
 // indicators (candidate order 1, 2, 3): w1 = omega_1/3, w3 = omega_3/6.
+// SCALE: rescale by a common power of two first (omega is scale-free); without
+// it every indicator must lie in [DFW_LO, DFW_HI).
+template <bool SCALE = true>
 __device__ __forceinline__ void df_weights(df B1, df B2, df B3, df& w1, df& w3) {
-  // common power-of-two scaling keeps the products in range (omega is scale-free)
-  const int E = max(exponent_of(B1.hi), max(exponent_of(B2.hi), exponent_of(B3.hi)));
-  const float sc = pow2f(-E);
-  B1 = df{B1.hi * sc, B1.lo * sc};
-  B2 = df{B2.hi * sc, B2.lo * sc};
-  B3 = df{B3.hi * sc, B3.lo * sc};
+  if (SCALE) {
+    const int E = max(exponent_of(B1.hi), max(exponent_of(B2.hi), exponent_of(B3.hi)));
+    const float sc = pow2f(-E);
+    B1 = df{B1.hi * sc, B1.lo * sc};
+    B2 = df{B2.hi * sc, B2.lo * sc};
+    B3 = df{B3.hi * sc, B3.lo * sc};
+  }
   const df p23 = df_mul(B2, B3);
   const df p13 = df_mul(B1, B3);
   const df p12 = df_mul(B1, B2);
@@ -181,6 +197,7 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
   }
 
   // ---- B: squared scaled smoothness indicators of every window ----------------
+  int need_scale = 0;
   {
     const double* q = sm + PL::OFF_Q;
     int range_bad = 0;
@@ -223,15 +240,18 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
         bw[(m * 3 + 2) * NW * W + o] = make_float2(B3.hi, B3.lo);
         // the float exponent range bounds the indicators (differences of the data
         // up to ~1e9); beyond it the host reports NS3D_ERANGE instead of a NaN
-        range_bad |= !(fmaxf(B1.hi, fmaxf(B2.hi, B3.hi)) < 1e36f);
+        const float bmax = fmaxf(B1.hi, fmaxf(B2.hi, B3.hi));
+        range_bad |= !(bmax < 1e36f);
+        need_scale |= !(bmax < DFW_HI && fminf(B1.hi, fminf(B2.hi, B3.hi)) >= DFW_LO);
       }
     }
     if (MODE == 1 && __any_sync(0xffffffffu, range_bad) && (tid & 31) == 0) atomicOr(a.status, ST_DF_RANGE);
   }
-  __syncthreads();
+  // one CTA-wide decision: rescaled weights only for tiles with extreme indicators
+  const bool tile_scale = __syncthreads_or(need_scale) != 0;
 
-  // ---- C: left/right WENO5 values at every interface --------------------------
-  {
+  // ---- C: left/right WENO5 reconstructions at every interface -------------------
+  if constexpr (MODE == 0) {
     const double* q = sm + PL::OFF_Q;
     double* rec = sm + PL::OFF_R;
     for (int item = tid; item < NQ * NI * W; item += PL::THREADS) {
@@ -239,34 +259,42 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
       int f, line;
       tile_split<D, W>(item - m * NI * W, NI, f, line);
       const double* qm = q + m * NP * W;
-      const double P1 = qm[tile_idx<D, W>(f + 1, line, NP)];
+      const double P0 = qm[tile_idx<D, W>(f, line, NP)], P1 = qm[tile_idx<D, W>(f + 1, line, NP)];
       const double P2 = qm[tile_idx<D, W>(f + 2, line, NP)], P3 = qm[tile_idx<D, W>(f + 3, line, NP)];
-      const double P4 = qm[tile_idx<D, W>(f + 4, line, NP)];
-      double vL, vR;
-      if (MODE == 0) {
-        const double P0 = qm[tile_idx<D, W>(f, line, NP)], P5 = qm[tile_idx<D, W>(f + 5, line, NP)];
-        // third-order candidates at the interface between P2 and P3
-        const double xR = fma(11.0 / 6.0, P2, fma(-7.0 / 6.0, P1, (1.0 / 3.0) * P0));
-        const double eR = fma(1.0 / 3.0, P3, fma(5.0 / 6.0, P2, (-1.0 / 6.0) * P1));
-        const double eL = fma(-1.0 / 6.0, P4, fma(5.0 / 6.0, P3, (1.0 / 3.0) * P2));
-        const double xL = fma(1.0 / 3.0, P5, fma(-7.0 / 6.0, P4, (11.0 / 6.0) * P3));
-        const double* b = sm + PL::OFF_B + m * 3 * NW * W;
-        const double B1f = b[0 * NW * W + tile_idx<D, W>(f, line, NW)];
-        const double B2f1 = b[1 * NW * W + tile_idx<D, W>(f + 1, line, NW)];
-        const double B3f2 = b[2 * NW * W + tile_idx<D, W>(f + 2, line, NW)];
-        const double B3f3 = b[2 * NW * W + tile_idx<D, W>(f + 3, line, NW)];
-        const double B2f2 = b[1 * NW * W + tile_idx<D, W>(f + 2, line, NW)];
-        const double B1f1 = b[0 * NW * W + tile_idx<D, W>(f + 1, line, NW)];
-        vL = weno_combine(B1f, B2f1, B3f2, xR, eR, eL);
-        vR = weno_combine(B3f3, B2f2, B1f1, xL, eL, eR);
-      } else {
-        // fhat_L = P2 + dL, fhat_R = P3 + dR with the offsets (differences only)
-        //   dL =  (2 g2 + g1)/6 + w1 (s0 - s1) + w3 (s1 - s2)      [w1 = omega_1/3, w3 = omega_3/6]
-        //   dR = -(2 g2 + g3)/6 + v1 (s3 - s2) - v3 (s1 - s2)
-        // (candidate 2 minus the point value, and F1 - F2, F3 - F2 as third differences),
-        // evaluated in double-float; only the two final additions use the FP64 pipe.
-        (void)P1;
-        (void)P4;
+      const double P4 = qm[tile_idx<D, W>(f + 4, line, NP)], P5 = qm[tile_idx<D, W>(f + 5, line, NP)];
+      // third-order candidates at the interface between P2 and P3
+      const double xR = fma(11.0 / 6.0, P2, fma(-7.0 / 6.0, P1, (1.0 / 3.0) * P0));
+      const double eR = fma(1.0 / 3.0, P3, fma(5.0 / 6.0, P2, (-1.0 / 6.0) * P1));
+      const double eL = fma(-1.0 / 6.0, P4, fma(5.0 / 6.0, P3, (1.0 / 3.0) * P2));
+      const double xL = fma(1.0 / 3.0, P5, fma(-7.0 / 6.0, P4, (11.0 / 6.0) * P3));
+      const double* b = sm + PL::OFF_B + m * 3 * NW * W;
+      const double B1f = b[0 * NW * W + tile_idx<D, W>(f, line, NW)];
+      const double B2f1 = b[1 * NW * W + tile_idx<D, W>(f + 1, line, NW)];
+      const double B3f2 = b[2 * NW * W + tile_idx<D, W>(f + 2, line, NW)];
+      const double B3f3 = b[2 * NW * W + tile_idx<D, W>(f + 3, line, NW)];
+      const double B2f2 = b[1 * NW * W + tile_idx<D, W>(f + 2, line, NW)];
+      const double B1f1 = b[0 * NW * W + tile_idx<D, W>(f + 1, line, NW)];
+      const int o = tile_idx<D, W>(f, line, NI);
+      rec[(2 * m) * NI * W + o] = weno_combine(B1f, B2f1, B3f2, xR, eR, eL);
+      rec[(2 * m + 1) * NI * W + o] = weno_combine(B3f3, B2f2, B1f1, xL, eL, eR);
+    }
+  } else {
+    // fhat_L = P2 + dL, fhat_R = P3 + dR with the offsets (differences only)
+    //   dL =  (2 g2 + g1)/6 + w1 (s0 - s1) + w3 (s1 - s2)      [w1 = omega_1/3, w3 = omega_3/6]
+    //   dR = -(2 g2 + g3)/6 + v1 (s3 - s2) - v3 (s1 - s2)
+    // (candidate 2 minus the point value, and F1 - F2, F3 - F2 as third differences),
+    // evaluated in double-float on the FP32 pipe.  The interface values are never
+    // formed in FP64: the Roe flux needs only
+    //   sigma = dL + dR            (fhat_L + fhat_R = P2 + P3 + sigma)
+    //   du    = g2 + dR - dL       (fhat_R - fhat_L, for the u-scalars)
+    // both double-float; phase D adds sigma to the FP64 point sum P2 + P3.
+    float2* rf = reinterpret_cast<float2*>(sm + PL::OFF_R);
+    auto phase_c = [&](auto scaled) {
+      constexpr bool SCALE = decltype(scaled)::value;
+      for (int item = tid; item < NQ * NI * W; item += PL::THREADS) {
+        const int m = item / (NI * W);
+        int f, line;
+        tile_split<D, W>(item - m * NI * W, NI, f, line);
         const float2* S = reinterpret_cast<const float2*>(sm + PL::OFF_S) + m * NW * W;
         const float2* G = reinterpret_cast<const float2*>(sm + PL::OFF_G) + m * NP * W;
         auto ldS = [&](int w) {
@@ -286,21 +314,29 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
           return df{v.x, v.y};
         };
         df w1, w3, v1, v3;
-        df_weights(ld(0, f), ld(1, f + 1), ld(2, f + 2), w1, w3);
-        df_weights(ld(2, f + 3), ld(1, f + 2), ld(0, f + 1), v1, v3);
+        df_weights<SCALE>(ld(0, f), ld(1, f + 1), ld(2, f + 2), w1, w3);
+        df_weights<SCALE>(ld(2, f + 3), ld(1, f + 2), ld(0, f + 1), v1, v3);
         const df sixth{a.sixth_hi, a.sixth_lo};
         const df g22 = df_mul_f(g2, 2.0f);
         const df eL0 = df_mul(df_add_fast(g22, g1), sixth);
         const df eR0 = df_mul(df_add_fast(g22, g3), sixth);
         const df dL = df_add_fast(eL0, df_add_fast(df_mul(w1, t0), df_mul(w3, tC)));
         const df dR = df_add_fast(df_neg(eR0), df_add_fast(df_mul(v1, t2), df_neg(df_mul(v3, tC))));
-        vL = (P2 + f2d_bits(dL.hi)) + f2d_bits(dL.lo);
-        vR = (P3 + f2d_bits(dR.hi)) + f2d_bits(dR.lo);
+        const int o = tile_idx<D, W>(f, line, NI);
+        if (m < 5) {
+          const df du = df_add_fast(g2, df_add_fast(dR, df_neg(dL)));
+          rf[(2 * m) * NI * W + o] = make_float2(du.hi, du.lo);
+        }
+        if (m >= 5 || m == 1 + D) {
+          const df sg = df_add_fast(dL, dR);
+          rf[(2 * m + 1) * NI * W + o] = make_float2(sg.hi, sg.lo);
+        }
       }
-      const int o = tile_idx<D, W>(f, line, NI);
-      rec[(2 * m) * NI * W + o] = vL;
-      rec[(2 * m + 1) * NI * W + o] = vR;
-    }
+    };
+    if (tile_scale)
+      phase_c(std::true_type{});
+    else
+      phase_c(std::false_type{});
   }
   __syncthreads();
 
@@ -329,28 +365,25 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
       int f, line;
       tile_split<D, W>(item, NI, f, line);
       const int o = tile_idx<D, W>(f, line, NI);
-      double uL[5], uR[5], fL[5], fR[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        uL[v] = rec[(2 * v) * NI * W + o];
-        uR[v] = rec[(2 * v + 1) * NI * W + o];
-      }
-#pragma unroll
-      for (int v = 1; v < 5; ++v) {
-        fL[v] = rec[(2 * (4 + v)) * NI * W + o];
-        fR[v] = rec[(2 * (4 + v) + 1) * NI * W + o];
-      }
-      fL[0] = uL[1 + D];
-      fR[0] = uR[1 + D];
       const int sa = tile_idx<D, W>(f + 2, line, NP), sb = tile_idx<D, W>(f + 3, line, NP);
       if (MODE == 1) {
-        // Roe dissipation X|Lambda|X^{-1} du in double-float; only du and the final
-        // combination 0.5 (f^L + f^R - diss) use the FP64 pipe
+        // Roe dissipation X|Lambda|X^{-1} du in double-float from the double-float jumps
+        // du of phase C; the flux is 0.5 (P2 + P3) + 0.5 (sigma - diss), with only the
+        // point sum P2 + P3 and the final combination on the FP64 pipe
         const float2* rf = reinterpret_cast<const float2*>(sm + PL::OFF_ROE);
         auto ldr = [&](int k, int sp) { const float2 v = rf[k * NP * W + sp]; return df{v.x, v.y}; };
-        df du[5];
+        const float2* rj = reinterpret_cast<const float2*>(rec);
+        auto ldj = [&](int slot) { const float2 v = rj[slot * NI * W + o]; return df{v.x, v.y}; };
+        df du[5], sg[5];
+        double pp[5];  // P2 + P3 of the five flux scalars (f_0 = u_{1+D})
 #pragma unroll
-        for (int v = 0; v < 5; ++v) du[v] = d2df_bits(uR[v] - uL[v]);
+        for (int v = 0; v < 5; ++v) {
+          du[v] = ldj(2 * v);
+          const int m = (v == 0) ? 1 + D : 4 + v;
+          sg[v] = ldj(2 * m + 1);
+          const double* qm = sm + PL::OFF_Q + m * NP * W;
+          pp[v] = qm[sa] + qm[sb];
+        }
         const df ra = ldr(0, sa), rb = ldr(0, sb);
         const df rsum = df_add_pos(ra, rb);
         const df rs = df_div(df{1.0f, 0.0f}, rsum);
@@ -397,10 +430,25 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
         diss[4] = df_add_fast(df_add_fast(df_mul(S, H), df_mul(cD, un)),
                               df_add_fast(df_mul(A2, q2h), df_add_fast(df_mul(A3, vt1), df_mul(A4, vt2))));
 #pragma unroll
-        for (int v = 0; v < 5; ++v)
-          rec[v * NI * W + o] = 0.5 * ((fL[v] + fR[v]) - (f2d_bits(diss[v].hi) + f2d_bits(diss[v].lo)));
+        for (int v = 0; v < 5; ++v) {
+          const df t = df_add_fast(sg[v], df_neg(diss[v]));
+          rec[v * NI * W + o] = fma(0.5, pp[v], f2d_bits(0.5f * t.hi)) + f2d_bits(0.5f * t.lo);
+        }
         continue;
       }
+      double uL[5], uR[5], fL[5], fR[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        uL[v] = rec[(2 * v) * NI * W + o];
+        uR[v] = rec[(2 * v + 1) * NI * W + o];
+      }
+#pragma unroll
+      for (int v = 1; v < 5; ++v) {
+        fL[v] = rec[(2 * (4 + v)) * NI * W + o];
+        fR[v] = rec[(2 * (4 + v) + 1) * NI * W + o];
+      }
+      fL[0] = uL[1 + D];
+      fR[0] = uR[1 + D];
       const double ra = r[sa], rb = r[sb];
       const double rsum = ra + rb;
       // MODE 1: FP32-seeded Newton reciprocals (FP64 accurate, ~4 FP64 operations
