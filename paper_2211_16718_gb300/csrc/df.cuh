@@ -92,6 +92,31 @@ __device__ __forceinline__ df df_mul_f(df x, float c) {
   return fast_two_sum(p.hi, e);
 }
 
+// Products left unnormalised.  (hi, lo) holds exactly the sum that the normalised
+// form would hold (Fast2Sum is an exact transformation), only with |lo| up to a few
+// ulp(hi) instead of ulp(hi)/2.  The operations in this file accept such operands
+// with error bounds larger by that small factor, so a product that feeds straight
+// into another double-float operation skips the three additions of renormalising.
+__device__ __forceinline__ df df_mul_u(df x, df y) {
+  const df p = two_prod(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.lo, p.lo);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return df{p.hi, e};
+}
+
+__device__ __forceinline__ df df_sqr_u(df x) {
+  const df p = two_prod(x.hi, x.hi);
+  return df{p.hi, __fmaf_rn(__fadd_rn(x.hi, x.hi), x.lo, p.lo)};
+}
+
+__device__ __forceinline__ df df_mul_f_u(df x, float c) {
+  const df p = two_prod(x.hi, c);
+  return df{p.hi, __fmaf_rn(x.lo, c, p.lo)};
+}
+
+// Exact scaling by 2 (barring overflow).
+__device__ __forceinline__ df df_twice(df x) { return df{2.0f * x.hi, 2.0f * x.lo}; }
+
 // Division x / y (y != 0): one correction step of the float quotient.
 __device__ __forceinline__ df df_div(df x, df y) {
   const float r = __frcp_rn(y.hi);

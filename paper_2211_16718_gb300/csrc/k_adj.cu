@@ -599,7 +599,6 @@ struct AdjPlanDF {
 using APF = AdjPlanDF<16, 4>;
 
 __device__ __forceinline__ df df_sub(df x, df y) { return df_add_fast(x, df_neg(y)); }
-__device__ __forceinline__ df df_twice(df x) { return df{2.0f * x.hi, 2.0f * x.lo}; }
 __device__ __forceinline__ float2 df_pack(df x) { return make_float2(x.hi, x.lo); }
 __device__ __forceinline__ df df_unpack(float2 v) { return df{v.x, v.y}; }
 

@@ -99,12 +99,12 @@ __device__ __forceinline__ void df_weights(df B1, df B2, df B3, df& w1, df& w3) 
     B2 = df{B2.hi * sc, B2.lo * sc};
     B3 = df{B3.hi * sc, B3.lo * sc};
   }
-  const df p23 = df_mul(B2, B3);
-  const df p13 = df_mul(B1, B3);
-  const df p12 = df_mul(B1, B2);
-  const df den = df_add_pos(p23, df_add_pos(df_mul_f(p13, 6.0f), df_mul_f(p12, 3.0f)));
-  w1 = df_div(p23, df_mul_f(den, 3.0f));
-  w3 = df_div(p12, df_mul_f(den, 2.0f));
+  const df p23 = df_mul_u(B2, B3);
+  const df p13 = df_mul_u(B1, B3);
+  const df p12 = df_mul_u(B1, B2);
+  const df den = df_add_pos(p23, df_add_pos(df_mul_f_u(p13, 6.0f), df_mul_f_u(p12, 3.0f)));
+  w1 = df_div(p23, df_mul_f_u(den, 3.0f));
+  w3 = df_div(p12, df_twice(den));
 }
 
 // One tile (tx, ty, tz) of the direction-D pass, executed by the whole CTA on the
@@ -228,13 +228,13 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
         const df dgm = df{g0.x, g0.y}, dgp = df{g1.x, g1.y};
         const df ds = df_add_fast(dgp, df_neg(dgm));
         reinterpret_cast<float2*>(sm + PL::OFF_S)[m * NW * W + o] = make_float2(ds.hi, ds.lo);
-        const df aa = df_add_pos(df_mul(df_sqr(ds), df{a.c133_hi, a.c133_lo}), df{a.eps4_hi, a.eps4_lo});
-        const df u1 = df_add_fast(df_mul_f(dgp, 3.0f), df_neg(dgm));
-        const df u2 = df_add_fast(dgm, dgp);
-        const df u3 = df_add_fast(dgp, df_neg(df_mul_f(dgm, 3.0f)));
-        const df B1 = df_sqr(df_add_pos(df_sqr(u1), aa));
-        const df B2 = df_sqr(df_add_pos(df_sqr(u2), aa));
-        const df B3 = df_sqr(df_add_pos(df_sqr(u3), aa));
+        const df aa = df_add_pos(df_mul_u(df_sqr_u(ds), df{a.c133_hi, a.c133_lo}), df{a.eps4_hi, a.eps4_lo});
+        const df u1 = df_add_fast(ds, df_twice(dgp));          // x - 4y + 3z = s + 2 g+
+        const df u2 = df_add_fast(dgm, dgp);                   // z - x
+        const df u3 = df_add_fast(ds, df_neg(df_twice(dgm)));  // 3x - 4y + z = s - 2 g-
+        const df B1 = df_sqr_u(df_add_pos(df_sqr_u(u1), aa));
+        const df B2 = df_sqr_u(df_add_pos(df_sqr_u(u2), aa));
+        const df B3 = df_sqr_u(df_add_pos(df_sqr_u(u3), aa));
         bw[(m * 3 + 0) * NW * W + o] = make_float2(B1.hi, B1.lo);
         bw[(m * 3 + 1) * NW * W + o] = make_float2(B2.hi, B2.lo);
         bw[(m * 3 + 2) * NW * W + o] = make_float2(B3.hi, B3.lo);
@@ -317,11 +317,11 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
         df_weights<SCALE>(ld(0, f), ld(1, f + 1), ld(2, f + 2), w1, w3);
         df_weights<SCALE>(ld(2, f + 3), ld(1, f + 2), ld(0, f + 1), v1, v3);
         const df sixth{a.sixth_hi, a.sixth_lo};
-        const df g22 = df_mul_f(g2, 2.0f);
-        const df eL0 = df_mul(df_add_fast(g22, g1), sixth);
-        const df eR0 = df_mul(df_add_fast(g22, g3), sixth);
-        const df dL = df_add_fast(eL0, df_add_fast(df_mul(w1, t0), df_mul(w3, tC)));
-        const df dR = df_add_fast(df_neg(eR0), df_add_fast(df_mul(v1, t2), df_neg(df_mul(v3, tC))));
+        const df g22 = df_twice(g2);
+        const df eL0 = df_mul_u(df_add_fast(g22, g1), sixth);
+        const df eR0 = df_mul_u(df_add_fast(g22, g3), sixth);
+        const df dL = df_add_fast(eL0, df_add_fast(df_mul_u(w1, t0), df_mul_u(w3, tC)));
+        const df dR = df_add_fast(df_neg(eR0), df_add_fast(df_mul_u(v1, t2), df_neg(df_mul_u(v3, tC))));
         const int o = tile_idx<D, W>(f, line, NI);
         if (m < 5) {
           const df du = df_add_fast(g2, df_add_fast(dR, df_neg(dL)));
@@ -387,12 +387,12 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
         const df ra = ldr(0, sa), rb = ldr(0, sb);
         const df rsum = df_add_pos(ra, rb);
         const df rs = df_div(df{1.0f, 0.0f}, rsum);
-        const df wa = df_mul(ra, rs), wb = df_mul(rb, rs);
+        const df wa = df_mul_u(ra, rs), wb = df_mul_u(rb, rs);
         df V[3];
 #pragma unroll
-        for (int m = 0; m < 3; ++m) V[m] = df_add_fast(df_mul(wa, ldr(1 + m, sa)), df_mul(wb, ldr(1 + m, sb)));
-        const df H = df_add_pos(df_mul(wa, ldr(4, sa)), df_mul(wb, ldr(4, sb)));
-        const df q2 = df_add_pos(df_sqr(V[0]), df_add_pos(df_sqr(V[1]), df_sqr(V[2])));
+        for (int m = 0; m < 3; ++m) V[m] = df_add_fast(df_mul_u(wa, ldr(1 + m, sa)), df_mul_u(wb, ldr(1 + m, sb)));
+        const df H = df_add_pos(df_mul_u(wa, ldr(4, sa)), df_mul_u(wb, ldr(4, sb)));
+        const df q2 = df_add_pos(df_sqr_u(V[0]), df_add_pos(df_sqr_u(V[1]), df_sqr_u(V[2])));
         const df q2h = df{0.5f * q2.hi, 0.5f * q2.lo};
         const df c2 = df_mul(df_add_fast(H, df_neg(q2h)), df{a.gm1_hi, a.gm1_lo});
         bad |= !(c2.hi > 0.0f);
@@ -402,33 +402,33 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
         constexpr int T1 = (D == 0) ? 1 : 0;
         constexpr int T2 = (D == 2) ? 1 : 2;
         const df un = V[D], vt1 = V[T1], vt2 = V[T2];
-        const df b1 = df_mul(df{a.gm1_hi, a.gm1_lo}, df_sqr(rc));
-        const df vdm = df_add_fast(df_mul(V[0], du[1]), df_add_fast(df_mul(V[1], du[2]), df_mul(V[2], du[3])));
-        const df phi = df_mul(b1, df_add_fast(df_add_fast(df_mul(q2h, du[0]), du[4]), df_neg(vdm)));
+        const df b1 = df_mul_u(df{a.gm1_hi, a.gm1_lo}, df_sqr_u(rc));
+        const df vdm = df_add_fast(df_mul_u(V[0], du[1]), df_add_fast(df_mul_u(V[1], du[2]), df_mul_u(V[2], du[3])));
+        const df phi = df_mul_u(b1, df_add_fast(df_add_fast(df_mul_u(q2h, du[0]), du[4]), df_neg(vdm)));
         const df a2 = df_add_fast(du[0], df_neg(phi));
-        const df a3 = df_add_fast(du[1 + T1], df_neg(df_mul(vt1, du[0])));
-        const df a4 = df_add_fast(du[1 + T2], df_neg(df_mul(vt2, du[0])));
-        const df ach0 = df_mul(df_add_fast(df_mul(un, du[0]), df_neg(du[1 + D])), rc);
+        const df a3 = df_add_fast(du[1 + T1], df_neg(df_mul_u(vt1, du[0])));
+        const df a4 = df_add_fast(du[1 + T2], df_neg(df_mul_u(vt2, du[0])));
+        const df ach0 = df_mul_u(df_add_fast(df_mul_u(un, du[0]), df_neg(du[1 + D])), rc);
         const df ach = df{0.5f * ach0.hi, 0.5f * ach0.lo};
         const df ph = df{0.5f * phi.hi, 0.5f * phi.lo};
         const df a1 = df_add_fast(ph, ach), a5 = df_add_fast(ph, df_neg(ach));
         df l1 = df_abs(df_add_fast(un, df_neg(c))), l5 = df_abs(df_add_fast(un, c));
         const df l2 = df_abs(un);
         const df delta = df_mul(c, df{a.hd_hi, a.hd_lo});
-        if (df_lt(l1, delta)) l1 = df_div(df_add_pos(df_sqr(l1), df_sqr(delta)), df{2.0f * delta.hi, 2.0f * delta.lo});
-        if (df_lt(l5, delta)) l5 = df_div(df_add_pos(df_sqr(l5), df_sqr(delta)), df{2.0f * delta.hi, 2.0f * delta.lo});
-        const df A1 = df_mul(l1, a1), A2 = df_mul(l2, a2), A3 = df_mul(l2, a3), A4 = df_mul(l2, a4);
-        const df A5 = df_mul(l5, a5);
+        if (df_lt(l1, delta)) l1 = df_div(df_add_pos(df_sqr_u(l1), df_sqr_u(delta)), df_twice(delta));
+        if (df_lt(l5, delta)) l5 = df_div(df_add_pos(df_sqr_u(l5), df_sqr_u(delta)), df_twice(delta));
+        const df A1 = df_mul_u(l1, a1), A2 = df_mul_u(l2, a2), A3 = df_mul_u(l2, a3), A4 = df_mul_u(l2, a4);
+        const df A5 = df_mul_u(l5, a5);
         const df S = df_add_fast(A1, A5);
         const df d0 = df_add_fast(S, A2);
-        const df cD = df_mul(c, df_add_fast(A5, df_neg(A1)));
+        const df cD = df_mul_u(c, df_add_fast(A5, df_neg(A1)));
         df diss[5];
         diss[0] = d0;
-        diss[1 + D] = df_add_fast(df_mul(d0, un), cD);
-        diss[1 + T1] = df_add_fast(df_mul(d0, vt1), A3);
-        diss[1 + T2] = df_add_fast(df_mul(d0, vt2), A4);
-        diss[4] = df_add_fast(df_add_fast(df_mul(S, H), df_mul(cD, un)),
-                              df_add_fast(df_mul(A2, q2h), df_add_fast(df_mul(A3, vt1), df_mul(A4, vt2))));
+        diss[1 + D] = df_add_fast(df_mul_u(d0, un), cD);
+        diss[1 + T1] = df_add_fast(df_mul_u(d0, vt1), A3);
+        diss[1 + T2] = df_add_fast(df_mul_u(d0, vt2), A4);
+        diss[4] = df_add_fast(df_add_fast(df_mul_u(S, H), df_mul_u(cD, un)),
+                              df_add_fast(df_mul_u(A2, q2h), df_add_fast(df_mul_u(A3, vt1), df_mul_u(A4, vt2))));
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           const df t = df_add_fast(sg[v], df_neg(diss[v]));

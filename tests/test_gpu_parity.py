@@ -72,7 +72,23 @@ CASES = [
     ("shock_tube_y", lambda: I.shock_tube(12, 40, 10, axis=1), dict(mu_eff=1e-3)),
     ("shock_plus_noise", lambda: I.shock_tube(36, 20, 16, axis=0) * (1.0 + 0.01 * np.sin(
         np.arange(36 * 20 * 16).reshape(16, 20, 36) * 0.37)), dict(mu_eff=0.0)),
+    # indicators above 2^60 next to the jump: those tiles take the rescaled double-float weights
+    ("strong_blast_rescaled_weights", lambda: _blast(40, 12, 10), dict(mu_eff=1e-3)),
+    # fluids at rest with eps = 1e-14: momentum indicators (4 eps)^2 below 2^-50, rescaled too
+    ("at_rest_small_eps", lambda: I.shock_tube(30, 10, 8, axis=2), dict(mu_eff=1e-3, weno_eps=1e-14)),
 ]
+
+
+def _blast(nx, ny, nz):
+    """Pressure jump 1e5 : 1 (density 1 : 0.125) with a small seeded velocity field, so that
+    every reconstructed scalar varies and the indicators span ~40 binary orders."""
+    rng = np.random.default_rng(7)
+    shp = (nz, ny, nx)
+    left = np.broadcast_to((np.arange(nx) < nx // 2)[None, None, :], shp)
+    rho = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1e5 / I.GAMMA, 0.1 / I.GAMMA)
+    vel = [0.01 * rng.standard_normal(shp) for _ in range(3)]
+    return I.to_conserved(rho, *vel, p)
 
 
 PRECISIONS = {"fp64": 0, "fp64_strict": 2}
