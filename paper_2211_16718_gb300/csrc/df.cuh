@@ -70,6 +70,13 @@ __device__ __forceinline__ df df_add_pos(df x, df y) {
   return fast_two_sum(s.hi, s.lo);
 }
 
+// The same, left unnormalised (see df_mul_u below): with both operands non-negative
+// there is no cancellation, so |lo| stays within ~1.5 ulp(hi).
+__device__ __forceinline__ df df_add_pos_u(df x, df y) {
+  const df s = two_sum(x.hi, y.hi);
+  return df{s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo))};
+}
+
 __device__ __forceinline__ df df_neg(df x) { return df{-x.hi, -x.lo}; }
 
 __device__ __forceinline__ df df_mul(df x, df y) {
@@ -117,9 +124,26 @@ __device__ __forceinline__ df df_mul_f_u(df x, float c) {
 // Exact scaling by 2 (barring overflow).
 __device__ __forceinline__ df df_twice(df x) { return df{2.0f * x.hi, 2.0f * x.lo}; }
 
-// Division x / y (y != 0): one correction step of the float quotient.
+// Reciprocal and square root seeds from the special-function unit (PTX rcp.approx /
+// sqrt.approx, relative error about 2^-23); the double-float operations below correct
+// them, so their results do not depend on the seeds being correctly rounded.
+__device__ __forceinline__ float rcp_seed(float y) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
+  return r;
+}
+
+__device__ __forceinline__ float sqrt_seed(float y) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
+  return r;
+}
+
+// Division x / y (y a normal float magnitude): float quotient q1 from the reciprocal
+// seed, exact remainder x - q1*y (TwoProd), one correction q2 = remainder / y.  Error
+// about eps_seed^2 + 2^-48 relative (eps_seed ~ 2^-23).
 __device__ __forceinline__ df df_div(df x, df y) {
-  const float r = __frcp_rn(y.hi);
+  const float r = rcp_seed(y.hi);
   const float q1 = __fmul_rn(x.hi, r);
   // remainder x - q1*y, evaluated with TwoProd
   df p = two_prod(q1, y.hi);
@@ -131,15 +155,15 @@ __device__ __forceinline__ df df_div(df x, df y) {
   return fast_two_sum(q1, q2);
 }
 
-// Square root of a positive double-word: float seed, one correction with the exact
-// square of the seed (Dekker's method).
+// Square root of a positive double-word (hi a normal float): float seed r, one
+// correction (x - r^2)/(2r) with the exact square of the seed (Dekker's method).
 __device__ __forceinline__ df df_sqrt(df x) {
-  const float r = __fsqrt_rn(x.hi);
+  const float r = sqrt_seed(x.hi);
   const df p = two_prod(r, r);
   float d = __fsub_rn(x.hi, p.hi);
   d = __fsub_rn(d, p.lo);
   d = __fadd_rn(d, x.lo);
-  return fast_two_sum(r, __fdiv_rn(d, __fadd_rn(r, r)));
+  return fast_two_sum(r, __fmul_rn(d, __fmul_rn(0.5f, rcp_seed(r))));
 }
 
 __device__ __forceinline__ df df_abs(df x) { return (x.hi < 0.0f) ? df_neg(x) : x; }
@@ -148,16 +172,18 @@ __device__ __forceinline__ df df_abs(df x) { return (x.hi < 0.0f) ? df_neg(x) : 
 __device__ __forceinline__ bool df_lt(df x, df y) { return x.hi < y.hi || (x.hi == y.hi && x.lo < y.lo); }
 
 // ---- conversions by bit manipulation (no FP64 instructions) -----------------
-// float -> double, exact for normal floats; zero and subnormals map to signed 0.
+// float -> double, exact for normal floats; zero and subnormals map to signed 0,
+// infinities and NaNs keep their class.  Branch-free: the float exponent is rebased
+// from 127 to 1023 by one integer addition on the shifted bit pattern.
 __device__ __forceinline__ double f2d_bits(float f) {
   const uint32_t b = __float_as_uint(f);
-  const uint32_t e8 = (b >> 23) & 0xffu;
+  const uint32_t mag = b & 0x7fffffffu;
   const uint32_t sign = b & 0x80000000u;
-  if (e8 == 0u) return __hiloint2double((int)sign, 0);
-  const uint32_t m = b & 0x7fffffu;
-  const uint32_t e11 = (e8 == 0xffu) ? 0x7ffu : (e8 + 896u);
-  const uint32_t hi = sign | (e11 << 20) | (m >> 3);
-  const uint32_t lo = m << 29;
+  uint32_t hi = (mag >> 3) + (896u << 20);       // (e8 + 896) << 20 | top 20 mantissa bits
+  hi = (mag >= 0x7f800000u) ? hi + (896u << 20) : hi;  // e8 = 255 -> e11 = 2047
+  const bool zero = mag < 0x00800000u;           // zero or subnormal
+  hi = zero ? sign : (hi | sign);
+  const uint32_t lo = zero ? 0u : (b << 29);
   return __hiloint2double((int)hi, (int)lo);
 }
 
@@ -165,29 +191,24 @@ __device__ __forceinline__ double f2d_bits(float f) {
 __device__ __forceinline__ float pow2f(int k) { return __uint_as_float((uint32_t)(k + 127) << 23); }
 
 // double -> double-float: hi = x truncated to 24 significant bits, lo = the next
-// 24 bits (rounded).  Values below 2^-126 in magnitude become 0; the lo part of
-// values below 2^-74 is dropped (relative error 2^-24 only for such tiny x).
+// 29 bits rounded to a float.  Values below 2^-126 in magnitude become (+-0, 0); the lo
+// part of values below 2^-74 is dropped (relative error 2^-24 only for such tiny x);
+// values beyond the float range become +-inf.  Branch-free integer arithmetic.
 __device__ __forceinline__ df d2df_bits(double x) {
   const uint32_t h = (uint32_t)__double2hiint(x);
   const uint32_t l = (uint32_t)__double2loint(x);
   const uint32_t sign = h & 0x80000000u;
   const int e11 = (int)((h >> 20) & 0x7ffu);
-  const int e8 = e11 - 896;
-  if (e8 <= 0) return df{__uint_as_float(sign), 0.0f};
-  if (e8 >= 255) {  // beyond the float range: +-inf, or NaN for a NaN input
-    const bool nan = (e11 == 0x7ff) && (((h & 0xfffffu) | l) != 0u);
-    return df{__uint_as_float(sign | 0x7f800000u | (nan ? 1u : 0u)), 0.0f};
-  }
-  const uint32_t m23 = ((h & 0xfffffu) << 3) | (l >> 29);
-  const float hi = __uint_as_float(sign | ((uint32_t)e8 << 23) | m23);
-  const uint32_t r29 = l & 0x1fffffffu;
-  float lo = 0.0f;
-  const int k = e11 - 1075;  // weight of the least significant mantissa bit
-  if (r29 != 0u && k >= -126) {
-    lo = __uint2float_rn(r29) * pow2f(k);
-    if (sign) lo = -lo;
-  }
-  return df{hi, lo};
+  // (h:l) << 3 keeps the low 9 exponent bits and the top 23 mantissa bits; adding
+  // 2^30 (= -896 << 23 modulo 2^32) rebases the exponent for 897 <= e11 <= 1150
+  uint32_t hb = (__funnelshift_l(l, h, 3) + 0x40000000u) | sign;
+  // lo = (29 remaining bits) * 2^(e11 - 1075), signed; scale 0 below the float range
+  const uint32_t ks = (uint32_t)max(e11 - 948, 0);
+  float lo = __uint2float_rn(l & 0x1fffffffu) * __uint_as_float((ks << 23) | sign);
+  const bool tiny = e11 <= 896, huge = e11 >= 1151;
+  hb = tiny ? sign : (huge ? (sign | 0x7f800000u) : hb);
+  lo = (tiny || huge) ? 0.0f : lo;
+  return df{__uint_as_float(hb), lo};
 }
 
 // Round-to-nearest FP64 -> FP32 by bit manipulation (finite values in the float

@@ -102,7 +102,7 @@ __device__ __forceinline__ void df_weights(df B1, df B2, df B3, df& w1, df& w3) 
   const df p23 = df_mul_u(B2, B3);
   const df p13 = df_mul_u(B1, B3);
   const df p12 = df_mul_u(B1, B2);
-  const df den = df_add_pos(p23, df_add_pos(df_mul_f_u(p13, 6.0f), df_mul_f_u(p12, 3.0f)));
+  const df den = df_add_pos_u(p23, df_add_pos_u(df_mul_f_u(p13, 6.0f), df_mul_f_u(p12, 3.0f)));
   w1 = df_div(p23, df_mul_f_u(den, 3.0f));
   w3 = df_div(p12, df_twice(den));
 }
@@ -228,13 +228,13 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
         const df dgm = df{g0.x, g0.y}, dgp = df{g1.x, g1.y};
         const df ds = df_add_fast(dgp, df_neg(dgm));
         reinterpret_cast<float2*>(sm + PL::OFF_S)[m * NW * W + o] = make_float2(ds.hi, ds.lo);
-        const df aa = df_add_pos(df_mul_u(df_sqr_u(ds), df{a.c133_hi, a.c133_lo}), df{a.eps4_hi, a.eps4_lo});
+        const df aa = df_add_pos_u(df_mul_u(df_sqr_u(ds), df{a.c133_hi, a.c133_lo}), df{a.eps4_hi, a.eps4_lo});
         const df u1 = df_add_fast(ds, df_twice(dgp));          // x - 4y + 3z = s + 2 g+
         const df u2 = df_add_fast(dgm, dgp);                   // z - x
         const df u3 = df_add_fast(ds, df_neg(df_twice(dgm)));  // 3x - 4y + z = s - 2 g-
-        const df B1 = df_sqr_u(df_add_pos(df_sqr_u(u1), aa));
-        const df B2 = df_sqr_u(df_add_pos(df_sqr_u(u2), aa));
-        const df B3 = df_sqr_u(df_add_pos(df_sqr_u(u3), aa));
+        const df B1 = df_sqr_u(df_add_pos_u(df_sqr_u(u1), aa));
+        const df B2 = df_sqr_u(df_add_pos_u(df_sqr_u(u2), aa));
+        const df B3 = df_sqr_u(df_add_pos_u(df_sqr_u(u3), aa));
         bw[(m * 3 + 0) * NW * W + o] = make_float2(B1.hi, B1.lo);
         bw[(m * 3 + 1) * NW * W + o] = make_float2(B2.hi, B2.lo);
         bw[(m * 3 + 2) * NW * W + o] = make_float2(B3.hi, B3.lo);
@@ -392,7 +392,7 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
 #pragma unroll
         for (int m = 0; m < 3; ++m) V[m] = df_add_fast(df_mul_u(wa, ldr(1 + m, sa)), df_mul_u(wb, ldr(1 + m, sb)));
         const df H = df_add_pos(df_mul_u(wa, ldr(4, sa)), df_mul_u(wb, ldr(4, sb)));
-        const df q2 = df_add_pos(df_sqr_u(V[0]), df_add_pos(df_sqr_u(V[1]), df_sqr_u(V[2])));
+        const df q2 = df_add_pos_u(df_sqr_u(V[0]), df_add_pos_u(df_sqr_u(V[1]), df_sqr_u(V[2])));
         const df q2h = df{0.5f * q2.hi, 0.5f * q2.lo};
         const df c2 = df_mul(df_add_fast(H, df_neg(q2h)), df{a.gm1_hi, a.gm1_lo});
         bad |= !(c2.hi > 0.0f);
@@ -415,8 +415,8 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
         df l1 = df_abs(df_add_fast(un, df_neg(c))), l5 = df_abs(df_add_fast(un, c));
         const df l2 = df_abs(un);
         const df delta = df_mul(c, df{a.hd_hi, a.hd_lo});
-        if (df_lt(l1, delta)) l1 = df_div(df_add_pos(df_sqr_u(l1), df_sqr_u(delta)), df_twice(delta));
-        if (df_lt(l5, delta)) l5 = df_div(df_add_pos(df_sqr_u(l5), df_sqr_u(delta)), df_twice(delta));
+        if (df_lt(l1, delta)) l1 = df_div(df_add_pos_u(df_sqr_u(l1), df_sqr_u(delta)), df_twice(delta));
+        if (df_lt(l5, delta)) l5 = df_div(df_add_pos_u(df_sqr_u(l5), df_sqr_u(delta)), df_twice(delta));
         const df A1 = df_mul_u(l1, a1), A2 = df_mul_u(l2, a2), A3 = df_mul_u(l2, a3), A4 = df_mul_u(l2, a4);
         const df A5 = df_mul_u(l5, a5);
         const df S = df_add_fast(A1, A5);
