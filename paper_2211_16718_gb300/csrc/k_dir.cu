@@ -12,7 +12,7 @@ namespace ns3d {
 namespace {
 
 template <int D, int MODE, int TP, int W>
-__global__ void __launch_bounds__(Plan<MODE, TP, W>::THREADS, MIN_CTAS_PER_SM) k_dir(const DirArgs a) {
+__global__ void __launch_bounds__(Plan<MODE, TP, W>::THREADS, Plan<MODE, TP, W>::MIN_CTAS) k_dir(const DirArgs a) {
   extern __shared__ double sm[];
   dir_tile<D, MODE, TP, W>(a, sm, blockIdx.x, blockIdx.y, blockIdx.z);
 }
@@ -27,14 +27,22 @@ cudaError_t launch_t(const DirArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Dynamic shared memory of the tile plan, and the largest shared-memory carveout so that
+// Plan::MIN_CTAS tiles fit on an SM (the rest of the unified L1 stays cache).
+template <typename K>
+cudaError_t set_func_attr(K* kernel, int bytes) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  return e;
+}
+
 template <int MODE, int TP, int W>
 cudaError_t set_attr() {
   const int bytes = Plan<MODE, TP, W>::BYTES;
-  cudaError_t e = cudaFuncSetAttribute(k_dir<0, MODE, TP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_dir<1, MODE, TP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_dir<2, MODE, TP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e = set_func_attr(k_dir<0, MODE, TP, W>, bytes);
+  if (e == cudaSuccess) e = set_func_attr(k_dir<1, MODE, TP, W>, bytes);
+  if (e == cudaSuccess) e = set_func_attr(k_dir<2, MODE, TP, W>, bytes);
   return e;
 }
 

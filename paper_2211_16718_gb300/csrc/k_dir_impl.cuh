@@ -48,28 +48,54 @@
 namespace ns3d {
 
 constexpr int NQ = 9;             // reconstructed scalars
-constexpr int MIN_CTAS_PER_SM = 3;
 
 // Tile plan of a direction pass: TP points along the pencil times W lines.
+// Shared memory in 8-byte words (doubles, or double-float pairs in MODE 1):
+//   MODE 0: Q [NQ][NP*W] point values, ROE [5][NP*W] sqrt(rho), u, v, w, H,
+//           FV [4][NP*W] viscous flux, B [NQ][3][NW*W] squared indicators,
+//           R [18][NI*W] interface values, later [5][NI*W] interface fluxes.
+//   MODE 1: Q [NQ][NP*W], dead after phase A2: ROE [5][NP*W] and FV [4][NP*W] then
+//           arrive there by cp.async (as FP64) while phases B and C run;
+//           B [NQ][3][NW*W] (double-float), dead after phase C: the epilogue
+//           operands then arrive there; S [NQ][NW*W] second differences;
+//           G [NQ][NG*W] first differences; R [10][NI*W]: jumps du of u_0..u_4
+//           (double-float, slots 0-4) and the sums of the five flux scalars
+//           (FP64, slots 5-9), later [5][NI*W] interface fluxes.
+//   The MODE 1 plan of a 24 x 4 tile is 57.2 KB, so that four CTAs of 256 threads
+//   (64 registers) share an SM.
 template <int MODE, int TP_, int W_>
 struct Plan {
   static constexpr int TP = TP_;                    // points per tile along the pencil
   static constexpr int W = W_;                      // lines per tile
   static constexpr int THREADS = (MODE == 0) ? 128 : 256;  // MODE 1: 8 warps share the tile (latency hiding)
+  static constexpr int MIN_CTAS = (MODE == 0) ? 3 : 4;     // resident CTAs per SM the registers allow
   static constexpr int NP = TP + 6;                 // points incl. 3-point halo each side
   static constexpr int NW = TP + 4;                 // 3-point windows centred at -2 .. TP+1
   static constexpr int NI = TP + 1;                 // interfaces -1/2 .. TP-1/2
-  // shared-memory plan (8-byte words: doubles, or double-float pairs in MODE 1)
-  static constexpr int OFF_Q = 0;                               // [NQ][NP*W] point values
-  static constexpr int OFF_ROE = OFF_Q + NQ * NP * W;           // [5][NP*W]: sqrt(rho), u, v, w, H
-  static constexpr int OFF_FV = OFF_ROE + 5 * NP * W;           // [4][NP*W]
-  static constexpr int OFF_B = OFF_FV + 4 * NP * W;             // [NQ][3][NW*W] squared indicators
-  static constexpr int OFF_S = OFF_B + NQ * 3 * NW * W;         // [NQ][NW*W] second differences (MODE 1)
-  static constexpr int OFF_G = OFF_S + (MODE == 1 ? NQ * NW * W : 0);  // [NQ][NP*W] first differences (MODE 1)
-  static constexpr int OFF_R = OFF_G + (MODE == 1 ? NQ * NP * W : 0);  // [18][NI*W], later [5][NI*W]
-  static constexpr int WORDS = OFF_R + 18 * NI * W;
+  static constexpr int NG = NP - 1;                 // first differences
+  static constexpr int OFF_Q = 0;
+  static constexpr int OFF_ROE = (MODE == 1) ? OFF_Q : OFF_Q + NQ * NP * W;
+  static constexpr int OFF_FV = OFF_ROE + 5 * NP * W;
+  static constexpr int OFF_B = (MODE == 1) ? OFF_Q + NQ * NP * W : OFF_FV + 4 * NP * W;
+  static constexpr int OFF_S = OFF_B + NQ * 3 * NW * W;
+  static constexpr int OFF_G = OFF_S + (MODE == 1 ? NQ * NW * W : 0);
+  static constexpr int OFF_R = OFF_G + (MODE == 1 ? NQ * NG * W : 0);
+  static constexpr int R_SLOTS = (MODE == 1) ? 10 : 18;
+  static constexpr int WORDS = OFF_R + R_SLOTS * NI * W;
   static constexpr int BYTES = WORDS * 8;
+  static_assert(MODE == 0 || OFF_FV + 4 * NP * W <= OFF_B, "ROE and FV fit the dead point values");
 };
+
+// Index of conserved component c among the reconstructed scalars.  MODE 0 keeps
+// the order u_0..u_4, f_1..f_4.  MODE 1 stores the normal momentum u_{1+D} fifth,
+// (u_0, u_{1+T1}, u_{1+T2}, u_4, u_{1+D}, f_1..f_4), so that scalars 0-4 are the
+// conserved variables and scalars 4-8 the five flux components (f_0 = u_{1+D}).
+template <int MODE, int D>
+__host__ __device__ constexpr int scalar_of(int c) {
+  if (MODE == 0 || c == 0) return c;
+  constexpr int T1 = (D == 0) ? 1 : 0, T2 = (D == 2) ? 1 : 2;
+  return (c == 1 + D) ? 4 : (c == 1 + T1) ? 1 : (c == 1 + T2) ? 2 : 3;
+}
 
 __device__ __forceinline__ double weno_combine(double B1, double B2, double B3, double F1, double F2, double F3) {
   const double p23 = B2 * B3;
@@ -151,49 +177,69 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
     const int s = tile_idx<D, W>(pos, line, NP);
     double* q = sm + PL::OFF_Q;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) q[v * NP * W + s] = U[v];
+    for (int v = 0; v < 5; ++v) q[scalar_of<MODE, D>(v) * NP * W + s] = U[v];
     q[5 * NP * W + s] = (D == 0) ? fma(U[1], un, pr) : U[1] * un;
     q[6 * NP * W + s] = (D == 1) ? fma(U[2], un, pr) : U[2] * un;
     q[7 * NP * W + s] = (D == 2) ? fma(U[3], un, pr) : U[3] * un;
     q[8 * NP * W + s] = (U[4] + pr) * un;
-    if (MODE == 1) {  // Roe inputs as double-float (the Roe flux runs on the FP32 pipe)
-      float2* r = reinterpret_cast<float2*>(sm + PL::OFF_ROE);
-      const df sr = d2df_bits(ldx<NC>(a.pm + PM_SR * N + p)), hh = d2df_bits(ldx<NC>(a.pm + PM_H * N + p));
-      const df dvx = d2df_bits(vx), dvy = d2df_bits(vy), dvz = d2df_bits(vz);
-      r[0 * NP * W + s] = make_float2(sr.hi, sr.lo);
-      r[1 * NP * W + s] = make_float2(dvx.hi, dvx.lo);
-      r[2 * NP * W + s] = make_float2(dvy.hi, dvy.lo);
-      r[3 * NP * W + s] = make_float2(dvz.hi, dvz.lo);
-      r[4 * NP * W + s] = make_float2(hh.hi, hh.lo);
-    } else {
+    if (MODE == 0) {  // MODE 1 fetches these after phase A2 (cp.async into the dead point values)
       double* r = sm + PL::OFF_ROE;
       r[0 * NP * W + s] = ldx<NC>(a.pm + PM_SR * N + p);
       r[1 * NP * W + s] = vx;
       r[2 * NP * W + s] = vy;
       r[3 * NP * W + s] = vz;
       r[4 * NP * W + s] = ldx<NC>(a.pm + PM_H * N + p);
-    }
-    if (a.fv != nullptr) {
-      double* f = sm + PL::OFF_FV;
+      if (a.fv != nullptr) {
+        double* f = sm + PL::OFF_FV;
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) f[cc * NP * W + s] = ldx<NC>(a.fv + (long long)(a.fv_dstride * D + cc) * N + p);
+        for (int cc = 0; cc < 4; ++cc) f[cc * NP * W + s] = ldx<NC>(a.fv + (long long)(a.fv_dstride * D + cc) * N + p);
+      }
     }
   }
   __syncthreads();
 
-  // ---- A2 (MODE 1): first differences g_j = q_{j+1} - q_j in FP64, kept as double-float
-  if (MODE == 1) {
+  // ---- A2 (MODE 1): first differences g_j = q_{j+1} - q_j in FP64, kept as double-float,
+  //      and the FP64 point sums q_j + q_{j+1} of the five flux scalars at interface j - 2
+  constexpr int PF0 = (MODE == 1) ? PL::THREADS - NP * W : 0;  // first prefetching thread (MODE 1)
+  static_assert(MODE == 0 || NP * W <= PL::THREADS, "one prefetched point per thread");
+  if constexpr (MODE == 1) {
+    constexpr int NG = PL::NG;
     const double* q = sm + PL::OFF_Q;
     float2* G = reinterpret_cast<float2*>(sm + PL::OFF_G);
-    for (int item = tid; item < NQ * (NP - 1) * W; item += PL::THREADS) {
-      const int m = item / ((NP - 1) * W);
+    double* R = sm + PL::OFF_R;
+    for (int item = tid; item < NQ * NG * W; item += PL::THREADS) {
+      const int m = item / (NG * W);
       int j, line;
-      tile_split<D, W>(item - m * (NP - 1) * W, NP - 1, j, line);
+      tile_split<D, W>(item - m * NG * W, NG, j, line);
       const double* qm = q + m * NP * W;
-      const df g = d2df_bits(qm[tile_idx<D, W>(j + 1, line, NP)] - qm[tile_idx<D, W>(j, line, NP)]);
-      G[m * NP * W + tile_idx<D, W>(j, line, NP)] = make_float2(g.hi, g.lo);
+      const double qa = qm[tile_idx<D, W>(j, line, NP)], qb = qm[tile_idx<D, W>(j + 1, line, NP)];
+      const df g = d2df_bits(qb - qa);
+      G[m * NG * W + tile_idx<D, W>(j, line, NG)] = make_float2(g.hi, g.lo);
+      if (m >= 4 && j >= 2 && j < NI + 2) R[(1 + m) * NI * W + tile_idx<D, W>(j - 2, line, NI)] = qa + qb;
     }
     __syncthreads();
+    // the point values are dead: fetch the Roe-average inputs and the viscous flux into
+    // their space while phases B and C run.  One point per thread, on the last NP*W
+    // threads (those with the fewest phase-C items), which also convert their Roe
+    // inputs to double-float in place before the barrier that ends phase C.
+    if (tid >= PF0) {
+      int pos, line;
+      tile_split<D, W>(tid - PF0, NP, pos, line);
+      const long long p = flat(wrap_idx(s0 - 3 + pos, nD), min(a0 + line, na - 1));
+      const int sp = tile_idx<D, W>(pos, line, NP);
+      double* r = sm + PL::OFF_ROE + sp;
+      cp_async8(r + 0 * NP * W, a.pm + PM_SR * N + p);
+      cp_async8(r + 1 * NP * W, a.pm + PM_U * N + p);
+      cp_async8(r + 2 * NP * W, a.pm + PM_V * N + p);
+      cp_async8(r + 3 * NP * W, a.pm + PM_W * N + p);
+      cp_async8(r + 4 * NP * W, a.pm + PM_H * N + p);
+      if (a.fv != nullptr) {
+        double* f = sm + PL::OFF_FV + sp;
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) cp_async8(f + cc * NP * W, a.fv + (long long)(a.fv_dstride * D + cc) * N + p);
+      }
+    }
+    cp_async_commit();
   }
 
   // ---- B: squared scaled smoothness indicators of every window ----------------
@@ -223,8 +269,8 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
         bw[(m * 3 + 2) * NW * W + o] = b3 * b3;
       } else {
         float2* bw = reinterpret_cast<float2*>(sm + PL::OFF_B);
-        const float2* G = reinterpret_cast<const float2*>(sm + PL::OFF_G) + m * NP * W;
-        const float2 g0 = G[tile_idx<D, W>(w, line, NP)], g1 = G[tile_idx<D, W>(w + 1, line, NP)];
+        const float2* G = reinterpret_cast<const float2*>(sm + PL::OFF_G) + m * PL::NG * W;
+        const float2 g0 = G[tile_idx<D, W>(w, line, PL::NG)], g1 = G[tile_idx<D, W>(w + 1, line, PL::NG)];
         const df dgm = df{g0.x, g0.y}, dgp = df{g1.x, g1.y};
         const df ds = df_add_fast(dgp, df_neg(dgm));
         reinterpret_cast<float2*>(sm + PL::OFF_S)[m * NW * W + o] = make_float2(ds.hi, ds.lo);
@@ -285,9 +331,8 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
     // (candidate 2 minus the point value, and F1 - F2, F3 - F2 as third differences),
     // evaluated in double-float on the FP32 pipe.  The interface values are never
     // formed in FP64: the Roe flux needs only
-    //   sigma = dL + dR            (fhat_L + fhat_R = P2 + P3 + sigma)
-    //   du    = g2 + dR - dL       (fhat_R - fhat_L, for the u-scalars)
-    // both double-float; phase D adds sigma to the FP64 point sum P2 + P3.
+    //   du    = g2 + dR - dL       (fhat_R - fhat_L, for the u-scalars; double-float)
+    //   fhat_L + fhat_R = (P2 + P3) + (dL + dR)   (for the flux scalars; FP64)
     float2* rf = reinterpret_cast<float2*>(sm + PL::OFF_R);
     auto phase_c = [&](auto scaled) {
       constexpr bool SCALE = decltype(scaled)::value;
@@ -296,13 +341,13 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
         int f, line;
         tile_split<D, W>(item - m * NI * W, NI, f, line);
         const float2* S = reinterpret_cast<const float2*>(sm + PL::OFF_S) + m * NW * W;
-        const float2* G = reinterpret_cast<const float2*>(sm + PL::OFF_G) + m * NP * W;
+        const float2* G = reinterpret_cast<const float2*>(sm + PL::OFF_G) + m * PL::NG * W;
         auto ldS = [&](int w) {
           const float2 v = S[tile_idx<D, W>(w, line, NW)];
           return df{v.x, v.y};
         };
         auto ldG = [&](int j) {
-          const float2 v = G[tile_idx<D, W>(j, line, NP)];
+          const float2 v = G[tile_idx<D, W>(j, line, PL::NG)];
           return df{v.x, v.y};
         };
         const df s0 = ldS(f), s1 = ldS(f + 1), s2 = ldS(f + 2), s3 = ldS(f + 3);
@@ -325,11 +370,12 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
         const int o = tile_idx<D, W>(f, line, NI);
         if (m < 5) {
           const df du = df_add_fast(g2, df_add_fast(dR, df_neg(dL)));
-          rf[(2 * m) * NI * W + o] = make_float2(du.hi, du.lo);
+          rf[m * NI * W + o] = make_float2(du.hi, du.lo);
         }
-        if (m >= 5 || m == 1 + D) {
+        if (m >= 4) {  // flux scalar: fhat_L + fhat_R = (P2 + P3) + sigma, the point sum from phase A2
           const df sg = df_add_fast(dL, dR);
-          rf[(2 * m + 1) * NI * W + o] = make_float2(sg.hi, sg.lo);
+          double* F = sm + PL::OFF_R + (1 + m) * NI * W + o;
+          *F = (*F + f2d_bits(sg.hi)) + f2d_bits(sg.lo);
         }
       }
     };
@@ -337,6 +383,17 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
       phase_c(std::true_type{});
     else
       phase_c(std::false_type{});
+    cp_async_wait_all();  // this thread's ROE / FV copies; the barrier publishes them
+    if (tid >= PF0) {     // Roe-average inputs to double-float, in place
+      int pos, line;
+      tile_split<D, W>(tid - PF0, NP, pos, line);
+      double* r = sm + PL::OFF_ROE + tile_idx<D, W>(pos, line, NP);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const df x = d2df_bits(r[k * NP * W]);
+        reinterpret_cast<float2*>(r)[k * NP * W] = make_float2(x.hi, x.lo);
+      }
+    }
   }
   __syncthreads();
 
@@ -368,21 +425,18 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
       const int sa = tile_idx<D, W>(f + 2, line, NP), sb = tile_idx<D, W>(f + 3, line, NP);
       if (MODE == 1) {
         // Roe dissipation X|Lambda|X^{-1} du in double-float from the double-float jumps
-        // du of phase C; the flux is 0.5 (P2 + P3) + 0.5 (sigma - diss), with only the
-        // point sum P2 + P3 and the final combination on the FP64 pipe
-        const float2* rf = reinterpret_cast<const float2*>(sm + PL::OFF_ROE);
+        // du of phase C and the FP64 Roe-average inputs (converted here); the flux is
+        // 0.5 (fhat_L + fhat_R) - 0.5 diss, two FP64 operations per component
+        const float2* rf = reinterpret_cast<const float2*>(r);
         auto ldr = [&](int k, int sp) { const float2 v = rf[k * NP * W + sp]; return df{v.x, v.y}; };
         const float2* rj = reinterpret_cast<const float2*>(rec);
-        auto ldj = [&](int slot) { const float2 v = rj[slot * NI * W + o]; return df{v.x, v.y}; };
-        df du[5], sg[5];
-        double pp[5];  // P2 + P3 of the five flux scalars (f_0 = u_{1+D})
+        df du[5];
+        double fs[5];  // fhat_L + fhat_R of the five flux components (f_0 = u_{1+D})
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          du[v] = ldj(2 * v);
-          const int m = (v == 0) ? 1 + D : 4 + v;
-          sg[v] = ldj(2 * m + 1);
-          const double* qm = sm + PL::OFF_Q + m * NP * W;
-          pp[v] = qm[sa] + qm[sb];
+          const float2 j = rj[scalar_of<MODE, D>(v) * NI * W + o];
+          du[v] = df{j.x, j.y};
+          fs[v] = rec[(5 + v) * NI * W + o];
         }
         const df ra = ldr(0, sa), rb = ldr(0, sb);
         const df rsum = df_add_pos(ra, rb);
@@ -430,10 +484,8 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
         diss[4] = df_add_fast(df_add_fast(df_mul_u(S, H), df_mul_u(cD, un)),
                               df_add_fast(df_mul_u(A2, q2h), df_add_fast(df_mul_u(A3, vt1), df_mul_u(A4, vt2))));
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          const df t = df_add_fast(sg[v], df_neg(diss[v]));
-          rec[v * NI * W + o] = fma(0.5, pp[v], f2d_bits(0.5f * t.hi)) + f2d_bits(0.5f * t.lo);
-        }
+        for (int v = 0; v < 5; ++v)
+          rec[v * NI * W + o] = fma(0.5, fs[v], f2d_bits(-0.5f * diss[v].hi)) + f2d_bits(-0.5f * diss[v].lo);
         continue;
       }
       double uL[5], uR[5], fL[5], fR[5];

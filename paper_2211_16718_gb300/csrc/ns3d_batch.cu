@@ -115,14 +115,14 @@ __global__ void __launch_bounds__(BT) kb_visc(BatchView b) {
 }
 
 template <int D, int MODE, int TP, int W>
-__global__ void __launch_bounds__(Plan<MODE, TP, W>::THREADS, MIN_CTAS_PER_SM) kb_dir(BatchView b, int s) {
+__global__ void __launch_bounds__(Plan<MODE, TP, W>::THREADS, Plan<MODE, TP, W>::MIN_CTAS) kb_dir(BatchView b, int s) {
   extern __shared__ double sm[];
   phase_dir<D, MODE, TP, W, true>(b, s, sm, blockIdx.x, gridDim.x);
 }
 
 // ---- persistent kernel: every step, stage, phase and instance in one launch ---------
 template <int MODE, int TP, int W>
-__global__ void __launch_bounds__(Plan<MODE, TP, W>::THREADS, MIN_CTAS_PER_SM) kb_persistent(BatchView b,
+__global__ void __launch_bounds__(Plan<MODE, TP, W>::THREADS, Plan<MODE, TP, W>::MIN_CTAS) kb_persistent(BatchView b,
                                                                                            int nsteps) {
   extern __shared__ double sm[];
   cg::grid_group grid = cg::this_grid();
@@ -148,15 +148,20 @@ __global__ void __launch_bounds__(Plan<MODE, TP, W>::THREADS, MIN_CTAS_PER_SM) k
 
 template <int MODE, int TP, int W>
 struct Kernels {
+  // dynamic shared memory of the tile plan and the largest carveout (Plan::MIN_CTAS per SM)
+  template <typename K>
+  static cudaError_t attr(K* kernel, int bytes) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    return e;
+  }
   static cudaError_t set_attr() {
     const int bytes = Plan<MODE, TP, W>::BYTES;
-    cudaError_t e = cudaFuncSetAttribute(kb_dir<0, MODE, TP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(kb_dir<1, MODE, TP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(kb_dir<2, MODE, TP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(kb_persistent<MODE, TP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = attr(kb_dir<0, MODE, TP, W>, bytes);
+    if (e == cudaSuccess) e = attr(kb_dir<1, MODE, TP, W>, bytes);
+    if (e == cudaSuccess) e = attr(kb_dir<2, MODE, TP, W>, bytes);
+    if (e == cudaSuccess) e = attr(kb_persistent<MODE, TP, W>, bytes);
     return e;
   }
   static cudaError_t dir(int d, const BatchView& v, int s, long long tiles, cudaStream_t st) {
