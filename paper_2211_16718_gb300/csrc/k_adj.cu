@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(APL::THREADS, 2) k_adj_dir(const AdjArgs a) {
   const int a0 = blockIdx.y * W;
   const int bz = blockIdx.z;
   const int tid = threadIdx.x;
-  const double rdx = 1.0 / a.g.h[D];
+  const double rdx = a.g.rh[D];
   const double gm1 = a.gamma - 1.0;
   double* q = sm + APL::OFF_Q;
   double* ri = sm + APL::OFF_RI;
@@ -693,7 +693,7 @@ __global__ void __launch_bounds__(APF::THREADS, 2) k_adj_dir_df(const AdjArgs a)
   const int a0 = blockIdx.y * W;
   const int bz = blockIdx.z;
   const int tid = threadIdx.x;
-  const double rdx = 1.0 / a.g.h[D];
+  const double rdx = a.g.rh[D];
   double* q = sm + APF::OFF_Q;
   double* ri = sm + APF::OFF_RI;
   double* lm = sm + APF::OFF_L;
@@ -986,7 +986,7 @@ __device__ __forceinline__ void point_gradients(const Grid& g, const double* pm,
   for (int d = 0; d < 3; ++d) {
     long long nb[4];
     neighbours(i, j, k, d, g, nb);
-    const double r12 = 1.0 / (12.0 * g.h[d]);
+    const double r12 = g.r12h[d];
 #pragma unroll
     for (int qv = 0; qv < 4; ++qv) {
       const int plane = (qv < 3) ? qv : PM_T;
@@ -1015,7 +1015,7 @@ __global__ void __launch_bounds__(256) k_visc_adj1(const Grid g, const double* _
     for (int d = 0; d < 3; ++d) {
       long long nb[4];
       neighbours(i, j, k, d, g, nb);
-      const double r12 = 1.0 / (12.0 * g.h[d]);
+      const double r12 = g.r12h[d];
       double Fb[4];  // adjoint of the viscous flux along d: -D_d lambda_{1+c}
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) {
@@ -1061,7 +1061,7 @@ __global__ void __launch_bounds__(256) k_visc_adj2(const Grid g, const double* _
     for (int e = 0; e < 3; ++e) {
       long long nb[4];
       neighbours(i, j, k, e, g, nb);
-      const double r12 = 1.0 / (12.0 * g.h[e]);
+      const double r12 = g.r12h[e];
 #pragma unroll
       for (int qv = 0; qv < 4; ++qv) {
         const double* A = sc + (long long)(qv * 3 + e) * N;

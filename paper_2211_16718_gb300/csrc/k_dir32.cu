@@ -250,8 +250,8 @@ __global__ void __launch_bounds__(THREADS) k_dir32(const DirArgs a) {
   // ---- E: FP64 conservative difference + viscous divergence + epilogue -------------
   cp_async_wait_all();
   {
-    const double rdx = 1.0 / a.g.h[D];
-    const double r12 = 1.0 / (12.0 * a.g.h[D]);
+    const double rdx = a.g.rh[D];
+    const double r12 = a.g.r12h[D];
     const double* F = smd + OFF_F / 2;
     const double* fvs = smd + OFF_FV / 2;
     for (int item = tid; item < TP * W; item += THREADS) {

@@ -565,8 +565,8 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
   // ---- E: conservative difference + viscous divergence + epilogue ----------------
   cp_async_wait_all();
   {
-    const double rdx = 1.0 / a.g.h[D];
-    const double r12 = 1.0 / (12.0 * a.g.h[D]);
+    const double rdx = a.g.rh[D];
+    const double r12 = a.g.r12h[D];
     const double* F = sm + PL::OFF_R;
     const double* fvs = sm + PL::OFF_FV;
     for (int item = tid; item < TP * W; item += PL::THREADS) {

@@ -190,12 +190,12 @@ __device__ Red block_reduce(Red r) {
 }
 
 __global__ void __launch_bounds__(ST_THREADS) k_stats(const double* __restrict__ u, const double* __restrict__ pm,
-                                                      int nx, int ny, int nz, double hx, double hy, double hz,
-                                                      double* __restrict__ partials) {
+                                                      const Grid g, double* __restrict__ partials) {
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const long long N = (long long)nx * ny * nz;
   const int n3[3] = {nx, ny, nz};
-  const double r12[3] = {1.0 / (12.0 * hx), 1.0 / (12.0 * hy), 1.0 / (12.0 * hz)};
-  const double rh[3] = {1.0 / hx, 1.0 / hy, 1.0 / hz};
+  const double* r12 = g.r12h;
+  const double* rh = g.rh;
   Red r;
 #pragma unroll
   for (int m = 0; m < NSUM; ++m) r.s[m] = 0.0;
@@ -294,7 +294,7 @@ cudaError_t launch_prim(const Grid& g, const double* u, double* pm, double gamma
 
 cudaError_t launch_visc(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s,
                         int only_d, int df) {
-  const double rx = 1.0 / (12.0 * g.h[0]), ry = 1.0 / (12.0 * g.h[1]), rz = 1.0 / (12.0 * g.h[2]);
+  const double rx = g.r12h[0], ry = g.r12h[1], rz = g.r12h[2];
   if (df)
     k_visc<true><<<plane_grid(g), PW_THREADS, 0, s>>>(pm, fv, g.n[0], g.n[1], g.n[2], rx, ry, rz, mu, kappa, only_d);
   else
@@ -323,8 +323,7 @@ int stats_num_blocks(const Grid& g) {
 cudaError_t launch_stats(const Grid& g, const double* u, const double* pm, double gamma, double* partials,
                          cudaStream_t s) {
   (void)gamma;
-  k_stats<<<stats_num_blocks(g), ST_THREADS, 0, s>>>(u, pm, g.n[0], g.n[1], g.n[2], g.h[0], g.h[1], g.h[2],
-                                                     partials);
+  k_stats<<<stats_num_blocks(g), ST_THREADS, 0, s>>>(u, pm, g, partials);
   return cudaGetLastError();
 }
 

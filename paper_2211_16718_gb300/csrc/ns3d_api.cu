@@ -234,9 +234,7 @@ int ns3d_init(const ns3d_params* p, void* cuda_stream, ns3d_ctx** out) {
   c->g.n[1] = p->ny;
   c->g.n[2] = p->nz;
   c->g.N = (long long)p->nx * p->ny * p->nz;
-  c->g.h[0] = p->lx / p->nx;
-  c->g.h[1] = p->ly / p->ny;
-  c->g.h[2] = p->lz / p->nz;
+  grid_set_spacing(c->g, p->lx, p->ly, p->lz);
   const size_t N = (size_t)c->g.N;
   c->nstat_blocks = stats_num_blocks(c->g);
   cudaError_t e = prepare_dir_kernels();

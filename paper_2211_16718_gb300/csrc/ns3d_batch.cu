@@ -537,9 +537,7 @@ int ns3d_batch_init(const ns3d_params* params, int count, void* cuda_stream, ns3
     in.g.n[1] = p.ny;
     in.g.n[2] = p.nz;
     in.g.N = (long long)p.nx * p.ny * p.nz;
-    in.g.h[0] = p.lx / p.nx;
-    in.g.h[1] = p.ly / p.ny;
-    in.g.h[2] = p.lz / p.nz;
+    grid_set_spacing(in.g, p.lx, p.ly, p.lz);
     in.gamma = p.gamma;
     in.mu = p.mu_eff;
     in.kappa = (p.mu_eff > 0.0) ? p.mu_eff / ((p.gamma - 1.0) * p.prandtl) : 0.0;

@@ -34,7 +34,19 @@ struct Grid {
   int n[3];          // nx, ny, nz
   long long N;       // nx*ny*nz
   double h[3];       // dx, dy, dz
+  double rh[3];      // 1/dx, 1/dy, 1/dz            (host-computed: no FP64 division per thread)
+  double r12h[3];    // 1/(12 dx), 1/(12 dy), 1/(12 dz)
 };
+
+// Spacing of the periodic box [0,lx) x [0,ly) x [0,lz) on the grid g.n (Sec. 2.2: x_i = i dx).
+inline void grid_set_spacing(Grid& g, double lx, double ly, double lz) {
+  const double len[3] = {lx, ly, lz};
+  for (int d = 0; d < 3; ++d) {
+    g.h[d] = len[d] / g.n[d];
+    g.rh[d] = 1.0 / g.h[d];
+    g.r12h[d] = 1.0 / (12.0 * g.h[d]);
+  }
+}
 
 struct DirArgs {
   Grid g;
