@@ -56,6 +56,14 @@ __device__ __forceinline__ double d4(double qm2, double qm1, double qp1, double 
   return __dmul_rn(fma(8.0, qp1 - qm1, -(qp2 - qm2)), r12h);
 }
 
+// d4 in double-float from the four stencil values (converted exactly to 48 bits): the
+// NS3D_FP64 form of the viscous and statistics kernels.
+__device__ __forceinline__ df d4_df(double qm2, double qm1, double qp1, double qp2, df r12h) {
+  const df d1 = df_add_fast(d2df_bits(qp1), df_neg(d2df_bits(qm1)));
+  const df d2 = df_add_fast(d2df_bits(qp2), df_neg(d2df_bits(qm2)));
+  return df_mul_u(df_add_fast(df_mul_f_u(d1, 8.0f), df_neg(d2)), r12h);
+}
+
 // Gradients of (u, v, w, T) at point p, then the three viscous flux vectors
 // f^v, g^v, h^v (Sec. 2.1 stresses with the symmetric strain rate, heat flux
 // q = -kappa grad T), written to fv[(4 d + c) N + p]; with only_d >= 0 just the
@@ -102,11 +110,12 @@ __device__ __forceinline__ void visc_point_ijk(const double* __restrict__ pm, do
   }
 }
 
-// visc_point in the NS3D_FP64 form: the stencil differences q_{+1} - q_{-1}, q_{+2} - q_{-2}
-// in FP64, everything after them (gradients, stresses, heat flux, work term) in double-float
-// on the FP32 pipe, and one FP64 addition per output (hi + lo).  The viscous fluxes are
-// ~mu |grad u| in size, so the double-float rounding (~1e-14 relative) stays far below the
-// FP64 rounding of the convective terms they are added to.
+// visc_point in the NS3D_FP64 form: the stencil values converted to double-float and
+// everything from the differences on (gradients, stresses, heat flux, work term) in
+// double-float on the FP32 pipe, with one FP64 addition per output (hi + lo).  The
+// viscous fluxes are ~mu |grad u| in size: the double-float rounding of the stencil
+// values (2^-48 |u|) gives an error ~mu 2^-48 |u| / dx^2 in the right-hand side, far below
+// the FP64 rounding of the convective terms it is added to.
 template <bool NC = true>
 __device__ __forceinline__ void visc_point_df_ijk(const double* __restrict__ pm, double* __restrict__ fv, int nx,
                                                   int ny, int nz, int i, int j, int k, const double r12[3], double mu,
@@ -130,16 +139,14 @@ __device__ __forceinline__ void visc_point_df_ijk(const double* __restrict__ pm,
     for (int q = 0; q < 4; ++q) {
       const int plane = (q < 3) ? q : PM_T;
       const double* A = pm + (long long)plane * N;
-      const df d1 = d2df_bits(ldx<NC>(A + nb[2]) - ldx<NC>(A + nb[1]));
-      const df d2 = d2df_bits(ldx<NC>(A + nb[3]) - ldx<NC>(A + nb[0]));
-      G[q][d] = df_mul(df_add_fast(df_mul_f(d1, 8.0f), df_neg(d2)), r);
+      G[q][d] = d4_df(ldx<NC>(A + nb[0]), ldx<NC>(A + nb[1]), ldx<NC>(A + nb[2]), ldx<NC>(A + nb[3]), r);
     }
   }
   const df vel[3] = {d2df_bits(pm[PM_U * N + p]), d2df_bits(pm[PM_V * N + p]), d2df_bits(pm[PM_W * N + p])};
   const df dmu = d2df_bits(mu), dkap = d2df_bits(kappa);
   const double two3 = 2.0 / 3.0;
   const df c23{(float)two3, (float)(two3 - (double)(float)two3)};
-  const df tdiv = df_mul(df_add_fast(G[0][0], df_add_fast(G[1][1], G[2][2])), c23);
+  const df tdiv = df_mul_u(df_add_fast(G[0][0], df_add_fast(G[1][1], G[2][2])), c23);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     if (only_d >= 0 && d != only_d) continue;
@@ -147,10 +154,10 @@ __device__ __forceinline__ void visc_point_df_ijk(const double* __restrict__ pm,
     df tau[3];
 #pragma unroll
     for (int m = 0; m < 3; ++m)
-      tau[m] = (m == d) ? df_mul(dmu, df_add_fast(df_mul_f(G[d][d], 2.0f), df_neg(tdiv)))
+      tau[m] = (m == d) ? df_mul(dmu, df_add_fast(df_twice(G[d][d]), df_neg(tdiv)))
                         : df_mul(dmu, df_add_fast(G[m][d], G[d][m]));
-    const df en = df_add_fast(df_add_fast(df_mul(vel[0], tau[0]), df_mul(vel[1], tau[1])),
-                              df_add_fast(df_mul(vel[2], tau[2]), df_mul(dkap, G[3][d])));
+    const df en = df_add_fast(df_add_fast(df_mul_u(vel[0], tau[0]), df_mul_u(vel[1], tau[1])),
+                              df_add_fast(df_mul_u(vel[2], tau[2]), df_mul_u(dkap, G[3][d])));
     fv[(long long)(b + 0) * N + p] = f2d_bits(tau[0].hi) + f2d_bits(tau[0].lo);
     fv[(long long)(b + 1) * N + p] = f2d_bits(tau[1].hi) + f2d_bits(tau[1].lo);
     fv[(long long)(b + 2) * N + p] = f2d_bits(tau[2].hi) + f2d_bits(tau[2].lo);

@@ -194,8 +194,9 @@ __global__ void __launch_bounds__(ST_THREADS) k_stats(const double* __restrict__
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const long long N = (long long)nx * ny * nz;
   const int n3[3] = {nx, ny, nz};
-  const double* r12 = g.r12h;
-  const double* rh = g.rh;
+  const df r12d[3] = {d2df_bits(g.r12h[0]), d2df_bits(g.r12h[1]), d2df_bits(g.r12h[2])};
+  const df rhd[3] = {d2df_bits(g.rh[0]), d2df_bits(g.rh[1]), d2df_bits(g.rh[2])};
+  df wmax{0.0f, 0.0f};
   Red r;
 #pragma unroll
   for (int m = 0; m < NSUM; ++m) r.s[m] = 0.0;
@@ -214,9 +215,14 @@ __global__ void __launch_bounds__(ST_THREADS) k_stats(const double* __restrict__
     r.s[2] += u[2 * N + p];
     r.s[3] += u[3 * N + p];
     r.s[4] += u[4 * N + p];
-    r.s[5] += 0.5 * rho * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
-    // velocity gradient entries needed by the vorticity: dv_m/dx_d, m != d
-    double G[3][3];
+    // kinetic energy, vorticity (its gradients: dv_m/dx_d, m != d), enstrophy and wave
+    // speed in double-float on the FP32 pipe; the sums themselves accumulate in FP64
+    const df rd = d2df_bits(rho);
+    const df rh2{0.5f * rd.hi, 0.5f * rd.lo};  // rho / 2, exact
+    const df vd[3] = {d2df_bits(vel[0]), d2df_bits(vel[1]), d2df_bits(vel[2])};
+    const df ke = df_mul_u(rh2, df_add_pos_u(df_sqr_u(vd[0]), df_add_pos_u(df_sqr_u(vd[1]), df_sqr_u(vd[2]))));
+    r.s[5] = (r.s[5] + f2d_bits(ke.hi)) + f2d_bits(ke.lo);
+    df G[3][3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       long long nb[4];
@@ -224,24 +230,31 @@ __global__ void __launch_bounds__(ST_THREADS) k_stats(const double* __restrict__
       for (int o = 0; o < 4; ++o) {
         const int off = (o < 2) ? (o - 2) : (o - 1);
         int c[3] = {i, j, k};
-        c[d] = wrap_idx(c[d] + off, n3[d]);
+        c[d] = wrap_near(c[d], off, n3[d]);
         nb[o] = flat3(c[0], c[1], c[2], nx, ny);
       }
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
         if (m == d) continue;
         const double* A = pm + (long long)m * N;
-        G[m][d] = d4(__ldg(A + nb[0]), __ldg(A + nb[1]), __ldg(A + nb[2]), __ldg(A + nb[3]), r12[d]);
+        G[m][d] = d4_df(__ldg(A + nb[0]), __ldg(A + nb[1]), __ldg(A + nb[2]), __ldg(A + nb[3]), r12d[d]);
       }
     }
-    const double wx = G[2][1] - G[1][2], wy = G[0][2] - G[2][0], wz = G[1][0] - G[0][1];
-    r.s[6] += 0.5 * rho * (wx * wx + wy * wy + wz * wz);
+    const df wx = df_add_fast(G[2][1], df_neg(G[1][2]));
+    const df wy = df_add_fast(G[0][2], df_neg(G[2][0]));
+    const df wz = df_add_fast(G[1][0], df_neg(G[0][1]));
+    const df en = df_mul_u(rh2, df_add_pos_u(df_sqr_u(wx), df_add_pos_u(df_sqr_u(wy), df_sqr_u(wz))));
+    r.s[6] = (r.s[6] + f2d_bits(en.hi)) + f2d_bits(en.lo);
     r.rmin = fmin(r.rmin, rho);
     r.pmin = fmin(r.pmin, pr);
-    const double c = sqrt(pm[PM_T * N + p]);
+    const df c = df_sqrt(d2df_bits(pm[PM_T * N + p]));
 #pragma unroll
-    for (int d = 0; d < 3; ++d) r.wmax = fmax(r.wmax, (fabs(vel[d]) + c) * rh[d]);
+    for (int d = 0; d < 3; ++d) {
+      const df w = df_mul(df_add_pos(df_abs(vd[d]), c), rhd[d]);
+      if (df_lt(wmax, w)) wmax = w;
+    }
   }
+  r.wmax = f2d_bits(wmax.hi) + f2d_bits(wmax.lo);
   r = block_reduce(r);
   if (threadIdx.x == 0) {
     double* o = partials + (long long)blockIdx.x * NRED;
