@@ -63,6 +63,7 @@ cudaError_t prepare_dir_kernels() {
   if (e == cudaSuccess) e = set_attr<1, 16, 4>();
   if (e == cudaSuccess) e = set_attr<1, 40, 2>();
   if (e == cudaSuccess) e = prepare_dir32_kernels();
+  if (e == cudaSuccess) e = prepare_visc_kernels();
   return e;
 }
 

@@ -56,12 +56,42 @@ __device__ __forceinline__ double d4(double qm2, double qm1, double qp1, double 
   return __dmul_rn(fma(8.0, qp1 - qm1, -(qp2 - qm2)), r12h);
 }
 
-// d4 in double-float from the four stencil values (converted exactly to 48 bits): the
-// NS3D_FP64 form of the viscous and statistics kernels.
-__device__ __forceinline__ df d4_df(double qm2, double qm1, double qp1, double qp2, df r12h) {
-  const df d1 = df_add_fast(d2df_bits(qp1), df_neg(d2df_bits(qm1)));
-  const df d2 = df_add_fast(d2df_bits(qp2), df_neg(d2df_bits(qm2)));
+// d4 in double-float from the four stencil values, already double-float (d2df_bits of
+// the FP64 values): the NS3D_FP64 form of the viscous and statistics kernels.
+__device__ __forceinline__ df d4_dfv(df qm2, df qm1, df qp1, df qp2, df r12h) {
+  const df d1 = df_add_fast(qp1, df_neg(qm1));
+  const df d2 = df_add_fast(qp2, df_neg(qm2));
   return df_mul_u(df_add_fast(df_mul_f_u(d1, 8.0f), df_neg(d2)), r12h);
+}
+__device__ __forceinline__ df d4_df(double qm2, double qm1, double qp1, double qp2, df r12h) {
+  return d4_dfv(d2df_bits(qm2), d2df_bits(qm1), d2df_bits(qp1), d2df_bits(qp2), r12h);
+}
+
+// Viscous flux vectors at point p from the double-float gradients G[q][d] = d(u,v,w,T)_q/dx_d
+// and velocity (Sec. 2.1 stresses with the symmetric strain rate, heat flux q = -kappa grad T),
+// each output rounded to FP64 once (hi + lo); layout as visc_point_ijk.
+__device__ __forceinline__ void visc_fluxes_df(const df G[4][3], const df vel[3], double mu, double kappa,
+                                               double* __restrict__ fv, long long N, long long p, int only_d) {
+  const df dmu = d2df_bits(mu), dkap = d2df_bits(kappa);
+  const double two3 = 2.0 / 3.0;
+  const df c23{(float)two3, (float)(two3 - (double)(float)two3)};
+  const df tdiv = df_mul_u(df_add_fast(G[0][0], df_add_fast(G[1][1], G[2][2])), c23);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (only_d >= 0 && d != only_d) continue;
+    const int b = (only_d >= 0) ? 0 : 4 * d;
+    df tau[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+      tau[m] = (m == d) ? df_mul(dmu, df_add_fast(df_twice(G[d][d]), df_neg(tdiv)))
+                        : df_mul(dmu, df_add_fast(G[m][d], G[d][m]));
+    const df en = df_add_fast(df_add_fast(df_mul_u(vel[0], tau[0]), df_mul_u(vel[1], tau[1])),
+                              df_add_fast(df_mul_u(vel[2], tau[2]), df_mul_u(dkap, G[3][d])));
+    fv[(long long)(b + 0) * N + p] = f2d_bits(tau[0].hi) + f2d_bits(tau[0].lo);
+    fv[(long long)(b + 1) * N + p] = f2d_bits(tau[1].hi) + f2d_bits(tau[1].lo);
+    fv[(long long)(b + 2) * N + p] = f2d_bits(tau[2].hi) + f2d_bits(tau[2].lo);
+    fv[(long long)(b + 3) * N + p] = f2d_bits(en.hi) + f2d_bits(en.lo);
+  }
 }
 
 // Gradients of (u, v, w, T) at point p, then the three viscous flux vectors
@@ -143,26 +173,7 @@ __device__ __forceinline__ void visc_point_df_ijk(const double* __restrict__ pm,
     }
   }
   const df vel[3] = {d2df_bits(pm[PM_U * N + p]), d2df_bits(pm[PM_V * N + p]), d2df_bits(pm[PM_W * N + p])};
-  const df dmu = d2df_bits(mu), dkap = d2df_bits(kappa);
-  const double two3 = 2.0 / 3.0;
-  const df c23{(float)two3, (float)(two3 - (double)(float)two3)};
-  const df tdiv = df_mul_u(df_add_fast(G[0][0], df_add_fast(G[1][1], G[2][2])), c23);
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    if (only_d >= 0 && d != only_d) continue;
-    const int b = (only_d >= 0) ? 0 : 4 * d;
-    df tau[3];
-#pragma unroll
-    for (int m = 0; m < 3; ++m)
-      tau[m] = (m == d) ? df_mul(dmu, df_add_fast(df_twice(G[d][d]), df_neg(tdiv)))
-                        : df_mul(dmu, df_add_fast(G[m][d], G[d][m]));
-    const df en = df_add_fast(df_add_fast(df_mul_u(vel[0], tau[0]), df_mul_u(vel[1], tau[1])),
-                              df_add_fast(df_mul_u(vel[2], tau[2]), df_mul_u(dkap, G[3][d])));
-    fv[(long long)(b + 0) * N + p] = f2d_bits(tau[0].hi) + f2d_bits(tau[0].lo);
-    fv[(long long)(b + 1) * N + p] = f2d_bits(tau[1].hi) + f2d_bits(tau[1].lo);
-    fv[(long long)(b + 2) * N + p] = f2d_bits(tau[2].hi) + f2d_bits(tau[2].lo);
-    fv[(long long)(b + 3) * N + p] = f2d_bits(en.hi) + f2d_bits(en.lo);
-  }
+  visc_fluxes_df(G, vel, mu, kappa, fv, N, p, only_d);
 }
 
 // The per-point forms above, addressed by the flat point index p (batched kernels).

@@ -32,9 +32,8 @@ __global__ void __launch_bounds__(PW_THREADS) k_prim(const double* __restrict__ 
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONPHYS);
 }
 
-// Gradients of (u, v, w, T) at every point, then the three viscous flux vectors (body:
-// visc_point, or visc_point_df in the NS3D_FP64 form).
-template <bool DF>
+// Gradients of (u, v, w, T) at every point, then the three viscous flux vectors, all FP64
+// (NS3D_FP64_STRICT; body: visc_point_ijk).  The NS3D_FP64 form is k_visc_tiled below.
 __global__ void __launch_bounds__(PW_THREADS) k_visc(const double* __restrict__ pm, double* __restrict__ fv,
                                                      int nx, int ny, int nz, double r12hx, double r12hy,
                                                      double r12hz, double mu, double kappa, int only_d) {
@@ -42,8 +41,64 @@ __global__ void __launch_bounds__(PW_THREADS) k_visc(const double* __restrict__ 
   const int i = blockIdx.x * 32 + threadIdx.x % 32, j = blockIdx.y * 8 + threadIdx.x / 32, k = blockIdx.z;
   if (i >= nx || j >= ny) return;
   const double r12[3] = {r12hx, r12hy, r12hz};
-  if (DF) visc_point_df_ijk(pm, fv, nx, ny, nz, i, j, k, r12, mu, kappa, only_d);
-  else visc_point_ijk(pm, fv, nx, ny, nz, i, j, k, r12, mu, kappa, only_d);
+  visc_point_ijk(pm, fv, nx, ny, nz, i, j, k, r12, mu, kappa, only_d);
+}
+
+// Tiled NS3D_FP64 viscous-flux kernel.  A CTA owns a 32 x 8 block of x-y columns and
+// marches along z through VT_CZ planes.  Each plane of (u, v, w, T), with a 2-point x-y
+// halo, is converted to double-float once into a ring of 5 planes (z-2 .. z+2) in shared
+// memory, so every stencil value is converted once rather than once per stencil that
+// uses it (12 times).  The per-point arithmetic is that of visc_point_df_ijk: the same
+// conversions, the same gradient and flux operations, so the same bits.
+constexpr int VT_X = 32, VT_Y = 8, VT_HX = VT_X + 4, VT_HY = VT_Y + 4, VT_PLANE = VT_HX * VT_HY;
+constexpr int VT_RING = 5, VT_CZ = 16;
+constexpr int VT_SMEM = VT_RING * 4 * VT_PLANE * (int)sizeof(float2);  // 69,120 bytes
+
+__global__ void __launch_bounds__(VT_X * VT_Y, 3) k_visc_tiled(const double* __restrict__ pm, double* __restrict__ fv,
+                                                                const Grid g, double mu, double kappa, int only_d) {
+  extern __shared__ float2 ring[];  // [VT_RING][4][VT_HY][VT_HX]
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const long long N = g.N;
+  const int x0 = blockIdx.x * VT_X, y0 = blockIdx.y * VT_Y, z0 = blockIdx.z * VT_CZ;
+  const int z1 = min(z0 + VT_CZ, nz);
+  const int tid = threadIdx.x, tx = tid % VT_X, ty = tid / VT_X;
+  const df r12[3] = {d2df_bits(g.r12h[0]), d2df_bits(g.r12h[1]), d2df_bits(g.r12h[2])};
+  auto slot = [&](int zz) { return ring + ((zz - z0 + 2) % VT_RING) * 4 * VT_PLANE; };
+  auto load_plane = [&](int zz) {  // plane zz (periodic) of the four fields, with halo
+    const int zw = wrap_idx(zz, nz);
+    float2* R = slot(zz);
+    for (int pos = tid; pos < VT_PLANE; pos += VT_X * VT_Y) {
+      const int hy = pos / VT_HX, hx = pos - hy * VT_HX;
+      const long long p = flat3(wrap_idx(x0 - 2 + hx, nx), wrap_idx(y0 - 2 + hy, ny), zw, nx, ny);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const df v = d2df_bits(__ldg(pm + (long long)((q < 3) ? q : PM_T) * N + p));
+        R[q * VT_PLANE + pos] = make_float2(v.hi, v.lo);
+      }
+    }
+  };
+  auto ld = [](const float2* P, int i) { const float2 v = P[i]; return df{v.x, v.y}; };
+  for (int zz = z0 - 2; zz < z0 + 2; ++zz) load_plane(zz);
+  for (int z = z0; z < z1; ++z) {
+    load_plane(z + 2);
+    __syncthreads();
+    if (x0 + tx < nx && y0 + ty < ny) {
+      const int c = (ty + 2) * VT_HX + (tx + 2);
+      const float2 *Zm2 = slot(z - 2), *Zm1 = slot(z - 1), *Z0 = slot(z), *Zp1 = slot(z + 1), *Zp2 = slot(z + 2);
+      df G[4][3];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2* P = Z0 + q * VT_PLANE;
+        G[q][0] = d4_dfv(ld(P, c - 2), ld(P, c - 1), ld(P, c + 1), ld(P, c + 2), r12[0]);
+        G[q][1] = d4_dfv(ld(P, c - 2 * VT_HX), ld(P, c - VT_HX), ld(P, c + VT_HX), ld(P, c + 2 * VT_HX), r12[1]);
+        const int o = q * VT_PLANE + c;
+        G[q][2] = d4_dfv(ld(Zm2, o), ld(Zm1, o), ld(Zp1, o), ld(Zp2, o), r12[2]);
+      }
+      const df vel[3] = {ld(Z0, c), ld(Z0 + VT_PLANE, c), ld(Z0 + 2 * VT_PLANE, c)};
+      visc_fluxes_df(G, vel, mu, kappa, fv, N, flat3(x0 + tx, y0 + ty, z, nx, ny), only_d);
+    }
+    __syncthreads();  // the slot of plane z - 2 takes plane z + 3 next
+  }
 }
 
 // Launch geometry of the stencil point kernels: 32 x 8 x 1 blocks over (x, y, z).
@@ -308,11 +363,16 @@ cudaError_t launch_prim(const Grid& g, const double* u, double* pm, double gamma
 cudaError_t launch_visc(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s,
                         int only_d, int df) {
   const double rx = g.r12h[0], ry = g.r12h[1], rz = g.r12h[2];
-  if (df)
-    k_visc<true><<<plane_grid(g), PW_THREADS, 0, s>>>(pm, fv, g.n[0], g.n[1], g.n[2], rx, ry, rz, mu, kappa, only_d);
-  else
-    k_visc<false><<<plane_grid(g), PW_THREADS, 0, s>>>(pm, fv, g.n[0], g.n[1], g.n[2], rx, ry, rz, mu, kappa, only_d);
+  if (df) {
+    const dim3 grid((g.n[0] + VT_X - 1) / VT_X, (g.n[1] + VT_Y - 1) / VT_Y, (g.n[2] + VT_CZ - 1) / VT_CZ);
+    k_visc_tiled<<<grid, VT_X * VT_Y, VT_SMEM, s>>>(pm, fv, g, mu, kappa, only_d);
+  } else
+    k_visc<<<plane_grid(g), PW_THREADS, 0, s>>>(pm, fv, g.n[0], g.n[1], g.n[2], rx, ry, rz, mu, kappa, only_d);
   return cudaGetLastError();
+}
+
+cudaError_t prepare_visc_kernels() {
+  return cudaFuncSetAttribute(k_visc_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, VT_SMEM);
 }
 
 cudaError_t launch_prim32(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s) {

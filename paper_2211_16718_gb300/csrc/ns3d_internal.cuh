@@ -88,6 +88,7 @@ cudaError_t launch_dir(int d, const DirArgs& a, cudaStream_t s);  // dispatches 
 void dir_tile_shape(int mode, int variant, int* tp, int* w);      // points x lines of a tile
 constexpr int DIR_VARIANTS = 3;                                   // tile variants of MODE 1
 cudaError_t prepare_dir32_kernels();
+cudaError_t prepare_visc_kernels();
 cudaError_t launch_dir32(int d, const DirArgs& a, cudaStream_t s);  // FP32-bulk (a.mode == 2)
 int stats_num_blocks(const Grid& g);
 cudaError_t launch_stats(const Grid& g, const double* u, const double* pm, double gamma, double* partials,
