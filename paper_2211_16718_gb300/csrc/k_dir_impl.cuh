@@ -384,12 +384,13 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
     else
       phase_c(std::false_type{});
     cp_async_wait_all();  // this thread's ROE / FV copies; the barrier publishes them
-    if (tid >= PF0) {     // Roe-average inputs to double-float, in place
+    if (tid >= PF0) {  // velocities to double-float, in place (sqrt(rho) and H arrive as
+                       // double-float: planes of the NS3D_FP64 primitive layout)
       int pos, line;
       tile_split<D, W>(tid - PF0, NP, pos, line);
       double* r = sm + PL::OFF_ROE + tile_idx<D, W>(pos, line, NP);
 #pragma unroll
-      for (int k = 0; k < 5; ++k) {
+      for (int k = 1; k < 4; ++k) {
         const df x = d2df_bits(r[k * NP * W]);
         reinterpret_cast<float2*>(r)[k * NP * W] = make_float2(x.hi, x.lo);
       }
@@ -425,7 +426,7 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
       const int sa = tile_idx<D, W>(f + 2, line, NP), sb = tile_idx<D, W>(f + 3, line, NP);
       if (MODE == 1) {
         // Roe dissipation X|Lambda|X^{-1} du in double-float from the double-float jumps
-        // du of phase C and the FP64 Roe-average inputs (converted here); the flux is
+        // du of phase C and the double-float Roe-average inputs; the flux is
         // 0.5 (fhat_L + fhat_R) - 0.5 diss, two FP64 operations per component
         const float2* rf = reinterpret_cast<const float2*>(r);
         auto ldr = [&](int k, int sp) { const float2 v = rf[k * NP * W + sp]; return df{v.x, v.y}; };

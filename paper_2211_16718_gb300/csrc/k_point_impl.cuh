@@ -17,11 +17,52 @@ __device__ __forceinline__ double ldx(const double* p) {
   return *p;
 }
 
+// Positive and finite, from the bit pattern (integer compare, no FP64 instruction).
+__device__ __forceinline__ bool pos_finite(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b < 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool is_finite_bits(double x) {
+  return ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff;
+}
+
+// A double-float value stored in an 8-byte plane slot (hi, lo as two floats).
+__device__ __forceinline__ void store_df(double* slot, df v) { *reinterpret_cast<float2*>(slot) = make_float2(v.hi, v.lo); }
+__device__ __forceinline__ df load_df(const double* slot) {
+  const float2 v = *reinterpret_cast<const float2*>(slot);
+  return df{v.x, v.y};
+}
+
 // Primitive variables of point p (Sec. 2.1 equation of state): u, v, w, p,
 // T = gamma p / rho, H = (e + p)/rho, sqrt(rho).  Returns 1 if non-physical.
+// DF (the NS3D_FP64 layout): u, v, w, p in FP64; T, H and sqrt(rho), which are only
+// consumed as double-float (Roe average, viscous and statistics kernels), stored as
+// double-float pairs and computed on the FP32 pipe; 1/rho from a double-float seed and
+// one FP64 Newton step (FP64-accurate: the seed's error squared is ~2^-92).  FP64 work
+// per point: 11 instructions instead of ~32 with the IEEE division and square root.
+template <bool DF = false>
 __device__ __forceinline__ int prim_point(const double* __restrict__ u, double* __restrict__ pm, long long N,
                                           long long p, double gamma) {
   const double rho = u[p], mx = u[N + p], my = u[2 * N + p], mz = u[3 * N + p], e = u[4 * N + p];
+  if (DF) {
+    const df rd = d2df_bits(rho);
+    const df rr = df_div(df{1.0f, 0.0f}, rd);
+    double ri = f2d_bits(rr.hi) + f2d_bits(rr.lo);
+    ri = fma(ri, fma(-rho, ri, 1.0), ri);
+    const double vx = mx * ri, vy = my * ri, vz = mz * ri;
+    const double ke2 = fma(mx, vx, fma(my, vy, mz * vz));
+    const double pr = (gamma - 1.0) * fma(-0.5, ke2, e);  // = (gamma-1)(e - ke2/2), one rounding as e - ke
+    pm[PM_U * N + p] = vx;
+    pm[PM_V * N + p] = vy;
+    pm[PM_W * N + p] = vz;
+    pm[PM_P * N + p] = pr;
+    const df dp = d2df_bits(pr);
+    store_df(pm + PM_T * N + p, df_mul(df_mul_u(d2df_bits(gamma), dp), rr));
+    store_df(pm + PM_H * N + p, df_mul(df_add_fast(d2df_bits(e), dp), rr));
+    store_df(pm + PM_SR * N + p, df_sqrt(rd));
+    return !pos_finite(rho) | !pos_finite(pr) | !is_finite_bits(e) | !is_finite_bits(mx) | !is_finite_bits(my) |
+           !is_finite_bits(mz);
+  }
   const double ri = 1.0 / rho;
   const double vx = mx * ri, vy = my * ri, vz = mz * ri;
   const double ke = 0.5 * fma(mx, vx, fma(my, vy, mz * vz));  // explicit: the same bits in every kernel
@@ -140,7 +181,8 @@ __device__ __forceinline__ void visc_point_ijk(const double* __restrict__ pm, do
   }
 }
 
-// visc_point in the NS3D_FP64 form: the stencil values converted to double-float and
+// visc_point in the NS3D_FP64 form (primitives in the layout of prim_point<true>: the
+// temperature plane holds double-float pairs): the stencil values converted to double-float and
 // everything from the differences on (gradients, stresses, heat flux, work term) in
 // double-float on the FP32 pipe, with one FP64 addition per output (hi + lo).  The
 // viscous fluxes are ~mu |grad u| in size: the double-float rounding of the stencil
@@ -166,10 +208,17 @@ __device__ __forceinline__ void visc_point_df_ijk(const double* __restrict__ pm,
     }
     const df r = d2df_bits(r12[d]);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int plane = (q < 3) ? q : PM_T;
-      const double* A = pm + (long long)plane * N;
+    for (int q = 0; q < 3; ++q) {
+      const double* A = pm + (long long)q * N;
       G[q][d] = d4_df(ldx<NC>(A + nb[0]), ldx<NC>(A + nb[1]), ldx<NC>(A + nb[2]), ldx<NC>(A + nb[3]), r);
+    }
+    {  // T: a double-float plane in the NS3D_FP64 layout (prim_point<true>)
+      const double* A = pm + (long long)PM_T * N;
+      auto t = [&](long long q) {
+        const double v = ldx<NC>(A + q);
+        return df{__int_as_float(__double2loint(v)), __int_as_float(__double2hiint(v))};
+      };
+      G[3][d] = d4_dfv(t(nb[0]), t(nb[1]), t(nb[2]), t(nb[3]), r);
     }
   }
   const df vel[3] = {d2df_bits(pm[PM_U * N + p]), d2df_bits(pm[PM_V * N + p]), d2df_bits(pm[PM_W * N + p])};

@@ -23,12 +23,13 @@ int grid_for(long long n, int threads) {
   return (int)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
-// Primitive variables of every point (body: prim_point).
+// Primitive variables of every point (body: prim_point; DF: the NS3D_FP64 layout).
+template <bool DF>
 __global__ void __launch_bounds__(PW_THREADS) k_prim(const double* __restrict__ u, double* __restrict__ pm,
                                                      long long N, double gamma, int* __restrict__ status) {
   int bad = 0;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x)
-    bad |= prim_point(u, pm, N, p, gamma);
+    bad |= prim_point<DF>(u, pm, N, p, gamma);
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONPHYS);
 }
 
@@ -44,7 +45,7 @@ __global__ void __launch_bounds__(PW_THREADS) k_visc(const double* __restrict__ 
   visc_point_ijk(pm, fv, nx, ny, nz, i, j, k, r12, mu, kappa, only_d);
 }
 
-// Tiled NS3D_FP64 viscous-flux kernel.  A CTA owns a 32 x 8 block of x-y columns and
+// Tiled NS3D_FP64 viscous-flux kernel (primitives in the layout of prim_point<true>).  A CTA owns a 32 x 8 block of x-y columns and
 // marches along z through VT_CZ planes.  Each plane of (u, v, w, T), with a 2-point x-y
 // halo, is converted to double-float once into a ring of 5 planes (z-2 .. z+2) in shared
 // memory, so every stencil value is converted once rather than once per stencil that
@@ -71,10 +72,11 @@ __global__ void __launch_bounds__(VT_X * VT_Y, 3) k_visc_tiled(const double* __r
       const int hy = pos / VT_HX, hx = pos - hy * VT_HX;
       const long long p = flat3(wrap_idx(x0 - 2 + hx, nx), wrap_idx(y0 - 2 + hy, ny), zw, nx, ny);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const df v = d2df_bits(__ldg(pm + (long long)((q < 3) ? q : PM_T) * N + p));
+      for (int q = 0; q < 3; ++q) {
+        const df v = d2df_bits(__ldg(pm + (long long)q * N + p));
         R[q * VT_PLANE + pos] = make_float2(v.hi, v.lo);
       }
+      R[3 * VT_PLANE + pos] = __ldg(reinterpret_cast<const float2*>(pm + (long long)PM_T * N + p));  // double-float plane
     }
   };
   auto ld = [](const float2* P, int i) { const float2 v = P[i]; return df{v.x, v.y}; };
@@ -244,6 +246,7 @@ __device__ Red block_reduce(Red r) {
   return r;
 }
 
+template <bool DFT>  // DFT: the temperature plane holds double-float pairs (prim_point<true>)
 __global__ void __launch_bounds__(ST_THREADS) k_stats(const double* __restrict__ u, const double* __restrict__ pm,
                                                       const Grid g, double* __restrict__ partials) {
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(ST_THREADS) k_stats(const double* __restrict__
     r.s[6] = (r.s[6] + f2d_bits(en.hi)) + f2d_bits(en.lo);
     r.rmin = fmin(r.rmin, rho);
     r.pmin = fmin(r.pmin, pr);
-    const df c = df_sqrt(d2df_bits(pm[PM_T * N + p]));
+    const df c = df_sqrt(DFT ? load_df(pm + PM_T * N + p) : d2df_bits(pm[PM_T * N + p]));
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const df w = df_mul(df_add_pos(df_abs(vd[d]), c), rhd[d]);
@@ -355,8 +358,12 @@ __global__ void __launch_bounds__(ST_THREADS) k_stats_final(const double* __rest
 
 }  // namespace
 
-cudaError_t launch_prim(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s) {
-  k_prim<<<grid_for(g.N, PW_THREADS), PW_THREADS, 0, s>>>(u, pm, g.N, gamma, status);
+cudaError_t launch_prim(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s,
+                        int df) {
+  if (df)
+    k_prim<true><<<grid_for(g.N, PW_THREADS), PW_THREADS, 0, s>>>(u, pm, g.N, gamma, status);
+  else
+    k_prim<false><<<grid_for(g.N, PW_THREADS), PW_THREADS, 0, s>>>(u, pm, g.N, gamma, status);
   return cudaGetLastError();
 }
 
@@ -394,9 +401,12 @@ int stats_num_blocks(const Grid& g) {
 }
 
 cudaError_t launch_stats(const Grid& g, const double* u, const double* pm, double gamma, double* partials,
-                         cudaStream_t s) {
+                         cudaStream_t s, int df) {
   (void)gamma;
-  k_stats<<<stats_num_blocks(g), ST_THREADS, 0, s>>>(u, pm, g, partials);
+  if (df)
+    k_stats<true><<<stats_num_blocks(g), ST_THREADS, 0, s>>>(u, pm, g, partials);
+  else
+    k_stats<false><<<stats_num_blocks(g), ST_THREADS, 0, s>>>(u, pm, g, partials);
   return cudaGetLastError();
 }
 

@@ -71,9 +71,10 @@ namespace ns3d {
 // x and y passes accumulating into k, z pass with the given epilogue.
 int rhs_pass(ns3d_ctx* c, const double* u, int epi, double* out, const double* un, double coef) {
   const bool f32 = (c->p.precision == NS3D_FP32_BULK);
+  const int df = (c->p.precision == NS3D_FP64) ? 1 : 0;
   int rc = timed(c, NS3D_K_PRIM, [&] {
     return f32 ? launch_prim32(c->g, u, c->pm, c->p.gamma, c->status, c->stream)
-               : launch_prim(c->g, u, c->pm, c->p.gamma, c->status, c->stream);
+               : launch_prim(c->g, u, c->pm, c->p.gamma, c->status, c->stream, df);
   }, "primitive kernel");
   if (rc) return rc;
   const bool visc = c->p.mu_eff > 0.0;
@@ -82,8 +83,7 @@ int rhs_pass(ns3d_ctx* c, const double* u, int epi, double* out, const double* u
   auto visc_flux = [&](int only_d) {
     return timed(c, NS3D_K_VISC, [&] {
       return f32 ? launch_visc32(c->g, c->pm, c->fv, c->p.mu_eff, kappa, c->stream, only_d)
-                 : launch_visc(c->g, c->pm, c->fv, c->p.mu_eff, kappa, c->stream, only_d,
-                               c->p.precision == NS3D_FP64 ? 1 : 0);
+                 : launch_visc(c->g, c->pm, c->fv, c->p.mu_eff, kappa, c->stream, only_d, df);
     }, "viscous-flux kernel");
   };
   if (visc && !c->lean && (rc = visc_flux(-1))) return rc;
@@ -105,10 +105,13 @@ int rhs_pass(ns3d_ctx* c, const double* u, int epi, double* out, const double* u
 }
 
 int stats_pass(ns3d_ctx* c, const double* u, double* out_dev) {
-  int rc = timed(c, NS3D_K_PRIM, [&] { return launch_prim(c->g, u, c->pm, c->p.gamma, c->status, c->stream); },
+  const int df = (c->p.precision == NS3D_FP64) ? 1 : 0;
+  int rc = timed(c, NS3D_K_PRIM,
+                 [&] { return launch_prim(c->g, u, c->pm, c->p.gamma, c->status, c->stream, df); },
                  "primitive kernel");
   if (rc) return rc;
-  rc = timed(c, NS3D_K_STATS, [&] { return launch_stats(c->g, u, c->pm, c->p.gamma, c->partials, c->stream); },
+  rc = timed(c, NS3D_K_STATS,
+             [&] { return launch_stats(c->g, u, c->pm, c->p.gamma, c->partials, c->stream, df); },
              "statistics kernel");
   if (rc) return rc;
   return timed(c, NS3D_K_STATS_FINAL,

@@ -69,7 +69,8 @@ __device__ __forceinline__ void phase_prim(const BatchView& b, int s, long long 
   for (long long x = t0; x < tot; x += stride) {
     const int i = find_inst(b.pt_off, b.count, x);
     const Inst& in = b.inst[i];
-    bad |= prim_point(in.uin[s], in.pm, in.g.N, x - b.pt_off[i], in.gamma);
+    bad |= b.df ? prim_point<true>(in.uin[s], in.pm, in.g.N, x - b.pt_off[i], in.gamma)
+                : prim_point<false>(in.uin[s], in.pm, in.g.N, x - b.pt_off[i], in.gamma);
   }
 }
 
@@ -360,7 +361,7 @@ int step_sequential(ns3d_batch* b) {
   for (int i = 0; i < b->count; ++i) {
     const Inst& in = b->inst[i];
     for (int s = 0; s < b->nstages; ++s) {
-      cudaError_t e = launch_prim(in.g, in.uin[s], in.pm, in.gamma, b->d_status, b->stream);
+      cudaError_t e = launch_prim(in.g, in.uin[s], in.pm, in.gamma, b->d_status, b->stream, b->mode);
       if (e == cudaSuccess && in.fv) e = launch_visc(in.g, in.pm, in.fv, in.mu, in.kappa, b->stream, -1, b->mode);
       for (int d = 0; d < 3 && e == cudaSuccess; ++d) e = launch_dir(d, in.dir[s][d], b->stream);
       if (e != cudaSuccess) return berr(b, NS3D_ECUDA, cudaGetErrorString(e));
@@ -647,8 +648,8 @@ int ns3d_batch_stats(ns3d_batch* b, double* out_dev) {
   if (!b->ready) return berr(b, NS3D_EINVAL, "set states and dt first");
   for (int i = 0; i < b->count; ++i) {
     const Inst& in = b->inst[i];
-    cudaError_t e = launch_prim(in.g, b->u[i], in.pm, in.gamma, b->d_status, b->stream);
-    if (e == cudaSuccess) e = launch_stats(in.g, b->u[i], in.pm, in.gamma, b->partials, b->stream);
+    cudaError_t e = launch_prim(in.g, b->u[i], in.pm, in.gamma, b->d_status, b->stream, b->mode);
+    if (e == cudaSuccess) e = launch_stats(in.g, b->u[i], in.pm, in.gamma, b->partials, b->stream, b->mode);
     if (e == cudaSuccess)
       e = launch_stats_final(in.g, b->partials, stats_num_blocks(in.g), b->d_status,
                              out_dev + (size_t)i * NS3D_STATS_NDOUBLE, b->stream);

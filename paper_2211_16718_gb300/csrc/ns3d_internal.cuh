@@ -74,9 +74,12 @@ struct DirArgs {
 };
 
 // Launchers (return cudaGetLastError() of the launch).
-cudaError_t launch_prim(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s);
+// df: the NS3D_FP64 primitive layout (T, H and sqrt(rho) as double-float pairs, see
+// prim_point); the viscous, direction and statistics kernels of the same context read it.
+cudaError_t launch_prim(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s,
+                        int df = 0);
 // only_d < 0: all three viscous flux vectors into fv[12][N]; only_d = d: the flux along d into fv[4][N];
-// df: the NS3D_FP64 form (double-float after the stencil differences)
+// df: the NS3D_FP64 form (double-float from the stencil values on; primitives from launch_prim(df=1))
 cudaError_t launch_visc(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s,
                         int only_d = -1, int df = 0);
 // FP32-bulk variants (FP32 arithmetic, results widened to FP64)
@@ -92,7 +95,7 @@ cudaError_t prepare_visc_kernels();
 cudaError_t launch_dir32(int d, const DirArgs& a, cudaStream_t s);  // FP32-bulk (a.mode == 2)
 int stats_num_blocks(const Grid& g);
 cudaError_t launch_stats(const Grid& g, const double* u, const double* pm, double gamma, double* partials,
-                         cudaStream_t s);
+                         cudaStream_t s, int df = 0);
 cudaError_t launch_stats_final(const Grid& g, const double* partials, int nblocks, const int* status,
                                double* out, cudaStream_t s);
 int alu_probe(double out[5]);
