@@ -199,7 +199,7 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
   __syncthreads();
 
   // ---- A2 (MODE 1): first differences g_j = q_{j+1} - q_j in FP64, kept as double-float,
-  //      and the FP64 point sums q_j + q_{j+1} of the five flux scalars at interface j - 2
+  //      and the point values q_j of the five flux scalars copied to interface j - 2
   constexpr int PF0 = (MODE == 1) ? PL::THREADS - NP * W : 0;  // first prefetching thread (MODE 1)
   static_assert(MODE == 0 || NP * W <= PL::THREADS, "one prefetched point per thread");
   if constexpr (MODE == 1) {
@@ -215,7 +215,7 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
       const double qa = qm[tile_idx<D, W>(j, line, NP)], qb = qm[tile_idx<D, W>(j + 1, line, NP)];
       const df g = d2df_bits(qb - qa);
       G[m * NG * W + tile_idx<D, W>(j, line, NG)] = make_float2(g.hi, g.lo);
-      if (m >= 4 && j >= 2 && j < NI + 2) R[(1 + m) * NI * W + tile_idx<D, W>(j - 2, line, NI)] = qa + qb;
+      if (m >= 4 && j >= 2 && j < NI + 2) R[(1 + m) * NI * W + tile_idx<D, W>(j - 2, line, NI)] = qa;
     }
     __syncthreads();
     // the point values are dead: fetch the Roe-average inputs and the viscous flux into
@@ -332,7 +332,7 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
     // evaluated in double-float on the FP32 pipe.  The interface values are never
     // formed in FP64: the Roe flux needs only
     //   du    = g2 + dR - dL       (fhat_R - fhat_L, for the u-scalars; double-float)
-    //   fhat_L + fhat_R = (P2 + P3) + (dL + dR)   (for the flux scalars; FP64)
+    //   fhat_L + fhat_R = 2 P2 + (g2 + dL + dR)   (for the flux scalars; FP64)
     float2* rf = reinterpret_cast<float2*>(sm + PL::OFF_R);
     auto phase_c = [&](auto scaled) {
       constexpr bool SCALE = decltype(scaled)::value;
@@ -372,10 +372,10 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
           const df du = df_add_fast(g2, df_add_fast(dR, df_neg(dL)));
           rf[m * NI * W + o] = make_float2(du.hi, du.lo);
         }
-        if (m >= 4) {  // flux scalar: fhat_L + fhat_R = (P2 + P3) + sigma, the point sum from phase A2
-          const df sg = df_add_fast(dL, dR);
+        if (m >= 4) {  // flux scalar: fhat_L + fhat_R = 2 P2 + (g2 + dL + dR), P2 copied in phase A2
+          const df t = df_add_fast(g2, df_add_fast(dL, dR));
           double* F = sm + PL::OFF_R + (1 + m) * NI * W + o;
-          *F = (*F + f2d_bits(sg.hi)) + f2d_bits(sg.lo);
+          *F = fma(2.0, *F, f2d_bits(t.hi)) + f2d_bits(t.lo);
         }
       }
     };
@@ -426,8 +426,9 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
       const int sa = tile_idx<D, W>(f + 2, line, NP), sb = tile_idx<D, W>(f + 3, line, NP);
       if (MODE == 1) {
         // Roe dissipation X|Lambda|X^{-1} du in double-float from the double-float jumps
-        // du of phase C and the double-float Roe-average inputs; the flux is
-        // 0.5 (fhat_L + fhat_R) - 0.5 diss, two FP64 operations per component
+        // du of phase C and the double-float Roe-average inputs; the flux, already divided
+        // by dx for phase E, is (fhat_L + fhat_R)/(2 dx) - diss/(2 dx): two FP64 operations
+        // per component
         const float2* rf = reinterpret_cast<const float2*>(r);
         auto ldr = [&](int k, int sp) { const float2 v = rf[k * NP * W + sp]; return df{v.x, v.y}; };
         const float2* rj = reinterpret_cast<const float2*>(rec);
@@ -484,9 +485,12 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
         diss[1 + T2] = df_add_fast(df_mul_u(d0, vt2), A4);
         diss[4] = df_add_fast(df_add_fast(df_mul_u(S, H), df_mul_u(cD, un)),
                               df_add_fast(df_mul_u(A2, q2h), df_add_fast(df_mul_u(A3, vt1), df_mul_u(A4, vt2))));
+        const df mhr = df_neg(d2df_bits(a.g.hrh[D]));
 #pragma unroll
-        for (int v = 0; v < 5; ++v)
-          rec[v * NI * W + o] = fma(0.5, fs[v], f2d_bits(-0.5f * diss[v].hi)) + f2d_bits(-0.5f * diss[v].lo);
+        for (int v = 0; v < 5; ++v) {
+          const df t = df_mul(diss[v], mhr);
+          rec[v * NI * W + o] = fma(a.g.hrh[D], fs[v], f2d_bits(t.hi)) + f2d_bits(t.lo);
+        }
         continue;
       }
       double uL[5], uR[5], fL[5], fR[5];
@@ -576,6 +580,22 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
       if (s0 + pp >= nD || a0 + line >= na) continue;
       double cv[5];
       const int op = tile_idx<D, W>(pp + 1, line, NI), om = tile_idx<D, W>(pp, line, NI);
+      if (MODE == 1) {  // interface fluxes already divided by dx; viscous fluxes double-float
+#pragma unroll
+        for (int v = 0; v < 5; ++v) cv[v] = F[v * NI * W + om] - F[v * NI * W + op];
+        if (a.fv != nullptr) {
+          const df r12d = d2df_bits(r12);
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            const float2* fc = reinterpret_cast<const float2*>(fvs + cc * NP * W);
+            auto ld = [&](int j) { const float2 v = fc[tile_idx<D, W>(j, line, NP)]; return df{v.x, v.y}; };
+            const df t = d4_dfv(ld(pp + 1), ld(pp + 2), ld(pp + 4), ld(pp + 5), r12d);
+            cv[1 + cc] = (cv[1 + cc] + f2d_bits(t.hi)) + f2d_bits(t.lo);
+          }
+        }
+        dir_epilogue_pre(a, flat(s0 + pp, a0 + line), cv, pre);
+        continue;
+      }
 #pragma unroll
       for (int v = 0; v < 5; ++v) cv[v] = (F[v * NI * W + om] - F[v * NI * W + op]) * rdx;
       if (a.fv != nullptr) {

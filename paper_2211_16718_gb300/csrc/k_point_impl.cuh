@@ -110,7 +110,8 @@ __device__ __forceinline__ df d4_df(double qm2, double qm1, double qp1, double q
 
 // Viscous flux vectors at point p from the double-float gradients G[q][d] = d(u,v,w,T)_q/dx_d
 // and velocity (Sec. 2.1 stresses with the symmetric strain rate, heat flux q = -kappa grad T),
-// each output rounded to FP64 once (hi + lo); layout as visc_point_ijk.
+// stored as double-float pairs (the direction pass of NS3D_FP64 takes their divergence in
+// double-float); plane layout as visc_point_ijk.
 __device__ __forceinline__ void visc_fluxes_df(const df G[4][3], const df vel[3], double mu, double kappa,
                                                double* __restrict__ fv, long long N, long long p, int only_d) {
   const df dmu = d2df_bits(mu), dkap = d2df_bits(kappa);
@@ -128,10 +129,10 @@ __device__ __forceinline__ void visc_fluxes_df(const df G[4][3], const df vel[3]
                         : df_mul(dmu, df_add_fast(G[m][d], G[d][m]));
     const df en = df_add_fast(df_add_fast(df_mul_u(vel[0], tau[0]), df_mul_u(vel[1], tau[1])),
                               df_add_fast(df_mul_u(vel[2], tau[2]), df_mul_u(dkap, G[3][d])));
-    fv[(long long)(b + 0) * N + p] = f2d_bits(tau[0].hi) + f2d_bits(tau[0].lo);
-    fv[(long long)(b + 1) * N + p] = f2d_bits(tau[1].hi) + f2d_bits(tau[1].lo);
-    fv[(long long)(b + 2) * N + p] = f2d_bits(tau[2].hi) + f2d_bits(tau[2].lo);
-    fv[(long long)(b + 3) * N + p] = f2d_bits(en.hi) + f2d_bits(en.lo);
+    store_df(fv + (long long)(b + 0) * N + p, tau[0]);
+    store_df(fv + (long long)(b + 1) * N + p, tau[1]);
+    store_df(fv + (long long)(b + 2) * N + p, tau[2]);
+    store_df(fv + (long long)(b + 3) * N + p, en);
   }
 }
 

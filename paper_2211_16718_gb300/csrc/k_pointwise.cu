@@ -65,12 +65,24 @@ __global__ void __launch_bounds__(VT_X * VT_Y, 3) k_visc_tiled(const double* __r
   const int tid = threadIdx.x, tx = tid % VT_X, ty = tid / VT_X;
   const df r12[3] = {d2df_bits(g.r12h[0]), d2df_bits(g.r12h[1]), d2df_bits(g.r12h[2])};
   auto slot = [&](int zz) { return ring + ((zz - z0 + 2) % VT_RING) * 4 * VT_PLANE; };
+  // in-plane offsets of this thread's halo-tile positions (the same for every plane)
+  constexpr int NPOS = (VT_PLANE + VT_X * VT_Y - 1) / (VT_X * VT_Y);
+  int xy[NPOS];
+#pragma unroll
+  for (int k = 0; k < NPOS; ++k) {
+    const int pos = tid + k * VT_X * VT_Y;
+    const int hy = pos / VT_HX, hx = pos - hy * VT_HX;
+    xy[k] = wrap_idx(y0 - 2 + hy, ny) * nx + wrap_idx(x0 - 2 + hx, nx);
+  }
+  const long long plane_n = (long long)nx * ny;
   auto load_plane = [&](int zz) {  // plane zz (periodic) of the four fields, with halo
-    const int zw = wrap_idx(zz, nz);
+    const long long zoff = (long long)wrap_idx(zz, nz) * plane_n;
     float2* R = slot(zz);
-    for (int pos = tid; pos < VT_PLANE; pos += VT_X * VT_Y) {
-      const int hy = pos / VT_HX, hx = pos - hy * VT_HX;
-      const long long p = flat3(wrap_idx(x0 - 2 + hx, nx), wrap_idx(y0 - 2 + hy, ny), zw, nx, ny);
+#pragma unroll
+    for (int k = 0; k < NPOS; ++k) {
+      const int pos = tid + k * VT_X * VT_Y;
+      if (pos >= VT_PLANE) break;
+      const long long p = zoff + xy[k];
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const df v = d2df_bits(__ldg(pm + (long long)q * N + p));
