@@ -35,13 +35,13 @@ UNIT = "Gpts/s"
 RK_STAGES = 4
 # FP64 lane operations (FP64 instructions per thread, an FMA counting once) per grid point of
 # one direction pass, counted from each formulation without the halo's share:
-#  NS3D_FP64 (double-float weights, offsets, interface sums/jumps and Roe dissipation): point
-#   fluxes 5, first differences 9, per flux component the point sum P_i + P_{i+1} and the final
-#   combination 0.5 (P_i + P_{i+1}) + 0.5 (sigma - diss) 3 x 5, flux difference 10, viscous
-#   divergence 16.
+#  NS3D_FP64 (double-float weights, offsets, interface jumps, Roe dissipation and viscous
+#   divergence): point fluxes 5, first differences 9, per flux component the interface sum
+#   2 P_i + (g + dL + dR) 2 x 5 and the combination (fhat_L + fhat_R - diss)/(2 dx) 2 x 5, flux
+#   difference 5, adding the double-float viscous divergence 2 x 4.
 #  NS3D_FP64_STRICT: point fluxes 5, smoothness indicators 9 x 14, candidates and weighted sums
 #   (with the division sequence) 9 x 50, Roe flux ~100 (two divisions, a square root), 26.
-OPS_DIR_FP64 = 5 + 9 + 15 + 10 + 16
+OPS_DIR_FP64 = 5 + 9 + 10 + 10 + 5 + 8
 OPS_DIR_STRICT = 5 + 9 * 14 + 9 * 50 + 100 + 26
 OPS_RK_EPI = 15            # RK4 stage update in the z pass (5 components x 3)
 # The method's FP64 flops per point and pass (FMA = 2) in its all-FP64 form, for context.
@@ -371,9 +371,9 @@ def run_ours(args, world, rank, local):
     for k in ("avg_launch_ms", "method_fp64_flops_per_point", "method_equiv_tflops", "share_of_device_time",
               "algorithmic_bytes_per_point", "hbm_gbs_algorithmic"):
         roofline[k] = fp64_view[k]
-    roofline["note"] = ("the double-float weights, offsets, interface sums and Roe dissipation run ~6k FP32-pipe "
-                        "instructions per point and pass (FP32 runs 63x the FP64 rate); FP64 work is 55 lane-ops "
-                        "per point and pass + the RK epilogue (fp64_pipe)")
+    roofline["note"] = ("the double-float weights, offsets, interface jumps, Roe dissipation and viscous divergence "
+                        "run ~4.7k FP32-pipe instructions per point and pass (FP32 runs 63x the FP64 rate); FP64 "
+                        "work is 47 lane-ops per point and pass + the RK epilogue (fp64_pipe)")
     tr = ncu_traffic_per_point("k_dir", kernel_source_sha())
     if tr is not None:
         bpp, src, grid = tr
