@@ -106,18 +106,24 @@ __device__ __forceinline__ double weno_combine(double B1, double B2, double B3, 
   return num / den;
 }
 
-// Range of the squared indicators inside which df_weights needs no rescaling:
-// products of two stay below 2^120 (no overflow through the denominator and its
-// multiples) and above 2^-100 (their TwoProd error terms stay normal floats, so
-// the double-float products keep full precision).
-constexpr float DFW_LO = 0x1p-50f, DFW_HI = 0x1p60f;
+// Range of the squared indicators inside which df_offset needs no rescaling: products of
+// two stay below 2^80, so that they times a third difference (below 2^12 for such tiles,
+// since |third difference| <= 4 |first differences| <= 4 B^(1/4)) and the denominator times
+// the candidate difference stay inside the float range; and above 2^-100, so that their
+// TwoProd error terms stay normal floats and the products keep full precision.
+constexpr float DFW_LO = 0x1p-50f, DFW_HI = 0x1p40f;
 
-// Double-float weights of one reconstruction from its three squared, scaled
-// indicators (candidate order 1, 2, 3): w1 = omega_1/3, w3 = omega_3/6.
-// SCALE: rescale by a common power of two first (omega is scale-free); without
-// it every indicator must lie in [DFW_LO, DFW_HI).
+// Offset of one reconstruction from its candidate-2 value, in double-float, from the three
+// squared scaled indicators B_k (candidate order 1, 2, 3) and three differences:
+//   d = e/6 + omega_1/3 * ta + omega_3/6 * tb,   omega_k = c_k prod_{m!=k} B_m / den,
+// over the common denominator 6 den = 6 (B2 B3 + 6 B1 B3 + 3 B1 B2):
+//   d = [den * e + 2 B2 B3 * ta + 3 B1 B2 * tb] / (6 den)        (one division).
+// Left-biased: e = 2 g2 + g1, ta = s0 - s1, tb = s1 - s2; right-biased (mirrored):
+// e = -(2 g2 + g3), ta = s3 - s2, tb = -(s1 - s2).
+// SCALE: rescale the B_k by a common power of two first (the weights are scale-free);
+// without it every B_k must lie in [DFW_LO, DFW_HI).
 template <bool SCALE = true>
-__device__ __forceinline__ void df_weights(df B1, df B2, df B3, df& w1, df& w3) {
+__device__ __forceinline__ df df_offset(df B1, df B2, df B3, df e, df ta, df tb) {
   if (SCALE) {
     const int E = max(exponent_of(B1.hi), max(exponent_of(B2.hi), exponent_of(B3.hi)));
     const float sc = pow2f(-E);
@@ -129,8 +135,8 @@ __device__ __forceinline__ void df_weights(df B1, df B2, df B3, df& w1, df& w3) 
   const df p13 = df_mul_u(B1, B3);
   const df p12 = df_mul_u(B1, B2);
   const df den = df_add_pos_u(p23, df_add_pos_u(df_mul_f_u(p13, 6.0f), df_mul_f_u(p12, 3.0f)));
-  w1 = df_div(p23, df_mul_f_u(den, 3.0f));
-  w3 = df_div(p12, df_twice(den));
+  const df num = df_add_fast(df_mul_u(den, e), df_add_fast(df_twice(df_mul_u(p23, ta)), df_mul_f_u(df_mul_u(p12, tb), 3.0f)));
+  return df_div(num, df_mul_f_u(den, 6.0f));
 }
 
 // One tile (tx, ty, tz) of the direction-D pass, executed by the whole CTA on the
@@ -358,15 +364,10 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
           const float2 v = b[k * NW * W + tile_idx<D, W>(w, line, NW)];
           return df{v.x, v.y};
         };
-        df w1, w3, v1, v3;
-        df_weights<SCALE>(ld(0, f), ld(1, f + 1), ld(2, f + 2), w1, w3);
-        df_weights<SCALE>(ld(2, f + 3), ld(1, f + 2), ld(0, f + 1), v1, v3);
-        const df sixth{a.sixth_hi, a.sixth_lo};
         const df g22 = df_twice(g2);
-        const df eL0 = df_mul_u(df_add_fast(g22, g1), sixth);
-        const df eR0 = df_mul_u(df_add_fast(g22, g3), sixth);
-        const df dL = df_add_fast(eL0, df_add_fast(df_mul_u(w1, t0), df_mul_u(w3, tC)));
-        const df dR = df_add_fast(df_neg(eR0), df_add_fast(df_mul_u(v1, t2), df_neg(df_mul_u(v3, tC))));
+        const df dL = df_offset<SCALE>(ld(0, f), ld(1, f + 1), ld(2, f + 2), df_add_fast(g22, g1), t0, tC);
+        const df dR = df_offset<SCALE>(ld(2, f + 3), ld(1, f + 2), ld(0, f + 1), df_neg(df_add_fast(g22, g3)), t2,
+                                       df_neg(tC));
         const int o = tile_idx<D, W>(f, line, NI);
         if (m < 5) {
           const df du = df_add_fast(g2, df_add_fast(dR, df_neg(dL)));
