@@ -604,20 +604,22 @@ __device__ __forceinline__ df df_unpack(float2 v) { return df{v.x, v.y}; }
 
 // The three weights of one reconstruction from its b_k (candidate order 0, 1, 2; optimal
 // weights 1, 6, 3 over 10), with a common power-of-two scaling (omega is scale-free).
+// Products and positive sums in this section are left unnormalised where they feed another
+// double-float operation (df_mul_u and friends: the same values, |lo| a few ulp(hi)).
 __device__ __forceinline__ void df_omega(df b0, df b1, df b2, df om[3]) {
-  df B0 = df_sqr(b0), B1 = df_sqr(b1), B2 = df_sqr(b2);
+  df B0 = df_sqr_u(b0), B1 = df_sqr_u(b1), B2 = df_sqr_u(b2);
   const int E = max(exponent_of(B0.hi), max(exponent_of(B1.hi), exponent_of(B2.hi)));
   const float sc = pow2f(-E);
   B0 = df{B0.hi * sc, B0.lo * sc};
   B1 = df{B1.hi * sc, B1.lo * sc};
   B2 = df{B2.hi * sc, B2.lo * sc};
-  const df a0 = df_mul(B1, B2);
-  const df a1 = df_mul_f(df_mul(B0, B2), 6.0f);
-  const df a2 = df_mul_f(df_mul(B0, B1), 3.0f);
-  const df r = df_div(df{1.0f, 0.0f}, df_add_pos(a0, df_add_pos(a1, a2)));
-  om[0] = df_mul(a0, r);
-  om[1] = df_mul(a1, r);
-  om[2] = df_mul(a2, r);
+  const df a0 = df_mul_u(B1, B2);
+  const df a1 = df_mul_f_u(df_mul_u(B0, B2), 6.0f);
+  const df a2 = df_mul_f_u(df_mul_u(B0, B1), 3.0f);
+  const df r = df_div(df{1.0f, 0.0f}, df_add_pos_u(a0, df_add_pos_u(a1, a2)));
+  om[0] = df_mul_u(a0, r);
+  om[1] = df_mul_u(a1, r);
+  om[2] = df_mul_u(a2, r);
 }
 
 struct DFConst {
@@ -630,14 +632,14 @@ __device__ __forceinline__ df df_offset(df g0, df g1, df g2, df g3, const df om[
   s[0] = df_sub(g1, g0);
   s[1] = df_sub(g2, g1);
   s[2] = df_sub(g3, g2);
-  E0 = df_mul(df_sub(s[0], s[1]), k.third);
-  E2 = df_mul(df_sub(s[1], s[2]), k.sixth);
-  return df_add_fast(df_mul(om[0], E0), df_mul(om[2], E2));
+  E0 = df_mul_u(df_sub(s[0], s[1]), k.third);
+  E2 = df_mul_u(df_sub(s[1], s[2]), k.sixth);
+  return df_add_fast(df_mul_u(om[0], E0), df_mul_u(om[2], E2));
 }
 
 // FP64 value of the reconstruction with centre value pc: pc + (2 g2 + g1)/6 + M.
 __device__ __forceinline__ double df_value(double pc, df g1, df g2, df M, const DFConst& k) {
-  const df d = df_add_fast(df_mul(df_add_fast(df_twice(g2), g1), k.sixth), M);
+  const df d = df_add_fast(df_mul_u(df_add_fast(df_twice(g2), g1), k.sixth), M);
   return (pc + f2d_bits(d.hi)) + f2d_bits(d.lo);
 }
 
@@ -647,33 +649,33 @@ __device__ __forceinline__ void df_recon_adjoint(df g0, df g1, df g2, df g3, df 
                                                  df y, const DFConst& k, df out[5]) {
   df s[3], E0, E2;
   const df M = df_offset(g0, g1, g2, g3, om, k, E0, E2, s);
-  const df v0 = df_sub(df_mul_f(g1, 3.0f), g0);
+  const df v0 = df_sub(df_mul_f_u(g1, 3.0f), g0);
   const df v1 = df_add_fast(g1, g2);
-  const df v2 = df_sub(g3, df_mul_f(g2, 3.0f));
-  const df y0 = df_mul(y, om[0]), y1 = df_mul(y, om[1]), y2 = df_mul(y, om[2]);
+  const df v2 = df_sub(g3, df_mul_f_u(g2, 3.0f));
+  const df y0 = df_mul_u(y, om[0]), y1 = df_mul_u(y, om[1]), y2 = df_mul_u(y, om[2]);
   // adjoints of b_k: -2 y_k (q_k - q) / b_k with q_0 - q = E0 - M, q_1 - q = -M, q_2 - q = E2 - M
-  const df k0 = df_twice(df_div(df_mul(y0, df_sub(M, E0)), b0));
-  const df k1 = df_twice(df_div(df_mul(y1, M), b1));
-  const df k2 = df_twice(df_div(df_mul(y2, df_sub(M, E2)), b2));
+  const df k0 = df_twice(df_div(df_mul_u(y0, df_sub(M, E0)), b0));
+  const df k1 = df_twice(df_div(df_mul_u(y1, M), b1));
+  const df k2 = df_twice(df_div(df_mul_u(y2, df_sub(M, E2)), b2));
   // direct term sum_k y_k dq_k/dq_t
-  out[0] = df_mul(y0, k.third);
-  out[1] = df_neg(df_mul(df_add_fast(df_mul_f(y0, 7.0f), y1), k.sixth));
-  out[2] = df_mul(df_add_fast(df_mul_f(y0, 11.0f), df_add_fast(df_mul_f(y1, 5.0f), df_twice(y2))), k.sixth);
-  out[3] = df_mul(df_add_fast(df_twice(y1), df_mul_f(y2, 5.0f)), k.sixth);
-  out[4] = df_neg(df_mul(y2, k.sixth));
+  out[0] = df_mul_u(y0, k.third);
+  out[1] = df_neg(df_mul_u(df_add_fast(df_mul_f_u(y0, 7.0f), y1), k.sixth));
+  out[2] = df_mul_u(df_add_fast(df_mul_f_u(y0, 11.0f), df_add_fast(df_mul_f_u(y1, 5.0f), df_twice(y2))), k.sixth);
+  out[3] = df_mul_u(df_add_fast(df_twice(y1), df_mul_f_u(y2, 5.0f)), k.sixth);
+  out[4] = df_neg(df_mul_u(y2, k.sixth));
   // db/d(x, y, z) of a window = 26/3 s (1, -2, 1) + 2 v dv/d(x, y, z)
-  df t = df_mul(df_mul(s[0], k0), k.c263), r = df_twice(df_mul(v0, k0));  // dv = (1, -4, 3)
+  df t = df_mul_u(df_mul_u(s[0], k0), k.c263), r = df_twice(df_mul_u(v0, k0));  // dv = (1, -4, 3)
   out[0] = df_add_fast(out[0], df_add_fast(t, r));
   out[1] = df_sub(out[1], df_add_fast(df_twice(t), df_twice(df_twice(r))));
-  out[2] = df_add_fast(out[2], df_add_fast(t, df_mul_f(r, 3.0f)));
-  t = df_mul(df_mul(s[1], k1), k.c263);
-  r = df_twice(df_mul(v1, k1));  // dv = (-1, 0, 1)
+  out[2] = df_add_fast(out[2], df_add_fast(t, df_mul_f_u(r, 3.0f)));
+  t = df_mul_u(df_mul_u(s[1], k1), k.c263);
+  r = df_twice(df_mul_u(v1, k1));  // dv = (-1, 0, 1)
   out[1] = df_add_fast(out[1], df_sub(t, r));
   out[2] = df_sub(out[2], df_twice(t));
   out[3] = df_add_fast(out[3], df_add_fast(t, r));
-  t = df_mul(df_mul(s[2], k2), k.c263);
-  r = df_twice(df_mul(v2, k2));  // dv = (3, -4, 1)
-  out[2] = df_add_fast(out[2], df_add_fast(t, df_mul_f(r, 3.0f)));
+  t = df_mul_u(df_mul_u(s[2], k2), k.c263);
+  r = df_twice(df_mul_u(v2, k2));  // dv = (3, -4, 1)
+  out[2] = df_add_fast(out[2], df_add_fast(t, df_mul_f_u(r, 3.0f)));
   out[3] = df_sub(out[3], df_add_fast(df_twice(t), df_twice(df_twice(r))));
   out[4] = df_add_fast(out[4], df_add_fast(t, r));
 }
@@ -782,10 +784,10 @@ __global__ void __launch_bounds__(APF::THREADS, 2) k_adj_dir_df(const AdjArgs a)
     const float2* Gm = G + m * NP * W;
     const df g0 = df_unpack(Gm[tile_idx<D, W>(w, line, NP)]), g1 = df_unpack(Gm[tile_idx<D, W>(w + 1, line, NP)]);
     const df sw = df_sub(g1, g0);
-    const df aa = df_add_pos(df_mul(df_sqr(sw), c133), eps4);
-    const df b0 = df_add_pos(df_sqr(df_sub(df_mul_f(g1, 3.0f), g0)), aa);
-    const df b1 = df_add_pos(df_sqr(df_add_fast(g0, g1)), aa);
-    const df b2 = df_add_pos(df_sqr(df_sub(g1, df_mul_f(g0, 3.0f))), aa);
+    const df aa = df_add_pos_u(df_mul_u(df_sqr_u(sw), c133), eps4);
+    const df b0 = df_add_pos_u(df_sqr_u(df_sub(df_mul_f_u(g1, 3.0f), g0)), aa);
+    const df b1 = df_add_pos_u(df_sqr_u(df_add_fast(g0, g1)), aa);
+    const df b2 = df_add_pos_u(df_sqr_u(df_sub(g1, df_mul_f_u(g0, 3.0f))), aa);
     const int o = tile_idx<D, W>(w, line, NW);
     Bw[(m * 3 + 0) * NW * W + o] = df_pack(b0);
     Bw[(m * 3 + 1) * NW * W + o] = df_pack(b1);
