@@ -57,7 +57,7 @@ constexpr int NQ = 9;             // reconstructed scalars
 //   MODE 1: Q [NQ][NP*W], dead after phase A2: ROE [5][NP*W] and FV [4][NP*W] then
 //           arrive there by cp.async (as FP64) while phases B and C run;
 //           B [NQ][3][NW*W] (double-float), dead after phase C: the epilogue
-//           operands then arrive there; S [NQ][NW*W] second differences;
+//           operands then arrive there; S [NQ][NW*W] third differences;
 //           G [NQ][NG*W] first differences; R [10][NI*W]: jumps du of u_0..u_4
 //           (double-float, slots 0-4) and the sums of the five flux scalars
 //           (FP64, slots 5-9), later [5][NI*W] interface fluxes.
@@ -77,7 +77,7 @@ struct Plan {
   static constexpr int OFF_ROE = (MODE == 1) ? OFF_Q : OFF_Q + NQ * NP * W;
   static constexpr int OFF_FV = OFF_ROE + 5 * NP * W;
   static constexpr int OFF_B = (MODE == 1) ? OFF_Q + NQ * NP * W : OFF_FV + 4 * NP * W;
-  static constexpr int OFF_S = OFF_B + NQ * 3 * NW * W;
+  static constexpr int OFF_S = OFF_B + NQ * 3 * NW * W;  // MODE 1: third differences
   static constexpr int OFF_G = OFF_S + (MODE == 1 ? NQ * NW * W : 0);
   static constexpr int OFF_R = OFF_G + (MODE == 1 ? NQ * NG * W : 0);
   static constexpr int R_SLOTS = (MODE == 1) ? 10 : 18;
@@ -278,15 +278,28 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
         const float2* G = reinterpret_cast<const float2*>(sm + PL::OFF_G) + m * PL::NG * W;
         const float2 g0 = G[tile_idx<D, W>(w, line, PL::NG)], g1 = G[tile_idx<D, W>(w + 1, line, PL::NG)];
         const df dgm = df{g0.x, g0.y}, dgp = df{g1.x, g1.y};
-        const df ds = df_add_fast(dgp, df_neg(dgm));
-        reinterpret_cast<float2*>(sm + PL::OFF_S)[m * NW * W + o] = make_float2(ds.hi, ds.lo);
-        const df aa = df_add_pos_u(df_mul_u(df_sqr_u(ds), df{a.c133_hi, a.c133_lo}), df{a.eps4_hi, a.eps4_lo});
-        const df u1 = df_add_fast(ds, df_twice(dgp));          // x - 4y + 3z = s + 2 g+
-        const df u2 = df_add_fast(dgm, dgp);                   // z - x
-        const df u3 = df_add_fast(ds, df_neg(df_twice(dgm)));  // 3x - 4y + z = s - 2 g-
-        const df B1 = df_sqr_u(df_add_pos_u(df_sqr_u(u1), aa));
-        const df B2 = df_sqr_u(df_add_pos_u(df_sqr_u(u2), aa));
-        const df B3 = df_sqr_u(df_add_pos_u(df_sqr_u(u3), aa));
+        const df ds = df_add_fast(dgp, df_neg(dgm));  // second difference s_w
+        // third difference T_w = s_w - s_{w+1} (phase C needs T_f, T_{f+1}, T_{f+2}; the last
+        // window has no s_{w+1} in the tile and its T is never read)
+        df T{0.0f, 0.0f};
+        if (w + 2 < PL::NG) {
+          const float2 g2 = G[tile_idx<D, W>(w + 2, line, PL::NG)];
+          T = df_add_fast(ds, df_neg(df_add_fast(df{g2.x, g2.y}, df_neg(dgp))));
+        }
+        reinterpret_cast<float2*>(sm + PL::OFF_S)[m * NW * W + o] = make_float2(T.hi, T.lo);
+        // scaled indicators b_k = u_k^2 + aa, aa = (13/3) s^2 + 4 eps, with u_2 = z - x and
+        // u_1 = x - 4y + 3z = u_2 + 2s, u_3 = 3x - 4y + z = 2s - u_2:
+        //   b_2 = u_2^2 + aa,  b_{1,3} = (b_2 + 4 s^2) +- 4 u_2 s   (b_k >= aa >= (13/3) s^2, so
+        // b_2 + 4 s^2 <= ~3 b_{1,3}: no harmful cancellation)
+        const df s2 = df_sqr_u(ds);
+        const df aa = df_add_pos_u(df_mul_u(s2, df{a.c133_hi, a.c133_lo}), df{a.eps4_hi, a.eps4_lo});
+        const df u2 = df_add_fast(dgm, dgp);
+        const df b2 = df_add_pos_u(df_sqr_u(u2), aa);
+        const df pq = df_add_pos_u(b2, df_twice(df_twice(s2)));
+        const df r4 = df_twice(df_twice(df_mul_u(u2, ds)));
+        const df B1 = df_sqr_u(df_add_fast(pq, r4));
+        const df B2 = df_sqr_u(b2);
+        const df B3 = df_sqr_u(df_add_fast(pq, df_neg(r4)));
         bw[(m * 3 + 0) * NW * W + o] = make_float2(B1.hi, B1.lo);
         bw[(m * 3 + 1) * NW * W + o] = make_float2(B2.hi, B2.lo);
         bw[(m * 3 + 2) * NW * W + o] = make_float2(B3.hi, B3.lo);
@@ -356,8 +369,8 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
           const float2 v = G[tile_idx<D, W>(j, line, PL::NG)];
           return df{v.x, v.y};
         };
-        const df s0 = ldS(f), s1 = ldS(f + 1), s2 = ldS(f + 2), s3 = ldS(f + 3);
-        const df t0 = df_add_fast(s0, df_neg(s1)), tC = df_add_fast(s1, df_neg(s2)), t2 = df_add_fast(s3, df_neg(s2));
+        // third differences (phase B): s0 - s1 = T_f, s1 - s2 = T_{f+1}, s3 - s2 = -T_{f+2}
+        const df t0 = ldS(f), tC = ldS(f + 1), t2 = df_neg(ldS(f + 2));
         const df g1 = ldG(f + 1), g2 = ldG(f + 2), g3 = ldG(f + 3);
         const float2* b = reinterpret_cast<const float2*>(sm + PL::OFF_B) + m * 3 * NW * W;
         auto ld = [&](int k, int w) {
