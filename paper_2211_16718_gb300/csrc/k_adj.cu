@@ -637,11 +637,6 @@ __device__ __forceinline__ df df_offset(df g0, df g1, df g2, df g3, const df om[
   return df_add_fast(df_mul_u(om[0], E0), df_mul_u(om[2], E2));
 }
 
-// FP64 value of the reconstruction with centre value pc: pc + (2 g2 + g1)/6 + M.
-__device__ __forceinline__ double df_value(double pc, df g1, df g2, df M, const DFConst& k) {
-  const df d = df_add_fast(df_mul_u(df_add_fast(df_twice(g2), g1), k.sixth), M);
-  return (pc + f2d_bits(d.hi)) + f2d_bits(d.lo);
-}
 
 // y * d(value)/d(q_t), t = 0..4, of the reconstruction of stencil differences g0..g3 with
 // window terms b0..b2 and weights om (as weno_adjoint, in double-float).
@@ -797,7 +792,7 @@ __global__ void __launch_bounds__(APF::THREADS, 2) k_adj_dir_df(const AdjArgs a)
   }
   __syncthreads();
 
-  // ---- C: values of the u reconstructions (for the Roe adjoint) --------------------------
+  // ---- C: jumps of the u reconstructions (for the Roe adjoint) ----------------------------
   for (int item = tid; item < 5 * NI * W; item += APF::THREADS) {
     const int m = item / (NI * W);
     int f, line;
@@ -808,17 +803,18 @@ __global__ void __launch_bounds__(APF::THREADS, 2) k_adj_dir_df(const AdjArgs a)
     for (int j = 0; j < 5; ++j) g[j] = df_unpack(Gm[tile_idx<D, W>(f + j, line, NP)]);
     const float2* B = Bw + m * 3 * NW * W;
     auto ldb = [&](int k, int w) { return df_unpack(B[k * NW * W + tile_idx<D, W>(w, line, NW)]); };
-    const double* qm = q + m * NP * W;
     df omL[3], omR[3], s[3], E0, E2;
     df_omega(ldb(0, f), ldb(1, f + 1), ldb(2, f + 2), omL);
     const df ML = df_offset(g[0], g[1], g[2], g[3], omL, kc, E0, E2, s);
-    const double vL = df_value(qm[tile_idx<D, W>(f + 2, line, NP)], g[1], g[2], ML, kc);
     df_omega(ldb(2, f + 3), ldb(1, f + 2), ldb(0, f + 1), omR);
     const df MR = df_offset(df_neg(g[4]), df_neg(g[3]), df_neg(g[2]), df_neg(g[1]), omR, kc, E0, E2, s);
-    const double vR = df_value(qm[tile_idx<D, W>(f + 3, line, NP)], df_neg(g[3]), df_neg(g[2]), MR, kc);
+    // the jump ûR - ûL = (P3 - P2) - (2 g2 + g3)/6 + MR - (2 g2 + g1)/6 - ML, in double-float
+    // (the values themselves are not needed)
+    const df g22 = df_twice(g[2]);
+    const df lin = df_mul_u(df_add_fast(df_add_fast(g22, g[1]), df_add_fast(g22, g[3])), kc.sixth);
+    const df du = df_add_fast(df_add_fast(g[2], df_neg(lin)), df_add_fast(MR, df_neg(ML)));
     const int o = tile_idx<D, W>(f, line, NI);
-    rec[(2 * m) * NI * W + o] = vL;
-    rec[(2 * m + 1) * NI * W + o] = vR;
+    reinterpret_cast<float2*>(rec)[m * NI * W + o] = df_pack(du);
     // the weights, for phase E (which overwrites these slots with its contributions)
     float2* wm = wc + m * 6 * NI * W;
 #pragma unroll
@@ -840,7 +836,8 @@ __global__ void __launch_bounds__(APF::THREADS, 2) k_adj_dir_df(const AdjArgs a)
       double du[5], Lh[5], Va[3], Vb[3];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        du[v] = rec[(2 * v + 1) * NI * W + o] - rec[(2 * v) * NI * W + o];
+        const df j = df_unpack(reinterpret_cast<const float2*>(rec)[v * NI * W + o]);
+        du[v] = f2d_bits(j.hi) + f2d_bits(j.lo);
         Lh[v] = (lm[v * NP * W + sb] - lm[v * NP * W + sa]) * rdx;
       }
 #pragma unroll
