@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(PW_THREADS) k_visc32(const double* __restrict_
 
 // ---- statistics ------------------------------------------------------------
 constexpr int ST_THREADS = 256;
-constexpr int ST_MAX_BLOCKS = 1024;
+constexpr int ST_MAX_BLOCKS = 4096;
 constexpr int NSUM = 7;   // mass, 3 momenta, energy, ke, enstrophy
 constexpr int NRED = 10;  // + rho_min, p_min, max wavespeed/dx
 
@@ -258,14 +258,28 @@ __device__ Red block_reduce(Red r) {
   return r;
 }
 
-template <bool DFT>  // DFT: the temperature plane holds double-float pairs (prim_point<true>)
-__global__ void __launch_bounds__(ST_THREADS) k_stats(const double* __restrict__ u, const double* __restrict__ pm,
-                                                      const Grid g, double* __restrict__ partials) {
+// Statistics: a block walks its tiles of
+// 32 x 8 x-y columns times VT_CZ planes in a fixed order; the velocity planes, with a 2-point
+// x-y halo, are converted to double-float once into a 5-plane ring (z-2 .. z+2) for the
+// vorticity stencils.  The accumulation order is fixed by the grid shape, so the result is
+// deterministic.  Sums, minima and counts in FP64; kinetic energy, vorticity, enstrophy and
+// wave speed in double-float on the FP32 pipe.  DFT: the temperature plane holds
+// double-float pairs (prim_point<true>).
+constexpr int SR_SMEM = VT_RING * 3 * VT_PLANE * (int)sizeof(float2);  // 51,840 bytes
+
+template <bool DFT>
+__global__ void __launch_bounds__(ST_THREADS, 4) k_stats_tiled(const double* __restrict__ u, const double* __restrict__ pm,
+                                                                const Grid g, double* __restrict__ partials, int ntx,
+                                                                int nty, long long ntiles) {
+  extern __shared__ float2 ring[];  // [VT_RING][3][VT_HY][VT_HX]
+  static_assert(VT_X * VT_Y == ST_THREADS, "one point per thread and plane");
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  const long long N = (long long)nx * ny * nz;
-  const int n3[3] = {nx, ny, nz};
+  const long long N = g.N;
+  const long long plane_n = (long long)nx * ny;
   const df r12d[3] = {d2df_bits(g.r12h[0]), d2df_bits(g.r12h[1]), d2df_bits(g.r12h[2])};
   const df rhd[3] = {d2df_bits(g.rh[0]), d2df_bits(g.rh[1]), d2df_bits(g.rh[2])};
+  const int tid = threadIdx.x, tx = tid % VT_X, ty = tid / VT_X;
+  constexpr int NPOS = (VT_PLANE + ST_THREADS - 1) / ST_THREADS;
   df wmax{0.0f, 0.0f};
   Red r;
 #pragma unroll
@@ -273,55 +287,83 @@ __global__ void __launch_bounds__(ST_THREADS) k_stats(const double* __restrict__
   r.rmin = INFINITY;
   r.pmin = INFINITY;
   r.wmax = 0.0;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(p % nx);
-    const int j = (int)((p / nx) % ny);
-    const int k = (int)(p / ((long long)nx * ny));
-    const double rho = u[p];
-    const double vel[3] = {pm[PM_U * N + p], pm[PM_V * N + p], pm[PM_W * N + p]};
-    const double pr = pm[PM_P * N + p];
-    r.s[0] += rho;
-    r.s[1] += u[N + p];
-    r.s[2] += u[2 * N + p];
-    r.s[3] += u[3 * N + p];
-    r.s[4] += u[4 * N + p];
-    // kinetic energy, vorticity (its gradients: dv_m/dx_d, m != d), enstrophy and wave
-    // speed in double-float on the FP32 pipe; the sums themselves accumulate in FP64
-    const df rd = d2df_bits(rho);
-    const df rh2{0.5f * rd.hi, 0.5f * rd.lo};  // rho / 2, exact
-    const df vd[3] = {d2df_bits(vel[0]), d2df_bits(vel[1]), d2df_bits(vel[2])};
-    const df ke = df_mul_u(rh2, df_add_pos_u(df_sqr_u(vd[0]), df_add_pos_u(df_sqr_u(vd[1]), df_sqr_u(vd[2]))));
-    r.s[5] = (r.s[5] + f2d_bits(ke.hi)) + f2d_bits(ke.lo);
-    df G[3][3];
+  auto ld = [](const float2* P, int i) { const float2 v = P[i]; return df{v.x, v.y}; };
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int x0 = (int)(t % ntx) * VT_X;
+    const long long rest = t / ntx;
+    const int y0 = (int)(rest % nty) * VT_Y, z0 = (int)(rest / nty) * VT_CZ;
+    const int z1 = min(z0 + VT_CZ, nz);
+    auto slot = [&](int zz) { return ring + ((zz - z0 + 2) % VT_RING) * 3 * VT_PLANE; };
+    int xy[NPOS];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      long long nb[4];
-#pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        const int off = (o < 2) ? (o - 2) : (o - 1);
-        int c[3] = {i, j, k};
-        c[d] = wrap_near(c[d], off, n3[d]);
-        nb[o] = flat3(c[0], c[1], c[2], nx, ny);
-      }
-#pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        if (m == d) continue;
-        const double* A = pm + (long long)m * N;
-        G[m][d] = d4_df(__ldg(A + nb[0]), __ldg(A + nb[1]), __ldg(A + nb[2]), __ldg(A + nb[3]), r12d[d]);
-      }
+    for (int k = 0; k < NPOS; ++k) {
+      const int pos = tid + k * ST_THREADS;
+      const int hy = pos / VT_HX, hx = pos - hy * VT_HX;
+      xy[k] = wrap_idx(y0 - 2 + hy, ny) * nx + wrap_idx(x0 - 2 + hx, nx);
     }
-    const df wx = df_add_fast(G[2][1], df_neg(G[1][2]));
-    const df wy = df_add_fast(G[0][2], df_neg(G[2][0]));
-    const df wz = df_add_fast(G[1][0], df_neg(G[0][1]));
-    const df en = df_mul_u(rh2, df_add_pos_u(df_sqr_u(wx), df_add_pos_u(df_sqr_u(wy), df_sqr_u(wz))));
-    r.s[6] = (r.s[6] + f2d_bits(en.hi)) + f2d_bits(en.lo);
-    r.rmin = fmin(r.rmin, rho);
-    r.pmin = fmin(r.pmin, pr);
-    const df c = df_sqrt(DFT ? load_df(pm + PM_T * N + p) : d2df_bits(pm[PM_T * N + p]));
+    auto load_plane = [&](int zz) {
+      const long long zoff = (long long)wrap_idx(zz, nz) * plane_n;
+      float2* R = slot(zz);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const df w = df_mul(df_add_pos(df_abs(vd[d]), c), rhd[d]);
-      if (df_lt(wmax, w)) wmax = w;
+      for (int k = 0; k < NPOS; ++k) {
+        const int pos = tid + k * ST_THREADS;
+        if (pos >= VT_PLANE) break;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const df v = d2df_bits(__ldg(pm + (long long)q * N + zoff + xy[k]));
+          R[q * VT_PLANE + pos] = make_float2(v.hi, v.lo);
+        }
+      }
+    };
+    __syncthreads();  // the previous tile's last reads of the ring
+    for (int zz = z0 - 2; zz < z0 + 2; ++zz) load_plane(zz);
+    for (int z = z0; z < z1; ++z) {
+      load_plane(z + 2);
+      __syncthreads();
+      if (x0 + tx < nx && y0 + ty < ny) {
+        const long long p = (long long)z * plane_n + (long long)(y0 + ty) * nx + (x0 + tx);
+        const int c = (ty + 2) * VT_HX + (tx + 2);
+        const float2 *Zm2 = slot(z - 2), *Zm1 = slot(z - 1), *Z0 = slot(z), *Zp1 = slot(z + 1), *Zp2 = slot(z + 2);
+        const double rho = __ldg(u + p);
+        const double pr = __ldg(pm + PM_P * N + p);
+        r.s[0] += rho;
+        r.s[1] += __ldg(u + N + p);
+        r.s[2] += __ldg(u + 2 * N + p);
+        r.s[3] += __ldg(u + 3 * N + p);
+        r.s[4] += __ldg(u + 4 * N + p);
+        const df rd = d2df_bits(rho);
+        const df rh2{0.5f * rd.hi, 0.5f * rd.lo};  // rho / 2, exact
+        const df vd[3] = {ld(Z0, c), ld(Z0 + VT_PLANE, c), ld(Z0 + 2 * VT_PLANE, c)};
+        const df ke = df_mul_u(rh2, df_add_pos_u(df_sqr_u(vd[0]), df_add_pos_u(df_sqr_u(vd[1]), df_sqr_u(vd[2]))));
+        r.s[5] = (r.s[5] + f2d_bits(ke.hi)) + f2d_bits(ke.lo);
+        // vorticity: dv_m/dx_d for m != d
+        auto gx = [&](int m) {
+          const float2* P = Z0 + m * VT_PLANE;
+          return d4_dfv(ld(P, c - 2), ld(P, c - 1), ld(P, c + 1), ld(P, c + 2), r12d[0]);
+        };
+        auto gy = [&](int m) {
+          const float2* P = Z0 + m * VT_PLANE;
+          return d4_dfv(ld(P, c - 2 * VT_HX), ld(P, c - VT_HX), ld(P, c + VT_HX), ld(P, c + 2 * VT_HX), r12d[1]);
+        };
+        auto gz = [&](int m) {
+          const int o = m * VT_PLANE + c;
+          return d4_dfv(ld(Zm2, o), ld(Zm1, o), ld(Zp1, o), ld(Zp2, o), r12d[2]);
+        };
+        const df wx = df_add_fast(gy(2), df_neg(gz(1)));
+        const df wy = df_add_fast(gz(0), df_neg(gx(2)));
+        const df wz = df_add_fast(gx(1), df_neg(gy(0)));
+        const df en = df_mul_u(rh2, df_add_pos_u(df_sqr_u(wx), df_add_pos_u(df_sqr_u(wy), df_sqr_u(wz))));
+        r.s[6] = (r.s[6] + f2d_bits(en.hi)) + f2d_bits(en.lo);
+        r.rmin = fmin(r.rmin, rho);
+        r.pmin = fmin(r.pmin, pr);
+        const df cs = df_sqrt(DFT ? load_df(pm + PM_T * N + p) : d2df_bits(__ldg(pm + PM_T * N + p)));
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const df w = df_mul(df_add_pos(df_abs(vd[d]), cs), rhd[d]);
+          if (df_lt(wmax, w)) wmax = w;
+        }
+      }
+      __syncthreads();  // the slot of plane z - 2 takes plane z + 3 next
     }
   }
   r.wmax = f2d_bits(wmax.hi) + f2d_bits(wmax.lo);
@@ -391,7 +433,10 @@ cudaError_t launch_visc(const Grid& g, const double* pm, double* fv, double mu, 
 }
 
 cudaError_t prepare_visc_kernels() {
-  return cudaFuncSetAttribute(k_visc_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, VT_SMEM);
+  cudaError_t e = cudaFuncSetAttribute(k_visc_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, VT_SMEM);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stats_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SR_SMEM);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stats_tiled<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SR_SMEM);
+  return e;
 }
 
 cudaError_t launch_prim32(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s) {
@@ -415,10 +460,14 @@ int stats_num_blocks(const Grid& g) {
 cudaError_t launch_stats(const Grid& g, const double* u, const double* pm, double gamma, double* partials,
                          cudaStream_t s, int df) {
   (void)gamma;
+  const int ntx = (g.n[0] + VT_X - 1) / VT_X, nty = (g.n[1] + VT_Y - 1) / VT_Y, ntz = (g.n[2] + VT_CZ - 1) / VT_CZ;
+  const long long ntiles = (long long)ntx * nty * ntz;
+  // exactly stats_num_blocks(g) blocks: the partials k_stats_final reduces (blocks without a
+  // tile write neutral partials)
   if (df)
-    k_stats<true><<<stats_num_blocks(g), ST_THREADS, 0, s>>>(u, pm, g, partials);
+    k_stats_tiled<true><<<stats_num_blocks(g), ST_THREADS, SR_SMEM, s>>>(u, pm, g, partials, ntx, nty, ntiles);
   else
-    k_stats<false><<<stats_num_blocks(g), ST_THREADS, 0, s>>>(u, pm, g, partials);
+    k_stats_tiled<false><<<stats_num_blocks(g), ST_THREADS, SR_SMEM, s>>>(u, pm, g, partials, ntx, nty, ntiles);
   return cudaGetLastError();
 }
 
