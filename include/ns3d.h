@@ -58,11 +58,15 @@ enum {
 
 enum { NS3D_RK4 = 0, NS3D_SSPRK3 = 1 };           /* time integrators (Sec. 2.2) */
 /* Arithmetic of the reconstruction and upwinding:
- *  NS3D_FP64        FP64 state, candidates, interpolated values, Roe flux, viscous terms
- *                   and RK update; the nonlinear WENO weights (which only multiply
- *                   third differences of the data) in double-float arithmetic (two
- *                   FP32 words, ~48 bits) on the FP32 pipe.  Agrees with the all-FP64
- *                   evaluation to FP64 rounding.  Requires weno_eps >= 1e-15.
+ *  NS3D_FP64        FP64 state, point values and their first differences, point fluxes,
+ *                   interface-flux sums and RK update; what only multiplies small
+ *                   differences or enters through a dissipation or viscous term (the
+ *                   nonlinear WENO weights and offsets, the interface jumps, the Roe
+ *                   dissipation, the viscous fluxes and their divergence, the statistics'
+ *                   kinetic energy, vorticity and wave speed) in double-float arithmetic
+ *                   (two FP32 words, ~48 bits) on the FP32 pipe.  Agrees with the all-FP64
+ *                   evaluation to within the parity tolerance of the FP64 path (1e-12
+ *                   relative on the right-hand side).  Requires weno_eps >= 1e-15.
  *  NS3D_FP32_BULK   smoothness indicators, weights, interface values and Roe flux in
  *                   FP32; state, RK accumulation and reductions in FP64.
  *  NS3D_FP64_STRICT every operation in FP64 (one FP64 division per reconstruction). */
