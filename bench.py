@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--precision", choices=["fp64", "strict"], default="fp64",
                     help="context precision of --study vjp (NS3D_FP64 or NS3D_FP64_STRICT)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (Taylor-Green 64^3) measurement")
-    ap.add_argument("--study", choices=["fp32", "ensemble", "adjoint", "vjp", "big"], default=None,
+    ap.add_argument("--study", choices=["fp32", "ensemble", "adjoint", "vjp", "big", "oracle"], default=None,
                     help="fp32: FP64 vs FP32-bulk over --steps steps at --n^3 (KE/enstrophy every step); "
                          "ensemble: 48 uneven realisations, --steps steps per schedule")
     return ap.parse_args()
@@ -242,6 +242,46 @@ def cpu_oracle_sample(u0, mu, n, dt, full_step: bool):
         what = f"one RHS of the {n}^3 state"
     el = time.perf_counter() - t0
     return pts / el / 1e9, el, O.get_threads() if O.has_openmp() else 1, what
+
+
+def run_study_oracle():
+    """Timing table of the CPU oracle as it stands (FP64 C, OpenMP over lines/points): one RHS and
+    one RK4 step of the isotropic-turbulence state at 32^3 .. 256^3 on one thread (256^3: the RHS
+    only) and on all host cores, the 32^3 Taylor-Green case (10 RK4 steps) end to end, and one
+    RHS at 512^3 on all cores.  CPU work only (the CPU baseline); the GPU is not used."""
+    from oracle import oracle as O
+    from paper_2211_16718_gb300 import inputs as I
+    O.build()
+    allc = os.cpu_count() or 1
+    rows = []
+
+    def timed(fn):
+        t0 = time.perf_counter()
+        fn()
+        return time.perf_counter() - t0
+
+    for n in (32, 64, 128, 256):
+        u0, mu = hit_state(n)
+        P = O.Params(n, n, n, mu_eff=mu)
+        for th in (1, allc):
+            O.set_threads(th)
+            t_rhs = timed(lambda: O.rhs(P, u0))
+            row = {"grid": n, "threads": O.get_threads() if O.has_openmp() else 1,
+                   "rhs_s": t_rhs, "rhs_gpts": n ** 3 / t_rhs / 1e9}
+            if th > 1 or n < 256:  # a single-threaded 256^3 RK4 step would take minutes
+                t_rk = timed(lambda: O.rk_step(P, u0, 1e-3, 1))
+                row.update({"rk4_step_s": t_rk, "rk4_gpts": n ** 3 * RK_STAGES / t_rk / 1e9})
+            rows.append(row)
+    O.set_threads(allc)
+    u = I.taylor_green(32)
+    P = O.Params(32, 32, 32, mu_eff=6.25e-5)
+    t_tgv = timed(lambda: O.rk_step(P, u, 0.089, 10))
+    u0, mu = hit_state(512)
+    P = O.Params(512, 512, 512, mu_eff=mu)
+    t_512 = timed(lambda: O.rhs(P, u0))
+    return {"study": "oracle", "host_cores": allc, "openmp": O.has_openmp(), "table": rows,
+            "taylor_green_32_10_rk4_steps_s": t_tgv,
+            "hit512_one_rhs_all_cores": {"s": t_512, "gpts": 512 ** 3 / t_512 / 1e9}}
 
 
 def run_reference(args, world, rank):
@@ -803,6 +843,9 @@ def main():
         return
     if args.study == "fp32":
         run_study_fp32(args, int(os.environ.get("LOCAL_RANK", "0")))
+        return
+    if args.study == "oracle":
+        print(json.dumps(run_study_oracle()), flush=True)
         return
     if args.study == "big":
         import torch
