@@ -45,9 +45,6 @@ DirArgs base_args(ns3d_ctx* c, const double* u) {
   a.c133_lo = (float)(c133 - (double)a.c133_hi);
   a.eps4_hi = (float)eps4;
   a.eps4_lo = (float)(eps4 - (double)a.eps4_hi);
-  const double sixth = 1.0 / 6.0;
-  a.sixth_hi = (float)sixth;
-  a.sixth_lo = (float)(sixth - (double)a.sixth_hi);
   const double gm1 = c->p.gamma - 1.0;
   a.gm1_hi = (float)gm1;
   a.gm1_lo = (float)(gm1 - (double)a.gm1_hi);

@@ -312,13 +312,11 @@ int rebuild(ns3d_batch* b) {
         a.status = b->d_status;
         a.mode = b->mode;
         a.variant = b->variant;
-        const double c133 = 13.0 / 3.0, eps4 = 4.0 * b->p[i].weno_eps, sixth = 1.0 / 6.0;
+        const double c133 = 13.0 / 3.0, eps4 = 4.0 * b->p[i].weno_eps;
         a.c133_hi = (float)c133;
         a.c133_lo = (float)(c133 - (double)a.c133_hi);
         a.eps4_hi = (float)eps4;
         a.eps4_lo = (float)(eps4 - (double)a.eps4_hi);
-        a.sixth_hi = (float)sixth;
-        a.sixth_lo = (float)(sixth - (double)a.sixth_hi);
         const double gm1 = in.gamma - 1.0, hd = b->p[i].harten_delta;
         a.gm1_hi = (float)gm1;
         a.gm1_lo = (float)(gm1 - (double)a.gm1_hi);

@@ -70,7 +70,6 @@ struct DirArgs {
   int variant;       // tile-shape variant of MODE 1 (see dir_tile_shape)
   float c133_hi, c133_lo;  // 13/3 as a double-float
   float eps4_hi, eps4_lo;  // 4 * weno_eps as a double-float
-  float sixth_hi, sixth_lo;  // 1/6 as a double-float
   float gm1_hi, gm1_lo;      // gamma - 1 as a double-float
   float hd_hi, hd_lo;        // Harten fraction as a double-float
 };
