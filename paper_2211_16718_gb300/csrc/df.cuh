@@ -77,6 +77,22 @@ __device__ __forceinline__ df df_add_pos_u(df x, df y) {
   return df{s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo))};
 }
 
+// Double-word addition when |x| >= c |y| is known with a margin c > 1 well above the
+// relative size of the lo parts (then |x.hi| >= |y.hi| and Fast2Sum on the hi parts is
+// exact).  Left unnormalised like df_mul_u; with the margin, x + y can cancel at most by
+// the factor c/(c-1), so |lo| stays within a few ulp(hi).
+__device__ __forceinline__ df df_add_ordered_u(df x, df y) {
+  const df s = fast_two_sum(x.hi, y.hi);
+  return df{s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo))};
+}
+
+// The same, renormalised (for sums that are squared next, where a larger |lo| would cost
+// accuracy).
+__device__ __forceinline__ df df_add_ordered(df x, df y) {
+  const df s = df_add_ordered_u(x, y);
+  return fast_two_sum(s.hi, s.lo);
+}
+
 __device__ __forceinline__ df df_neg(df x) { return df{-x.hi, -x.lo}; }
 
 __device__ __forceinline__ df df_mul(df x, df y) {

@@ -295,11 +295,13 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
         const df aa = df_add_pos_u(df_mul_u(s2, df{a.c133_hi, a.c133_lo}), df{a.eps4_hi, a.eps4_lo});
         const df u2 = df_add_fast(dgm, dgp);
         const df b2 = df_add_pos_u(df_sqr_u(u2), aa);
-        const df pq = df_add_pos_u(b2, df_twice(df_twice(s2)));
+        // Fast2Sum order with margins: b_2 >= aa >= (13/12) 4 s^2, and
+        // pq = u_2^2 + (4 + 13/3) s^2 + 4 eps >= 1.44 |4 u_2 s| (minimum over u_2)
+        const df pq = df_add_ordered_u(b2, df_twice(df_twice(s2)));
         const df r4 = df_twice(df_twice(df_mul_u(u2, ds)));
-        const df B1 = df_sqr_u(df_add_fast(pq, r4));
+        const df B1 = df_sqr_u(df_add_ordered(pq, r4));
         const df B2 = df_sqr_u(b2);
-        const df B3 = df_sqr_u(df_add_fast(pq, df_neg(r4)));
+        const df B3 = df_sqr_u(df_add_ordered(pq, df_neg(r4)));
         bw[(m * 3 + 0) * NW * W + o] = make_float2(B1.hi, B1.lo);
         bw[(m * 3 + 1) * NW * W + o] = make_float2(B2.hi, B2.lo);
         bw[(m * 3 + 2) * NW * W + o] = make_float2(B3.hi, B3.lo);
