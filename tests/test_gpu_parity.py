@@ -171,6 +171,38 @@ def test_stats_match_oracle(ns3d, orc):
             assert sg[k] == pytest.approx(v, rel=1e-12, abs=0), k
 
 
+STATS_CASES = [
+    ("ragged_37x29x23", lambda: I.random_smooth(37, 29, 23, seed=8, amp=0.1, mach=0.4, lx=3.0, ly=2.0, lz=1.5),
+     dict(lx=3.0, ly=2.0, lz=1.5)),
+    ("partial_tiles_40x12x20", lambda: I.random_smooth(40, 12, 20, seed=9, amp=0.1, mach=0.5), {}),
+    ("tiny_5x7x3", lambda: I.random_smooth(5, 7, 3, seed=10, amp=0.1), {}),
+    ("line_x_1x16x12", lambda: I.random_smooth(1, 16, 12, seed=11, amp=0.1), {}),
+    ("line_16x1x1", lambda: I.random_smooth(16, 1, 1, seed=12, amp=0.1), {}),
+    ("hit48", lambda: I.isotropic_turbulence(48, seed=3), {}),
+]
+
+
+@pytest.mark.parametrize("prec", list(PRECISIONS))
+@pytest.mark.parametrize("name,make,kw", STATS_CASES, ids=[c[0] for c in STATS_CASES])
+def test_stats_match_oracle_ragged(ns3d, orc, name, make, kw, prec):
+    """Statistics on grids that leave partial x-y tiles and z-chunks, and on one-point
+    dimensions, in both primitive layouts (NS3D_FP64 and the all-FP64 one)."""
+    u = make()
+    nz, ny, nx = u.shape[1:]
+    so = orc.stats(orc.Params(nx, ny, nz, **kw), u)
+    s = ns3d.Solver(nx, ny, nz, precision=PRECISIONS[prec], **kw)
+    sg = s.stats(_gpu(u))
+    assert sg["status"] == 0
+    for k, v in so.items():
+        if k.startswith("mom"):
+            assert abs(sg[k] - v) <= 1e-12 * so["mass"], (name, k)
+        elif k == "enstrophy" and abs(v) < 1e-300:
+            assert abs(sg[k]) <= 1e-30, (name, k)
+        else:
+            assert sg[k] == pytest.approx(v, rel=1e-12, abs=0), (name, k)
+    s.close()
+
+
 def test_stats_async_equals_stats(ns3d):
     import torch
     u = _gpu(I.taylor_green(16))
