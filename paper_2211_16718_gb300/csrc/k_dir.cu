@@ -14,16 +14,28 @@ namespace {
 template <int D, int MODE, int TP, int W>
 __global__ void __launch_bounds__(Plan<MODE, TP, W>::THREADS, Plan<MODE, TP, W>::MIN_CTAS) k_dir(const DirArgs a) {
   extern __shared__ double sm[];
-  dir_tile<D, MODE, TP, W>(a, sm, blockIdx.x, blockIdx.y, blockIdx.z);
+  if (D == 2)
+    dir_tile<D, MODE, TP, W>(a, sm, a.t0 + blockIdx.x, blockIdx.y, blockIdx.z);
+  else
+    dir_tile<D, MODE, TP, W>(a, sm, blockIdx.x, blockIdx.y, a.t0 + blockIdx.z);
 }
 
+// Tiles [lo, hi) along the range axis (hi < 0: all): blockIdx.x (tiles along the pencil) for
+// D = 2, blockIdx.z (planes z) for D = 0, 1.
 template <int D, int MODE, int TP, int W>
-cudaError_t launch_t(const DirArgs& a, cudaStream_t s) {
+cudaError_t launch_t(const DirArgs& a, cudaStream_t s, int lo = 0, int hi = -1) {
   using PL = Plan<MODE, TP, W>;
   constexpr int AX = (D == 0) ? 1 : 0;
   constexpr int BX = (D == 2) ? 1 : 2;
   dim3 grid((a.g.n[D] + TP - 1) / TP, (a.g.n[AX] + W - 1) / W, a.g.n[BX]);
-  k_dir<D, MODE, TP, W><<<grid, PL::THREADS, PL::BYTES, s>>>(a);
+  unsigned& ext = (D == 2) ? grid.x : grid.z;
+  if (hi < 0) hi = (int)ext;
+  if (lo < 0 || hi > (int)ext || lo > hi) return cudaErrorInvalidValue;
+  if (lo == hi) return cudaSuccess;
+  ext = (unsigned)(hi - lo);
+  DirArgs r = a;
+  r.t0 = lo;
+  k_dir<D, MODE, TP, W><<<grid, PL::THREADS, PL::BYTES, s>>>(r);
   return cudaGetLastError();
 }
 
@@ -47,11 +59,11 @@ cudaError_t set_attr() {
 }
 
 template <int MODE, int TP, int W>
-cudaError_t launch_dirs(int d, const DirArgs& a, cudaStream_t s) {
+cudaError_t launch_dirs(int d, const DirArgs& a, cudaStream_t s, int lo = 0, int hi = -1) {
   switch (d) {
-    case 0: return launch_t<0, MODE, TP, W>(a, s);
-    case 1: return launch_t<1, MODE, TP, W>(a, s);
-    default: return launch_t<2, MODE, TP, W>(a, s);
+    case 0: return launch_t<0, MODE, TP, W>(a, s, lo, hi);
+    case 1: return launch_t<1, MODE, TP, W>(a, s, lo, hi);
+    default: return launch_t<2, MODE, TP, W>(a, s, lo, hi);
   }
 }
 
@@ -88,11 +100,16 @@ void dir_tile_shape(int mode, int variant, int* tp, int* w) {
 
 cudaError_t launch_dir(int d, const DirArgs& a, cudaStream_t s) {
   if (a.mode == 2) return launch_dir32(d, a, s);
-  if (a.mode == 0) return launch_dirs<0, 32, 4>(d, a, s);
+  return launch_dir_range(d, a, s, 0, -1);
+}
+
+cudaError_t launch_dir_range(int d, const DirArgs& a, cudaStream_t s, int lo, int hi) {
+  if (a.mode == 2) return cudaErrorInvalidValue;
+  if (a.mode == 0) return launch_dirs<0, 32, 4>(d, a, s, lo, hi);
   switch (a.variant) {
-    case 1: return launch_dirs<1, 16, 4>(d, a, s);
-    case 2: return launch_dirs<1, 40, 2>(d, a, s);
-    default: return launch_dirs<1, 24, 4>(d, a, s);
+    case 1: return launch_dirs<1, 16, 4>(d, a, s, lo, hi);
+    case 2: return launch_dirs<1, 40, 2>(d, a, s, lo, hi);
+    default: return launch_dirs<1, 24, 4>(d, a, s, lo, hi);
   }
 }
 

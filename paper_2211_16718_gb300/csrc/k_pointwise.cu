@@ -26,9 +26,10 @@ int grid_for(long long n, int threads) {
 // Primitive variables of every point (body: prim_point; DF: the NS3D_FP64 layout).
 template <bool DF>
 __global__ void __launch_bounds__(PW_THREADS) k_prim(const double* __restrict__ u, double* __restrict__ pm,
-                                                     long long N, double gamma, int* __restrict__ status) {
+                                                     long long N, long long p0, long long p1, double gamma,
+                                                     int* __restrict__ status) {
   int bad = 0;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x)
+  for (long long p = p0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; p < p1; p += (long long)gridDim.x * blockDim.x)
     bad |= prim_point<DF>(u, pm, N, p, gamma);
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONPHYS);
 }
@@ -37,9 +38,9 @@ __global__ void __launch_bounds__(PW_THREADS) k_prim(const double* __restrict__ 
 // (NS3D_FP64_STRICT; body: visc_point_ijk).  The NS3D_FP64 form is k_visc_tiled below.
 __global__ void __launch_bounds__(PW_THREADS) k_visc(const double* __restrict__ pm, double* __restrict__ fv,
                                                      int nx, int ny, int nz, double r12hx, double r12hy,
-                                                     double r12hz, double mu, double kappa, int only_d) {
-  // one thread per point of a 32 x 8 block of an x-y plane; blockIdx.z = the plane
-  const int i = blockIdx.x * 32 + threadIdx.x % 32, j = blockIdx.y * 8 + threadIdx.x / 32, k = blockIdx.z;
+                                                     double r12hz, double mu, double kappa, int only_d, int z0) {
+  // one thread per point of a 32 x 8 block of an x-y plane; blockIdx.z = the plane (from z0)
+  const int i = blockIdx.x * 32 + threadIdx.x % 32, j = blockIdx.y * 8 + threadIdx.x / 32, k = z0 + blockIdx.z;
   if (i >= nx || j >= ny) return;
   const double r12[3] = {r12hx, r12hy, r12hz};
   visc_point_ijk(pm, fv, nx, ny, nz, i, j, k, r12, mu, kappa, only_d);
@@ -52,15 +53,16 @@ __global__ void __launch_bounds__(PW_THREADS) k_visc(const double* __restrict__ 
 // uses it (12 times).  The per-point arithmetic is that of visc_point_df_ijk: the same
 // conversions, the same gradient and flux operations, so the same bits.
 constexpr int VT_X = 32, VT_Y = 8, VT_HX = VT_X + 4, VT_HY = VT_Y + 4, VT_PLANE = VT_HX * VT_HY;
-constexpr int VT_RING = 5, VT_CZ = 16;
+constexpr int VT_RING = 5, VT_CZ = VISC_ZCHUNK;
 constexpr int VT_SMEM = VT_RING * 4 * VT_PLANE * (int)sizeof(float2);  // 69,120 bytes
 
 __global__ void __launch_bounds__(VT_X * VT_Y, 3) k_visc_tiled(const double* __restrict__ pm, double* __restrict__ fv,
-                                                                const Grid g, double mu, double kappa, int only_d) {
+                                                                const Grid g, double mu, double kappa, int only_d,
+                                                                int zc0) {
   extern __shared__ float2 ring[];  // [VT_RING][4][VT_HY][VT_HX]
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const long long N = g.N;
-  const int x0 = blockIdx.x * VT_X, y0 = blockIdx.y * VT_Y, z0 = blockIdx.z * VT_CZ;
+  const int x0 = blockIdx.x * VT_X, y0 = blockIdx.y * VT_Y, z0 = (zc0 + blockIdx.z) * VT_CZ;
   const int z1 = min(z0 + VT_CZ, nz);
   const int tid = threadIdx.x, tx = tid % VT_X, ty = tid / VT_X;
   const df r12[3] = {d2df_bits(g.r12h[0]), d2df_bits(g.r12h[1]), d2df_bits(g.r12h[2])};
@@ -413,22 +415,34 @@ __global__ void __launch_bounds__(ST_THREADS) k_stats_final(const double* __rest
 }  // namespace
 
 cudaError_t launch_prim(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s,
-                        int df) {
+                        int df, long long p0, long long p1) {
+  if (p1 < 0) p1 = g.N;
+  if (p0 < 0 || p1 > g.N || p0 >= p1) return p0 == p1 ? cudaSuccess : cudaErrorInvalidValue;
+  const int grid = grid_for(p1 - p0, PW_THREADS);
   if (df)
-    k_prim<true><<<grid_for(g.N, PW_THREADS), PW_THREADS, 0, s>>>(u, pm, g.N, gamma, status);
+    k_prim<true><<<grid, PW_THREADS, 0, s>>>(u, pm, g.N, p0, p1, gamma, status);
   else
-    k_prim<false><<<grid_for(g.N, PW_THREADS), PW_THREADS, 0, s>>>(u, pm, g.N, gamma, status);
+    k_prim<false><<<grid, PW_THREADS, 0, s>>>(u, pm, g.N, p0, p1, gamma, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_visc(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s,
-                        int only_d, int df) {
+                        int only_d, int df, int z0, int z1) {
   const double rx = g.r12h[0], ry = g.r12h[1], rz = g.r12h[2];
+  const int nz = g.n[2];
+  if (z1 < 0) z1 = nz;
+  if (z0 < 0 || z1 > nz || z0 > z1) return cudaErrorInvalidValue;
+  if (z0 == z1) return cudaSuccess;
   if (df) {
-    const dim3 grid((g.n[0] + VT_X - 1) / VT_X, (g.n[1] + VT_Y - 1) / VT_Y, (g.n[2] + VT_CZ - 1) / VT_CZ);
-    k_visc_tiled<<<grid, VT_X * VT_Y, VT_SMEM, s>>>(pm, fv, g, mu, kappa, only_d);
-  } else
-    k_visc<<<plane_grid(g), PW_THREADS, 0, s>>>(pm, fv, g.n[0], g.n[1], g.n[2], rx, ry, rz, mu, kappa, only_d);
+    if (z0 % VT_CZ != 0 || (z1 % VT_CZ != 0 && z1 != nz)) return cudaErrorInvalidValue;
+    const int zc0 = z0 / VT_CZ, zc1 = (z1 + VT_CZ - 1) / VT_CZ;
+    const dim3 grid((g.n[0] + VT_X - 1) / VT_X, (g.n[1] + VT_Y - 1) / VT_Y, zc1 - zc0);
+    k_visc_tiled<<<grid, VT_X * VT_Y, VT_SMEM, s>>>(pm, fv, g, mu, kappa, only_d, zc0);
+  } else {
+    dim3 grid = plane_grid(g);
+    grid.z = z1 - z0;
+    k_visc<<<grid, PW_THREADS, 0, s>>>(pm, fv, g.n[0], g.n[1], nz, rx, ry, rz, mu, kappa, only_d, z0);
+  }
   return cudaGetLastError();
 }
 

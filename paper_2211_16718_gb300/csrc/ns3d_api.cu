@@ -40,6 +40,7 @@ DirArgs base_args(ns3d_ctx* c, const double* u) {
   a.status = c->status;
   a.mode = (c->p.precision == NS3D_FP64_STRICT) ? 0 : (c->p.precision == NS3D_FP32_BULK) ? 2 : 1;
   a.variant = c->variant;
+  a.t0 = 0;
   const double c133 = 13.0 / 3.0, eps4 = 4.0 * c->p.weno_eps;
   a.c133_hi = (float)c133;
   a.c133_lo = (float)(c133 - (double)a.c133_hi);
@@ -66,37 +67,86 @@ namespace ns3d {
 
 // One full right-hand-side evaluation of state u: primitives, viscous fluxes,
 // x and y passes accumulating into k, z pass with the given epilogue.
-int rhs_pass(ns3d_ctx* c, const double* u, int epi, double* out, const double* un, double coef) {
+int rhs_pass(ns3d_ctx* c, const double* u, int epi, double* out, const double* un, double coef,
+             const SlabPipe* pin, const SlabPipe* pout) {
   const bool f32 = (c->p.precision == NS3D_FP32_BULK);
   const int df = (c->p.precision == NS3D_FP64) ? 1 : 0;
-  int rc = timed(c, NS3D_K_PRIM, [&] {
-    return f32 ? launch_prim32(c->g, u, c->pm, c->p.gamma, c->status, c->stream)
-               : launch_prim(c->g, u, c->pm, c->p.gamma, c->status, c->stream, df);
-  }, "primitive kernel");
-  if (rc) return rc;
+  const Grid& g = c->g;
+  const long long plane = (long long)g.n[0] * g.n[1];
+  auto prim = [&](int z0, int z1) {
+    return timed(c, NS3D_K_PRIM, [&] {
+      return f32 ? launch_prim32(g, u, c->pm, c->p.gamma, c->status, c->stream)
+                 : launch_prim(g, u, c->pm, c->p.gamma, c->status, c->stream, df, z0 * plane, z1 * plane);
+    }, "primitive kernel");
+  };
   const bool visc = c->p.mu_eff > 0.0;
   const double kappa = visc ? c->p.mu_eff / ((c->p.gamma - 1.0) * c->p.prandtl) : 0.0;
-  // viscous fluxes of all directions (only_d < 0), or of direction only_d (lean storage)
-  auto visc_flux = [&](int only_d) {
+  // viscous fluxes of all directions (only_d < 0), or of direction only_d (lean storage), planes [z0, z1)
+  auto visc_flux = [&](int only_d, int z0, int z1) {
     return timed(c, NS3D_K_VISC, [&] {
-      return f32 ? launch_visc32(c->g, c->pm, c->fv, c->p.mu_eff, kappa, c->stream, only_d)
-                 : launch_visc(c->g, c->pm, c->fv, c->p.mu_eff, kappa, c->stream, only_d, df);
+      return f32 ? launch_visc32(g, c->pm, c->fv, c->p.mu_eff, kappa, c->stream, only_d)
+                 : launch_visc(g, c->pm, c->fv, c->p.mu_eff, kappa, c->stream, only_d, df, z0, z1);
     }, "viscous-flux kernel");
   };
-  if (visc && !c->lean && (rc = visc_flux(-1))) return rc;
   DirArgs a = base_args(c, u);
   static const int kid[3] = {NS3D_K_DIR_X, NS3D_K_DIR_Y, NS3D_K_DIR_Z};
   static const char* what[3] = {"x-direction kernel", "y-direction kernel", "z-direction kernel"};
-  for (int d = 0; d < 3; ++d) {
-    if (visc && c->lean && (rc = visc_flux(d))) return rc;
+  // direction pass d over the tiles [lo, hi) of its range axis (hi < 0: whole grid)
+  auto dir = [&](int d, int lo, int hi) {
     a.epi = (d == 0) ? EPI_ACC_WRITE : (d == 1) ? EPI_ACC_ADD : epi;
     if (d == 2) {
       a.out = out;
       a.un = un;
       a.a = coef;
     }
-    rc = timed(c, kid[d], [&] { return launch_dir(d, a, c->stream); }, what[d]);
-    if (rc) return rc;
+    return timed(c, kid[d], [&] {
+      return hi < 0 ? launch_dir(d, a, c->stream) : launch_dir_range(d, a, c->stream, lo, hi);
+    }, what[d]);
+  };
+  int rc;
+  if (pin) {
+    // slab j of u is usable after pin->ev[j].  The viscous stencil reaches 2 planes into the
+    // neighbouring slabs (periodically), so the viscous, x and y kernels of slab j run once the
+    // primitives of slabs j - 1 .. j + 1 exist: slabs 1 .. n-2 as the copies land, then n-1 and 0.
+    const int n = pin->n;
+    auto xy_slab = [&](int j) {
+      const int z0 = pin->lo[j], z1 = pin->lo[j + 1];
+      int r = (visc ? visc_flux(-1, z0, z1) : NS3D_OK);
+      if (!r) r = dir(0, z0, z1);
+      if (!r) r = dir(1, z0, z1);
+      return r;
+    };
+    for (int j = 0; j < n; ++j) {
+      const cudaError_t e = cudaStreamWaitEvent(c->stream, pin->ev[j], 0);
+      if (e != cudaSuccess) return cuda_fail(c, e, "wait for a state slab");
+      if ((rc = prim(pin->lo[j], pin->lo[j + 1]))) return rc;
+      if (j >= 2 && (rc = xy_slab(j - 1))) return rc;
+    }
+    if (n > 1 && (rc = xy_slab(n - 1))) return rc;
+    if ((rc = xy_slab(0))) return rc;
+  } else {
+    if ((rc = prim(0, g.n[2]))) return rc;
+    if (visc && !c->lean && (rc = visc_flux(-1, 0, -1))) return rc;
+    for (int d = 0; d < 2; ++d) {
+      if (visc && c->lean && (rc = visc_flux(d, 0, -1))) return rc;
+      if ((rc = dir(d, 0, -1))) return rc;
+    }
+  }
+  if (visc && c->lean && (rc = visc_flux(2, 0, -1))) return rc;
+  if (!pout) return dir(2, 0, -1);
+  // the z pass per slab of tiles; each slab of out is final after its launch and goes to the host
+  // on the copy stream while the next slabs compute
+  for (int j = 0; j < pout->n; ++j) {
+    if ((rc = dir(2, pout->lo[j], pout->lo[j + 1]))) return rc;
+    const int z0 = pout->lo[j] * pout->tp, z1 = min(pout->lo[j + 1] * pout->tp, g.n[2]);
+    cudaError_t e = cudaEventRecord(pout->ev[j], c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy_stream, pout->ev[j], 0);
+    for (int v = 0; v < 5 && e == cudaSuccess; ++v) {
+      const long long off = v * g.N + z0 * plane;
+      e = cudaMemcpyAsync(pout->host + off, out + off, sizeof(double) * (size_t)((z1 - z0) * plane),
+                          cudaMemcpyDeviceToHost, c->copy_stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy of a state slab");
   }
   return NS3D_OK;
 }
@@ -125,18 +175,18 @@ int ensure_stage_buffers(ns3d_ctx* c) {
   return NS3D_OK;
 }
 
-int rk_one_step(ns3d_ctx* c, double* u, double dt) {
+int rk_one_step(ns3d_ctx* c, double* u, double dt, const SlabPipe* pin, const SlabPipe* pout) {
   int rc = ensure_stage_buffers(c);
   if (rc) return rc;
   if (c->p.rk == NS3D_RK4) {
-    if ((rc = rhs_pass(c, u, EPI_RK4_FIRST, c->ua, u, 0.5 * dt))) return rc;
+    if ((rc = rhs_pass(c, u, EPI_RK4_FIRST, c->ua, u, 0.5 * dt, pin))) return rc;
     if ((rc = rhs_pass(c, c->ua, EPI_RK4_MID, c->ub, u, 0.5 * dt))) return rc;
     if ((rc = rhs_pass(c, c->ub, EPI_RK4_MID, c->ua, u, dt))) return rc;
-    return rhs_pass(c, c->ua, EPI_RK4_LAST, u, u, dt / 6.0);
+    return rhs_pass(c, c->ua, EPI_RK4_LAST, u, u, dt / 6.0, nullptr, pout);
   }
-  if ((rc = rhs_pass(c, u, EPI_SSP_1, c->ua, u, dt))) return rc;
+  if ((rc = rhs_pass(c, u, EPI_SSP_1, c->ua, u, dt, pin))) return rc;
   if ((rc = rhs_pass(c, c->ua, EPI_SSP_2, c->ub, u, dt))) return rc;
-  return rhs_pass(c, c->ub, EPI_SSP_3, u, u, dt);
+  return rhs_pass(c, c->ub, EPI_SSP_3, u, u, dt, nullptr, pout);
 }
 
 }  // namespace ns3d
@@ -300,6 +350,12 @@ void ns3d_free(ns3d_ctx* c) {
     cudaEventDestroy(t.e1);
   }
   for (auto e : c->pool) cudaEventDestroy(e);
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+  }
+  for (auto e : c->slab_ev)
+    if (e) cudaEventDestroy(e);
   cudaFree(c->pm);
   cudaFree(c->fv);
   cudaFree(c->k);
@@ -387,6 +443,34 @@ int ns3d_check(ns3d_ctx* c) {
   return NS3D_OK;
 }
 
+namespace {
+
+// Whether ns3d_step_host overlaps its copies with the kernels: the direction passes of
+// NS3D_FP64 / NS3D_FP64_STRICT with all viscous fluxes stored, on grids of at least four
+// viscous z chunks (smaller grids copy in well under a millisecond).
+bool slab_pipeline_ok(const ns3d_ctx* c, int nsteps) {
+  return nsteps >= 1 && !c->lean && c->p.precision != NS3D_FP32_BULK && c->g.n[2] >= 4 * VISC_ZCHUNK;
+}
+
+int ensure_copy_stream(ns3d_ctx* c) {
+  if (c->copy_stream) return NS3D_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+  for (int k = 0; k < 2 * ns3d_ctx::MAX_SLABS + 1 && e == cudaSuccess; ++k)
+    e = cudaEventCreateWithFlags(&c->slab_ev[k], cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copy stream");
+  return NS3D_OK;
+}
+
+// n slabs with boundaries at multiples of unit: lo[j] = unit * round(j * units / n), lo[n] = end
+// (units = end / unit, the last slab taking the remainder).
+void slab_bounds(SlabPipe& s, int n, int units, int unit, int end) {
+  s.n = n;
+  for (int j = 0; j < n; ++j) s.lo[j] = unit * (int)(((long long)j * units + n / 2) / n);
+  s.lo[n] = end;
+}
+
+}  // namespace
+
 int ns3d_step_host(ns3d_ctx* c, double* u_host, double dt, int nsteps, ns3d_stats_t* stats_host) {
   if (!c) return NS3D_EINVAL;
   if (!u_host) return set_err(c, NS3D_EINVAL, "null host state");
@@ -394,20 +478,67 @@ int ns3d_step_host(ns3d_ctx* c, double* u_host, double dt, int nsteps, ns3d_stat
   const size_t bytes = sizeof(double) * 5 * (size_t)c->g.N;
   if (!c->uhost_dev && !dev_alloc(c, (void**)&c->uhost_dev, bytes))
     return set_err(c, NS3D_ENOMEM, "device state for host stepping");
-  cudaError_t e = cudaMemcpyAsync(c->uhost_dev, u_host, bytes, cudaMemcpyHostToDevice, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
-  int rc = ns3d_rk_step(c, c->uhost_dev, dt, nsteps);
-  if (rc) return rc;
-  if (stats_host) {
-    rc = stats_pass(c, c->uhost_dev, c->stats_dev);
+  int rc = NS3D_OK;
+  cudaError_t e = cudaSuccess;
+  if (slab_pipeline_ok(c, nsteps)) {
+    // z-slabs in on the copy stream, the first stage's kernels following them slab by slab; the
+    // last stage's z pass per slab of tiles, each slab out on the copy stream behind it
+    if ((rc = ensure_copy_stream(c)) || (rc = ensure_stage_buffers(c))) return rc;
+    const Grid& g = c->g;
+    const long long plane = (long long)g.n[0] * g.n[1];
+    SlabPipe pin, pout;
+    const int chunks = g.n[2] / VISC_ZCHUNK;
+    slab_bounds(pin, min(chunks, (int)ns3d_ctx::MAX_SLABS), chunks, VISC_ZCHUNK, g.n[2]);
+    pin.ev = c->slab_ev;
+    int tp = 0, w = 0;
+    dir_tile_shape(c->p.precision == NS3D_FP64_STRICT ? 0 : 1, c->variant, &tp, &w);
+    const int ztiles = (g.n[2] + tp - 1) / tp;
+    slab_bounds(pout, min(ztiles, (int)ns3d_ctx::MAX_SLABS), ztiles, 1, ztiles);
+    pout.ev = c->slab_ev + ns3d_ctx::MAX_SLABS;
+    pout.host = u_host;
+    pout.tp = tp;
+    cudaEvent_t entry = c->slab_ev[2 * ns3d_ctx::MAX_SLABS];
+    e = cudaEventRecord(entry, c->stream);  // the copies follow the work already on the stream
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy_stream, entry, 0);
+    for (int j = 0; j < pin.n && e == cudaSuccess; ++j) {
+      const long long z0 = pin.lo[j], z1 = pin.lo[j + 1];
+      for (int v = 0; v < 5 && e == cudaSuccess; ++v) {
+        const long long off = v * g.N + z0 * plane;
+        e = cudaMemcpyAsync(c->uhost_dev + off, u_host + off, sizeof(double) * (size_t)((z1 - z0) * plane),
+                            cudaMemcpyHostToDevice, c->copy_stream);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(pin.ev[j], c->copy_stream);
+    }
+    if (e != cudaSuccess) rc = cuda_fail(c, e, "host-to-device copy of a state slab");
+    for (int s = 0; s < nsteps && !rc; ++s)
+      rc = rk_one_step(c, c->uhost_dev, dt, s == 0 ? &pin : nullptr, s == nsteps - 1 ? &pout : nullptr);
+    if (!rc && stats_host) rc = stats_pass(c, c->uhost_dev, c->stats_dev);
+    if (!rc && stats_host) {
+      e = cudaMemcpyAsync(c->stats_host, c->stats_dev, sizeof(double) * NS3D_STATS_NDOUBLE, cudaMemcpyDeviceToHost,
+                          c->stream);
+      if (e != cudaSuccess) rc = cuda_fail(c, e, "statistics copy");
+    }
+    // the host buffer is in use until both streams are done, also after a failure
+    const cudaError_t e1 = cudaStreamSynchronize(c->copy_stream);
+    const cudaError_t e2 = cudaStreamSynchronize(c->stream);
     if (rc) return rc;
-    e = cudaMemcpyAsync(c->stats_host, c->stats_dev, sizeof(double) * NS3D_STATS_NDOUBLE, cudaMemcpyDeviceToHost,
-                        c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "statistics copy");
+    if (e1 != cudaSuccess || e2 != cudaSuccess) return cuda_fail(c, e1 != cudaSuccess ? e1 : e2, "host stepping");
+  } else {
+    e = cudaMemcpyAsync(c->uhost_dev, u_host, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
+    rc = ns3d_rk_step(c, c->uhost_dev, dt, nsteps);
+    if (rc) return rc;
+    if (stats_host) {
+      rc = stats_pass(c, c->uhost_dev, c->stats_dev);
+      if (rc) return rc;
+      e = cudaMemcpyAsync(c->stats_host, c->stats_dev, sizeof(double) * NS3D_STATS_NDOUBLE, cudaMemcpyDeviceToHost,
+                          c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "statistics copy");
+    }
+    e = cudaMemcpyAsync(u_host, c->uhost_dev, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
   }
-  e = cudaMemcpyAsync(u_host, c->uhost_dev, bytes, cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
   if (stats_host) {
     fill_stats(c->stats_host, stats_host);
     if (stats_host->status) return set_err(c, stats_host->status, "%s", ns3d_strerror(stats_host->status));

@@ -29,6 +29,11 @@ struct ns3d_ctx {
   double* stats_dev = nullptr; // [NS3D_STATS_NDOUBLE]
   int* status = nullptr;       // sticky status word
   double* uhost_dev = nullptr; // device state for ns3d_step_host (lazy)
+  // ns3d_step_host: a stream for the host<->device copies of z-slabs, overlapped with the kernels,
+  // and the events that order them (lazy): [0, MAX) slabs in, [MAX, 2 MAX) slabs out, [2 MAX] entry
+  static constexpr int MAX_SLABS = 8;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t slab_ev[2 * MAX_SLABS + 1] = {};
   double* stats_host = nullptr;// pinned [NS3D_STATS_NDOUBLE]
   int nstat_blocks = 0;
   int variant = 0;             // tile-shape variant of the direction passes
@@ -111,12 +116,26 @@ inline bool dev_alloc(ns3d_ctx* c, void** p, size_t bytes) {
 
 // Allocate the Runge-Kutta stage states (and the RK4 accumulator) on first use (ns3d_api.cu).
 int ensure_stage_buffers(ns3d_ctx* c);
-// One right-hand-side evaluation of u with the given z-pass epilogue (ns3d_api.cu).
-int rhs_pass(ns3d_ctx* c, const double* u, int epi, double* out, const double* un, double coef);
+// z-slabs of a state moving between host and device while the kernels run (ns3d_step_host):
+// slab j is [lo[j], lo[j+1]) in planes (copies in) or in tiles of the z pass (copies out).
+struct SlabPipe {
+  int n = 0;
+  int lo[ns3d_ctx::MAX_SLABS + 1] = {};
+  cudaEvent_t* ev = nullptr;  // ev[j]: slab j is on the device (in) / final on the device (out)
+  double* host = nullptr;     // out: destination of the slabs ([5][N] like the device state)
+  int tp = 0;                 // out: points along z of a z-pass tile
+};
+// One right-hand-side evaluation of u with the given z-pass epilogue (ns3d_api.cu).  pin: u arrives
+// slab by slab (the primitive, viscous, x and y kernels run per slab after its event); pout: the z
+// pass runs per slab of tiles, each followed by the copy of that slab of out to pout->host on
+// c->copy_stream.
+int rhs_pass(ns3d_ctx* c, const double* u, int epi, double* out, const double* un, double coef,
+             const SlabPipe* pin = nullptr, const SlabPipe* pout = nullptr);
 // Statistics of u into out_dev[NS3D_STATS_NDOUBLE] (ns3d_api.cu).
 int stats_pass(ns3d_ctx* c, const double* u, double* out_dev);
-// One Runge-Kutta step of u in place (ns3d_api.cu).
-int rk_one_step(ns3d_ctx* c, double* u, double dt);
+// One Runge-Kutta step of u in place (ns3d_api.cu); pin / pout as for rhs_pass, applied to the
+// first / last stage.
+int rk_one_step(ns3d_ctx* c, double* u, double dt, const SlabPipe* pin = nullptr, const SlabPipe* pout = nullptr);
 // Release the adjoint and trajectory buffers (ns3d_adjoint.cu).
 void adjoint_free(ns3d_ctx* c);
 

@@ -68,6 +68,8 @@ struct DirArgs {
   int* status;
   int mode;          // 0: all FP64; 1: FP64 values, double-float weights/offsets; 2: FP32 bulk
   int variant;       // tile-shape variant of MODE 1 (see dir_tile_shape)
+  int t0;            // partial launches (launch_dir_range): index of the first tile row of the range
+                     // (planes for D = 0, 1; tiles along z for D = 2); 0 for whole-grid launches
   float c133_hi, c133_lo;  // 13/3 as a double-float
   float eps4_hi, eps4_lo;  // 4 * weno_eps as a double-float
   float gm1_hi, gm1_lo;      // gamma - 1 as a double-float
@@ -77,18 +79,25 @@ struct DirArgs {
 // Launchers (return cudaGetLastError() of the launch).
 // df: the NS3D_FP64 primitive layout (T, H and sqrt(rho) as double-float pairs, see
 // prim_point); the viscous, direction and statistics kernels of the same context read it.
+// [p0, p1): the points of a partial launch (p1 < 0: through N).
 cudaError_t launch_prim(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s,
-                        int df = 0);
+                        int df = 0, long long p0 = 0, long long p1 = -1);
 // only_d < 0: all three viscous flux vectors into fv[12][N]; only_d = d: the flux along d into fv[4][N];
 // df: the NS3D_FP64 form (double-float from the stencil values on; primitives from launch_prim(df=1))
+// [z0, z1): the planes of a partial launch (z1 < 0: through nz); with df, z0 and z1 (unless nz) must be
+// multiples of VISC_ZCHUNK, the z extent of one CTA of the tiled kernel.
+constexpr int VISC_ZCHUNK = 16;
 cudaError_t launch_visc(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s,
-                        int only_d = -1, int df = 0);
+                        int only_d = -1, int df = 0, int z0 = 0, int z1 = -1);
 // FP32-bulk variants (FP32 arithmetic, results widened to FP64)
 cudaError_t launch_prim32(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s);
 cudaError_t launch_visc32(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s,
                           int only_d = -1);
 cudaError_t prepare_dir_kernels();  // per device, before the first launch
 cudaError_t launch_dir(int d, const DirArgs& a, cudaStream_t s);  // dispatches on a.mode, a.variant
+// The tiles [lo, hi) of a direction pass along its range axis: planes z for d = 0, 1, tiles along z
+// (dir_tile_shape points each) for d = 2.  MODE 0 and 1 only.
+cudaError_t launch_dir_range(int d, const DirArgs& a, cudaStream_t s, int lo, int hi);
 void dir_tile_shape(int mode, int variant, int* tp, int* w);      // points x lines of a tile
 constexpr int DIR_VARIANTS = 3;                                   // tile variants of MODE 1
 cudaError_t prepare_dir32_kernels();
