@@ -179,7 +179,12 @@ int ns3d_stats_noalloc(const ns3d_params *p, const double *u_dev, double *out_de
 /* End-to-end call with host buffers: copies u_host to library-owned device
  * memory, advances nsteps steps of size dt, computes the statistics of the
  * final state into *stats_host (may be NULL), copies the state back into
- * u_host.  Synchronises. */
+ * u_host.  Synchronises.  On grids with nz >= 64 (FP64 modes, full viscous
+ * storage) the copies run in z-slabs on a library-owned second stream and
+ * overlap with the first and last RK stages; the result is bitwise that of
+ * ns3d_rk_step on a device copy of the state.  u_host should be pinned
+ * (page-locked) for the copies to overlap; it is in use until the call
+ * returns, also when it fails. */
 int ns3d_step_host(ns3d_ctx *ctx, double *u_host, double dt, int nsteps, ns3d_stats_t *stats_host);
 
 /* Read and clear the sticky status word (synchronises): NS3D_OK or NS3D_ENONPHYSICAL. */

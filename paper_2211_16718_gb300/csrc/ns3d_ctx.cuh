@@ -31,7 +31,7 @@ struct ns3d_ctx {
   double* uhost_dev = nullptr; // device state for ns3d_step_host (lazy)
   // ns3d_step_host: a stream for the host<->device copies of z-slabs, overlapped with the kernels,
   // and the events that order them (lazy): [0, MAX) slabs in, [MAX, 2 MAX) slabs out, [2 MAX] entry
-  static constexpr int MAX_SLABS = 8;
+  static constexpr int MAX_SLABS = 16;
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t slab_ev[2 * MAX_SLABS + 1] = {};
   double* stats_host = nullptr;// pinned [NS3D_STATS_NDOUBLE]
