@@ -683,6 +683,7 @@ def run_big(n: int, steps: int, cfl: float, n_sample: int = 24) -> dict:
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    s.timing_enable(True)
     clocks.start()
     e0.record(stream)
     for i in range(steps):
@@ -692,6 +693,8 @@ def run_big(n: int, steps: int, cfl: float, n_sample: int = 24) -> dict:
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
+    kt = s.timing_read()
+    s.timing_enable(False)
     st = stats_buf.cpu().numpy()
     st1 = s.stats(u)
     info1 = s.storage_info()
@@ -709,7 +712,8 @@ def run_big(n: int, steps: int, cfl: float, n_sample: int = 24) -> dict:
             "parity_rhs_sampled": parity, "conservation_drift": drift,
             "ke": [float(st0["ke"])] + [float(x) for x in st[:, 5]],
             "enstrophy": [float(st0["enstrophy"])] + [float(x) for x in st[:, 6]],
-            "status_ok": bool(np.all(st[:, 10] == 0)), "clocks": clk}
+            "status_ok": bool(np.all(st[:, 10] == 0)), "clocks": clk,
+            "kernel_ms_per_step": {k: v[0] / steps for k, v in kt.items() if v[1] > 0}}
 
 
 def run_study_fp32(args, local):

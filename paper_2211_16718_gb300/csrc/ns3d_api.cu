@@ -41,6 +41,7 @@ DirArgs base_args(ns3d_ctx* c, const double* u) {
   a.mode = (c->p.precision == NS3D_FP64_STRICT) ? 0 : (c->p.precision == NS3D_FP32_BULK) ? 2 : 1;
   a.variant = c->variant;
   a.t0 = 0;
+  a.zorder = (c->zorder >= 0) ? c->zorder : dir_zorder(c->g);
   const double c133 = 13.0 / 3.0, eps4 = 4.0 * c->p.weno_eps;
   a.c133_hi = (float)c133;
   a.c133_lo = (float)(c133 - (double)a.c133_hi);
@@ -572,6 +573,12 @@ int ns3d_timing_read(ns3d_ctx* c, double* ms_out, long long* launches_out, int n
     if (ms_out) ms_out[k] = c->ms[k];
     if (launches_out) launches_out[k] = c->launches[k];
   }
+  return NS3D_OK;
+}
+
+int ns3d_set_zorder(ns3d_ctx* c, int order) {
+  if (!c || order < -1 || order > 1) return NS3D_EINVAL;
+  c->zorder = order;
   return NS3D_OK;
 }
 

@@ -37,6 +37,7 @@ struct ns3d_ctx {
   double* stats_host = nullptr;// pinned [NS3D_STATS_NDOUBLE]
   int nstat_blocks = 0;
   int variant = 0;             // tile-shape variant of the direction passes
+  int zorder = -1;             // CTA order of the z pass (DirArgs::zorder); -1: dir_zorder by grid size
   int lean = 0;                // viscous fluxes one direction at a time ([4][N] instead of [12][N])
   size_t bytes = 0;            // library-owned device bytes
   // adjoint (allocated on first use): RK stage states, incoming adjoint copy,

@@ -70,6 +70,7 @@ struct DirArgs {
   int variant;       // tile-shape variant of MODE 1 (see dir_tile_shape)
   int t0;            // partial launches (launch_dir_range): index of the first tile row of the range
                      // (planes for D = 0, 1; tiles along z for D = 2); 0 for whole-grid launches
+  int zorder;        // z pass: 0 = consecutive CTAs walk the tiles along z, 1 = the line groups (dir_zorder)
   float c133_hi, c133_lo;  // 13/3 as a double-float
   float eps4_hi, eps4_lo;  // 4 * weno_eps as a double-float
   float gm1_hi, gm1_lo;      // gamma - 1 as a double-float
@@ -98,6 +99,8 @@ cudaError_t launch_dir(int d, const DirArgs& a, cudaStream_t s);  // dispatches 
 // The tiles [lo, hi) of a direction pass along its range axis: planes z for d = 0, 1, tiles along z
 // (dir_tile_shape points each) for d = 2.  MODE 0 and 1 only.
 cudaError_t launch_dir_range(int d, const DirArgs& a, cudaStream_t s, int lo, int hi);
+// CTA order of the z pass for grid g (DirArgs::zorder).
+int dir_zorder(const Grid& g);
 void dir_tile_shape(int mode, int variant, int* tp, int* w);      // points x lines of a tile
 constexpr int DIR_VARIANTS = 3;                                   // tile variants of MODE 1
 cudaError_t prepare_dir32_kernels();

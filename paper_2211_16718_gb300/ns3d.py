@@ -401,3 +401,9 @@ class Batch:
 def set_solver_variant(solver: Solver, v: int):
     rc = _batch_fn("ns3d_set_variant", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int])(solver._ctx, int(v))
     solver._check(rc)
+
+
+def set_solver_zorder(solver: Solver, order: int):
+    """CTA order of the z pass (ns3d_set_zorder): 0 tiles along z first, 1 line groups first, -1 by size."""
+    rc = _batch_fn("ns3d_set_zorder", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int])(solver._ctx, int(order))
+    solver._check(rc)

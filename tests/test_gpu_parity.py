@@ -251,6 +251,42 @@ def test_step_host_slab_pipeline_equals_device_path(ns3d, shape, prec, rk, mu, n
     s.close()
 
 
+@pytest.mark.parametrize("prec", list(PRECISIONS))
+def test_z_pass_cta_order_gives_same_bits(ns3d, prec):
+    """The two CTA orders of the z pass (tiles along z first, or line groups first as on
+    grids of 2^28 points and more) on a ragged grid: RHS, RK steps and the slab-overlapped
+    host stepping all bitwise equal."""
+    import torch
+    u0 = I.random_smooth(37, 29, 23, seed=41, amp=0.1, mach=0.4)
+    res = []
+    for order in (0, 1):
+        s = ns3d.Solver(37, 29, 23, mu_eff=2e-3, precision=PRECISIONS[prec])
+        ns3d.set_solver_zorder(s, order)
+        ud = _gpu(u0)
+        r = s.rhs(ud).cpu().numpy()
+        s.rk_step(ud, 0.004, 2)
+        res.append((r, ud.cpu().numpy()))
+        s.close()
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    u1 = I.random_smooth(24, 20, 72, seed=42, amp=0.1, mach=0.4)
+    outs = []
+    for order in (0, 1):
+        s = ns3d.Solver(24, 20, 72, mu_eff=1e-3, precision=PRECISIONS[prec])
+        ns3d.set_solver_zorder(s, order)
+        uh = torch.from_numpy(u1.copy()).pin_memory().numpy()
+        s.step_host(uh, 0.004, 1)
+        outs.append(uh.copy())
+        s.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_set_zorder_rejects_bad_order(ns3d):
+    s = ns3d.Solver(8, 8, 8)
+    with pytest.raises(ns3d.Ns3dError):
+        ns3d.set_solver_zorder(s, 2)
+    s.close()
+
+
 def test_nonphysical_state_is_reported_and_cleared(ns3d):
     u = I.random_smooth(16, 16, 16, seed=10, amp=0.1)
     u[0, 3, 4, 5] = -1.0
