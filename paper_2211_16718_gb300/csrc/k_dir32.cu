@@ -66,8 +66,9 @@ __global__ void __launch_bounds__(THREADS) k_dir32(const DirArgs a) {
   constexpr int AX = (D == 0) ? 1 : 0;
   const int na = a.g.n[AX];
   const long long N = a.g.N;
-  const int s0 = blockIdx.x * TP;
-  const int a0 = blockIdx.y * W;
+  const bool swap = (D == 2 && a.zorder);  // z pass with the line groups first (dir_zorder)
+  const int s0 = (swap ? blockIdx.y : blockIdx.x) * TP;
+  const int a0 = (swap ? blockIdx.x : blockIdx.y) * W;
   const int bz = blockIdx.z;
   const int tid = threadIdx.x;
 
@@ -281,6 +282,11 @@ cudaError_t launch32(const DirArgs& a, cudaStream_t s) {
   constexpr int AX = (D == 0) ? 1 : 0;
   constexpr int BX = (D == 2) ? 1 : 2;
   dim3 grid((a.g.n[D] + TP - 1) / TP, (a.g.n[AX] + W - 1) / W, a.g.n[BX]);
+  if (D == 2 && a.zorder) {
+    const unsigned t = grid.x;
+    grid.x = grid.y;
+    grid.y = t;
+  }
   k_dir32<D, TP, W><<<grid, THREADS, P32<TP, W>::BYTES, s>>>(a);
   return cudaGetLastError();
 }

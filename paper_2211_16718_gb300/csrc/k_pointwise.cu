@@ -101,14 +101,19 @@ __global__ void __launch_bounds__(VT_X * VT_Y, 3) k_visc_tiled(const double* __r
     if (x0 + tx < nx && y0 + ty < ny) {
       const int c = (ty + 2) * VT_HX + (tx + 2);
       const float2 *Zm2 = slot(z - 2), *Zm1 = slot(z - 1), *Z0 = slot(z), *Zp1 = slot(z + 1), *Zp2 = slot(z + 2);
+      // the flux along only_d (lean storage) needs 8 of the 12 gradients: d(u, v, w, T)/dx_d, the
+      // derivatives of the velocity component along only_d, and the diagonal (divergence)
       df G[4][3];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const float2* P = Z0 + q * VT_PLANE;
-        G[q][0] = d4_dfv(ld(P, c - 2), ld(P, c - 1), ld(P, c + 1), ld(P, c + 2), r12[0]);
-        G[q][1] = d4_dfv(ld(P, c - 2 * VT_HX), ld(P, c - VT_HX), ld(P, c + VT_HX), ld(P, c + 2 * VT_HX), r12[1]);
+        auto need = [&](int e) { return only_d < 0 || e == only_d || (q < 3 && (q == only_d || q == e)); };
+        const df zero{0.0f, 0.0f};
+        G[q][0] = need(0) ? d4_dfv(ld(P, c - 2), ld(P, c - 1), ld(P, c + 1), ld(P, c + 2), r12[0]) : zero;
+        G[q][1] = need(1) ? d4_dfv(ld(P, c - 2 * VT_HX), ld(P, c - VT_HX), ld(P, c + VT_HX), ld(P, c + 2 * VT_HX), r12[1])
+                          : zero;
         const int o = q * VT_PLANE + c;
-        G[q][2] = d4_dfv(ld(Zm2, o), ld(Zm1, o), ld(Zp1, o), ld(Zp2, o), r12[2]);
+        G[q][2] = need(2) ? d4_dfv(ld(Zm2, o), ld(Zm1, o), ld(Zp1, o), ld(Zp2, o), r12[2]) : zero;
       }
       const df vel[3] = {ld(Z0, c), ld(Z0 + VT_PLANE, c), ld(Z0 + 2 * VT_PLANE, c)};
       visc_fluxes_df(G, vel, mu, kappa, fv, N, flat3(x0 + tx, y0 + ty, z, nx, ny), only_d);

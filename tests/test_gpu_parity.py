@@ -280,6 +280,20 @@ def test_z_pass_cta_order_gives_same_bits(ns3d, prec):
     assert np.array_equal(outs[0], outs[1])
 
 
+def test_z_pass_cta_order_gives_same_bits_fp32_bulk(ns3d):
+    u0 = I.random_smooth(37, 29, 23, seed=43, amp=0.1, mach=0.4)
+    res = []
+    for order in (0, 1):
+        s = ns3d.Solver(37, 29, 23, mu_eff=2e-3, precision=ns3d.NS3D_FP32_BULK)
+        ns3d.set_solver_zorder(s, order)
+        ud = _gpu(u0)
+        r = s.rhs(ud).cpu().numpy()
+        s.rk_step(ud, 0.004, 2)
+        res.append((r, ud.cpu().numpy()))
+        s.close()
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
 def test_set_zorder_rejects_bad_order(ns3d):
     s = ns3d.Solver(8, 8, 8)
     with pytest.raises(ns3d.Ns3dError):
