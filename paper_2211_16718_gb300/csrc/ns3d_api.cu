@@ -455,10 +455,19 @@ bool slab_pipeline_ok(const ns3d_ctx* c, int nsteps) {
 
 int ensure_copy_stream(ns3d_ctx* c) {
   if (c->copy_stream) return NS3D_OK;
-  cudaError_t e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
   for (int k = 0; k < 2 * ns3d_ctx::MAX_SLABS + 1 && e == cudaSuccess; ++k)
     e = cudaEventCreateWithFlags(&c->slab_ev[k], cudaEventDisableTiming);
-  if (e != cudaSuccess) return cuda_fail(c, e, "copy stream");
+  if (e != cudaSuccess) {  // leave nothing half made: the next call starts over
+    for (auto& ev : c->slab_ev) {
+      if (ev) cudaEventDestroy(ev);
+      ev = nullptr;
+    }
+    if (s) cudaStreamDestroy(s);
+    return cuda_fail(c, e, "copy stream");
+  }
+  c->copy_stream = s;
   return NS3D_OK;
 }
 

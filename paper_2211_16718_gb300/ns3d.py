@@ -182,7 +182,9 @@ class Solver:
         return out
 
     def step_host(self, u_host, dt: float, nsteps: int = 1) -> dict:
-        """End to end with a host numpy array (float64, C-contiguous, 5*N): copied in, stepped, copied back."""
+        """End to end with a host numpy array (float64, C-contiguous, 5*N): copied in, stepped, copied back.
+        On grids with nz >= 64 the copies overlap with the first and last RK stages (in z-slabs) when
+        u_host is pinned, e.g. torch.empty(..., pin_memory=True).numpy()."""
         import numpy as np
         if not (isinstance(u_host, np.ndarray) and u_host.dtype == np.float64 and u_host.flags.c_contiguous
                 and u_host.size == 5 * self.N):
