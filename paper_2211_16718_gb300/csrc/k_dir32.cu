@@ -99,12 +99,13 @@ __global__ void __launch_bounds__(THREADS) k_dir32(const DirArgs a) {
     r[2 * NP * W + s] = vy;
     r[3 * NP * W + s] = vz;
     r[4 * NP * W + s] = d2f_rn(__ldg(a.pm + PM_H * N + p));
-    if (a.fv != nullptr) {
+    if (a.fv != nullptr) {  // FP64 as stored, first read in phase E: copied asynchronously
       double* f = smd + OFF_FV / 2;
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) f[cc * NP * W + s] = __ldg(a.fv + (long long)(a.fv_dstride * D + cc) * N + p);
+      for (int cc = 0; cc < 4; ++cc) cp_async8(f + cc * NP * W + s, a.fv + (long long)(a.fv_dstride * D + cc) * N + p);
     }
   }
+  cp_async_commit();
   __syncthreads();
 
   // ---- B: squared scaled smoothness indicators (FP32) --------------------------
@@ -159,6 +160,7 @@ __global__ void __launch_bounds__(THREADS) k_dir32(const DirArgs a) {
       rec[(2 * m + 1) * NI * W + o] = vR;
     }
   }
+  cp_async_wait_all();  // this thread's viscous-flux copies; the barrier publishes them
   __syncthreads();
 
   // ---- epilogue operands: fetched asynchronously into the (now unused) indicator space
