@@ -76,6 +76,9 @@ def test_null_arguments(lib):
     assert lib.ns3d_functional(None, None, 0, None, None) == ns3d.NS3D_EINVAL
     assert lib.ns3d_traj_forward(None, None, 0.1, 1, 1) == ns3d.NS3D_EINVAL
     assert lib.ns3d_traj_vjp(None, None) == ns3d.NS3D_EINVAL
+    assert lib.ns3d_step_host(None, None, 0.1, 1, None) == ns3d.NS3D_EINVAL
+    assert lib.ns3d_set_zorder(None, 0) == ns3d.NS3D_EINVAL
+    assert lib.ns3d_set_variant(None, 0) == ns3d.NS3D_EINVAL
     lib.ns3d_free(None)
 
 
