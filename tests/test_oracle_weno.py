@@ -186,3 +186,20 @@ def test_right_biased_is_mirror_of_left(oracle):
     for i in range(n):
         j = (n - 2 - i) % n
         assert qL[i] == rR[j] and qR[i] == rL[j]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_weight_exponent_acts_on_eps_plus_beta(oracle, seed):
+    """Reading of Sec. 2.2's nonlinear weights: alpha_k = c_k / (eps + beta_k)^p.  Whatever the
+    indicators are, the ratio (omega_j / omega_k) / (c_j / c_k) = ((eps + beta_k) / (eps + beta_j))^p,
+    so the p = 2 ratio is the square and the p = 3 ratio the cube of the p = 1 ratio.  A
+    misplaced exponent (eps + beta_k^p) or a dropped one breaks these relations."""
+    rng = np.random.default_rng(seed)
+    c = np.array([0.1, 0.6, 0.3])
+    for _ in range(20):
+        q = rng.normal(size=5) * rng.uniform(1e-2, 1.0)
+        w = {p: oracle.weno5_weights(q, eps=1e-6, p=p) for p in (1, 2, 3)}
+        for j, k in ((0, 1), (2, 1), (0, 2)):
+            r = {p: (w[p][j] / w[p][k]) / (c[j] / c[k]) for p in (1, 2, 3)}
+            assert r[2] == pytest.approx(r[1] ** 2, rel=1e-12)
+            assert r[3] == pytest.approx(r[1] ** 3, rel=1e-12)
