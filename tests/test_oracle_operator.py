@@ -227,6 +227,23 @@ def test_tgv_statistics_closed_forms(oracle):
     assert st["p_min"] == pytest.approx(1 / GAMMA - 3 * v0 * v0 / 8, rel=1e-13)
 
 
+def test_tgv_isothermal_extremes_and_wave_speed(oracle):
+    """Isothermal Taylor-Green (rho = gamma p, so p/rho = 1/gamma and c = 1 at every point) on
+    a grid holding x, y = pi/2 and z = 0: p_min = 1/gamma - 3 V0^2/8 where
+    (cos 2x + cos 2y)(cos 2z + 2) = -6, rho_min = gamma p_min at the same point, the largest
+    (|u_d| + c)/dx_d is (V0 + 1)/h (|u| = V0 at x = pi/2, y = z = 0), and the total mass is the
+    box volume (the cosines sum to zero over the grid)."""
+    n, v0 = 16, 0.1
+    u = I.taylor_green(n, v0=v0, isothermal=True)
+    st = oracle.stats(_P(oracle, n, n, n), u)
+    h = 2 * math.pi / n
+    pmin = 1 / GAMMA - 3 * v0 * v0 / 8
+    assert st["p_min"] == pytest.approx(pmin, rel=1e-13)
+    assert st["rho_min"] == pytest.approx(GAMMA * pmin, rel=1e-13)
+    assert st["max_wavespeed_over_dx"] == pytest.approx((v0 + 1) / h, rel=1e-13)
+    assert st["mass"] == pytest.approx((2 * math.pi) ** 3, rel=1e-13)
+
+
 def test_uniform_state_wave_speed(oracle):
     u = I.uniform(8, 6, 4, rho=2.0, u=0.3, v=-0.5, w=0.1, p=0.7)
     P = _P(oracle, 8, 6, 4, lx=1.0, ly=2.0, lz=3.0)
