@@ -225,3 +225,33 @@ def test_roe_average_of_reconstructed_states_keeps_free_stream_and_conservation(
     scale = np.abs(R).max()
     for m in range(5):
         assert abs(R[m].sum()) <= 1e-13 * scale * R[m].size
+
+
+def test_roe_average_of_the_two_grid_points_satisfies_the_roe_property(oracle):
+    """The reading taken for Sec. 2.2's Roe average: the grid points i, i+1 on either side of the
+    interface.  Pin: with linear weights and a stencil U_j = U_a + phi_j dU (every component
+    varying along one state-space direction), each reconstruction is U_a + phi^ dU, so the jump
+    u^R - u^L = kappa (U_{i+1} - U_i) with kappa = (phi^R - phi^L)/(phi_{i+1} - phi_i).  Roe's
+    property for the pair (U_i, U_{i+1}) then makes the supersonic (|A| = A) interface flux
+    exactly (f^L + f^R)/2 - kappa (f(U_{i+1}) - f(U_i))/2, with f^L, f^R the reconstructions of
+    the point fluxes.  Another pair of states for the average breaks the identity."""
+    from oracle.oracle import Params
+    rng = np.random.default_rng(29)
+    P = Params(8, 8, 8, weno_linear=1, harten_delta=0.0)
+    for d in range(3):
+        for _ in range(5):
+            rho, p = rng.uniform(0.8, 1.2), rng.uniform(0.6, 0.9)
+            vel = rng.uniform(-0.1, 0.1, size=3)
+            vel[d] += 2.5 * np.sqrt(GAMMA * p / rho)  # Mach ~2.5 along d
+            Ua = _state(rho, *vel, p)
+            dU = _state(1.0, *rng.uniform(-0.5, 0.5, size=3), 1.0) * rng.uniform(-0.05, 0.05, size=5)
+            phi = rng.uniform(-1.0, 1.0, size=6)
+            phi[3] = phi[2] + rng.uniform(0.3, 0.8)  # a well-conditioned kappa
+            us = np.array([Ua + phi[j] * dU for j in range(6)])
+            fl = np.array([oracle.flux(s, d) for s in us])
+            fL = np.array([oracle.weno5(fl[0:5, m], linear=True) for m in range(5)])
+            fR = np.array([oracle.weno5(fl[5:0:-1, m], linear=True) for m in range(5)])
+            kappa = (oracle.weno5(phi[5:0:-1], linear=True) - oracle.weno5(phi[0:5], linear=True)) / (phi[3] - phi[2])
+            expect = 0.5 * (fL + fR) - 0.5 * kappa * (oracle.flux(us[3], d) - oracle.flux(us[2], d))
+            F = oracle.interface_flux(P, d, us)
+            np.testing.assert_allclose(F, expect, rtol=1e-11, atol=1e-11 * np.abs(expect).max())
