@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Benchmark of the compressible Navier-Stokes RHS + RK4 hot path on GB300.
 
-Workload: decaying isotropic turbulence on a 256^3 triply periodic grid (FP64,
+Workload: decaying isotropic turbulence on a 512^3 triply periodic grid (FP64,
 rho = 1, p = 1/gamma, u0 = 0.3, k0 = 4, mu_eff for Re_lambda = 50, dt at CFL 0.4),
 one step = one classical RK4 step (4 right-hand-side evaluations) plus the
 statistics (kinetic energy, enstrophy, conservation sums, CFL) of the new state,
@@ -10,9 +10,14 @@ second (Gpts/s) = points * 4 * steps / time, summed over ranks.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the FP64 CPU oracle on the host cores (one RHS of the
-same 256^3 state per step).  Multi-GPU: independent replicas, one per rank
-(no collective on the data path), barrier + max-over-ranks timing.
+The same line carries the comparison modes: the all-FP64 form, FP32-bulk over 100
+steps from the same state (speed and error against FP64), the adjoint (Taylor-Green
+64^3 gradient), the 48-instance ensemble (50 steps per schedule) and 1024^3 with
+SSP-RK3 on one GPU.
+
+--impl reference times the FP64 CPU oracle on the host cores (per step, the RHS of a
+periodic 72-plane z-slab of the same 512^3 state).  Multi-GPU: independent replicas,
+one per rank (no collective on the data path), barrier + max-over-ranks timing.
 """
 from __future__ import annotations
 
@@ -58,9 +63,17 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=256, help="grid points per direction")
+    ap.add_argument("--n", type=int, default=512, help="grid points per direction")
     ap.add_argument("--cfl", type=float, default=0.4)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--compare-steps", type=int, default=100,
+                    help="steps of the FP64 vs FP32-bulk comparison (from the same state and dt)")
+    ap.add_argument("--parity-points", type=int, default=64,
+                    help="sampled points of the headline's RHS checked against the oracle")
+    ap.add_argument("--ens-steps", type=int, default=50, help="steps per schedule of the 48-instance ensemble")
+    ap.add_argument("--big", type=int, default=1024, help="grid of the SSP-RK3 single-GPU run (0: skip)")
+    ap.add_argument("--big-steps", type=int, default=3)
+    ap.add_argument("--big-points", type=int, default=512, help="sampled oracle windows of the big run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-strict", action="store_true", help="skip the all-FP64 comparison run")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk comparison run")
@@ -209,9 +222,25 @@ def ncu_issue_per_point(kernel: str, sha: str):
     return None
 
 
+def measured_peaks() -> dict:
+    """HBM copy bandwidth of this GPU pool (MEASURED_PEAKS.json, written by the driver of the
+    measurement runs), else the fallback figure of one earlier GB300 measurement."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured (MEASURED_PEAKS.json: STREAM-style copy)"}
+    except (OSError, ValueError, KeyError):
+        return {"hbm_gbs": 6800.0, "source": "fallback (6.8 TB/s, one earlier GB300 copy measurement)"}
+
+
 def hit_state(n: int):
+    """Host state of the decaying-turbulence problem (hit_velocity(n, seed 0)), for the
+    CPU-side studies and the small adjoint kernel comparison."""
     from paper_2211_16718_gb300 import inputs as I
     return I.isotropic_turbulence(n, seed=0), I.hit_mu_eff()
+
+
+HIT_NBASE = 64  # base grid of the device-built turbulence field (spectral interpolant, exact up to ~1e-52)
 
 
 def workload_config(n: int, cfl: float, mu: float, dt: float) -> dict:
@@ -219,8 +248,10 @@ def workload_config(n: int, cfl: float, mu: float, dt: float) -> dict:
             "grid": [n, n, n], "domain": "[0,2pi)^3 periodic", "integrator": "classical RK4",
             "rhs_per_step": RK_STAGES, "u0": 0.3, "k0": 4, "re_lambda": 50, "mu_eff": mu, "cfl": cfl,
             "dt": dt, "seed": 0,
+            "initial_field": f"rho = 1, p = 1/gamma, velocity hit_velocity({HIT_NBASE}, seed 0) spectrally "
+                             f"interpolated to {n}^3 (E(k) ~ k^4 exp(-2 (k/k0)^2), all shells < {HIT_NBASE // 2})",
             "l2": f"inputs larger than L2: state {5 * n ** 3 * 8 / 1e6:.0f} MB, working set "
-                  f"{(5 * 4 + 7 + 12) * n ** 3 * 8 / 1e9:.2f} GB vs 129 MB L2",
+                  f"{(5 * 4 + 7 + 12) * n ** 3 * 8 / 1e9:.2f} GB vs 129 MB L2; L2 flushed before the timed region",
             "parallelism": "replicas (one independent grid per GPU)"}
 
 
@@ -284,26 +315,59 @@ def run_study_oracle():
             "hit512_one_rhs_all_cores": {"s": t_512, "gpts": 512 ** 3 / t_512 / 1e9}}
 
 
+REF_SLAB = 64     # planes of the workload per reference step ...
+REF_HALO = 4      # ... plus the 4-plane reach of the stencil on each side (WENO5 3, viscous composite 4)
+
+
 def run_reference(args, world, rank):
+    """The oracle as it stands on the host cores, on a bounded sample of the workload per step:
+    the right-hand side of a periodic slab of REF_SLAB + 2 REF_HALO z-planes of the n^3 state
+    (every x-y plane of the slab is a full n x n plane of the workload; the inner REF_SLAB planes
+    equal the n^3 RHS exactly, since the stencil reaches 4 planes).  value = points evaluated
+    (all planes of the slab) / time."""
     if rank != 0:
         return
-    u0, mu = hit_state(args.n)
-    dt = 0.0025
+    from oracle import oracle as O
+    from paper_2211_16718_gb300 import inputs as I
+    n = args.n
+    mu = I.hit_mu_eff()
+    nzs = min(n, REF_SLAB + 2 * REF_HALO)
+    slab = I.isotropic_turbulence_planes(n, seed=0, z0=n // 2 - nzs // 2, count=nzs, nbase=min(HIT_NBASE, n))
+    O.build()
+    O.set_threads(os.cpu_count() or 1)
+    h = 2 * math.pi / n
+    P = O.Params(n, n, nzs, lx=2 * math.pi, ly=2 * math.pi, lz=nzs * h, mu_eff=mu)
     times = []
     for s in range(args.warmup + args.steps):
-        g, el, cores, what = cpu_oracle_sample(u0, mu, args.n, dt, full_step=False)
+        t0 = time.perf_counter()
+        O.rhs(P, slab)
+        el = time.perf_counter() - t0
         if s >= args.warmup:
             times.append(el)
     tot = sum(times)
-    value = args.n ** 3 * len(times) / tot / 1e9
+    pts = n * n * nzs
+    value = pts * len(times) / tot / 1e9
+    cores = O.get_threads() if O.has_openmp() else 1
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / len(times) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args.n, args.cfl, mu, dt),
+            "data": "synthetic", "config": workload_config(n, args.cfl, mu, None),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"per step: {what} (plain FP64 C oracle, OpenMP over lines/points)"},
+                             "sample": f"per step: one RHS of a {n}x{n}x{nzs} periodic z-slab of the {n}^3 state "
+                                       f"(plain FP64 C oracle, OpenMP over lines/points; {pts} points per step)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _guard(name: str, fn):
+    """Run one comparison mode; a failure is recorded in the line instead of ending the run."""
+    try:
+        return fn()
+    except Exception as e:  # noqa: BLE001 - reported, not hidden
+        import torch
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        return {"error": f"{type(e).__name__}: {e}"[:400], "mode": name}
 
 
 def run_ours(args, world, rank, local):
@@ -313,23 +377,35 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     from paper_2211_16718_gb300 import build as B
     B.build()
+    from paper_2211_16718_gb300 import inputs as I
     from paper_2211_16718_gb300 import ns3d
 
     n = args.n
-    u0, mu = hit_state(n)
+    N = n ** 3
+    mu = I.hit_mu_eff()
+    u0_dev = I.isotropic_turbulence_device(n, seed=0, nbase=min(HIT_NBASE, n))
+    torch.cuda.synchronize()
     K, W = args.steps, args.warmup
+    n_cmp = max(args.compare_steps, W + K)  # steps of the FP64 / FP32-bulk comparison (config: 100)
     stream = torch.cuda.current_stream()
+    peaks = measured_peaks()
+    HBM = peaks["hbm_gbs"]
+    solver0 = ns3d.Solver(n, n, n, mu_eff=mu)
+    dt = solver0.dt_from_cfl(u0_dev, args.cfl)
+    solver0.close()
 
-    def timed_loop(precision: int, K: int, W: int, sample_clocks: bool):
-        """W untimed + K timed steps (RK4 step + statistics into a device log)."""
+    def timed_loop(precision: int, K: int, W: int, sample_clocks: bool, total: int):
+        """W untimed + K timed steps (RK4 step + statistics into a device log), then untimed steps
+        up to `total` (statistics logged every step), all from the same initial state and dt."""
         solver = ns3d.Solver(n, n, n, mu_eff=mu, precision=precision)
-        ud = torch.from_numpy(u0.copy()).cuda()
-        dt = solver.dt_from_cfl(ud, args.cfl)
-        stats_buf = torch.zeros((W + K, ns3d.NS3D_STATS_NDOUBLE), dtype=torch.float64, device="cuda")
+        ud = u0_dev.clone()
+        total = max(total, W + K)
+        stats_buf = torch.zeros((total + 1, ns3d.NS3D_STATS_NDOUBLE), dtype=torch.float64, device="cuda")
+        solver.stats_async(ud, stats_buf[0])
 
         def step(i):
             solver.rk_step(ud, dt, 1)
-            solver.stats_async(ud, stats_buf[i])
+            solver.stats_async(ud, stats_buf[i + 1])
 
         for i in range(W):
             step(i)
@@ -356,12 +432,15 @@ def run_ours(args, world, rank, local):
         ms = max_over_ranks(e0.elapsed_time(e1), world)
         ktimes = solver.timing_read()
         solver.timing_enable(False)
+        for i in range(W + K, total):
+            step(i)
+        torch.cuda.synchronize()
         st = stats_buf.cpu().numpy()
-        return solver, ud, dt, ms, ktimes, st, clk
+        return solver, ud, ms, ktimes, st, clk
 
     # headline: NS3D_FP64 (FP64 values, double-float WENO weights)
-    solver, ud, dt, ms, ktimes, st, clk = timed_loop(ns3d.NS3D_FP64, K, W, True)
-    pts_total = sum_over_ranks(float(n ** 3 * RK_STAGES * K), world)
+    solver, ud, ms, ktimes, st, clk = timed_loop(ns3d.NS3D_FP64, K, W, True, n_cmp)
+    pts_total = sum_over_ranks(float(N * RK_STAGES * K), world)
     value = pts_total / (ms * 1e-3) / 1e9
     status_ok = bool(np.all(st[:, 10] == 0))
     launches = int(sum(c for _, c in ktimes.values()))
@@ -372,7 +451,7 @@ def run_ours(args, world, rank, local):
         dir_launches = sum(kt[k][1] for k in ("dir_x", "dir_y", "dir_z"))
         avg_launch_s = dir_ms / dir_launches * 1e-3
         ops_pt = ops_dir + OPS_RK_EPI / 3.0
-        achieved = ops_pt * n ** 3 / avg_launch_s / 1e12
+        achieved = ops_pt * N / avg_launch_s / 1e12
         step_ms_total = sum(v[0] for v in kt.values())
         return {"bound": "alu", "kernel": f"k_dir ({form}: fused WENO5 + Roe + difference + viscous divergence)",
                 "achieved": achieved, "peak": FP64_LANEOPS_PEAK_T,
@@ -381,11 +460,7 @@ def run_ours(args, world, rank, local):
                 "peak_source": "152 SMs x 2 FP64 lanes/clk x 2070 MHz (unit counts, max clock; "
                                "ns3d_alu_probe measures 626 G DFMA lane-ops/s)",
                 "fp64_ops_per_point": ops_pt, "avg_launch_ms": avg_launch_s * 1e3,
-                "method_fp64_flops_per_point": FLOPS_DIR + 5,
-                "method_equiv_tflops": (FLOPS_DIR + 5) * n ** 3 / avg_launch_s / 1e12,
-                "share_of_device_time": dir_ms / step_ms_total if step_ms_total > 0 else None,
-                "algorithmic_bytes_per_point": 8 * (5 + 6 + 4 + 5 + 5),
-                "hbm_gbs_algorithmic": 8 * (5 + 6 + 4 + 5 + 5) * n ** 3 / avg_launch_s / 1e9}
+                "share_of_device_time": dir_ms / step_ms_total if step_ms_total > 0 else None}
 
     fp64_view = roofline_of(ktimes, OPS_DIR_FP64, "NS3D_FP64")
     avg_launch_s = fp64_view["avg_launch_ms"] * 1e-3
@@ -397,7 +472,7 @@ def run_ours(args, world, rank, local):
         # is the issue rate (warp instructions of this formulation per point, from the ncu
         # capture tied to the kernel source hash, x points per launch / live launch time).
         ipp, src, grid = iss
-        ach = ipp * n ** 3 / avg_launch_s / 1e9
+        ach = ipp * N / avg_launch_s / 1e9
         roofline = {"bound": "alu", "resource": "instruction issue",
                     "kernel": fp64_view["kernel"], "achieved": ach, "peak": ISSUE_PEAK_G,
                     "unit": "G warp instructions/s", "frac": ach / ISSUE_PEAK_G, "traffic": None,
@@ -408,83 +483,96 @@ def run_ours(args, world, rank, local):
     else:
         roofline = dict(fp64_view)
         roofline["resource"] = "FP64 pipe (issue view unavailable: kernel sources changed since the ncu capture)"
-    for k in ("avg_launch_ms", "method_fp64_flops_per_point", "method_equiv_tflops", "share_of_device_time",
-              "algorithmic_bytes_per_point", "hbm_gbs_algorithmic"):
+    for k in ("avg_launch_ms", "share_of_device_time"):
         roofline[k] = fp64_view[k]
-    roofline["note"] = ("the double-float weights, offsets, interface jumps, Roe dissipation and viscous divergence "
-                        "run ~4.7k FP32-pipe instructions per point and pass (FP32 runs 63x the FP64 rate); FP64 "
-                        "work is 47 lane-ops per point and pass + the RK epilogue (fp64_pipe)")
+    # the method's own work per launch, beside the issue view: the scope table's algorithmic bytes
+    # (a fused RK4 stage reads U_s, U_n, acc and writes acc, U_s+1: 200 B/pt, 160 B/pt in the
+    # first and last stage, so 720 B/pt per step over 12 direction launches) and the method's
+    # all-FP64 flops, with the pipe each part of them runs on in this formulation
+    step_bytes = 160 + 200 + 200 + 160
+    launch_bytes = step_bytes / 12.0
+    step_ms = ms / K
+    roofline["method"] = {
+        "algorithmic_bytes_per_point_per_launch": launch_bytes,
+        "algorithmic_bytes_source": "fused RK4 stage: read U_s, U_n, acc, write acc, U_s+1 (200 B/pt; stages 1 "
+                                    "and 4: 160 B/pt) = 720 B/pt per step over 3 x 4 direction launches",
+        "method_hbm_gbs": launch_bytes * N / avg_launch_s / 1e9,
+        "method_hbm_frac": launch_bytes * N / avg_launch_s / 1e9 / HBM,
+        "step_method_hbm_frac": (step_bytes + 40) * N / (step_ms * 1e-3) / 1e9 / HBM,
+        "hbm_peak_gbs": HBM, "hbm_peak_source": peaks["source"],
+        "method_flops_per_point_per_launch": FLOPS_DIR + 5,
+        "method_flops_source": "all-FP64 form of one direction pass (FMA = 2): point fluxes 6, smoothness "
+                               "indicators 9 x 20, candidates and weighted sums 9 x 46, Roe flux 96, "
+                               "difference + viscous divergence 34, RK epilogue 5",
+        "method_tflops": (FLOPS_DIR + 5) * N / avg_launch_s / 1e12,
+        "method_fp64_frac": (FLOPS_DIR + 5) * N / avg_launch_s / 1e12 / FP64_PEAK_TFLOPS,
+        "fp64_peak_tflops": FP64_PEAK_TFLOPS,
+        "pipes": {"fp64_pipe_lane_ops_per_point": OPS_DIR_FP64 + OPS_RK_EPI / 3.0,
+                  "fp64_pipe_part": "point values, first differences, point fluxes, interface-flux sums, flux "
+                                    "difference, RK update",
+                  "fp32_pipe_part": "WENO weights and offsets, interface jumps, Roe dissipation, viscous "
+                                    "fluxes and divergence, as double-float (~4.3k FP32 instructions per point "
+                                    "and pass, ncu)"},
+        "note": "method_fp64_frac above 1 means the formulation runs the method faster than the FP64 pipe "
+                "could in all-FP64 arithmetic; the binding resource is instruction issue (frac)"}
     tr = ncu_traffic_per_point("k_dir", kernel_source_sha())
     if tr is not None:
         bpp, src, grid = tr
-        roofline["traffic"] = bpp * n ** 3
+        roofline["traffic"] = bpp * N
         roofline["traffic_note"] = (f"ncu dram read+write per launch at {grid}^3 ({src}), "
                                     f"{bpp:.1f} B/point scaled to {n}^3 (streaming kernel: traffic ~ points)")
-        roofline["hbm_frac_measured"] = bpp * n ** 3 / avg_launch_s / 1e9 / 6713.6
+        roofline["hbm_frac_measured"] = bpp * N / avg_launch_s / 1e9 / HBM
+
+    # sampled parity of the headline's initial right-hand side against the oracle
+    parity = _guard("parity", lambda: _sampled_parity(solver, u0_dev, mu, args.parity_points))
 
     # end to end through the C ABI with host buffers (pinned): H2D state, RK4 step,
     # statistics, D2H state + statistics, every step
-    uh_t = torch.from_numpy(u0.copy()).pin_memory()
-    uh = uh_t.numpy()
-    solver.step_host(uh, dt, 1)
-    barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        solver.step_host(uh, dt, 1)
-    el = max_over_ranks(time.perf_counter() - t0, world)
-    e2e_pts = sum_over_ranks(float(n ** 3 * RK_STAGES * args.e2e_steps), world)
-    state_bytes = 5 * n ** 3 * 8
-    e2e = {"value": e2e_pts / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
-           "d2h_bytes_per_step": state_bytes + 8 * ns3d.NS3D_STATS_NDOUBLE,
-           "call": "ns3d_step_host (pinned host state in, 1 RK4 step + statistics, state out)"}
+    e2e = _guard("e2e", lambda: _e2e(solver, u0_dev, dt, args.e2e_steps, world, step_ms))
 
-    u64_final = ud.clone()
     solver.close()
-    del ud
+    del solver
 
-    # the all-FP64 evaluation of the same workload, for comparison
     modes = {"fp64": {"value": value, "ms_per_step": ms / K,
                       "weights": "double-float (FP32 pairs), all else FP64"}}
     if not args.no_strict:
-        Ks = max(2, K // 2)
-        s2, u2, _, ms2, kt2, _, _ = timed_loop(ns3d.NS3D_FP64_STRICT, Ks, max(1, W - 1), False)
-        s2.close()
-        del u2
-        v2 = sum_over_ranks(float(n ** 3 * RK_STAGES * Ks), world) / (ms2 * 1e-3) / 1e9
-        modes["fp64_strict"] = {"value": v2, "ms_per_step": ms2 / Ks, "steps": Ks, "weights": "FP64",
-                                "roofline": roofline_of(kt2, OPS_DIR_STRICT, "NS3D_FP64_STRICT")}
+        def strict():
+            Ks, Ws = 2, 1
+            s2, u2, ms2, kt2, _, _ = timed_loop(ns3d.NS3D_FP64_STRICT, Ks, Ws, False, Ws + Ks)
+            s2.close()
+            del u2
+            v2 = sum_over_ranks(float(N * RK_STAGES * Ks), world) / (ms2 * 1e-3) / 1e9
+            return {"value": v2, "ms_per_step": ms2 / Ks, "steps": Ks, "weights": "FP64",
+                    "speed_vs_fp64": v2 / value, "roofline": roofline_of(kt2, OPS_DIR_STRICT, "NS3D_FP64_STRICT")}
+        modes["fp64_strict"] = _guard("fp64_strict", strict)
+    torch.cuda.empty_cache()
     if not args.no_fp32:
-        # FP32-bulk: same W + K steps from the same state; error against the FP64 path
-        s3, u3, _, ms3, kt3, st3, _ = timed_loop(ns3d.NS3D_FP32_BULK, K, W, False)
-        s3.close()
-        v3 = sum_over_ranks(float(n ** 3 * RK_STAGES * K), world) / (ms3 * 1e-3) / 1e9
-        dmax = float((u3 - u64_final).abs().max().item())
-        umax = float(u64_final.abs().max().item())
-        modes["fp32_bulk"] = {
-            "value": v3, "ms_per_step": ms3 / K, "speedup_vs_fp64": v3 / value,
-            "arithmetic": "FP32 indicators, weights, interface values, Roe flux; FP64 state, difference, "
-                          "viscous terms, RK, reductions",
-            "error_vs_fp64_after_steps": W + K,
-            "ke_rel_err": float(abs(st3[-1, 5] - st[-1, 5]) / abs(st[-1, 5])),
-            "enstrophy_rel_err": float(abs(st3[-1, 6] - st[-1, 6]) / abs(st[-1, 6])),
-            "field_maxnorm_rel_err": dmax / umax,
-            "dir_kernel_ms": sum(kt3[k][0] for k in ("dir_x", "dir_y", "dir_z")) / K}
-        del u3
-    del u64_final
-
+        modes["fp32_bulk"] = _guard("fp32_bulk", lambda: _fp32_compare(timed_loop, ud, st, n_cmp, K, W, value,
+                                                                       world, N, ns3d))
+    del ud
+    torch.cuda.empty_cache()
     if not args.no_adjoint:
-        modes["adjoint"] = run_adjoint()
-
+        modes["adjoint"] = _guard("adjoint", run_adjoint)
+    torch.cuda.empty_cache()
     if not args.no_ensemble:
-        # batched ensemble of uneven grids (10 steps per schedule; the full 50-step run is
-        # bench.py --study ensemble --steps 50)
-        modes["ensemble_48"] = run_ensemble(10, args.cfl)
+        modes["ensemble_48"] = _guard("ensemble_48", lambda: run_ensemble(args.ens_steps, args.cfl))
+    torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        g, el_cpu, cores, what = cpu_oracle_sample(u0, mu, n, dt, full_step=True)
-        cpu = {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{what}, {el_cpu:.1f} s on the host cores (plain FP64 C oracle)"}
+        def cpu_leg():
+            u0_host = u0_dev.cpu().numpy()
+            g, el_cpu, cores, what = cpu_oracle_sample(u0_host, mu, n, dt, full_step=False)
+            return {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle",
+                    "sample": f"{what} (the headline's initial state), {el_cpu:.1f} s on the host cores "
+                              f"(plain FP64 C oracle, OpenMP over lines/points)"}
+        cpu = _guard("cpu_baseline", cpu_leg)
+    del u0_dev
+    torch.cuda.empty_cache()
+    if args.big > 0:
+        modes["big_1024"] = _guard("big_1024", lambda: run_big(args.big, args.big_steps, args.cfl,
+                                                               n_sample=args.big_points))
+        torch.cuda.empty_cache()
 
     if rank == 0:
         cfg = workload_config(n, args.cfl, mu, dt)
@@ -493,9 +581,94 @@ def run_ours(args, world, rank, local):
                 "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic", "config": cfg,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "kernel_ms": {k: v[0] for k, v in ktimes.items()}, "clocks": clk, "modes": modes,
-                "final_stats": {"ke": float(st[-1, 5]), "enstrophy": float(st[-1, 6]), "status_ok": status_ok}}
+                "kernel_ms": {k: v[0] for k, v in ktimes.items()}, "clocks": clk, "parity_rhs_sampled": parity,
+                "modes": modes,
+                "final_stats": {"after_steps": W + K, "ke": float(st[W + K, 5]), "enstrophy": float(st[W + K, 6]),
+                                "status_ok": status_ok}}
         print(json.dumps(line), flush=True)
+
+
+def _sampled_parity(solver, u_dev, mu, points: int) -> dict:
+    import torch
+    if points <= 0:
+        return None
+    rhs = torch.empty_like(u_dev)
+    solver.rhs(u_dev, rhs)
+    solver.check()
+    out = window_oracle_check(u_dev, rhs, mu, points)
+    del rhs
+    torch.cuda.empty_cache()
+    return out
+
+
+def _e2e(solver, u0_dev, dt, steps: int, world: int, device_step_ms: float) -> dict:
+    """ns3d_step_host with a pinned host state: H2D, one RK4 step, statistics, D2H every step;
+    with the pinned-copy bandwidth of this machine and the share of the copy time hidden behind
+    the kernels."""
+    import torch
+    from paper_2211_16718_gb300 import ns3d
+    n = u0_dev.shape[-1]
+    uh_t = u0_dev.cpu().pin_memory()
+    uh = uh_t.numpy()
+    solver.step_host(uh, dt, 1)  # warm-up (allocates the device copy and the copy stream)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        solver.step_host(uh, dt, 1)
+    el = max_over_ranks(time.perf_counter() - t0, world)
+    pts = sum_over_ranks(float(n ** 3 * RK_STAGES * steps), world)
+    state_bytes = 5 * n ** 3 * 8
+    # pinned-copy bandwidth of this box, one whole state each way
+    dev = torch.empty_like(u0_dev)
+    stream = torch.cuda.current_stream()
+    bw = {}
+    for name, (dst, src) in (("h2d", (dev, uh_t)), ("d2h", (uh_t, dev))):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            dst.copy_(src, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bw[name] = 3 * state_bytes / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del dev
+    t_copy = state_bytes / (bw["h2d"] * 1e9) + state_bytes / (bw["d2h"] * 1e9)
+    t_step = el / steps
+    serial = device_step_ms * 1e-3 + t_copy
+    return {"value": pts / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+            "d2h_bytes_per_step": state_bytes + 8 * ns3d.NS3D_STATS_NDOUBLE,
+            "call": "ns3d_step_host (pinned host state in, 1 RK4 step + statistics, state out)",
+            "steps": steps, "ms_per_step": t_step * 1e3, "timer": "host perf_counter around the synchronising calls",
+            "pinned_copy_gbs": bw, "copy_ms_per_step_serial": t_copy * 1e3,
+            "device_ms_per_step": device_step_ms,
+            "copy_time_hidden_frac": max(0.0, min(1.0, (serial - t_step) / t_copy)) if t_copy > 0 else None}
+
+
+def _fp32_compare(timed_loop, u64, st64, n_cmp, K, W, value64, world, N, ns3d) -> dict:
+    """FP32-bulk over the same steps from the same state and dt: speed, and its error against
+    the FP64 path after n_cmp steps (KE and enstrophy every step, field max-norm at the end)."""
+    import numpy as np
+    s3, u3, ms3, kt3, st3, _ = timed_loop(ns3d.NS3D_FP32_BULK, K, W, False, n_cmp)
+    s3.close()
+    v3 = sum_over_ranks(float(N * RK_STAGES * K), world) / (ms3 * 1e-3) / 1e9
+    a, b = st64[: n_cmp + 1], st3[: n_cmp + 1]
+    diff = (u3 - u64).abs().reshape(5, -1).amax(dim=1).cpu().numpy()
+    scale = u64.abs().reshape(5, -1).amax(dim=1).cpu().numpy()
+    del u3
+    return {"value": v3, "ms_per_step": ms3 / K, "speedup_vs_fp64": v3 / value64,
+            "arithmetic": "FP32 indicators, weights, interface values, Roe flux; FP64 state, difference, "
+                          "viscous terms, RK, reductions",
+            "steps_compared": n_cmp, "dt": "the FP64 headline's",
+            "ke_rel_err_max_over_steps": float((np.abs(b[:, 5] - a[:, 5]) / np.abs(a[:, 5])).max()),
+            "enstrophy_rel_err_max_over_steps": float((np.abs(b[:, 6] - a[:, 6]) / np.abs(a[:, 6])).max()),
+            "ke_final": [float(a[-1, 5]), float(b[-1, 5])], "enstrophy_final": [float(a[-1, 6]), float(b[-1, 6])],
+            "field_maxnorm_rel_err": float(diff.max() / scale.max()),
+            "field_maxnorm_rel_err_per_variable": (diff / scale).tolist(),
+            "mass_rel_drift": float(abs(b[-1, 0] - b[0, 0]) / abs(b[0, 0])),
+            "energy_rel_drift": float(abs(b[-1, 4] - b[0, 4]) / abs(b[0, 4])),
+            "status_ok": bool(np.all(b[:, 10] == 0)),
+            "kernel_ms_per_step": {k: v[0] / K for k, v in kt3.items() if v[1] > 0}}
 
 
 ADJ_N, ADJ_STEPS, ADJ_EVERY, ADJ_MU, ADJ_CFL, ADJ_FD_DIRS, ADJ_FD_EPS = 64, 256, 16, 2.5e-4, 0.5, 8, 1e-6
@@ -626,11 +799,13 @@ def run_adjoint(n: int = ADJ_N, nsteps: int = ADJ_STEPS, every: int = ADJ_EVERY,
             "kernels": kern}
 
 
-def window_oracle_check(u_dev, rhs_dev, mu: float, n_sample: int, seed: int = 0) -> dict:
+def window_oracle_check(u_dev, rhs_dev, mu: float, n_sample: int, seed: int = 0, tile: int = 24) -> dict:
     """Compare the GPU right-hand side at sampled points of an n^3 grid with the oracle
     evaluated on the 11^3 periodic window centred on each point: the RHS at a point
     reads the state within 4 points of it along the axes, so the window's own
-    periodic wrap never reaches the centre's stencil and the oracle's value is exact."""
+    periodic wrap never reaches the centre's stencil and the oracle's value is exact.
+    Besides the random points: the grid corners and points on the periodic seams and on
+    the tile edges of the direction passes (multiples of `tile` along each axis)."""
     import numpy as np
     import torch
     from oracle import oracle as O
@@ -639,17 +814,32 @@ def window_oracle_check(u_dev, rhs_dev, mu: float, n_sample: int, seed: int = 0)
     h = 2 * math.pi / n
     P = O.Params(w, w, w, lx=w * h, ly=w * h, lz=w * h, mu_eff=mu)
     scale = float(rhs_dev.abs().max().item())
-    pts = np.random.default_rng(seed).integers(0, n, size=(n_sample, 3))
-    off = torch.arange(-r, r + 1, device=u_dev.device)
+    rng = np.random.default_rng(seed)
+    edge = sorted({0, 1, n - 1, n - 2, tile - 1, tile, tile + 1, n // 2, (n // tile) * tile % n,
+                   ((n // tile) * tile - 1) % n})
+    special = [(a, b, c) for a in (0, n - 1) for b in (0, n - 1) for c in (0, n - 1)]
+    special += [(int(rng.choice(edge)), int(rng.choice(edge)), int(rng.integers(0, n))) for _ in range(n_sample // 8)]
+    special += [(int(rng.integers(0, n)), int(rng.choice(edge)), int(rng.choice(edge))) for _ in range(n_sample // 8)]
+    nrand = max(0, n_sample - len(special))
+    pts = np.concatenate([np.array(special, dtype=np.int64).reshape(-1, 3),
+                          rng.integers(0, n, size=(nrand, 3))])[:max(n_sample, 8)]
+    off = np.arange(-r, r + 1)
+    ix = (pts[:, 0:1] + off) % n
+    iy = (pts[:, 1:2] + off) % n
+    iz = (pts[:, 2:3] + off) % n
+    flat = (iz[:, :, None, None] * n + iy[:, None, :, None]) * n + ix[:, None, None, :]  # [P, w, w, w]
+    fi = torch.from_numpy(flat.reshape(-1)).to(u_dev.device)
+    wins = u_dev.reshape(5, -1)[:, fi].reshape(5, len(pts), w, w, w).cpu().numpy()
+    ci = torch.from_numpy(((pts[:, 2] * n + pts[:, 1]) * n + pts[:, 0]).astype(np.int64)).to(u_dev.device)
+    got = rhs_dev.reshape(5, -1)[:, ci].cpu().numpy()
     worst = 0.0
-    for i, j, k in pts:
-        iz, iy, ix = (off + int(k)) % n, (off + int(j)) % n, (off + int(i)) % n
-        win = u_dev[:, iz][:, :, iy][:, :, :, ix].cpu().numpy()
-        ref = O.rhs_points(P, win, [(r * w + r) * w + r])[0]
-        got = rhs_dev[:, int(k), int(j), int(i)].cpu().numpy()
-        worst = max(worst, float(np.abs(got - ref).max()) / scale)
-    return {"points": n_sample, "window": "11^3 periodic, centred", "max_rel_err": worst,
-            "normalisation": "max |R| over the whole grid (all 5 variables)"}
+    for q in range(len(pts)):
+        ref = O.rhs_points(P, np.ascontiguousarray(wins[:, q]), [(r * w + r) * w + r])[0]
+        worst = max(worst, float(np.abs(got[:, q] - ref).max()) / scale)
+    return {"points": int(len(pts)), "special_points": int(min(len(special), len(pts))),
+            "window": "11^3 periodic, centred", "max_rel_err": worst,
+            "normalisation": "max |R| over the whole grid (all 5 variables)",
+            "special": "grid corners, periodic seams and direction-pass tile edges"}
 
 
 def run_big(n: int, steps: int, cfl: float, n_sample: int = 24) -> dict:
@@ -776,7 +966,8 @@ ENSEMBLE_SIZES = (32, 48, 64, 96, 128)
 def run_ensemble(steps: int, cfl: float, count: int = 48, cache_path=None, sizes_cycle=ENSEMBLE_SIZES) -> dict:
     """Ensemble of `count` decaying-turbulence realisations (seed i, grid sizes_cycle[i % len]^3,
     dt_i from CFL `cfl` of its own initial state): `steps` RK4 steps in each schedule (from
-    the same initial states), after the autotuner has picked the tile shape."""
+    the same initial states), after the autotuner has picked the tile shape per grid size and
+    the graph's branch count."""
     import numpy as np
     import torch
     from paper_2211_16718_gb300 import inputs as I
@@ -789,26 +980,27 @@ def run_ensemble(steps: int, cfl: float, count: int = 48, cache_path=None, sizes
     b = ns3d.Batch(params)
     states = [torch.from_numpy(h.copy()).cuda() for h in host]
     b.set_states(states)
-    b.set_dt([1.0] * count)
-    ws = b.stats().cpu().numpy()[:, 9]
-    dts = [cfl / w for w in ws]
-    b.set_dt(dts)
-    variant, tune_ms = b.autotune(cache_path)
+    b.set_dt_from_cfl(cfl)
+    t0 = time.perf_counter()
+    tune = b.autotune(cache_path)
+    tune_s = time.perf_counter() - t0
+    shapes = {0: "24x4", 1: "16x4", 2: "40x2"}
+    per_size = {}
+    for i, n in enumerate(sizes):
+        per_size.setdefault(f"{n}^3", {"tile_shape": shapes[tune["variants"][i]],
+                                       "ms_per_step_by_shape": dict(zip(shapes.values(), tune["ms_variants"][i]))})
     out = {"instances": count, "sizes": f"seed i: {tuple(sizes_cycle)}[i % {len(sizes_cycle)}]^3", "points": pts,
-           "steps": steps,
-           "autotuned_variant": variant, "autotune_ms_per_step": tune_ms,
-           "tile_shapes": {"0": "24x4", "1": "16x4", "2": "40x2"}}
+           "steps": steps, "autotune": {"per_size": per_size, "graph_branches": tune["branches"],
+                                        "ms_per_step_by_branches": {str(k + 1): m for k, m in
+                                                                    enumerate(tune["ms_branches"]) if m > 0},
+                                        "seconds": tune_s}}
     finals = {}
     for schedule in ("sequential", "graph", "persistent"):
         for s, h in zip(states, host):
             s.copy_(torch.from_numpy(h))
-        b.step(1, schedule)  # warm-up (and graph capture for this step count)
+        b.step(1, schedule)  # warm-up (and graph capture)
         for s, h in zip(states, host):
             s.copy_(torch.from_numpy(h))
-        if schedule != "sequential":
-            b.step(steps, schedule)  # capture the full-length graph once, untimed
-            for s, h in zip(states, host):
-                s.copy_(torch.from_numpy(h))
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -817,10 +1009,12 @@ def run_ensemble(steps: int, cfl: float, count: int = 48, cache_path=None, sizes
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         out[schedule] = {"ms": ms, "gpts": pts * RK_STAGES * steps / (ms * 1e-3) / 1e9}
-        finals[schedule] = [s.cpu().numpy() for s in states[:3]]
+        finals[schedule] = [s.cpu().numpy() for s in states[:5]]
     b.check()
-    out["persistent_in_graph"] = b.info()["persistent_in_graph"]
-    out["persistent_ctas_per_sm"] = b.info()["persistent_ctas_per_sm"]
+    info = b.info()
+    out["persistent_in_graph"] = info["persistent_in_graph"]
+    out["persistent_ctas_per_sm"] = info["persistent_ctas_per_sm"]
+    out["persistent_tile_shape"] = shapes[info["variant"]]
     out["schedules_bitwise_equal"] = all(np.array_equal(a, c) for k in ("graph", "persistent")
                                          for a, c in zip(finals[k], finals["sequential"]))
     out["speedup_persistent_vs_sequential"] = out["persistent"]["gpts"] / out["sequential"]["gpts"]
@@ -856,8 +1050,8 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         from paper_2211_16718_gb300 import build as B
         B.build()
-        n = args.n if args.n != 256 else 1024
-        print(json.dumps({"study": "big", "result": run_big(n, args.steps, args.cfl)}), flush=True)
+        print(json.dumps({"study": "big", "result": run_big(args.big, args.steps, args.cfl, n_sample=args.big_points)}),
+              flush=True)
         return
     if args.study == "vjp":
         # --steps K right-hand-side vector-Jacobian products of the --n^3 turbulence state

@@ -26,7 +26,7 @@
  *  - Streams: all device work of a call is enqueued on the context's stream
  *    (given to ns3d_init, changeable with ns3d_set_stream).  Only the calls
  *    that return host data (ns3d_stats, ns3d_check, ns3d_step_host,
- *    ns3d_timing_read) synchronise that stream.
+ *    ns3d_dt_from_cfl, ns3d_timing_read) synchronise that stream.
  *  - Errors: every int-returning call returns NS3D_OK (0) or a negative code;
  *    nothing aborts or traps.  ns3d_last_error(ctx) gives a message.
  *    Non-physical states (rho <= 0, p <= 0, a non-finite value, or a negative
@@ -51,7 +51,10 @@ enum {
   NS3D_ENOMEM = -2,        /* device or pinned-host allocation failed */
   NS3D_ECUDA = -3,         /* CUDA launch/runtime error (see ns3d_last_error) */
   NS3D_ENONPHYSICAL = -4,  /* non-physical state detected by a kernel */
-  NS3D_ETIMEOUT = -5,      /* a bounded device-side wait gave up */
+  NS3D_ETIMEOUT = -5,      /* reserved for a bounded device-side wait that gives up; no call
+                              returns it: no kernel of the library spins on a flag (the
+                              persistent ensemble kernel separates its phases with the grid
+                              barriers of a cooperative launch, whose CTAs are co-resident) */
   NS3D_ERANGE = -6         /* data beyond the range of the double-float WENO weights
                               (differences of the data above ~1e9): use NS3D_FP64_STRICT */
 };
@@ -176,6 +179,14 @@ int ns3d_stats_async(ns3d_ctx *ctx, const double *u_dev, double *out_dev);
  *    Calls no cudaMalloc, cudaFree or other allocating routine. */
 int ns3d_stats_noalloc(const ns3d_params *p, const double *u_dev, double *out_dev, void *cuda_stream);
 
+/* Time step from a CFL number (Sec. 2.3 reading: CFL = dt * max over grid points and
+ * directions d of (|u_d| + c)/dx_d, c the speed of sound): *dt_out = cfl / that maximum
+ * for the state u_dev, computed by the statistics kernels (synchronises the stream, and
+ * reads and clears the sticky status word as ns3d_stats does).  Returns NS3D_EINVAL for
+ * a null pointer or a cfl that is not finite and > 0, NS3D_ENONPHYSICAL if the state is
+ * non-physical or the maximum is not finite and > 0 (*dt_out is then unchanged). */
+int ns3d_dt_from_cfl(ns3d_ctx *ctx, const double *u_dev, double cfl, double *dt_out);
+
 /* End-to-end call with host buffers: copies u_host to library-owned device
  * memory, advances nsteps steps of size dt, computes the statistics of the
  * final state into *stats_host (may be NULL), copies the state back into
@@ -203,13 +214,17 @@ const char *ns3d_last_error(const ns3d_ctx *ctx);
  * precision, which must be NS3D_FP64 or NS3D_FP64_STRICT, and rk), its own
  * caller-owned state and its own dt.  The schedules compute bitwise identical
  * results:
- *  NS3D_BATCH_SEQUENTIAL  per-instance launches (5 per RK stage per instance);
- *  NS3D_BATCH_GRAPH       one launch per phase for all instances over a flattened
- *                         (instance, tile) work list, the whole nsteps loop captured
- *                         once in a CUDA graph and replayed with one graph launch;
+ *  NS3D_BATCH_SEQUENTIAL  per-instance launches (5 per RK stage per instance), one
+ *                         instance after the other on the batch's stream;
+ *  NS3D_BATCH_GRAPH       the same per-instance launches for one step, captured once
+ *                         in a CUDA graph whose parallel branches each advance a share
+ *                         of the instances (balanced by points, largest first), so that
+ *                         small instances run beside the large ones; one graph launch
+ *                         per step;
  *  NS3D_BATCH_PERSISTENT  one cooperative kernel for all steps, stages, phases and
- *                         instances, phases separated by grid-wide barriers
- *                         (captured in a CUDA graph when the runtime allows it). */
+ *                         instances over a flattened (instance, tile) work list, phases
+ *                         separated by grid-wide barriers (captured in a CUDA graph
+ *                         when the runtime allows it). */
 enum { NS3D_BATCH_SEQUENTIAL = 0, NS3D_BATCH_GRAPH = 1, NS3D_BATCH_PERSISTENT = 2 };
 typedef struct ns3d_batch ns3d_batch;
 
@@ -225,20 +240,40 @@ int ns3d_batch_set_dt(ns3d_batch *b, const double *dt);
 int ns3d_batch_step(ns3d_batch *b, int nsteps, int schedule);
 /* Statistics of every instance into out_dev[count * NS3D_STATS_NDOUBLE] (no sync). */
 int ns3d_batch_stats(ns3d_batch *b, double *out_dev);
+/* Per-instance time steps from one CFL number (as ns3d_dt_from_cfl, each instance from
+ * its own current state) applied as by ns3d_batch_set_dt and, if dt_out is not NULL,
+ * copied to dt_out[count].  Synchronises.  NS3D_EINVAL for a cfl that is not finite and
+ * > 0 or before ns3d_batch_set_states; NS3D_ENONPHYSICAL if an instance has no finite
+ * positive wave speed (the time steps are then unchanged). */
+int ns3d_batch_set_dt_from_cfl(ns3d_batch *b, double cfl, double *dt_out);
 /* Read and clear the batch's sticky status word (synchronises). */
 int ns3d_batch_check(ns3d_batch *b);
 /* Tile shape of the direction passes: variant 0 (24 x 4), 1 (16 x 4), 2 (40 x 2)
- * points x lines; results do not depend on it. */
+ * points x lines, for every instance and the persistent kernel; results do not
+ * depend on it.  NS3D_FP64_STRICT batches have the one shape 0 (32 x 4). */
 int ns3d_batch_set_variant(ns3d_batch *b, int variant);
-/* Autotuner: times one graph-scheduled step of every tile variant on copies of the
- * current states (which are not advanced), selects the fastest and appends
- * {"key": ..., "variant": ..., "ms_per_step": [...]} to the JSON-lines file
- * cache_path (NULL: no cache); a key already in the cache is used without timing.
- * ms_out[3] (may be NULL) receives the timings (-1 when taken from the cache). */
+/* Tile shape of instance i alone (SEQUENTIAL and GRAPH schedules; the persistent
+ * kernel keeps the shape of ns3d_batch_set_variant). */
+int ns3d_batch_set_instance_variant(ns3d_batch *b, int i, int variant);
+/* Parallel branches of the GRAPH schedule, 1..8 (default 4). */
+int ns3d_batch_set_branches(ns3d_batch *b, int branches);
+/* Autotuner: for every grid size of the ensemble (instances with the same nx, ny, nz
+ * and viscous or not), times one step of that size's instances with each tile shape
+ * (sequential launches, on copies of the current states, which are not advanced) and
+ * gives those instances the fastest; then times one GRAPH-scheduled step with 1, 2, 4
+ * and 8 branches and keeps the fastest count.  Each choice is appended to the
+ * JSON-lines file cache_path as {"key": ..., "variant": ... | "branches": ...,
+ * "ms_per_step": [...]} (NULL: no cache); keys already in the cache are used
+ * without timing.  ms_out (may be NULL) has room for 3 * count + 8 doubles:
+ * ms_out[3 i + v] = the time of shape v on instance i's size, then the time with
+ * 1..8 branches (-1 where not timed).  NS3D_ENOMEM if the state copies do not fit. */
 int ns3d_batch_autotune(ns3d_batch *b, const char *cache_path, double *ms_out);
-/* Current variant, CTAs per SM of the persistent kernel (0 before its first use)
+/* Current tile shape of the persistent kernel, its CTAs per SM (0 before its first use)
  * and whether it runs captured in a graph (1), as a direct launch (0) or not yet (-1). */
 int ns3d_batch_info(const ns3d_batch *b, int *variant, int *persistent_ctas_per_sm, int *persistent_in_graph);
+/* Per-instance tile shapes into variants[count] and the GRAPH schedule's branch count
+ * (either pointer may be NULL). */
+int ns3d_batch_schedule_info(const ns3d_batch *b, int *variants, int *branches);
 const char *ns3d_batch_last_error(const ns3d_batch *b);
 
 /* Tile shape of the direction passes of a single context (see ns3d_batch_set_variant). */

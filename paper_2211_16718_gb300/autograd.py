@@ -37,14 +37,9 @@ class RKStep(torch.autograd.Function):
     def forward(ctx, u, solver: Solver, dt: float, nsteps: int):
         u0 = u.detach().contiguous()
         ctx.solver, ctx.dt, ctx.nsteps = solver, float(dt), int(nsteps)
-        if nsteps <= 1:
-            ctx.save_for_backward(u0)
-            out = u0.clone()
-            solver.rk_step(out, dt, nsteps)
-            return out
-        out = u0.clone()
-        solver.traj_forward(out, dt, nsteps, nsteps)
         ctx.save_for_backward(u0)
+        out = u0.clone()
+        solver.rk_step(out, dt, nsteps)  # the same launches as a recorded trajectory: the same bits
         return out
 
     @staticmethod
@@ -62,18 +57,27 @@ class RKStep(torch.autograd.Function):
 
 class Trajectory(torch.autograd.Function):
     """u_N = step^N(u_0) with checkpoints every `every` steps kept by the library; the
-    backward reverses the recorded trajectory (one trajectory per Solver at a time)."""
+    backward reverses the recorded trajectory.  The library holds one recording per
+    Solver: if another trajectory was recorded on the same Solver after this forward
+    (a later trajectory() or rk_step(nsteps > 1) backward), this backward records its
+    own again from the saved initial state before reversing it."""
 
     @staticmethod
     def forward(ctx, u, solver: Solver, dt: float, nsteps: int, every: int):
-        out = u.detach().contiguous().clone()
+        u0 = u.detach().contiguous()
+        out = u0.clone()
         solver.traj_forward(out, dt, nsteps, every)
-        ctx.solver = solver
+        ctx.solver, ctx.args, ctx.generation = solver, (float(dt), int(nsteps), int(every)), solver.traj_generation
+        ctx.save_for_backward(u0)
         return out
 
     @staticmethod
     def backward(ctx, g):
+        (u0,) = ctx.saved_tensors
         gb = g.detach().contiguous().clone()
+        if ctx.solver.traj_generation != ctx.generation:
+            dt, nsteps, every = ctx.args
+            ctx.solver.traj_forward(u0.clone(), dt, nsteps, every)
         ctx.solver.traj_vjp(gb)
         return gb, None, None, None, None
 

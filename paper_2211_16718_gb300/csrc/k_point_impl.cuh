@@ -74,7 +74,7 @@ __device__ __forceinline__ int prim_point(const double* __restrict__ u, double* 
   pm[PM_T * N + p] = gamma * pr * ri;
   pm[PM_H * N + p] = (e + pr) * ri;
   pm[PM_SR * N + p] = sqrt(rho);
-  return !(rho > 0.0) | !(pr > 0.0) | !isfinite(e) | !isfinite(mx + my + mz);
+  return !(rho > 0.0) | !isfinite(rho) | !(pr > 0.0) | !isfinite(e) | !isfinite(mx + my + mz);
 }
 
 __device__ __forceinline__ long long flat3(int i, int j, int k, int nx, int ny) {

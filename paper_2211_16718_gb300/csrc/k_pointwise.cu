@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(PW_THREADS) k_prim32(const double* __restrict_
     pm[PM_T * N + p] = f2d_bits(gamma * pr * ri);
     pm[PM_H * N + p] = f2d_bits((e + pr) * ri);
     pm[PM_SR * N + p] = f2d_bits(__fsqrt_rn(rho));
-    bad |= !(rho > 0.0f) | !(pr > 0.0f) | !isfinite(e) | !isfinite(mx + my + mz);
+    bad |= !(rho > 0.0f) | !isfinite(rho) | !(pr > 0.0f) | !isfinite(e) | !isfinite(mx + my + mz);
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONPHYS);
 }

@@ -262,7 +262,7 @@ const char* ns3d_strerror(int code) {
     case NS3D_ENOMEM: return "out of memory";
     case NS3D_ECUDA: return "CUDA error";
     case NS3D_ENONPHYSICAL: return "non-physical state (rho <= 0, p <= 0, or non-finite value)";
-    case NS3D_ETIMEOUT: return "device-side wait timed out";
+    case NS3D_ETIMEOUT: return "device-side wait timed out (reserved: no call returns it)";
     case NS3D_ERANGE: return "data beyond the range of the double-float WENO weights (use NS3D_FP64_STRICT)";
     default: return "unknown error";
   }
@@ -430,6 +430,19 @@ int ns3d_stats(ns3d_ctx* c, const double* u, ns3d_stats_t* out) {
   if (e != cudaSuccess) return cuda_fail(c, e, "statistics copy");
   fill_stats(c->stats_host, out);
   if (out->status) return set_err(c, out->status, "%s", ns3d_strerror(out->status));
+  return NS3D_OK;
+}
+
+int ns3d_dt_from_cfl(ns3d_ctx* c, const double* u, double cfl, double* dt_out) {
+  if (!c) return NS3D_EINVAL;
+  if (!u || !dt_out) return set_err(c, NS3D_EINVAL, "null pointer");
+  if (!(cfl > 0.0) || !isfinite(cfl)) return set_err(c, NS3D_EINVAL, "cfl must be finite and > 0");
+  ns3d_stats_t st;
+  int rc = ns3d_stats(c, u, &st);
+  if (rc) return rc;
+  const double w = st.max_wavespeed_over_dx;
+  if (!(w > 0.0) || !isfinite(w)) return set_err(c, NS3D_ENONPHYSICAL, "no finite positive wave speed");
+  *dt_out = cfl / w;
   return NS3D_OK;
 }
 

@@ -1,22 +1,27 @@
 // Batched ensembles of independent grids of uneven sizes (e.g. many turbulence
 // realisations), advanced together.  Three schedules of the same arithmetic
 // (bitwise identical results):
-//   SEQUENTIAL  every instance with its own launches (5 per RK stage per instance);
-//   GRAPH       one batched launch per phase for all instances, over a flattened
-//               (instance, tile) work list, the whole multi-step loop captured in
-//               one CUDA graph and replayed with a single graph launch;
+//   SEQUENTIAL  every instance with its own launches (5 per RK stage per instance),
+//               one instance after the other on the caller's stream;
+//   GRAPH       the same per-instance launches for one step, captured once in a CUDA
+//               graph whose parallel branches each advance a share of the instances
+//               (balanced by points), so that small instances run beside large ones
+//               instead of behind them; the graph is replayed once per step;
 //   PERSISTENT  one cooperative kernel for all steps, stages, phases and
-//               instances; phases are separated by grid-wide barriers
-//               (cooperative groups), so co-residency of all CTAs is guaranteed by
-//               the cooperative launch and there is no hand-written spin-wait.
-// The tile shape of the direction passes is chosen by ns3d_batch_autotune, which
-// times the candidate shapes on the actual ensemble and caches the choice in a
-// JSON-lines file keyed by device and ensemble.
+//               instances over a flattened (instance, tile) work list; phases are
+//               separated by grid-wide barriers (cooperative groups), so co-residency
+//               of all CTAs is guaranteed by the cooperative launch and there is no
+//               hand-written spin-wait.
+// ns3d_batch_autotune picks, per grid size present in the ensemble, the tile shape of
+// the direction passes (timing every candidate on that size's instances), and the
+// number of graph branches, and caches both in a JSON-lines file keyed by device and
+// size (or ensemble).
 #include <cooperative_groups.h>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -35,6 +40,7 @@ constexpr int BT = 256;  // threads of the pointwise batched kernels
 
 struct Inst {
   Grid g;
+  int variant;                    // tile shape of this instance's direction passes (SEQUENTIAL, GRAPH)
   double gamma, mu, kappa;
   double r12[3];
   const double* uin[MAX_STAGES];  // stage input states
@@ -104,23 +110,6 @@ __device__ __forceinline__ void phase_dir(const BatchView& b, int s, double* sm,
   }
 }
 
-// ---- batched kernels (one launch per phase for all instances) ------------------------
-__global__ void __launch_bounds__(BT) kb_prim(BatchView b, int s) {
-  int bad = 0;
-  phase_prim(b, s, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x, bad);
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(b.status, ST_NONPHYS);
-}
-
-__global__ void __launch_bounds__(BT) kb_visc(BatchView b) {
-  phase_visc<true>(b, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
-}
-
-template <int D, int MODE, int TP, int W>
-__global__ void __launch_bounds__(Plan<MODE, TP, W>::THREADS, Plan<MODE, TP, W>::MIN_CTAS) kb_dir(BatchView b, int s) {
-  extern __shared__ double sm[];
-  phase_dir<D, MODE, TP, W, true>(b, s, sm, blockIdx.x, gridDim.x);
-}
-
 // ---- persistent kernel: every step, stage, phase and instance in one launch ---------
 template <int MODE, int TP, int W>
 __global__ void __launch_bounds__(Plan<MODE, TP, W>::THREADS, Plan<MODE, TP, W>::MIN_CTAS) kb_persistent(BatchView b,
@@ -157,22 +146,7 @@ struct Kernels {
       e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     return e;
   }
-  static cudaError_t set_attr() {
-    const int bytes = Plan<MODE, TP, W>::BYTES;
-    cudaError_t e = attr(kb_dir<0, MODE, TP, W>, bytes);
-    if (e == cudaSuccess) e = attr(kb_dir<1, MODE, TP, W>, bytes);
-    if (e == cudaSuccess) e = attr(kb_dir<2, MODE, TP, W>, bytes);
-    if (e == cudaSuccess) e = attr(kb_persistent<MODE, TP, W>, bytes);
-    return e;
-  }
-  static cudaError_t dir(int d, const BatchView& v, int s, long long tiles, cudaStream_t st) {
-    const int bytes = Plan<MODE, TP, W>::BYTES, th = Plan<MODE, TP, W>::THREADS;
-    const unsigned grid = (unsigned)(tiles > 0 ? tiles : 1);
-    if (d == 0) kb_dir<0, MODE, TP, W><<<grid, th, bytes, st>>>(v, s);
-    else if (d == 1) kb_dir<1, MODE, TP, W><<<grid, th, bytes, st>>>(v, s);
-    else kb_dir<2, MODE, TP, W><<<grid, th, bytes, st>>>(v, s);
-    return cudaGetLastError();
-  }
+  static cudaError_t set_attr() { return attr(kb_persistent<MODE, TP, W>, Plan<MODE, TP, W>::BYTES); }
   static cudaError_t persistent(const BatchView& v, int nsteps, int ctas_per_sm, int sms, cudaStream_t st) {
     const int bytes = Plan<MODE, TP, W>::BYTES, th = Plan<MODE, TP, W>::THREADS;
     BatchView vv = v;
@@ -219,11 +193,16 @@ cudaError_t prepare_batch_kernels() {
 }  // namespace
 
 struct ns3d_batch {
+  static constexpr int MAX_BRANCHES = 8;
   int count = 0;
   std::vector<ns3d_params> p;
   cudaStream_t stream = nullptr;      // caller's stream: every launch runs here
   cudaStream_t cap_stream = nullptr;  // private stream that graph captures record on
-  int mode = 1, variant = 0, nstages = 4, sms = 0;
+  cudaStream_t branch[MAX_BRANCHES] = {};  // captured branches of the GRAPH schedule
+  cudaEvent_t fork = nullptr, join[MAX_BRANCHES] = {};
+  int branches = 4;                   // parallel branches of the GRAPH schedule
+  int mode = 1, variant = 0, nstages = 4, sms = 0;  // variant: tile shape of the PERSISTENT kernel
+  std::vector<int> ivar;              // per-instance tile shape (SEQUENTIAL, GRAPH)
   std::vector<Inst> inst;
   std::vector<double*> bufs;  // per-instance scratch allocations
   std::vector<double*> u;
@@ -234,10 +213,10 @@ struct ns3d_batch {
   long long* d_tile_off = nullptr;
   int* d_status = nullptr;
   double* partials = nullptr;
+  double* d_stats = nullptr;  // [count][NS3D_STATS_NDOUBLE] (ns3d_batch_set_dt_from_cfl)
   int nstat_blocks = 0;
   bool ready = false;
-  cudaGraphExec_t gexec = nullptr;
-  int g_nsteps = -1;
+  cudaGraphExec_t gexec = nullptr;  // one step of the GRAPH schedule
   cudaGraphExec_t pexec = nullptr;
   int p_nsteps = -1;
   int persistent_graph = -1;  // 1: captured in a graph, 0: direct cooperative launch, -1: not yet
@@ -257,7 +236,7 @@ void drop_graphs(ns3d_batch* b) {
   if (b->pexec) cudaGraphExecDestroy(b->pexec);
   b->gexec = nullptr;
   b->pexec = nullptr;
-  b->g_nsteps = b->p_nsteps = -1;
+  b->p_nsteps = -1;
 }
 
 BatchView view_of(const ns3d_batch* b) {
@@ -277,10 +256,11 @@ BatchView view_of(const ns3d_batch* b) {
 int rebuild(ns3d_batch* b) {
   if (b->u.empty() || b->dt.empty()) return NS3D_OK;
   int tp = 0, w = 0;
-  dir_tile_shape(b->mode, b->variant, &tp, &w);
+  dir_tile_shape(b->mode, b->variant, &tp, &w);  // the persistent kernel's tile list
   b->tile_off.assign(3 * (b->count + 1), 0);
   for (int i = 0; i < b->count; ++i) {
     Inst& in = b->inst[i];
+    in.variant = (b->mode == 1) ? b->ivar[i] : 0;
     double* u = b->u[i];
     double* ua = b->bufs[6 * i + 2];
     double* ub = b->bufs[6 * i + 3];
@@ -311,7 +291,7 @@ int rebuild(ns3d_batch* b) {
         a.hdelta = b->p[i].harten_delta;
         a.status = b->d_status;
         a.mode = b->mode;
-        a.variant = b->variant;
+        a.variant = in.variant;
         const double c133 = 13.0 / 3.0, eps4 = 4.0 * b->p[i].weno_eps;
         a.c133_hi = (float)c133;
         a.c133_lo = (float)(c133 - (double)a.c133_hi);
@@ -354,66 +334,84 @@ int rebuild(ns3d_batch* b) {
   return NS3D_OK;
 }
 
-// One step of every instance with per-instance launches.
-int step_sequential(ns3d_batch* b) {
-  for (int i = 0; i < b->count; ++i) {
-    const Inst& in = b->inst[i];
-    for (int s = 0; s < b->nstages; ++s) {
-      cudaError_t e = launch_prim(in.g, in.uin[s], in.pm, in.gamma, b->d_status, b->stream, b->mode);
-      if (e == cudaSuccess && in.fv) e = launch_visc(in.g, in.pm, in.fv, in.mu, in.kappa, b->stream, -1, b->mode);
-      for (int d = 0; d < 3 && e == cudaSuccess; ++d) e = launch_dir(d, in.dir[s][d], b->stream);
-      if (e != cudaSuccess) return berr(b, NS3D_ECUDA, cudaGetErrorString(e));
-    }
-  }
-  return NS3D_OK;
-}
-
-// Enqueue nsteps steps of batched launches on stream st (graph capture body).
-cudaError_t enqueue_batched(ns3d_batch* b, int nsteps, cudaStream_t st) {
-  const BatchView v = view_of(b);
-  const long long pts = b->pt_off[b->count];
-  long long blocks = (pts + BT - 1) / BT;
-  const unsigned pgrid = (unsigned)(blocks < 152LL * 16 ? (blocks > 0 ? blocks : 1) : 152LL * 16);
-  bool visc = false;
-  for (const Inst& in : b->inst) visc |= (in.fv != nullptr);
+// One RK step of instance i with its own launches on stream st.
+cudaError_t step_instance(const ns3d_batch* b, int i, cudaStream_t st) {
+  const Inst& in = b->inst[i];
   cudaError_t e = cudaSuccess;
-  for (int step = 0; step < nsteps && e == cudaSuccess; ++step) {
-    for (int s = 0; s < b->nstages && e == cudaSuccess; ++s) {
-      kb_prim<<<pgrid, BT, 0, st>>>(v, s);
-      e = cudaGetLastError();
-      if (e == cudaSuccess && visc) {
-        kb_visc<<<pgrid, BT, 0, st>>>(v);
-        e = cudaGetLastError();
-      }
-      for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
-        const long long tiles = b->tile_off[d * (b->count + 1) + b->count];
-        e = with_kernels(b->mode, b->variant, [&](auto K) { return decltype(K)::dir(d, v, s, tiles, st); });
-      }
-    }
+  for (int s = 0; s < b->nstages && e == cudaSuccess; ++s) {
+    e = launch_prim(in.g, in.uin[s], in.pm, in.gamma, b->d_status, st, b->mode);
+    if (e == cudaSuccess && in.fv) e = launch_visc(in.g, in.pm, in.fv, in.mu, in.kappa, st, -1, b->mode);
+    for (int d = 0; d < 3 && e == cudaSuccess; ++d) e = launch_dir(d, in.dir[s][d], st);
   }
   return e;
 }
 
-int step_graph(ns3d_batch* b, int nsteps) {
-  if (!b->gexec || b->g_nsteps != nsteps) {
-    if (b->gexec) cudaGraphExecDestroy(b->gexec);
-    b->gexec = nullptr;
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+// One step of the instances in `which` (all if empty), one after the other on the caller's stream.
+int step_sequential(ns3d_batch* b, const std::vector<int>& which = {}) {
+  const int n = which.empty() ? b->count : (int)which.size();
+  for (int k = 0; k < n; ++k) {
+    const cudaError_t e = step_instance(b, which.empty() ? k : which[k], b->stream);
     if (e != cudaSuccess) return berr(b, NS3D_ECUDA, cudaGetErrorString(e));
-    cudaError_t eq = enqueue_batched(b, nsteps, b->cap_stream);
-    e = cudaStreamEndCapture(b->cap_stream, &g);
-    if (eq != cudaSuccess || e != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      return berr(b, NS3D_ECUDA, cudaGetErrorString(eq != cudaSuccess ? eq : e));
-    }
-    e = cudaGraphInstantiate(&b->gexec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return berr(b, NS3D_ECUDA, cudaGetErrorString(e));
-    b->g_nsteps = nsteps;
   }
-  cudaError_t e = cudaGraphLaunch(b->gexec, b->stream);
+  return NS3D_OK;
+}
+
+// Instances of each GRAPH branch: largest first, each to the branch with the fewest points so
+// far (longest-processing-time rule; work per point is the same for every instance).
+std::vector<std::vector<int>> branch_lists(const ns3d_batch* b, int nb) {
+  std::vector<int> order(b->count);
+  for (int i = 0; i < b->count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return b->inst[x].g.N > b->inst[y].g.N; });
+  std::vector<std::vector<int>> lists(nb);
+  std::vector<long long> load(nb, 0);
+  for (int i : order) {
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    lists[k].push_back(i);
+    load[k] += b->inst[i].g.N;
+  }
+  return lists;
+}
+
+// Capture one step of every instance (per-instance launches in parallel branches) and
+// instantiate it.
+int capture_graph(ns3d_batch* b) {
+  const int nb = std::max(1, std::min(b->branches, std::min(b->count, (int)ns3d_batch::MAX_BRANCHES)));
+  const std::vector<std::vector<int>> lists = branch_lists(b, nb);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return berr(b, NS3D_ECUDA, cudaGetErrorString(e));
+  cudaError_t eq = cudaEventRecord(b->fork, b->cap_stream);
+  for (int k = 0; k < nb && eq == cudaSuccess; ++k) {
+    eq = cudaStreamWaitEvent(b->branch[k], b->fork, 0);
+    for (size_t j = 0; j < lists[k].size() && eq == cudaSuccess; ++j) eq = step_instance(b, lists[k][j], b->branch[k]);
+    if (eq == cudaSuccess) eq = cudaEventRecord(b->join[k], b->branch[k]);
+    if (eq == cudaSuccess) eq = cudaStreamWaitEvent(b->cap_stream, b->join[k], 0);
+  }
+  e = cudaStreamEndCapture(b->cap_stream, &g);
+  if (eq != cudaSuccess || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return berr(b, NS3D_ECUDA, cudaGetErrorString(eq != cudaSuccess ? eq : e));
+  }
+  e = cudaGraphInstantiate(&b->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    b->gexec = nullptr;
+    return berr(b, NS3D_ECUDA, cudaGetErrorString(e));
+  }
+  return NS3D_OK;
+}
+
+int step_graph(ns3d_batch* b, int nsteps) {
+  if (!b->gexec) {
+    const int rc = capture_graph(b);
+    if (rc) return rc;
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    const cudaError_t e = cudaGraphLaunch(b->gexec, b->stream);
+    if (e != cudaSuccess) return berr(b, NS3D_ECUDA, cudaGetErrorString(e));
+  }
   return NS3D_OK;
 }
 
@@ -464,33 +462,72 @@ std::string device_name() {
   return prop.name;
 }
 
-std::string tune_key(const ns3d_batch* b) {
-  std::string k = device_name() + "|batch|mode" + std::to_string(b->mode) + "|stages" + std::to_string(b->nstages) +
-                  "|";
+std::string params_key(const ns3d_params& p) {
+  return std::to_string(p.nx) + "x" + std::to_string(p.ny) + "x" + std::to_string(p.nz) + ((p.mu_eff > 0.0) ? "v" : "e");
+}
+
+std::string key_prefix(const ns3d_batch* b) {
+  return device_name() + "|batch|mode" + std::to_string(b->mode) + "|stages" + std::to_string(b->nstages) + "|";
+}
+
+// Cache key of the tile shape of one grid size.
+std::string size_key(const ns3d_batch* b, int i) { return key_prefix(b) + "size|" + params_key(b->p[i]); }
+
+// Cache key of the branch count of the whole ensemble.
+std::string ensemble_key(const ns3d_batch* b) {
+  std::string k = key_prefix(b) + "branches|";
   for (int i = 0; i < b->count; ++i) {
-    k += std::to_string(b->p[i].nx) + "x" + std::to_string(b->p[i].ny) + "x" + std::to_string(b->p[i].nz);
-    k += (b->p[i].mu_eff > 0.0) ? "v" : "e";
+    k += params_key(b->p[i]);
     if (i + 1 < b->count) k += ",";
   }
   return k;
 }
 
-// Look the key up in a JSON-lines cache ({"key": "...", "variant": N, ...} per line).
-int cache_lookup(const char* path, const std::string& key) {
+// Look the key up in a JSON-lines cache ({"key": "...", "<field>": N, ...} per line); the last
+// matching line wins, -1 if none.
+int cache_lookup(const char* path, const std::string& key, const char* field) {
   if (!path) return -1;
   FILE* f = fopen(path, "r");
   if (!f) return -1;
-  const std::string needle = "\"key\": \"" + key + "\"";
-  std::vector<char> line(1 << 16);
+  const std::string needle = "\"key\": \"" + key + "\",";
+  const std::string fneedle = std::string("\"") + field + "\": ";
+  std::vector<char> line(1 << 17);
   int found = -1;
   while (fgets(line.data(), (int)line.size(), f)) {
     if (strstr(line.data(), needle.c_str())) {
-      const char* v = strstr(line.data(), "\"variant\": ");
-      if (v) found = atoi(v + 11);
+      const char* v = strstr(line.data(), fneedle.c_str());
+      if (v) found = atoi(v + fneedle.size());
     }
   }
   fclose(f);
   return found;
+}
+
+void cache_append(const char* path, const std::string& key, const char* field, int value, const double* ms, int nms) {
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "{\"key\": \"%s\", \"%s\": %d, \"ms_per_step\": [", key.c_str(), field, value);
+  for (int k = 0; k < nms; ++k) fprintf(f, "%s%.4f", k ? ", " : "", ms[k]);
+  fprintf(f, "]}\n");
+  fclose(f);
+}
+
+// Time one step of fn() on b->stream (after one untimed warm-up step); -1 on failure.
+template <typename F>
+double time_step(ns3d_batch* b, F&& fn) {
+  if (fn() != NS3D_OK) return -1.0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1.0;
+  float t = -1.f;
+  cudaEventRecord(e0, b->stream);
+  const int rc = fn();
+  cudaEventRecord(e1, b->stream);
+  if (rc != NS3D_OK || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+    t = -1.f;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return t;
 }
 
 }  // namespace
@@ -520,11 +557,18 @@ int ns3d_batch_init(const ns3d_params* params, int count, void* cuda_stream, ns3
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
-  if (prepare_batch_kernels() != cudaSuccess ||
-      cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
-    delete b;
+  bool sok = prepare_batch_kernels() == cudaSuccess &&
+             cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; k < ns3d_batch::MAX_BRANCHES && sok; ++k)
+    sok = cudaStreamCreateWithFlags(&b->branch[k], cudaStreamNonBlocking) == cudaSuccess &&
+          cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!sok) {
+    cudaGetLastError();
+    ns3d_batch_free(b);
     return NS3D_ECUDA;
   }
+  b->ivar.assign(count, 0);
   b->inst.resize(count);
   b->pt_off.assign(count + 1, 0);
   long long maxN = 0;
@@ -568,7 +612,8 @@ int ns3d_batch_init(const ns3d_params* params, int count, void* cuda_stream, ns3
             cudaMalloc(&b->d_pt_off, sizeof(long long) * (count + 1)) == cudaSuccess &&
             cudaMalloc(&b->d_tile_off, sizeof(long long) * 3 * (count + 1)) == cudaSuccess &&
             cudaMalloc(&b->d_status, sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&b->partials, sizeof(double) * 16 * (size_t)b->nstat_blocks) == cudaSuccess;
+            cudaMalloc(&b->partials, sizeof(double) * 16 * (size_t)b->nstat_blocks) == cudaSuccess &&
+            cudaMalloc(&b->d_stats, sizeof(double) * NS3D_STATS_NDOUBLE * (size_t)count) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     ns3d_batch_free(b);
@@ -596,7 +641,13 @@ void ns3d_batch_free(ns3d_batch* b) {
   cudaFree(b->d_tile_off);
   cudaFree(b->d_status);
   cudaFree(b->partials);
+  cudaFree(b->d_stats);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (int k = 0; k < ns3d_batch::MAX_BRANCHES; ++k) {
+    if (b->branch[k]) cudaStreamDestroy(b->branch[k]);
+    if (b->join[k]) cudaEventDestroy(b->join[k]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   delete b;
 }
 
@@ -620,9 +671,26 @@ int ns3d_batch_set_variant(ns3d_batch* b, int variant) {
   if (!b || variant < 0 || variant >= DIR_VARIANTS) return NS3D_EINVAL;
   if (b->mode == 0 && variant != 0) return NS3D_EINVAL;
   b->variant = variant;
+  b->ivar.assign(b->count, variant);
   b->pers_ctas = 0;
   b->persistent_graph = -1;
+  drop_graphs(b);
   return rebuild(b);
+}
+
+int ns3d_batch_set_instance_variant(ns3d_batch* b, int i, int variant) {
+  if (!b || i < 0 || i >= b->count || variant < 0 || variant >= DIR_VARIANTS) return NS3D_EINVAL;
+  if (b->mode == 0 && variant != 0) return NS3D_EINVAL;
+  b->ivar[i] = variant;
+  drop_graphs(b);
+  return rebuild(b);
+}
+
+int ns3d_batch_set_branches(ns3d_batch* b, int branches) {
+  if (!b || branches < 1 || branches > ns3d_batch::MAX_BRANCHES) return NS3D_EINVAL;
+  b->branches = branches;
+  drop_graphs(b);
+  return NS3D_OK;
 }
 
 int ns3d_batch_step(ns3d_batch* b, int nsteps, int schedule) {
@@ -643,7 +711,7 @@ int ns3d_batch_step(ns3d_batch* b, int nsteps, int schedule) {
 
 int ns3d_batch_stats(ns3d_batch* b, double* out_dev) {
   if (!b || !out_dev) return NS3D_EINVAL;
-  if (!b->ready) return berr(b, NS3D_EINVAL, "set states and dt first");
+  if (b->u.empty()) return berr(b, NS3D_EINVAL, "set states first");
   for (int i = 0; i < b->count; ++i) {
     const Inst& in = b->inst[i];
     cudaError_t e = launch_prim(in.g, b->u[i], in.pm, in.gamma, b->d_status, b->stream, b->mode);
@@ -654,6 +722,28 @@ int ns3d_batch_stats(ns3d_batch* b, double* out_dev) {
     if (e != cudaSuccess) return berr(b, NS3D_ECUDA, cudaGetErrorString(e));
   }
   return NS3D_OK;
+}
+
+int ns3d_batch_set_dt_from_cfl(ns3d_batch* b, double cfl, double* dt_out) {
+  if (!b) return NS3D_EINVAL;
+  if (!(cfl > 0.0) || !isfinite(cfl)) return berr(b, NS3D_EINVAL, "cfl must be finite and > 0");
+  if (b->u.empty()) return berr(b, NS3D_EINVAL, "set states first");
+  int rc = ns3d_batch_stats(b, b->d_stats);
+  if (rc) return rc;
+  std::vector<double> st((size_t)b->count * NS3D_STATS_NDOUBLE);
+  cudaError_t e = cudaMemcpyAsync(st.data(), b->d_stats, sizeof(double) * st.size(), cudaMemcpyDeviceToHost,
+                                  b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return berr(b, NS3D_ECUDA, cudaGetErrorString(e));
+  std::vector<double> dt(b->count);
+  for (int i = 0; i < b->count; ++i) {
+    const double w = st[(size_t)i * NS3D_STATS_NDOUBLE + 9];
+    if (!(w > 0.0) || !isfinite(w)) return berr(b, NS3D_ENONPHYSICAL, "an instance has no finite positive wave speed");
+    dt[i] = cfl / w;
+  }
+  rc = ns3d_batch_set_dt(b, dt.data());
+  if (rc == NS3D_OK && dt_out) memcpy(dt_out, dt.data(), sizeof(double) * b->count);
+  return rc;
 }
 
 int ns3d_batch_check(ns3d_batch* b) {
@@ -671,66 +761,117 @@ int ns3d_batch_check(ns3d_batch* b) {
 int ns3d_batch_autotune(ns3d_batch* b, const char* cache_path, double* ms_out) {
   if (!b) return NS3D_EINVAL;
   if (!b->ready) return berr(b, NS3D_EINVAL, "set states and dt first");
-  if (b->mode == 0) return NS3D_OK;  // a single tile shape
-  const std::string key = tune_key(b);
-  const int cached = cache_lookup(cache_path, key);
-  if (cached >= 0 && cached < DIR_VARIANTS) {
-    if (ms_out)
-      for (int v = 0; v < DIR_VARIANTS; ++v) ms_out[v] = -1.0;
-    return ns3d_batch_set_variant(b, cached);
+  if (ms_out)
+    for (int k = 0; k < DIR_VARIANTS * b->count + ns3d_batch::MAX_BRANCHES; ++k) ms_out[k] = -1.0;
+  // size classes: instances with the same grid (and viscous or not)
+  std::vector<std::string> cls(b->count);
+  std::vector<std::string> names;
+  std::vector<std::vector<int>> members;
+  for (int i = 0; i < b->count; ++i) {
+    cls[i] = size_key(b, i);
+    const size_t c = std::find(names.begin(), names.end(), cls[i]) - names.begin();
+    if (c == names.size()) {
+      names.push_back(cls[i]);
+      members.emplace_back();
+    }
+    members[c].push_back(i);
+  }
+  std::vector<int> pending;  // classes that need timing
+  for (size_t c = 0; c < names.size(); ++c) {
+    const int v = (b->mode == 1) ? cache_lookup(cache_path, names[c], "variant") : 0;  // strict: one shape
+    if (v >= 0 && v < DIR_VARIANTS) {
+      for (int i : members[c]) b->ivar[i] = v;
+    } else {
+      pending.push_back((int)c);
+    }
+  }
+  const std::string ekey = ensemble_key(b);
+  const int cached_branches = cache_lookup(cache_path, ekey, "branches");
+  if (pending.empty() && cached_branches >= 1 && cached_branches <= ns3d_batch::MAX_BRANCHES) {
+    b->branches = cached_branches;
+    drop_graphs(b);
+    return rebuild(b);
   }
   // time the candidates on copies of the states (the caller's states are not advanced)
   std::vector<double*> saved = b->u, tmp(b->count, nullptr);
   int rc = NS3D_OK;
   for (int i = 0; i < b->count && rc == NS3D_OK; ++i) {
     const size_t bytes = sizeof(double) * 5 * (size_t)b->inst[i].g.N;
-    if (cudaMalloc(&tmp[i], bytes) != cudaSuccess) rc = NS3D_ENOMEM;
-    else if (cudaMemcpyAsync(tmp[i], saved[i], bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
-      rc = NS3D_ECUDA;
+    if (cudaMalloc(&tmp[i], bytes) != cudaSuccess) {
+      cudaGetLastError();
+      rc = berr(b, NS3D_ENOMEM, "autotuner state copies");
+    } else if (cudaMemcpyAsync(tmp[i], saved[i], bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess) {
+      rc = berr(b, NS3D_ECUDA, "autotuner state copies");
+    }
   }
-  double ms[DIR_VARIANTS] = {0};
-  int best = 0;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
   if (rc == NS3D_OK) {
     b->u = tmp;
-    for (int v = 0; v < DIR_VARIANTS && rc == NS3D_OK; ++v) {
-      rc = ns3d_batch_set_variant(b, v);
-      if (rc == NS3D_OK) rc = ns3d_batch_step(b, 1, NS3D_BATCH_GRAPH);  // warm-up + capture
-      if (rc == NS3D_OK) {
-        cudaEventRecord(e0, b->stream);
-        rc = ns3d_batch_step(b, 1, NS3D_BATCH_GRAPH);
-        cudaEventRecord(e1, b->stream);
-        float t = 0.f;
-        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
-          rc = NS3D_ECUDA;
-        ms[v] = t;
-        if (t < ms[best]) best = v;
+    // tile shape per size class: one sequential step of the class's instances per candidate
+    for (int c : pending) {
+      double ms[DIR_VARIANTS];
+      int best = 0;
+      for (int v = 0; v < DIR_VARIANTS; ++v) {
+        ms[v] = -1.0;
+        if (b->mode == 0 && v > 0) continue;
+        for (int i : members[c]) b->ivar[i] = v;
+        if ((rc = rebuild(b)) != NS3D_OK) break;
+        ms[v] = time_step(b, [&] { return step_sequential(b, members[c]); });
+        if (ms[v] < 0) {
+          rc = berr(b, NS3D_ECUDA, "autotuner timing");
+          break;
+        }
+        if (ms[v] < ms[best]) best = v;
+      }
+      if (rc != NS3D_OK) break;
+      for (int i : members[c]) {
+        b->ivar[i] = best;
+        if (ms_out)
+          for (int v = 0; v < DIR_VARIANTS; ++v) ms_out[i * DIR_VARIANTS + v] = ms[v];
+      }
+      if (b->mode == 1) cache_append(cache_path, names[c], "variant", best, ms, DIR_VARIANTS);
+    }
+    // graph branches for the chosen shapes: one graph-scheduled step per candidate count
+    if (rc == NS3D_OK && (rc = rebuild(b)) == NS3D_OK) {
+      if (cached_branches >= 1 && cached_branches <= ns3d_batch::MAX_BRANCHES) {
+        b->branches = cached_branches;
+      } else {
+        double ms[ns3d_batch::MAX_BRANCHES];
+        int best = 1;
+        for (int nb = 1; nb <= ns3d_batch::MAX_BRANCHES; ++nb) ms[nb - 1] = -1.0;
+        for (int nb = 1; nb <= std::min(b->count, (int)ns3d_batch::MAX_BRANCHES); nb *= 2) {
+          b->branches = nb;
+          drop_graphs(b);
+          ms[nb - 1] = time_step(b, [&] { return step_graph(b, 1); });
+          if (ms[nb - 1] < 0) {
+            rc = berr(b, NS3D_ECUDA, "autotuner timing");
+            break;
+          }
+          if (ms[nb - 1] < ms[best - 1]) best = nb;
+        }
+        if (rc == NS3D_OK) {
+          b->branches = best;
+          if (ms_out)
+            for (int k = 0; k < ns3d_batch::MAX_BRANCHES; ++k) ms_out[DIR_VARIANTS * b->count + k] = ms[k];
+          cache_append(cache_path, ekey, "branches", best, ms, ns3d_batch::MAX_BRANCHES);
+        }
       }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   cudaStreamSynchronize(b->stream);
   for (double* p : tmp) cudaFree(p);
   b->u = saved;
+  drop_graphs(b);
   ns3d_batch_check(b);  // the timing runs may have flagged the copies; clear the word
-  if (rc != NS3D_OK) {
-    rebuild(b);
-    return rc;
-  }
-  if (ms_out)
-    for (int v = 0; v < DIR_VARIANTS; ++v) ms_out[v] = ms[v];
-  if (cache_path) {
-    FILE* f = fopen(cache_path, "a");
-    if (f) {
-      fprintf(f, "{\"key\": \"%s\", \"variant\": %d, \"ms_per_step\": [%.4f, %.4f, %.4f]}\n", key.c_str(), best, ms[0],
-              ms[1], ms[2]);
-      fclose(f);
-    }
-  }
-  return ns3d_batch_set_variant(b, best);
+  const int rc2 = rebuild(b);
+  return rc != NS3D_OK ? rc : rc2;
+}
+
+int ns3d_batch_schedule_info(const ns3d_batch* b, int* variants, int* branches) {
+  if (!b) return NS3D_EINVAL;
+  if (variants)
+    for (int i = 0; i < b->count; ++i) variants[i] = b->ivar[i];
+  if (branches) *branches = b->branches;
+  return NS3D_OK;
 }
 
 int ns3d_batch_info(const ns3d_batch* b, int* variant, int* persistent_ctas_per_sm, int* persistent_in_graph) {

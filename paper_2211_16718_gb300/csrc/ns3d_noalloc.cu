@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(NA_THREADS) k_stats_noalloc(const double* __re
     const double c = sqrt(gamma * pr * ri);
 #pragma unroll
     for (int d = 0; d < 3; ++d) r.wmax = fmax(r.wmax, (fabs(vel[d]) + c) * rh[d]);
-    if (!(rho > 0.0) || !(pr > 0.0) || !isfinite(e) || !isfinite(mx + my + mz)) r.bad = 1.0;
+    if (!(rho > 0.0) || !isfinite(rho) || !(pr > 0.0) || !isfinite(e) || !isfinite(mx + my + mz)) r.bad = 1.0;
   }
   r = na_block(r);
   if (threadIdx.x == 0) {

@@ -229,3 +229,31 @@ def isotropic_turbulence_device(n: int, seed: int, nbase: int = 64, u0: float = 
     p = 1.0 / gamma
     out[4] = p / (gamma - 1.0) + 0.5 * (out[1] * out[1] + out[2] * out[2] + out[3] * out[3])
     return out
+
+
+def isotropic_turbulence_planes(n: int, seed: int, z0: int, count: int, nbase: int = 64, u0: float = 0.3,
+                                k0: float = 4.0, gamma: float = GAMMA) -> np.ndarray:
+    """The z-planes z0, z0 + 1, ..., z0 + count - 1 (periodic) of the state that
+    isotropic_turbulence_device(n, seed, nbase) builds, computed on the host without the
+    whole n^3 field: the band-limited velocity is summed over its base-grid wavenumbers
+    along z at the requested planes only, then inverse-transformed in x and y plane by
+    plane.  Equal to the device field up to rounding.  Returns u[5, count, n, n]."""
+    if n < nbase:
+        raise ValueError("n must be >= nbase")
+    vel = hit_velocity(nbase, seed, u0, k0)
+    h = nbase // 2
+    zs = (z0 + np.arange(count)) % n
+    kz = np.fft.fftfreq(nbase, d=1.0 / nbase)
+    E = np.exp(2j * math.pi * np.outer(zs, kz) / n)  # [count, nbase]
+    out = np.empty((5, count, n, n), dtype=np.float64)
+    out[0] = 1.0
+    for c in range(3):
+        small = np.fft.rfftn(vel[c])  # [nbase (kz), nbase (ky), h + 1 (kx)]
+        a = np.tensordot(E, small, axes=(1, 0))  # [count, nbase (ky), h + 1]
+        big = np.zeros((count, n, n // 2 + 1), dtype=np.complex128)
+        big[:, :h, : h + 1] = a[:, :h]
+        big[:, n - h:, : h + 1] = a[:, h:]
+        out[1 + c] = np.fft.irfft2(big, s=(n, n), axes=(1, 2)) * (float(n) ** 2 / float(nbase) ** 3)
+    p = 1.0 / gamma
+    out[4] = p / (gamma - 1.0) + 0.5 * (out[1] * out[1] + out[2] * out[2] + out[3] * out[3])
+    return out

@@ -8,7 +8,6 @@ cannot be loaded, every call raises ``RuntimeError`` (there is no fallback).
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 import threading
 
@@ -27,7 +26,7 @@ FUNCTIONALS = {"ke": NS3D_FUNC_KE, "enstrophy": NS3D_FUNC_ENSTROPHY}
 EXPORTS = ("ns3d_default_params", "ns3d_init", "ns3d_free", "ns3d_set_stream", "ns3d_rhs", "ns3d_rk_step",
            "ns3d_stats", "ns3d_stats_async", "ns3d_step_host", "ns3d_check", "ns3d_strerror", "ns3d_last_error",
            "ns3d_timing_enable", "ns3d_timing_read", "ns3d_alu_probe", "ns3d_rhs_vjp", "ns3d_rk_step_vjp",
-           "ns3d_functional", "ns3d_traj_forward", "ns3d_traj_vjp", "ns3d_storage_info")
+           "ns3d_functional", "ns3d_traj_forward", "ns3d_traj_vjp", "ns3d_storage_info", "ns3d_dt_from_cfl")
 
 
 class Ns3dError(RuntimeError):
@@ -96,6 +95,7 @@ def lib():
                 "ns3d_traj_forward": (I, [P, P, D, I, I]),
                 "ns3d_traj_vjp": (I, [P, P]),
                 "ns3d_storage_info": (I, [P, P, P]),
+                "ns3d_dt_from_cfl": (I, [P, P, D, P]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(L, name)
@@ -137,6 +137,7 @@ class Solver:
         self.N = nx * ny * nz
         self.shape = (5, nz, ny, nx)
         self._ctx = ctypes.c_void_p()
+        self.traj_generation = 0  # counts ns3d_traj_forward calls: which recording the library holds
         rc = lib().ns3d_init(ctypes.byref(self.params), _stream_handle(), ctypes.byref(self._ctx))
         if rc != NS3D_OK:
             raise Ns3dError(rc, lib().ns3d_strerror(rc).decode())
@@ -236,6 +237,7 @@ class Solver:
     def traj_forward(self, u, dt: float, nsteps: int, every: int = 16):
         """Advance u by nsteps steps, recording checkpoints every `every` steps (ns3d_traj_forward)."""
         self._sync_stream()
+        self.traj_generation += 1
         self._check(lib().ns3d_traj_forward(self._ctx, _dptr(u, 5 * self.N), float(dt), int(nsteps), int(every)))
         return u
 
@@ -274,11 +276,11 @@ class Solver:
             pass
 
     def dt_from_cfl(self, u, cfl: float) -> float:
-        """dt = CFL / max over points and directions of (|u_d| + c)/dx_d (on the device)."""
-        w = self.stats(u)["max_wavespeed_over_dx"]
-        if not (w > 0 and math.isfinite(w)):
-            raise Ns3dError(NS3D_ENONPHYSICAL, "no finite positive wave speed")
-        return cfl / w
+        """dt = CFL / max over points and directions of (|u_d| + c)/dx_d (ns3d_dt_from_cfl)."""
+        dt = ctypes.c_double()
+        self._sync_stream()
+        self._check(lib().ns3d_dt_from_cfl(self._ctx, _dptr(u, 5 * self.N), float(cfl), ctypes.byref(dt)))
+        return dt.value
 
 
 def alu_probe() -> dict:
@@ -358,6 +360,14 @@ class Batch:
         arr = (ctypes.c_double * self.count)(*[float(d) for d in dts])
         self._err(_batch_fn("ns3d_batch_set_dt", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p])(self._b, arr))
 
+    def set_dt_from_cfl(self, cfl: float):
+        """Each instance's dt from its own current state at one CFL number
+        (ns3d_batch_set_dt_from_cfl); returns the time steps."""
+        arr = (ctypes.c_double * self.count)()
+        self._err(_batch_fn("ns3d_batch_set_dt_from_cfl", ctypes.c_int,
+                            [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p])(self._b, float(cfl), arr))
+        return list(arr)
+
     def set_variant(self, v: int):
         self._err(_batch_fn("ns3d_batch_set_variant", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int])(self._b, int(v)))
 
@@ -375,12 +385,32 @@ class Batch:
     def check(self):
         self._err(_batch_fn("ns3d_batch_check", ctypes.c_int, [ctypes.c_void_p])(self._b))
 
-    def autotune(self, cache_path=None):
-        ms = (ctypes.c_double * 3)()
+    def set_instance_variant(self, i: int, v: int):
+        self._err(_batch_fn("ns3d_batch_set_instance_variant", ctypes.c_int,
+                            [ctypes.c_void_p, ctypes.c_int, ctypes.c_int])(self._b, int(i), int(v)))
+
+    def set_branches(self, nb: int):
+        self._err(_batch_fn("ns3d_batch_set_branches", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int])(self._b, int(nb)))
+
+    def autotune(self, cache_path=None) -> dict:
+        """Per grid size the tile shape, then the graph's branch count (ns3d_batch_autotune).
+        Returns {"variants": per instance, "branches": n, "ms_variants": per instance [3],
+        "ms_branches": [8]} (-1: not timed)."""
+        ms = (ctypes.c_double * (3 * self.count + 8))()
         path = cache_path.encode() if cache_path else None
         self._err(_batch_fn("ns3d_batch_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_void_p])(
             self._b, path, ms))
-        return self.info()["variant"], list(ms)
+        out = self.schedule_info()
+        out["ms_variants"] = [list(ms[3 * i: 3 * i + 3]) for i in range(self.count)]
+        out["ms_branches"] = list(ms[3 * self.count:])
+        return out
+
+    def schedule_info(self) -> dict:
+        v = (ctypes.c_int * self.count)()
+        nb = ctypes.c_int()
+        self._err(_batch_fn("ns3d_batch_schedule_info", ctypes.c_int, [ctypes.c_void_p] * 3)(
+            self._b, v, ctypes.byref(nb)))
+        return {"variants": list(v), "branches": nb.value}
 
     def info(self) -> dict:
         v, c, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

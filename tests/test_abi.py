@@ -79,6 +79,10 @@ def test_null_arguments(lib):
     assert lib.ns3d_step_host(None, None, 0.1, 1, None) == ns3d.NS3D_EINVAL
     assert lib.ns3d_set_zorder(None, 0) == ns3d.NS3D_EINVAL
     assert lib.ns3d_set_variant(None, 0) == ns3d.NS3D_EINVAL
+    assert lib.ns3d_dt_from_cfl(None, None, 0.4, None) == ns3d.NS3D_EINVAL
+    fn = lib.ns3d_batch_set_dt_from_cfl
+    fn.restype, fn.argtypes = ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
+    assert fn(None, 0.4, None) == ns3d.NS3D_EINVAL
     lib.ns3d_free(None)
 
 

@@ -207,6 +207,45 @@ def test_autograd_functions_agree_with_the_c_calls(ns3d):
     s.close()
 
 
+def test_autograd_chained_trajectories_on_one_solver(ns3d):
+    """A trajectory followed by a multi-step rk_step on the same Solver: the rk_step's
+    backward runs first and records its own trajectory in the library, so the trajectory's
+    backward must not reverse that recording.  The gradient equals the C-call path (each
+    recording reversed in turn), and two trajectories recorded before one backward give
+    the gradient of the one they belong to."""
+    import torch
+    from paper_2211_16718_gb300 import autograd as A
+    n = (12, 10, 8)
+    u = I.random_smooth(*n, seed=3, amp=0.1, mach=0.4)
+    s = ns3d.Solver(*n, mu_eff=2e-3)
+    dt = 0.03
+    u0 = _dev(u).requires_grad_()
+    ke = A.functional(A.rk_step(A.trajectory(u0, s, dt, 5, every=2), s, dt, nsteps=3), s, "ke")
+    ke.backward()
+    ua = _dev(u)
+    s.traj_forward(ua, dt, 5, 2)
+    ub = ua.clone()
+    s.traj_forward(ub, dt, 3, 3)
+    val, g = s.functional(ub, "ke", grad=True)
+    assert ke.item() == val
+    s.traj_vjp(g)                   # reverse of the 3 steps
+    s.traj_forward(_dev(u), dt, 5, 2)
+    s.traj_vjp(g)                   # reverse of the first 5 steps
+    assert torch.equal(u0.grad, g)
+    # two recordings before one backward: the first trajectory's gradient is its own
+    u1 = _dev(u).requires_grad_()
+    y1 = A.trajectory(u1, s, dt, 4, every=2)
+    y2 = A.trajectory(_dev(u), s, dt, 2, every=1)  # records over the first one
+    A.functional(y1, s, "ke").backward()
+    uc = _dev(u)
+    s.traj_forward(uc, dt, 4, 2)
+    _, g1 = s.functional(uc, "ke", grad=True)
+    s.traj_vjp(g1)
+    assert torch.equal(u1.grad, g1)
+    del y2
+    s.close()
+
+
 def test_gradient_matches_central_differences_of_the_gpu_path(ns3d):
     """d KE(u_N)/d u_0 along seeded directions against central differences of the GPU
     forward path itself (relative step 1e-6 of each field's scale)."""

@@ -106,22 +106,99 @@ def test_strict_mode_persistent(ns3d):
 
 
 def test_autotune_caches_and_keeps_states(ns3d, tmp_path):
+    """Per grid size the fastest tile shape of its own timings, then the branch count; one
+    cache line per size plus one for the branches; a second call reads them back."""
     import torch
     states, params, dts = _ensemble(ns3d)
+    states = states + [s.copy() for s in states[:2]]  # two sizes with two instances each
+    params = params + params[:2]
+    dts = dts + dts[:2]
     cache = str(tmp_path / "tune.jsonl")
     b = ns3d.Batch(params)
     ud = [torch.from_numpy(u.copy()).cuda() for u in states]
     b.set_states(ud)
     b.set_dt(dts)
-    v, ms = b.autotune(cache)
-    assert 0 <= v < 3 and all(t > 0 for t in ms) and ms[v] == min(ms)
-    for t, u in zip(ud, states):
-        assert np.array_equal(t.cpu().numpy(), u)
+    t = b.autotune(cache)
+    sizes = [(p.nx, p.ny, p.nz, p.mu_eff > 0) for p in params]
+    for i, v in enumerate(t["variants"]):
+        ms = t["ms_variants"][i]
+        assert 0 <= v < 3 and all(m > 0 for m in ms) and ms[v] == min(ms)
+        for j in range(len(params)):
+            if sizes[j] == sizes[i]:
+                assert t["variants"][j] == v
+    timed = [m for m in t["ms_branches"] if m > 0]
+    assert len(timed) == 4 and t["ms_branches"][t["branches"] - 1] == min(timed)
+    for tt, u in zip(ud, states):
+        assert np.array_equal(tt.cpu().numpy(), u)
     lines = [json.loads(line) for line in open(cache)]
-    assert len(lines) == 1 and lines[0]["variant"] == v
-    v2, ms2 = b.autotune(cache)
-    assert v2 == v and all(t == -1.0 for t in ms2)
+    assert len(lines) == len(set(sizes)) + 1
+    assert sum("branches" in ln for ln in lines) == 1
+    t2 = b.autotune(cache)
+    assert t2["variants"] == t["variants"] and t2["branches"] == t["branches"]
+    assert all(m == -1.0 for row in t2["ms_variants"] for m in row) and all(m == -1.0 for m in t2["ms_branches"])
+    assert len(open(cache).readlines()) == len(lines)
     b.close()
+
+
+@pytest.mark.parametrize("branches", [1, 3, 8])
+def test_mixed_instance_variants_and_branches_bitwise(ns3d, branches):
+    """Per-instance tile shapes and any branch count give the bits of per-instance contexts."""
+    import torch
+    states, params, dts = _ensemble(ns3d)
+    ref = []
+    for u, p, dt in zip(states, params, dts):
+        s = ns3d.Solver(p.nx, p.ny, p.nz, mu_eff=p.mu_eff)
+        ud = torch.from_numpy(u.copy()).cuda()
+        s.rk_step(ud, dt, 2)
+        ref.append(ud.cpu().numpy())
+        s.close()
+    for schedule in ("sequential", "graph"):
+        b = ns3d.Batch(params)
+        ud = [torch.from_numpy(u.copy()).cuda() for u in states]
+        b.set_states(ud)
+        b.set_dt(dts)
+        for i in range(len(params)):
+            b.set_instance_variant(i, (i + branches) % 3)
+        b.set_branches(branches)
+        b.step(2, schedule)
+        b.check()
+        assert b.schedule_info() == {"variants": [(i + branches) % 3 for i in range(len(params))],
+                                     "branches": branches}
+        for t, r in zip(ud, ref):
+            assert np.array_equal(t.cpu().numpy(), r), schedule
+        b.close()
+
+
+def test_ensemble_of_the_benchmark_sizes(ns3d, oracle):
+    """The ensemble sizes of the benchmark (32^3 .. 128^3 decaying turbulence, two instances
+    per size, dt from CFL 0.4 each), autotuned, 2 graph-scheduled RK4 steps: one instance of
+    each size against the oracle (1e-10 relative after the steps), the other bitwise against
+    its own context."""
+    import torch
+    sizes = [32, 48, 64, 96, 128]
+    mu = I.hit_mu_eff()
+    states = [I.isotropic_turbulence(n, seed=k) for k in range(2) for n in sizes]
+    params = [ns3d.default_params(u.shape[-1], u.shape[-1], u.shape[-1], mu_eff=mu) for u in states]
+    b = ns3d.Batch(params)
+    ud = [torch.from_numpy(u.copy()).cuda() for u in states]
+    b.set_states(ud)
+    dts = b.set_dt_from_cfl(0.4)
+    b.autotune(None)
+    b.step(2, "graph")
+    b.check()
+    out = [t.cpu().numpy() for t in ud]
+    b.close()
+    for i, (u, p, dt) in enumerate(zip(states, params, dts)):
+        n = p.nx
+        if i < len(sizes):
+            ref = oracle.rk_step(oracle.Params(n, n, n, mu_eff=mu), u, dt, 2)
+            assert np.abs(out[i] - ref).max() / np.abs(ref).max() <= 1e-10, n
+        else:
+            s = ns3d.Solver(n, n, n, mu_eff=mu)
+            x = torch.from_numpy(u.copy()).cuda()
+            s.rk_step(x, dt, 2)
+            assert np.array_equal(out[i], x.cpu().numpy()), n
+            s.close()
 
 
 def test_batch_stats_match_contexts(ns3d):
@@ -137,6 +214,30 @@ def test_batch_stats_match_contexts(ns3d):
         out = torch.zeros(ns3d.NS3D_STATS_NDOUBLE, dtype=torch.float64, device="cuda")
         s.stats_async(torch.from_numpy(u.copy()).cuda(), out)
         assert np.array_equal(st[i, :10], out.cpu().numpy()[:10])
+    b.close()
+
+
+def test_batch_dt_from_cfl_equals_contexts(ns3d):
+    """ns3d_batch_set_dt_from_cfl gives each instance the time step its own context computes
+    (ns3d_dt_from_cfl, the same kernels: the same bits) and applies it."""
+    import torch
+    states, params, _ = _ensemble(ns3d)
+    b = ns3d.Batch(params)
+    ud = [torch.from_numpy(u.copy()).cuda() for u in states]
+    b.set_states(ud)
+    dts = b.set_dt_from_cfl(0.4)
+    ref = []
+    for u, p in zip(states, params):
+        s = ns3d.Solver(p.nx, p.ny, p.nz, mu_eff=p.mu_eff)
+        ref.append(s.dt_from_cfl(torch.from_numpy(u.copy()).cuda(), 0.4))
+        s.close()
+    assert dts == ref
+    b.step(1, "graph")
+    out = [t.cpu().numpy() for t in ud]
+    exp, _ = _run_batch(ns3d, states, params, ref, "graph", 1)
+    assert all(np.array_equal(a, e) for a, e in zip(out, exp))
+    with pytest.raises(ns3d.Ns3dError):
+        b.set_dt_from_cfl(-1.0)
     b.close()
 
 

@@ -203,6 +203,24 @@ def test_stats_match_oracle_ragged(ns3d, orc, name, make, kw, prec):
     s.close()
 
 
+def test_dt_from_cfl_matches_oracle(ns3d, orc):
+    """ns3d_dt_from_cfl: dt = CFL / max over points and directions of (|u_d| + c)/dx_d of the
+    state, against the oracle's wave speed; bad CFL numbers and non-physical states are errors."""
+    u = I.isotropic_turbulence(32, seed=2)
+    so = orc.stats(orc.Params(32, 32, 32), u)
+    s = ns3d.Solver(32, 32, 32, mu_eff=I.hit_mu_eff())
+    assert s.dt_from_cfl(_gpu(u), 0.4) == pytest.approx(0.4 / so["max_wavespeed_over_dx"], rel=1e-12, abs=0)
+    for bad in (0.0, -0.1, float("nan"), float("inf")):
+        with pytest.raises(ns3d.Ns3dError):
+            s.dt_from_cfl(_gpu(u), bad)
+    ub = u.copy()
+    ub[0, 1, 2, 3] = -1.0
+    with pytest.raises(ns3d.NonPhysicalError):
+        s.dt_from_cfl(_gpu(ub), 0.4)
+    s.check()
+    s.close()
+
+
 def test_stats_async_equals_stats(ns3d):
     import torch
     u = _gpu(I.taylor_green(16))
@@ -301,10 +319,12 @@ def test_set_zorder_rejects_bad_order(ns3d):
     s.close()
 
 
-def test_nonphysical_state_is_reported_and_cleared(ns3d):
+@pytest.mark.parametrize("prec", list(PRECISIONS) + ["fp32_bulk"])
+@pytest.mark.parametrize("rho_bad", [-1.0, float("inf")], ids=["negative_rho", "infinite_rho"])
+def test_nonphysical_state_is_reported_and_cleared(ns3d, rho_bad, prec):
     u = I.random_smooth(16, 16, 16, seed=10, amp=0.1)
-    u[0, 3, 4, 5] = -1.0
-    s = ns3d.Solver(16, 16, 16)
+    u[0, 3, 4, 5] = rho_bad
+    s = ns3d.Solver(16, 16, 16, precision=PRECISIONS.get(prec, ns3d.NS3D_FP32_BULK))
     ud = _gpu(u)
     s.rhs(ud)
     with pytest.raises(ns3d.NonPhysicalError):

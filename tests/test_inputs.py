@@ -108,3 +108,15 @@ def test_device_turbulence_is_the_spectral_interpolant_of_the_base_grid():
     div = sum(np.fft.ifftn(1j * k.reshape(sh) * np.fft.fftn(u[1 + c])).real
               for c, sh in enumerate([(1, 1, 48), (1, 48, 1), (48, 1, 1)]))
     assert np.abs(div).max() <= 1e-12
+
+
+def test_turbulence_planes_equal_the_device_field():
+    """The host-side planes generator gives the same planes as the device generator (run on
+    the CPU here), including planes across the periodic wrap."""
+    import numpy as np
+    pytest.importorskip("torch")
+    from paper_2211_16718_gb300 import inputs as I
+    full = I.isotropic_turbulence_device(48, seed=5, nbase=16, device="cpu").numpy()
+    planes = I.isotropic_turbulence_planes(48, seed=5, z0=44, count=9, nbase=16)
+    zs = [(44 + j) % 48 for j in range(9)]
+    assert np.abs(planes - full[:, zs]).max() <= 1e-14

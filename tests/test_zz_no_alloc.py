@@ -6,7 +6,8 @@ cudaMalloc (creating a context allocates scratch).  This entry point keeps its o
 scratch in a fixed file-scope device array.  The test calls it through the C ABI and
 compares it with the context-based statistics (ns3d_stats_async) within the tolerance
 the parity tests use for statistics (1e-12 relative), on two calls in a row with
-different grids, then checks that a non-physical flag does not carry over.
+different grids, compares one call directly with the CPU oracle's statistics, then
+checks that a non-physical flag (negative or infinite density) does not carry over.
 This file is collected last; it passes alone in a fresh process and after the others.
 """
 import ctypes
@@ -80,10 +81,31 @@ def test_noalloc_stats_match_context_stats_two_calls(ns3d):
         assert got[10] == 0.0 and ref[10] == 0.0
 
 
-def test_noalloc_flags_nonphysical_without_carry_over(ns3d):
+def test_noalloc_stats_match_oracle(ns3d):
+    """One call compared directly with the FP64 CPU oracle's statistics (Sec. 2.3 reading:
+    sums times the cell volume, volume means of KE and enstrophy, minima, CFL wave speed)."""
+    import torch
+    from oracle import oracle as O
+    O.build()
+    u_np = I.isotropic_turbulence(32, seed=6)
+    so = O.stats(O.Params(32, 32, 32), u_np)
+    p = ns3d.default_params(32, 32, 32)
+    out = torch.full((ns3d.NS3D_STATS_NDOUBLE,), float("nan"), dtype=torch.float64, device="cuda")
+    assert _call_c_abi(ns3d, p, torch.from_numpy(u_np).cuda(), out) == ns3d.NS3D_OK
+    got = out.cpu().numpy()
+    for k, name in enumerate(ns3d.STATS_FIELDS):
+        if name.startswith("mom"):
+            assert abs(got[k] - so[name]) <= STATS_TOL * so["mass"], name
+        else:
+            assert got[k] == pytest.approx(so[name], rel=STATS_TOL, abs=0.0), name
+    assert got[10] == 0.0
+
+
+@pytest.mark.parametrize("rho_bad", [-0.5, float("inf")], ids=["negative_rho", "infinite_rho"])
+def test_noalloc_flags_nonphysical_without_carry_over(ns3d, rho_bad):
     import torch
     bad = I.random_smooth(16, 16, 16, seed=5, amp=0.1)
-    bad[0, 2, 3, 4] = -0.5
+    bad[0, 2, 3, 4] = rho_bad
     good = I.random_smooth(16, 16, 16, seed=5, amp=0.1)
     p = ns3d.default_params(16, 16, 16)
     out = torch.zeros(ns3d.NS3D_STATS_NDOUBLE, dtype=torch.float64, device="cuda")
