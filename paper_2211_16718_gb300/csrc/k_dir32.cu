@@ -1,13 +1,25 @@
-// FP32-bulk direction pass (precision NS3D_FP32_BULK): the same fused WENO5 +
-// Roe + conservative difference + viscous divergence as k_dir.cu, with the
-// point fluxes, smoothness indicators, weights, interface values and the Roe
-// flux in FP32 (arXiv 2211.16718, Sec. 2.2 arithmetic unchanged, precision
-// reduced).  The interface fluxes are widened to FP64 before the conservative
-// difference, so the sum over the grid still telescopes exactly; the viscous
-// divergence, the accumulation / RK stage update and the state stay in FP64.
-// FP64 <-> FP32 conversions use integer bit manipulation (round to nearest), so
-// the FP64 pipe only carries the difference, the viscous divergence and the
-// epilogue.
+// FP32-bulk direction pass (precision NS3D_FP32_BULK): the fused WENO5 + Roe +
+// conservative difference + viscous divergence of k_dir.cu with the primitive
+// variables, point fluxes, smoothness indicators, weights, interface values, the
+// Roe flux and the viscous interface flux in FP32 (arXiv 2211.16718, Sec. 2.2
+// arithmetic unchanged, precision reduced).  The total interface flux is widened
+// to FP64 before the conservative difference, so the sums over the grid still
+// telescope exactly; the accumulation / RK stage update and the state stay FP64.
+//
+// Layout of one tile (TP points along the pencil x W lines, 256 threads):
+//  A   load the state (FP64, converted to FP32 by bit manipulation) at the tile's
+//      points and a 3-point halo, form the primitive variables and point fluxes in
+//      registers (no primitive planes are read), and the viscous flux of this
+//      direction (FP32 planes of the viscous kernel);
+//  BC  one item = one scalar on one line over SEG consecutive interfaces: the
+//      SEG + 5 point values are read once (vector loads) and slid through in
+//      registers: the window indicators, the left- and right-biased WENO5 values,
+//      and their jump (conserved variables) or sum (flux components);
+//  D   per interface: Roe average, wave strengths with Harten's fix, the central
+//      part, the viscous interface flux (-f_{i-1} + 7 f_i + 7 f_{i+1} - f_{i+2})/12,
+//      divided by dx and widened to FP64;
+//  E   per point: FP64 difference of its two interface fluxes, then the
+//      accumulation / RK epilogue (k prefetched by cp.async during D).
 #include <math.h>
 
 #include "df.cuh"
@@ -18,268 +30,402 @@ namespace ns3d {
 
 namespace {
 
-constexpr int NQ = 9;
-constexpr int THREADS = 256;  // 8 warps per tile: latency hiding for the FP32 chains
+constexpr int THREADS = 256;
+constexpr int TP = 27, W = 8;   // 27 points: 19 tiles cover 512 (513), 38 cover 1024 (1026)
+constexpr int NP = TP + 6;      // positions per line: 3-point halo on each side
+constexpr int NI = TP + 1;      // interfaces per line
+constexpr int SEG = 4;          // interfaces per reconstruction item
+constexpr int NSEG = NI / SEG;  // 7
+static_assert(NI % SEG == 0, "whole segments");
+constexpr int NQ = 9;           // reconstructed scalars: 5 conserved, 4 flux components (f_0 = u_{1+D})
+constexpr int NREC = 10;        // per interface: 5 jumps, the sum of u_{1+D}, 4 flux sums
+constexpr int LS = 36;          // line stride (floats) of the scalar planes: >= SEG*NSEG + 5 and a multiple of 4
+constexpr int L4 = NP;          // line stride (float4) of the Roe-input and viscous planes (odd: no bank conflicts)
+static_assert(SEG * (NSEG - 1) + SEG + 5 <= LS && LS % 4 == 0, "segment reads stay in the line");
+// shared-memory plan (bytes)
+constexpr int OFF_Q = 0;                              // float  [NQ][W][LS]
+constexpr int OFF_R4 = OFF_Q + NQ * W * LS * 4;       // float4 [W][L4]: sqrt(rho), u, v, w
+constexpr int OFF_H = OFF_R4 + W * L4 * 16;           // float  [W][L4]: H
+constexpr int OFF_V4 = OFF_H + ((W * L4 * 4 + 15) & ~15);  // float4 [W][L4]: viscous flux of this direction
+constexpr int OFF_REC = OFF_V4 + W * L4 * 16;         // float  [NREC][W][NI]
+constexpr int FS = 30;          // line stride (doubles) of the interface fluxes (no bank conflicts in y, z)
+constexpr int OFF_F = OFF_REC + NREC * W * NI * 4;    // double [5][W][FS]: interface flux / dx
+constexpr int BYTES = OFF_F + 5 * W * FS * 8;
+static_assert(FS >= NI, "interface-flux line");
+// epilogue operand k (5 doubles per point) prefetched into the scalar planes, dead after BC
+static_assert(5 * TP * W * 8 <= NQ * W * LS * 4, "prefetch slots fit the scalar planes");
+static_assert(OFF_R4 % 16 == 0 && OFF_V4 % 16 == 0 && OFF_F % 8 == 0 && OFF_REC % 16 == 0, "alignment");
+static_assert(TP * W <= THREADS && NI * W <= THREADS, "one point / interface per thread in D and E");
 
-// Tile plan: TP points along the pencil x W lines.  The y and z passes can run 32 x 4 or
-// 16 x 8 tiles (W consecutive x-lines per row of loads).  Every shape computes the same bits
-// (the per-interface arithmetic does not depend on the tiling).
-template <int TP_, int W_>
-struct P32 {
-  static constexpr int TP = TP_, W = W_;
-  static constexpr int NP = TP + 6, NW = TP + 4, NI = TP + 1;
-  // shared-memory plan (4-byte words)
-  static constexpr int OFF_Q = 0;                          // float [NQ][NP*W]
-  static constexpr int OFF_ROE = OFF_Q + NQ * NP * W;      // float [5][NP*W]
-  static constexpr int OFF_B = OFF_ROE + 5 * NP * W;       // float [NQ][3][NW*W]
-  static constexpr int OFF_R = OFF_B + NQ * 3 * NW * W;    // float [18][NI*W]
-  static constexpr int OFF_FV = (OFF_R + 18 * NI * W + 1) & ~1;  // double [4][NP*W]
-  static constexpr int OFF_F = OFF_FV + 2 * 4 * NP * W;    // double [5][NI*W]
-  static constexpr int WORDS = OFF_F + 2 * 5 * NI * W;
-  static constexpr int BYTES = WORDS * 4;
-};
+// FP64 -> FP32 by truncating the bit pattern (integer instructions only): sign and exponent
+// exact for |x| in [2^-126, 2^128); smaller magnitudes give signed zero, larger ones, infinities
+// and NaNs give +-inf (a non-finite state is then reported by the checks of phase A).
+__device__ __forceinline__ float d2f_tz(double x) {
+  const uint32_t h = (uint32_t)__double2hiint(x), l = (uint32_t)__double2loint(x);
+  const uint32_t e11 = (h >> 20) & 0x7ffu;
+  uint32_t b = __funnelshift_l(l, h, 3) + 0x40000000u;  // rebased exponent, top 23 mantissa bits
+  b = (e11 <= 896u) ? 0u : b;
+  b = (e11 >= 1151u) ? 0x7f800000u : b;
+  return __uint_as_float(b | (h & 0x80000000u));
+}
 
-__device__ __forceinline__ float weno_combine32(float B1, float B2, float B3, float F1, float F2, float F3) {
-  // common power-of-two scaling keeps the products in range (omega is scale-free)
+__device__ __forceinline__ float rcp_a(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_a(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Weighted WENO5 value from the squared scaled indicators B_k = (4 (eps + beta_k))^2 and the
+// candidate values: sum_k omega_k F_k with omega_k ~ c_k / B_k, c = (1, 6, 3)/10, written over the
+// common denominator.  F2x6 = 6 F_2 and F3x3 = 3 F_3 carry the linear weights.  Unscaled
+// products: valid while every B and product stays in the normal FP32 range (checked by the
+// caller), approximate division (2 ulp).
+__device__ __forceinline__ float weno_fast(float B1, float B2, float B3, float F1, float F2x6, float F3x3) {
+  const float p23 = B2 * B3, p13 = B1 * B3, p12 = B1 * B2;
+  const float num = fmaf(p23, F1, fmaf(p13, F2x6, p12 * F3x3));
+  const float den = fmaf(6.0f, p13, fmaf(3.0f, p12, p23));
+  return __fdividef(num, den);
+}
+
+// The same with the indicators rescaled by their common power of two and an IEEE division: any
+// data whose indicators are finite.
+__device__ __forceinline__ float weno_safe(float B1, float B2, float B3, float F1, float F2x6, float F3x3) {
   const int E = max(exponent_of(B1), max(exponent_of(B2), exponent_of(B3)));
-  const float sc = pow2f(-E);
+  const float sc = pow2f(max(-E, -126));
   B1 *= sc;
   B2 *= sc;
   B3 *= sc;
-  const float p23 = B2 * B3;
-  const float t13 = 6.0f * (B1 * B3);
-  const float t12 = 3.0f * (B1 * B2);
-  const float num = fmaf(p23, F1, fmaf(t13, F2, t12 * F3));
-  const float den = p23 + t13 + t12;
+  const float p23 = B2 * B3, p13 = B1 * B3, p12 = B1 * B2;
+  const float num = fmaf(p23, F1, fmaf(p13, F2x6, p12 * F3x3));
+  const float den = fmaf(6.0f, p13, fmaf(3.0f, p12, p23));
   return __fdiv_rn(num, den);
 }
 
-template <int D, int TP_, int W_>
-__global__ void __launch_bounds__(THREADS) k_dir32(const DirArgs a) {
-  using PL = P32<TP_, W_>;
-  constexpr int TP = PL::TP, W = PL::W, NP = PL::NP, NW = PL::NW, NI = PL::NI;
-  constexpr int OFF_Q = PL::OFF_Q, OFF_ROE = PL::OFF_ROE, OFF_B = PL::OFF_B, OFF_R = PL::OFF_R;
-  constexpr int OFF_FV = PL::OFF_FV, OFF_F = PL::OFF_F;
-  extern __shared__ float smf[];
-  double* smd = reinterpret_cast<double*>(smf);
-  const int nD = a.g.n[D];
+// Accumulation / RK epilogue with the operand k from the prefetch slots kp (other operands from
+// global memory, plain loads: the last stage writes the state it reads); the arithmetic of
+// dir_epilogue.
+__device__ __forceinline__ void epilogue32(const DirArgs& a, long long p, const double cv[5], const double* kp) {
+  const long long N = a.g.N;
+  switch (a.epi) {
+    case EPI_ACC_WRITE:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) a.k[v * N + p] = cv[v];
+      break;
+    case EPI_ACC_ADD:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) a.k[v * N + p] = kp[v] + cv[v];
+      break;
+    case EPI_RHS_OUT:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) a.out[v * N + p] = kp[v] + cv[v];
+      break;
+    case EPI_RK4_FIRST:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K = kp[v] + cv[v];
+        a.out[v * N + p] = fma(a.a, K, a.un[v * N + p]);
+        a.acc[v * N + p] = K;
+      }
+      break;
+    case EPI_RK4_MID:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K = kp[v] + cv[v];
+        a.out[v * N + p] = fma(a.a, K, a.un[v * N + p]);
+        a.acc[v * N + p] = fma(2.0, K, a.acc[v * N + p]);
+      }
+      break;
+    case EPI_RK4_LAST:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K = kp[v] + cv[v];
+        a.out[v * N + p] = fma(a.a, a.acc[v * N + p] + K, a.un[v * N + p]);
+      }
+      break;
+    case EPI_SSP_1:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K = kp[v] + cv[v];
+        a.out[v * N + p] = fma(a.a, K, a.un[v * N + p]);
+      }
+      break;
+    case EPI_SSP_2:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K = kp[v] + cv[v];
+        a.out[v * N + p] = 0.75 * a.un[v * N + p] + 0.25 * fma(a.a, K, a.u[v * N + p]);
+      }
+      break;
+    case EPI_SSP_3:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K = kp[v] + cv[v];
+        a.out[v * N + p] = (1.0 / 3.0) * a.un[v * N + p] + (2.0 / 3.0) * fma(a.a, K, a.u[v * N + p]);
+      }
+      break;
+    default:
+      break;
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(THREADS, 4) k_dir32(const DirArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* Q = reinterpret_cast<float*>(smem + OFF_Q);
+  float4* R4 = reinterpret_cast<float4*>(smem + OFF_R4);
+  float* HS = reinterpret_cast<float*>(smem + OFF_H);
+  float4* V4 = reinterpret_cast<float4*>(smem + OFF_V4);
+  float* REC = reinterpret_cast<float*>(smem + OFF_REC);
+  double* FD = reinterpret_cast<double*>(smem + OFF_F);
+  double* PRE = reinterpret_cast<double*>(smem + OFF_Q);
+
   constexpr int AX = (D == 0) ? 1 : 0;
-  const int na = a.g.n[AX];
+  const int nD = a.g.n[D], na = a.g.n[AX];
   const long long N = a.g.N;
   const bool swap = (D == 2 && a.zorder);  // z pass with the line groups first (dir_zorder)
   const int s0 = (swap ? blockIdx.y : blockIdx.x) * TP;
   const int a0 = (swap ? blockIdx.x : blockIdx.y) * W;
   const int bz = blockIdx.z;
   const int tid = threadIdx.x;
+  const float* fvf = reinterpret_cast<const float*>(a.fv);
+  const long long fv_plane = (long long)(a.fv_dstride * D);
+  const float gamma = (float)a.gamma, gm1 = gamma - 1.0f;
 
-  // ---- A: load, convert, point fluxes in FP32 ---------------------------------
-  for (int item = tid; item < NP * W; item += THREADS) {
+  // ---- A: load, convert, primitive variables and point fluxes -------------------------
+  int bad = 0;
+  for (int it = tid; it < NP * W; it += THREADS) {
     int pos, line;
-    tile_split<D, W>(item, NP, pos, line);
-    const int c = wrap_idx(s0 - 3 + pos, nD);
+    if (D == 0) {
+      line = it / NP;
+      pos = it - line * NP;
+    } else {
+      pos = it / W;
+      line = it - pos * W;
+    }
+    int c = s0 - 3 + pos;
+    if (c < 0 || c >= nD) c = wrap_idx(c, nD);
     const int la = min(a0 + line, na - 1);
     const long long p = tile_flat<D>(a.g, c, la, bz);
-    float U[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) U[v] = d2f_rn(__ldg(a.u + v * N + p));
-    const float vx = d2f_rn(__ldg(a.pm + PM_U * N + p)), vy = d2f_rn(__ldg(a.pm + PM_V * N + p));
-    const float vz = d2f_rn(__ldg(a.pm + PM_W * N + p)), pr = d2f_rn(__ldg(a.pm + PM_P * N + p));
+    const float rho = d2f_tz(__ldg(a.u + p)), mx = d2f_tz(__ldg(a.u + N + p));
+    const float my = d2f_tz(__ldg(a.u + 2 * N + p)), mz = d2f_tz(__ldg(a.u + 3 * N + p));
+    const float e = d2f_tz(__ldg(a.u + 4 * N + p));
+    float4 fv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (fvf != nullptr) {
+      const float* fp = fvf + fv_plane * N + p;
+      fv = make_float4(__ldg(fp), __ldg(fp + N), __ldg(fp + 2 * N), __ldg(fp + 3 * N));
+    }
+    const float ri = rcp_a(rho);
+    const float vx = mx * ri, vy = my * ri, vz = mz * ri;
+    const float ke2 = fmaf(mx, vx, fmaf(my, vy, mz * vz));
+    const float pr = gm1 * fmaf(-0.5f, ke2, e);
+    const float ep = e + pr;
+    bad |= !(rho > 0.0f && rho < INFINITY && pr > 0.0f && pr < INFINITY);
     const float un = (D == 0) ? vx : (D == 1) ? vy : vz;
-    const int s = tile_idx<D, W>(pos, line, NP);
-    float* q = smf + OFF_Q;
-#pragma unroll
-    for (int v = 0; v < 5; ++v) q[v * NP * W + s] = U[v];
-    q[5 * NP * W + s] = (D == 0) ? fmaf(U[1], un, pr) : U[1] * un;
-    q[6 * NP * W + s] = (D == 1) ? fmaf(U[2], un, pr) : U[2] * un;
-    q[7 * NP * W + s] = (D == 2) ? fmaf(U[3], un, pr) : U[3] * un;
-    q[8 * NP * W + s] = (U[4] + pr) * un;
-    float* r = smf + OFF_ROE;
-    r[0 * NP * W + s] = d2f_rn(__ldg(a.pm + PM_SR * N + p));
-    r[1 * NP * W + s] = vx;
-    r[2 * NP * W + s] = vy;
-    r[3 * NP * W + s] = vz;
-    r[4 * NP * W + s] = d2f_rn(__ldg(a.pm + PM_H * N + p));
-    if (a.fv != nullptr) {  // FP64 as stored, first read in phase E: copied asynchronously
-      double* f = smd + OFF_FV / 2;
-#pragma unroll
-      for (int cc = 0; cc < 4; ++cc) cp_async8(f + cc * NP * W + s, a.fv + (long long)(a.fv_dstride * D + cc) * N + p);
-    }
+    float* q = Q + line * LS + pos;
+    q[0 * W * LS] = rho;
+    q[1 * W * LS] = mx;
+    q[2 * W * LS] = my;
+    q[3 * W * LS] = mz;
+    q[4 * W * LS] = e;
+    q[5 * W * LS] = (D == 0) ? fmaf(mx, un, pr) : mx * un;
+    q[6 * W * LS] = (D == 1) ? fmaf(my, un, pr) : my * un;
+    q[7 * W * LS] = (D == 2) ? fmaf(mz, un, pr) : mz * un;
+    q[8 * W * LS] = ep * un;
+    float sr;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sr) : "f"(rho));
+    R4[line * L4 + pos] = make_float4(sr, vx, vy, vz);
+    HS[line * L4 + pos] = ep * ri;
+    V4[line * L4 + pos] = fv;
   }
-  cp_async_commit();
   __syncthreads();
 
-  // ---- B: squared scaled smoothness indicators (FP32) --------------------------
+  // ---- BC: WENO5 left/right values, SEG interfaces of one scalar on one line per item -------
   {
-    const float* q = smf + OFF_Q;
-    float* bw = smf + OFF_B;
     const float eps4 = (float)a.eps4;
-    for (int item = tid; item < NQ * NW * W; item += THREADS) {
-      const int m = item / (NW * W);
-      int w, line;
-      tile_split<D, W>(item - m * NW * W, NW, w, line);
-      const float* qm = q + m * NP * W;
-      const float x = qm[tile_idx<D, W>(w, line, NP)];
-      const float y = qm[tile_idx<D, W>(w + 1, line, NP)];
-      const float z = qm[tile_idx<D, W>(w + 2, line, NP)];
-      const float gm = y - x, gp = z - y, sd = gp - gm;
-      const float aa = fmaf((13.0f / 3.0f) * sd, sd, eps4);
-      const float u1 = fmaf(3.0f, gp, -gm), u2 = gm + gp, u3 = fmaf(-3.0f, gm, gp);
-      const float b1 = fmaf(u1, u1, aa), b2 = fmaf(u2, u2, aa), b3 = fmaf(u3, u3, aa);
-      const int o = tile_idx<D, W>(w, line, NW);
-      bw[(m * 3 + 0) * NW * W + o] = b1 * b1;
-      bw[(m * 3 + 1) * NW * W + o] = b2 * b2;
-      bw[(m * 3 + 2) * NW * W + o] = b3 * b3;
-    }
-  }
-  __syncthreads();
-
-  // ---- C: left/right WENO5 values (FP32) -------------------------------------------
-  {
-    const float* q = smf + OFF_Q;
-    const float* bw = smf + OFF_B;
-    float* rec = smf + OFF_R;
-    for (int item = tid; item < NQ * NI * W; item += THREADS) {
-      const int m = item / (NI * W);
-      int f, line;
-      tile_split<D, W>(item - m * NI * W, NI, f, line);
-      const float* qm = q + m * NP * W;
-      const float P0 = qm[tile_idx<D, W>(f, line, NP)], P1 = qm[tile_idx<D, W>(f + 1, line, NP)];
-      const float P2 = qm[tile_idx<D, W>(f + 2, line, NP)], P3 = qm[tile_idx<D, W>(f + 3, line, NP)];
-      const float P4 = qm[tile_idx<D, W>(f + 4, line, NP)], P5 = qm[tile_idx<D, W>(f + 5, line, NP)];
-      const float xR = fmaf(11.0f / 6.0f, P2, fmaf(-7.0f / 6.0f, P1, (1.0f / 3.0f) * P0));
-      const float eR = fmaf(1.0f / 3.0f, P3, fmaf(5.0f / 6.0f, P2, (-1.0f / 6.0f) * P1));
-      const float eL = fmaf(-1.0f / 6.0f, P4, fmaf(5.0f / 6.0f, P3, (1.0f / 3.0f) * P2));
-      const float xL = fmaf(1.0f / 3.0f, P5, fmaf(-7.0f / 6.0f, P4, (11.0f / 6.0f) * P3));
-      const float* b = bw + m * 3 * NW * W;
-      const float vL = weno_combine32(b[0 * NW * W + tile_idx<D, W>(f, line, NW)], b[1 * NW * W + tile_idx<D, W>(f + 1, line, NW)],
-                                      b[2 * NW * W + tile_idx<D, W>(f + 2, line, NW)], xR, eR, eL);
-      const float vR = weno_combine32(b[2 * NW * W + tile_idx<D, W>(f + 3, line, NW)], b[1 * NW * W + tile_idx<D, W>(f + 2, line, NW)],
-                                      b[0 * NW * W + tile_idx<D, W>(f + 1, line, NW)], xL, eL, eR);
-      const int o = tile_idx<D, W>(f, line, NI);
-      rec[(2 * m) * NI * W + o] = vL;
-      rec[(2 * m + 1) * NI * W + o] = vR;
-    }
-  }
-  cp_async_wait_all();  // this thread's viscous-flux copies; the barrier publishes them
-  __syncthreads();
-
-  // ---- epilogue operands: fetched asynchronously into the (now unused) indicator space
-  //      while phase D runs; each thread later reads only its own point's slots
-  static_assert(TP * W <= THREADS, "one epilogue point per thread");
-  static_assert(30 * TP * W <= NQ * 3 * NW * W && OFF_B % 2 == 0, "prefetch slots fit the indicator space");
-  double* pre = smd + OFF_B / 2 + 15 * tid;
-  if (tid < TP * W) {
-    int pp, line;
-    tile_split<D, W>(tid, TP, pp, line);
-    if (s0 + pp < nD && a0 + line < na) epilogue_prefetch(a, tile_flat<D>(a.g, s0 + pp, a0 + line, bz), pre);
-  }
-  cp_async_commit();
-
-  // ---- D: Roe flux (FP32), widened to FP64 -----------------------------------------
-  {
-    const float gm1 = (float)(a.gamma - 1.0);
-    const float hdelta = (float)a.hdelta;
-    const float* r = smf + OFF_ROE;
-    const float* rec = smf + OFF_R;
-    double* F = smd + OFF_F / 2;
-    int bad = 0;
-    for (int item = tid; item < NI * W; item += THREADS) {
-      int f, line;
-      tile_split<D, W>(item, NI, f, line);
-      const int o = tile_idx<D, W>(f, line, NI);
-      float uL[5], uR[5], fL[5], fR[5];
+    const bool eps_ok = eps4 >= 1e-9f && eps4 <= 1.0f;  // unscaled products stay in range (see below)
+    for (int it = tid; it < NQ * W * NSEG; it += THREADS) {
+      const int m = it / (W * NSEG);
+      const int rem = it - m * (W * NSEG);
+      const int line = rem / NSEG, seg = rem - line * NSEG;
+      const float* q = Q + (m * W + line) * LS + SEG * seg;
+      const float4 qa = *reinterpret_cast<const float4*>(q);
+      const float4 qb = *reinterpret_cast<const float4*>(q + 4);
+      const float P[SEG + 5] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w, q[8]};
+      // window indicators: window w = points w, w+1, w+2; roles 1..3 (its first-derivative term
+      // taken at its right end, centre, left end)
+      float B[SEG + 3][3];
+      float gmax = 0.0f;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        uL[v] = rec[(2 * v) * NI * W + o];
-        uR[v] = rec[(2 * v + 1) * NI * W + o];
+      for (int w = 0; w < SEG + 3; ++w) {
+        const float gm = P[w + 1] - P[w], gp = P[w + 2] - P[w + 1], sd = gp - gm;
+        gmax = fmaxf(gmax, fmaxf(fabsf(gm), fabsf(gp)));
+        const float aa = fmaf((13.0f / 3.0f) * sd, sd, eps4);
+        const float u1 = fmaf(3.0f, gp, -gm), u2 = gm + gp, u3 = fmaf(-3.0f, gm, gp);
+        const float b1 = fmaf(u1, u1, aa), b2 = fmaf(u2, u2, aa), b3 = fmaf(u3, u3, aa);
+        B[w][0] = b1 * b1;
+        B[w][1] = b2 * b2;
+        B[w][2] = b3 * b3;
       }
+      // With every first difference <= 64 in magnitude and 1e-9 <= 4 eps <= 1, each B lies in
+      // [(4 eps)^2, (34 * 64^2 + 1)^2] and the products and the numerator stay within the normal
+      // FP32 range for values up to ~1e16: the unscaled form is exact to FP32 rounding.
+      const bool fast = eps_ok && gmax <= 64.0f;
+      float vL[SEG], vR[SEG];
 #pragma unroll
-      for (int v = 1; v < 5; ++v) {
-        fL[v] = rec[(2 * (4 + v)) * NI * W + o];
-        fR[v] = rec[(2 * (4 + v) + 1) * NI * W + o];
-      }
-      fL[0] = uL[1 + D];
-      fR[0] = uR[1 + D];
-      const int sa = tile_idx<D, W>(f + 2, line, NP), sb = tile_idx<D, W>(f + 3, line, NP);
-      const float ra = r[sa], rb = r[sb];
-      const float rs = __frcp_rn(ra + rb);
-      const float wa = ra * rs, wb = rb * rs;
-      float V[3];
-#pragma unroll
-      for (int m = 0; m < 3; ++m) V[m] = fmaf(wa, r[(1 + m) * NP * W + sa], wb * r[(1 + m) * NP * W + sb]);
-      const float H = fmaf(wa, r[4 * NP * W + sa], wb * r[4 * NP * W + sb]);
-      const float q2h = 0.5f * fmaf(V[0], V[0], fmaf(V[1], V[1], V[2] * V[2]));
-      const float c2 = gm1 * (H - q2h);
-      bad |= !(c2 > 0.0f);
-      const float c = __fsqrt_rn(c2);
-      const float rc = __frcp_rn(c);
-      float du[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) du[v] = uR[v] - uL[v];
-      constexpr int T1 = (D == 0) ? 1 : 0;
-      constexpr int T2 = (D == 2) ? 1 : 2;
-      const float un = V[D], vt1 = V[T1], vt2 = V[T2];
-      const float b1 = gm1 * (rc * rc);
-      const float vdm = fmaf(V[0], du[1], fmaf(V[1], du[2], V[2] * du[3]));
-      const float phi = b1 * (fmaf(q2h, du[0], du[4]) - vdm);
-      const float a2 = du[0] - phi;
-      const float a3 = fmaf(-vt1, du[0], du[1 + T1]);
-      const float a4 = fmaf(-vt2, du[0], du[1 + T2]);
-      const float ach = 0.5f * (fmaf(un, du[0], -du[1 + D]) * rc);
-      const float ph = 0.5f * phi;
-      const float a1 = ph + ach, a5 = ph - ach;
-      float l1 = fabsf(un - c), l5 = fabsf(un + c);
-      const float l2 = fabsf(un);
-      const float delta = hdelta * c;
-      if (l1 < delta) l1 = (l1 * l1 + delta * delta) / (2.0f * delta);
-      if (l5 < delta) l5 = (l5 * l5 + delta * delta) / (2.0f * delta);
-      const float A1 = l1 * a1, A2 = l2 * a2, A3 = l2 * a3, A4 = l2 * a4, A5 = l5 * a5;
-      const float S = A1 + A5;
-      const float d0 = S + A2;
-      const float cD = c * (A5 - A1);
-      float diss[5];
-      diss[0] = d0;
-      diss[1 + D] = fmaf(d0, un, cD);
-      diss[1 + T1] = fmaf(d0, vt1, A3);
-      diss[1 + T2] = fmaf(d0, vt2, A4);
-      diss[4] = fmaf(S, H, fmaf(cD, un, fmaf(A2, q2h, fmaf(A3, vt1, A4 * vt2))));
-#pragma unroll
-      for (int v = 0; v < 5; ++v) F[v * NI * W + o] = f2d_bits(0.5f * (fL[v] + fR[v] - diss[v]));
-    }
-    if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(a.status, ST_NONPHYS);
-  }
-  __syncthreads();
-
-  // ---- E: FP64 conservative difference + viscous divergence + epilogue -------------
-  cp_async_wait_all();
-  {
-    const double rdx = a.g.rh[D];
-    const double r12 = a.g.r12h[D];
-    const double* F = smd + OFF_F / 2;
-    const double* fvs = smd + OFF_FV / 2;
-    for (int item = tid; item < TP * W; item += THREADS) {
-      int pp, line;
-      tile_split<D, W>(item, TP, pp, line);
-      if (s0 + pp >= nD || a0 + line >= na) continue;
-      double cv[5];
-      const int op = tile_idx<D, W>(pp + 1, line, NI), om = tile_idx<D, W>(pp, line, NI);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) cv[v] = (F[v * NI * W + om] - F[v * NI * W + op]) * rdx;
-      if (a.fv != nullptr) {
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-          const double* fc = fvs + cc * NP * W;
-          const double d1 = fc[tile_idx<D, W>(pp + 4, line, NP)] - fc[tile_idx<D, W>(pp + 2, line, NP)];
-          const double d2 = fc[tile_idx<D, W>(pp + 5, line, NP)] - fc[tile_idx<D, W>(pp + 1, line, NP)];
-          cv[1 + cc] = fma(fma(8.0, d1, -d2), r12, cv[1 + cc]);
+      for (int j = 0; j < SEG; ++j) {
+        const float P0 = P[j], P1 = P[j + 1], P2 = P[j + 2], P3 = P[j + 3], P4 = P[j + 4], P5 = P[j + 5];
+        const float xR = fmaf(11.0f / 6.0f, P2, fmaf(-7.0f / 6.0f, P1, (1.0f / 3.0f) * P0));
+        const float eR = fmaf(1.0f / 3.0f, P3, fmaf(5.0f / 6.0f, P2, (-1.0f / 6.0f) * P1));
+        const float eL = fmaf(-1.0f / 6.0f, P4, fmaf(5.0f / 6.0f, P3, (1.0f / 3.0f) * P2));
+        const float xL = fmaf(1.0f / 3.0f, P5, fmaf(-7.0f / 6.0f, P4, (11.0f / 6.0f) * P3));
+        if (fast) {
+          vL[j] = weno_fast(B[j][0], B[j + 1][1], B[j + 2][2], xR, 6.0f * eR, 3.0f * eL);
+          vR[j] = weno_fast(B[j + 3][2], B[j + 2][1], B[j + 1][0], xL, 6.0f * eL, 3.0f * eR);
+        } else {
+          vL[j] = weno_safe(B[j][0], B[j + 1][1], B[j + 2][2], xR, 6.0f * eR, 3.0f * eL);
+          vR[j] = weno_safe(B[j + 3][2], B[j + 2][1], B[j + 1][0], xL, 6.0f * eL, 3.0f * eR);
         }
       }
-      dir_epilogue_pre(a, tile_flat<D>(a.g, s0 + pp, a0 + line, bz), cv, pre);
+      float* r = REC + line * NI + SEG * seg;
+      if (m < 5) {
+        *reinterpret_cast<float4*>(r + m * W * NI) =
+            make_float4(vR[0] - vL[0], vR[1] - vL[1], vR[2] - vL[2], vR[3] - vL[3]);
+        if (m == 1 + D)
+          *reinterpret_cast<float4*>(r + 5 * W * NI) =
+              make_float4(vL[0] + vR[0], vL[1] + vR[1], vL[2] + vR[2], vL[3] + vR[3]);
+      } else {
+        *reinterpret_cast<float4*>(r + (m + 1) * W * NI) =
+            make_float4(vL[0] + vR[0], vL[1] + vR[1], vL[2] + vR[2], vL[3] + vR[3]);
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- epilogue operand k: fetched asynchronously into the dead scalar planes while D runs;
+  //      each thread later reads only its own point's slots
+  auto point_of = [&](int it, int& pp, int& line) {
+    if (D == 0) {
+      line = it / TP;
+      pp = it - line * TP;
+    } else {
+      pp = it / W;
+      line = it - pp * W;
+    }
+  };
+  const bool need_k = (a.epi != EPI_ACC_WRITE);
+  if (need_k && tid < TP * W) {
+    int pp, line;
+    point_of(tid, pp, line);
+    if (s0 + pp < nD && a0 + line < na) {
+      const long long p = tile_flat<D>(a.g, s0 + pp, a0 + line, bz);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) cp_async8(PRE + 5 * tid + v, a.k + v * N + p);
+    }
+  }
+  cp_async_commit();
+
+  // ---- D: Roe flux + viscous interface flux, / dx, widened to FP64 ----------------------
+  if (tid < NI * W) {
+    int r, line;
+    if (D == 0) {
+      line = tid / NI;
+      r = tid - line * NI;
+    } else {
+      r = tid / W;
+      line = tid - r * W;
+    }
+    // interface r lies between the tile's points r - 1 and r, i.e. positions r + 2 and r + 3
+    const float* rc_ = REC + line * NI + r;
+    float du[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) du[v] = rc_[v * W * NI];
+    const float S0 = rc_[5 * W * NI];
+    const float S1 = rc_[6 * W * NI], S2 = rc_[7 * W * NI], S3 = rc_[8 * W * NI], S4 = rc_[9 * W * NI];
+    const float4 qa = R4[line * L4 + r + 2], qb = R4[line * L4 + r + 3];
+    const float Ha = HS[line * L4 + r + 2], Hb = HS[line * L4 + r + 3];
+    const float rs = rcp_a(qa.x + qb.x);
+    const float wa = qa.x * rs, wb = qb.x * rs;
+    const float V0 = fmaf(wa, qa.y, wb * qb.y), V1 = fmaf(wa, qa.z, wb * qb.z), V2 = fmaf(wa, qa.w, wb * qb.w);
+    const float H = fmaf(wa, Ha, wb * Hb);
+    const float q2h = 0.5f * fmaf(V0, V0, fmaf(V1, V1, V2 * V2));
+    const float c2 = gm1 * (H - q2h);
+    bad |= !(c2 > 0.0f);
+    const float rc = rsqrt_a(c2);
+    const float c = c2 * rc;
+    constexpr int T1 = (D == 0) ? 1 : 0;
+    constexpr int T2 = (D == 2) ? 1 : 2;
+    const float V[3] = {V0, V1, V2};
+    const float un = V[D], vt1 = V[T1], vt2 = V[T2];
+    const float b1 = gm1 * (rc * rc);
+    const float vdm = fmaf(V0, du[1], fmaf(V1, du[2], V2 * du[3]));
+    const float phi = b1 * (fmaf(q2h, du[0], du[4]) - vdm);
+    const float a2 = du[0] - phi;
+    const float a3 = fmaf(-vt1, du[0], du[1 + T1]);
+    const float a4 = fmaf(-vt2, du[0], du[1 + T2]);
+    const float ach = 0.5f * (fmaf(un, du[0], -du[1 + D]) * rc);
+    const float ph = 0.5f * phi;
+    const float a1 = ph + ach, a5 = ph - ach;
+    float l1 = fabsf(un - c), l5 = fabsf(un + c);
+    const float l2 = fabsf(un);
+    const float hd = (float)a.hdelta;
+    const float delta = hd * c;
+    if (l1 < delta) l1 = fmaf(l1, l1, delta * delta) * __fdividef(0.5f, delta);
+    if (l5 < delta) l5 = fmaf(l5, l5, delta * delta) * __fdividef(0.5f, delta);
+    const float A1 = l1 * a1, A2 = l2 * a2, A3 = l2 * a3, A4 = l2 * a4, A5 = l5 * a5;
+    const float S = A1 + A5;
+    const float d0 = S + A2;
+    const float cD = c * (A5 - A1);
+    float diss[5];
+    diss[0] = d0;
+    diss[1 + D] = fmaf(d0, un, cD);
+    diss[1 + T1] = fmaf(d0, vt1, A3);
+    diss[1 + T2] = fmaf(d0, vt2, A4);
+    diss[4] = fmaf(S, H, fmaf(cD, un, fmaf(A2, q2h, fmaf(A3, vt1, A4 * vt2))));
+    // viscous interface flux: its difference over the two faces of a point is the 4th-order
+    // central derivative (f_{i-2} - 8 f_{i-1} + 8 f_{i+1} - f_{i+2}) / 12 of the point values
+    const float4 fm1 = V4[line * L4 + r + 1], f0 = V4[line * L4 + r + 2];
+    const float4 f1 = V4[line * L4 + r + 3], f2 = V4[line * L4 + r + 4];
+    const float G0 = fmaf(7.0f / 12.0f, f0.x + f1.x, (-1.0f / 12.0f) * (fm1.x + f2.x));
+    const float G1 = fmaf(7.0f / 12.0f, f0.y + f1.y, (-1.0f / 12.0f) * (fm1.y + f2.y));
+    const float G2 = fmaf(7.0f / 12.0f, f0.z + f1.z, (-1.0f / 12.0f) * (fm1.z + f2.z));
+    const float G3 = fmaf(7.0f / 12.0f, f0.w + f1.w, (-1.0f / 12.0f) * (fm1.w + f2.w));
+    const float rdx = (float)a.g.rh[D];
+    const float F0 = 0.5f * (S0 - diss[0]);
+    const float F1 = fmaf(0.5f, S1 - diss[1], -G0);
+    const float F2 = fmaf(0.5f, S2 - diss[2], -G1);
+    const float F3 = fmaf(0.5f, S3 - diss[3], -G2);
+    const float F4 = fmaf(0.5f, S4 - diss[4], -G3);
+    double* fd = FD + line * FS + r;
+    fd[0 * W * FS] = f2d_bits(F0 * rdx);
+    fd[1 * W * FS] = f2d_bits(F1 * rdx);
+    fd[2 * W * FS] = f2d_bits(F2 * rdx);
+    fd[3 * W * FS] = f2d_bits(F3 * rdx);
+    fd[4 * W * FS] = f2d_bits(F4 * rdx);
+  }
+  if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(a.status, ST_NONPHYS);
+  cp_async_wait_all();
+  __syncthreads();
+
+  // ---- E: FP64 conservative difference + epilogue ----------------------------------------
+  if (tid < TP * W) {
+    int pp, line;
+    point_of(tid, pp, line);
+    if (s0 + pp < nD && a0 + line < na) {
+      const double* fd = FD + line * FS + pp;
+      double cv[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) cv[v] = fd[v * W * FS] - fd[v * W * FS + 1];
+      epilogue32(a, tile_flat<D>(a.g, s0 + pp, a0 + line, bz), cv, PRE + 5 * tid);
     }
   }
 }
 
-template <int D, int TP, int W>
+template <int D>
 cudaError_t launch32(const DirArgs& a, cudaStream_t s) {
   constexpr int AX = (D == 0) ? 1 : 0;
   constexpr int BX = (D == 2) ? 1 : 2;
@@ -289,32 +435,32 @@ cudaError_t launch32(const DirArgs& a, cudaStream_t s) {
     grid.x = grid.y;
     grid.y = t;
   }
-  k_dir32<D, TP, W><<<grid, THREADS, P32<TP, W>::BYTES, s>>>(a);
+  k_dir32<D><<<grid, THREADS, BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int D, int TP, int W>
+template <int D>
 cudaError_t attr32() {
-  return cudaFuncSetAttribute(k_dir32<D, TP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, P32<TP, W>::BYTES);
+  cudaError_t e = cudaFuncSetAttribute(k_dir32<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_dir32<D>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  return e;
 }
 
 }  // namespace
 
 cudaError_t prepare_dir32_kernels() {
-  cudaError_t e = attr32<0, 32, 4>();
-  if (e == cudaSuccess) e = attr32<1, 16, 8>();
-  if (e == cudaSuccess) e = attr32<2, 16, 8>();
-  if (e == cudaSuccess) e = attr32<1, 32, 4>();
-  if (e == cudaSuccess) e = attr32<2, 32, 4>();
+  cudaError_t e = attr32<0>();
+  if (e == cudaSuccess) e = attr32<1>();
+  if (e == cudaSuccess) e = attr32<2>();
   return e;
 }
 
-// x pass: 32 x 4.  y and z passes by the context's variant: 0 -> y 32 x 4, z 16 x 8 (the fastest
-// measured on GB300 at 256^3 with the epilogue prefetch); 1 -> y and z 32 x 4; 2 -> y and z 16 x 8.
+// One tile shape (27 x 8) for every pass; the tile variants of the FP64 modes do not apply.
 cudaError_t launch_dir32(int d, const DirArgs& a, cudaStream_t s) {
-  if (d == 0) return launch32<0, 32, 4>(a, s);
-  if (d == 1) return (a.variant == 2) ? launch32<1, 16, 8>(a, s) : launch32<1, 32, 4>(a, s);
-  return (a.variant == 1) ? launch32<2, 32, 4>(a, s) : launch32<2, 16, 8>(a, s);
+  if (d == 0) return launch32<0>(a, s);
+  if (d == 1) return launch32<1>(a, s);
+  return launch32<2>(a, s);
 }
 
 }  // namespace ns3d

@@ -125,77 +125,105 @@ __global__ void __launch_bounds__(VT_X * VT_Y, 3) k_visc_tiled(const double* __r
 // Launch geometry of the stencil point kernels: 32 x 8 x 1 blocks over (x, y, z).
 inline dim3 plane_grid(const Grid& g) { return dim3((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, g.n[2]); }
 
-// ---- FP32-bulk variants: same formulas in FP32, results widened to FP64 -----------
-__global__ void __launch_bounds__(PW_THREADS) k_prim32(const double* __restrict__ u, double* __restrict__ pm,
-                                                       long long N, float gamma, int* __restrict__ status) {
-  int bad = 0;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-    const float rho = d2f_rn(u[p]), mx = d2f_rn(u[N + p]), my = d2f_rn(u[2 * N + p]);
-    const float mz = d2f_rn(u[3 * N + p]), e = d2f_rn(u[4 * N + p]);
-    const float ri = __frcp_rn(rho);
-    const float vx = mx * ri, vy = my * ri, vz = mz * ri;
-    const float ke = 0.5f * (mx * vx + my * vy + mz * vz);
-    const float pr = (gamma - 1.0f) * (e - ke);
-    pm[PM_U * N + p] = f2d_bits(vx);
-    pm[PM_V * N + p] = f2d_bits(vy);
-    pm[PM_W * N + p] = f2d_bits(vz);
-    pm[PM_P * N + p] = f2d_bits(pr);
-    pm[PM_T * N + p] = f2d_bits(gamma * pr * ri);
-    pm[PM_H * N + p] = f2d_bits((e + pr) * ri);
-    pm[PM_SR * N + p] = f2d_bits(__fsqrt_rn(rho));
-    bad |= !(rho > 0.0f) | !isfinite(rho) | !(pr > 0.0f) | !isfinite(e) | !isfinite(mx + my + mz);
+// ---- FP32-bulk viscous fluxes (NS3D_FP32_BULK) ---------------------------------------
+// The tiled form of k_visc_tiled in FP32, straight from the conserved state: a CTA owns a
+// 32 x 8 block of x-y columns and marches along z through VT_CZ planes; every plane of
+// (u, v, w, T), with a 2-point x-y halo, is formed once from the state (converted to FP32 by
+// bit manipulation) into a ring of 5 planes (z-2 .. z+2) of float4 in shared memory.  Each
+// point then takes the 12 gradients with the 4th-order central difference and writes the
+// viscous flux vectors as FP32 planes fv[4 d + c][N] (only_d = d: fv[c][N]), which the FP32-bulk
+// direction passes read.
+__device__ __forceinline__ float d2f_trunc_fast(double x) {
+  const uint32_t h = (uint32_t)__double2hiint(x), l = (uint32_t)__double2loint(x);
+  const uint32_t e11 = (h >> 20) & 0x7ffu;
+  uint32_t b = __funnelshift_l(l, h, 3) + 0x40000000u;
+  b = (e11 <= 896u) ? 0u : b;
+  b = (e11 >= 1151u) ? 0x7f800000u : b;
+  return __uint_as_float(b | (h & 0x80000000u));
+}
+
+constexpr int V32_SMEM = VT_RING * VT_PLANE * (int)sizeof(float4);  // 34,560 bytes
+
+__global__ void __launch_bounds__(VT_X * VT_Y, 4) k_visc32t(const double* __restrict__ u, float* __restrict__ fv,
+                                                             const Grid g, float gamma, float mu, float kappa,
+                                                             int only_d) {
+  extern __shared__ float4 ring4[];  // [VT_RING][VT_HY][VT_HX]: u, v, w, T
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const long long N = g.N;
+  const int x0 = blockIdx.x * VT_X, y0 = blockIdx.y * VT_Y, z0 = blockIdx.z * VT_CZ;
+  const int z1 = min(z0 + VT_CZ, nz);
+  const int tid = threadIdx.x, tx = tid % VT_X, ty = tid / VT_X;
+  const float r12[3] = {(float)g.r12h[0], (float)g.r12h[1], (float)g.r12h[2]};
+  const float gm1 = gamma - 1.0f;
+  auto slot = [&](int zz) { return ring4 + ((zz - z0 + 2) % VT_RING) * VT_PLANE; };
+  constexpr int NPOS = (VT_PLANE + VT_X * VT_Y - 1) / (VT_X * VT_Y);
+  int xy[NPOS];
+#pragma unroll
+  for (int k = 0; k < NPOS; ++k) {
+    const int pos = tid + k * VT_X * VT_Y;
+    const int hy = pos / VT_HX, hx = pos - hy * VT_HX;
+    xy[k] = wrap_idx(y0 - 2 + hy, ny) * nx + wrap_idx(x0 - 2 + hx, nx);
   }
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONPHYS);
-}
-
-__device__ __forceinline__ float d4f(float qm2, float qm1, float qp1, float qp2, float r12h) {
-  return fmaf(8.0f, qp1 - qm1, -(qp2 - qm2)) * r12h;
-}
-
-__global__ void __launch_bounds__(PW_THREADS) k_visc32(const double* __restrict__ pm, double* __restrict__ fv,
-                                                       int nx, int ny, int nz, float r12hx, float r12hy,
-                                                       float r12hz, float mu, float kappa, int only_d) {
-  const long long N = (long long)nx * ny * nz;
-  // one thread per point of a 32 x 8 block of an x-y plane; blockIdx.z = the plane
-  const int i = blockIdx.x * 32 + threadIdx.x % 32, j = blockIdx.y * 8 + threadIdx.x / 32, k = blockIdx.z;
-  if (i < nx && j < ny) {
-    const long long p = flat3(i, j, k, nx, ny);
-    float G[4][3];
-    const int n3[3] = {nx, ny, nz};
-    const float r12[3] = {r12hx, r12hy, r12hz};
+  const long long plane_n = (long long)nx * ny;
+  auto load_plane = [&](int zz) {
+    const long long zoff = (long long)wrap_idx(zz, nz) * plane_n;
+    float4* R = slot(zz);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      long long nb[4];
+    for (int k = 0; k < NPOS; ++k) {
+      const int pos = tid + k * VT_X * VT_Y;
+      if (pos >= VT_PLANE) break;
+      const long long p = zoff + xy[k];
+      const float rho = d2f_trunc_fast(__ldg(u + p)), mx = d2f_trunc_fast(__ldg(u + N + p));
+      const float my = d2f_trunc_fast(__ldg(u + 2 * N + p)), mz = d2f_trunc_fast(__ldg(u + 3 * N + p));
+      const float e = d2f_trunc_fast(__ldg(u + 4 * N + p));
+      const float ri = __fdividef(1.0f, rho);
+      const float vx = mx * ri, vy = my * ri, vz = mz * ri;
+      const float pr = gm1 * fmaf(-0.5f, fmaf(mx, vx, fmaf(my, vy, mz * vz)), e);
+      R[pos] = make_float4(vx, vy, vz, gamma * pr * ri);
+    }
+  };
+  for (int zz = z0 - 2; zz < z0 + 2; ++zz) load_plane(zz);
+  for (int z = z0; z < z1; ++z) {
+    load_plane(z + 2);
+    __syncthreads();
+    if (x0 + tx < nx && y0 + ty < ny) {
+      const int c = (ty + 2) * VT_HX + (tx + 2);
+      const float4 *Zm2 = slot(z - 2), *Zm1 = slot(z - 1), *Z0 = slot(z), *Zp1 = slot(z + 1), *Zp2 = slot(z + 2);
+      auto d4v = [](float4 m2, float4 m1, float4 p1, float4 p2, float r) {
+        return make_float4(fmaf(8.0f, p1.x - m1.x, -(p2.x - m2.x)) * r, fmaf(8.0f, p1.y - m1.y, -(p2.y - m2.y)) * r,
+                           fmaf(8.0f, p1.z - m1.z, -(p2.z - m2.z)) * r, fmaf(8.0f, p1.w - m1.w, -(p2.w - m2.w)) * r);
+      };
+      // G[d] = d(u, v, w, T)/dx_d
+      const float4 Gd[3] = {d4v(Z0[c - 2], Z0[c - 1], Z0[c + 1], Z0[c + 2], r12[0]),
+                            d4v(Z0[c - 2 * VT_HX], Z0[c - VT_HX], Z0[c + VT_HX], Z0[c + 2 * VT_HX], r12[1]),
+                            d4v(Zm2[c], Zm1[c], Zp1[c], Zp2[c], r12[2])};
+      float G[4][3];
 #pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        const int off = (o < 2) ? (o - 2) : (o - 1);
-        int c[3] = {i, j, k};
-        c[d] = wrap_near(c[d], off, n3[d]);
-        nb[o] = flat3(c[0], c[1], c[2], nx, ny);
+      for (int d = 0; d < 3; ++d) {
+        G[0][d] = Gd[d].x;
+        G[1][d] = Gd[d].y;
+        G[2][d] = Gd[d].z;
+        G[3][d] = Gd[d].w;
       }
+      const float4 v0 = Z0[c];
+      const float vel[3] = {v0.x, v0.y, v0.z};
+      const float tdiv = (2.0f / 3.0f) * (G[0][0] + G[1][1] + G[2][2]);
+      const long long p = flat3(x0 + tx, y0 + ty, z, nx, ny);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int plane = (q < 3) ? q : PM_T;
-        const double* A = pm + (long long)plane * N;
-        G[q][d] = d4f(d2f_rn(__ldg(A + nb[0])), d2f_rn(__ldg(A + nb[1])), d2f_rn(__ldg(A + nb[2])),
-                      d2f_rn(__ldg(A + nb[3])), r12[d]);
+      for (int d = 0; d < 3; ++d) {
+        if (only_d >= 0 && d != only_d) continue;
+        const int b = (only_d >= 0) ? 0 : 4 * d;
+        float tau[3];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) tau[m] = (m == d) ? mu * fmaf(2.0f, G[d][d], -tdiv) : mu * (G[m][d] + G[d][m]);
+        const float en = fmaf(vel[0], tau[0], fmaf(vel[1], tau[1], fmaf(vel[2], tau[2], kappa * G[3][d])));
+        fv[(long long)(b + 0) * N + p] = tau[0];
+        fv[(long long)(b + 1) * N + p] = tau[1];
+        fv[(long long)(b + 2) * N + p] = tau[2];
+        fv[(long long)(b + 3) * N + p] = en;
       }
     }
-    const float vel[3] = {d2f_rn(pm[PM_U * N + p]), d2f_rn(pm[PM_V * N + p]), d2f_rn(pm[PM_W * N + p])};
-    const float tdiv = (2.0f / 3.0f) * (G[0][0] + G[1][1] + G[2][2]);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      if (only_d >= 0 && d != only_d) continue;
-      const int b = (only_d >= 0) ? 0 : 4 * d;
-      float tau[3];
-#pragma unroll
-      for (int m = 0; m < 3; ++m) tau[m] = (m == d) ? mu * fmaf(2.0f, G[d][d], -tdiv) : mu * (G[m][d] + G[d][m]);
-      const float en = fmaf(vel[0], tau[0], fmaf(vel[1], tau[1], fmaf(vel[2], tau[2], kappa * G[3][d])));
-      fv[(long long)(b + 0) * N + p] = f2d_bits(tau[0]);
-      fv[(long long)(b + 1) * N + p] = f2d_bits(tau[1]);
-      fv[(long long)(b + 2) * N + p] = f2d_bits(tau[2]);
-      fv[(long long)(b + 3) * N + p] = f2d_bits(en);
-    }
+    __syncthreads();  // the slot of plane z - 2 takes plane z + 3 next
   }
 }
 
@@ -455,19 +483,14 @@ cudaError_t prepare_visc_kernels() {
   cudaError_t e = cudaFuncSetAttribute(k_visc_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, VT_SMEM);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stats_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SR_SMEM);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stats_tiled<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SR_SMEM);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_visc32t, cudaFuncAttributeMaxDynamicSharedMemorySize, V32_SMEM);
   return e;
 }
 
-cudaError_t launch_prim32(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s) {
-  k_prim32<<<grid_for(g.N, PW_THREADS), PW_THREADS, 0, s>>>(u, pm, g.N, (float)gamma, status);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_visc32(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s,
-                          int only_d) {
-  k_visc32<<<plane_grid(g), PW_THREADS, 0, s>>>(
-      pm, fv, g.n[0], g.n[1], g.n[2], (float)(1.0 / (12.0 * g.h[0])), (float)(1.0 / (12.0 * g.h[1])),
-      (float)(1.0 / (12.0 * g.h[2])), (float)mu, (float)kappa, only_d);
+cudaError_t launch_visc32(const Grid& g, const double* u, float* fv, double gamma, double mu, double kappa,
+                          cudaStream_t s, int only_d) {
+  const dim3 grid((g.n[0] + VT_X - 1) / VT_X, (g.n[1] + VT_Y - 1) / VT_Y, (g.n[2] + VT_CZ - 1) / VT_CZ);
+  k_visc32t<<<grid, VT_X * VT_Y, V32_SMEM, s>>>(u, fv, g, (float)gamma, (float)mu, (float)kappa, only_d);
   return cudaGetLastError();
 }
 

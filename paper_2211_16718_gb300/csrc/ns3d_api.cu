@@ -74,10 +74,11 @@ int rhs_pass(ns3d_ctx* c, const double* u, int epi, double* out, const double* u
   const int df = (c->p.precision == NS3D_FP64) ? 1 : 0;
   const Grid& g = c->g;
   const long long plane = (long long)g.n[0] * g.n[1];
+  // FP32-bulk: the direction and viscous kernels form their primitive variables from u themselves
   auto prim = [&](int z0, int z1) {
+    if (f32) return (int)NS3D_OK;
     return timed(c, NS3D_K_PRIM, [&] {
-      return f32 ? launch_prim32(g, u, c->pm, c->p.gamma, c->status, c->stream)
-                 : launch_prim(g, u, c->pm, c->p.gamma, c->status, c->stream, df, z0 * plane, z1 * plane);
+      return launch_prim(g, u, c->pm, c->p.gamma, c->status, c->stream, df, z0 * plane, z1 * plane);
     }, "primitive kernel");
   };
   const bool visc = c->p.mu_eff > 0.0;
@@ -85,7 +86,8 @@ int rhs_pass(ns3d_ctx* c, const double* u, int epi, double* out, const double* u
   // viscous fluxes of all directions (only_d < 0), or of direction only_d (lean storage), planes [z0, z1)
   auto visc_flux = [&](int only_d, int z0, int z1) {
     return timed(c, NS3D_K_VISC, [&] {
-      return f32 ? launch_visc32(g, c->pm, c->fv, c->p.mu_eff, kappa, c->stream, only_d)
+      return f32 ? launch_visc32(g, u, reinterpret_cast<float*>(c->fv), c->p.gamma, c->p.mu_eff, kappa, c->stream,
+                                 only_d)
                  : launch_visc(g, c->pm, c->fv, c->p.mu_eff, kappa, c->stream, only_d, df, z0, z1);
     }, "viscous-flux kernel");
   };
@@ -153,7 +155,8 @@ int rhs_pass(ns3d_ctx* c, const double* u, int epi, double* out, const double* u
 }
 
 int stats_pass(ns3d_ctx* c, const double* u, double* out_dev) {
-  const int df = (c->p.precision == NS3D_FP64) ? 1 : 0;
+  // the double-float primitive layout for NS3D_FP64 and NS3D_FP32_BULK (FP64 reductions either way)
+  const int df = (c->p.precision != NS3D_FP64_STRICT) ? 1 : 0;
   int rc = timed(c, NS3D_K_PRIM,
                  [&] { return launch_prim(c->g, u, c->pm, c->p.gamma, c->status, c->stream, df); },
                  "primitive kernel");
@@ -229,7 +232,7 @@ int validate(const ns3d_params* p, char* msg, size_t n) {
     return snprintf(msg, n, "unsupported precision mode"), NS3D_EINVAL;
   if (p->storage != NS3D_STORAGE_AUTO && p->storage != NS3D_STORAGE_FULL && p->storage != NS3D_STORAGE_LEAN)
     return snprintf(msg, n, "unknown storage mode"), NS3D_EINVAL;
-  if (p->precision == NS3D_FP64 && !(p->weno_eps >= 1e-15))
+  if (p->precision != NS3D_FP64_STRICT && !(p->weno_eps >= 1e-15))
     return snprintf(msg, n, "weno_eps below 1e-15 needs NS3D_FP64_STRICT"), NS3D_EINVAL;
   return NS3D_OK;
 }

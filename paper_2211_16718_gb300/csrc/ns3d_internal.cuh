@@ -54,7 +54,7 @@ struct DirArgs {
   Grid g;
   const double* u;   // stage input state [5][N]
   const double* pm;  // primitives of u [NPRIM][N]
-  const double* fv;  // viscous fluxes [NVISC][N] or nullptr (inviscid)
+  const double* fv;  // viscous fluxes [NVISC][N] or nullptr (inviscid); FP32-bulk: FP32 planes
   int fv_dstride;    // planes per direction in fv: 4 ([12][N], all directions) or 0 ([4][N], this direction)
   double* k;         // RHS accumulator [5][N]
   int epi;           // Epi
@@ -90,10 +90,10 @@ cudaError_t launch_prim(const Grid& g, const double* u, double* pm, double gamma
 constexpr int VISC_ZCHUNK = 16;
 cudaError_t launch_visc(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s,
                         int only_d = -1, int df = 0, int z0 = 0, int z1 = -1);
-// FP32-bulk variants (FP32 arithmetic, results widened to FP64)
-cudaError_t launch_prim32(const Grid& g, const double* u, double* pm, double gamma, int* status, cudaStream_t s);
-cudaError_t launch_visc32(const Grid& g, const double* pm, double* fv, double mu, double kappa, cudaStream_t s,
-                          int only_d = -1);
+// FP32-bulk viscous fluxes, straight from the state u: FP32 planes fv[12][N] (only_d = d: fv[4][N])
+// that the FP32-bulk direction passes read (DirArgs::fv then points at FP32 planes).
+cudaError_t launch_visc32(const Grid& g, const double* u, float* fv, double gamma, double mu, double kappa,
+                          cudaStream_t s, int only_d = -1);
 cudaError_t prepare_dir_kernels();  // per device, before the first launch
 cudaError_t launch_dir(int d, const DirArgs& a, cudaStream_t s);  // dispatches on a.mode, a.variant
 // The tiles [lo, hi) of a direction pass along its range axis: planes z for d = 0, 1, tiles along z
