@@ -19,7 +19,7 @@
 //      part, the viscous interface flux (-f_{i-1} + 7 f_i + 7 f_{i+1} - f_{i+2})/12,
 //      divided by dx and widened to FP64;
 //  E   per point: FP64 difference of its two interface fluxes, then the
-//      accumulation / RK epilogue (k prefetched by cp.async during D).
+//      accumulation / RK epilogue (its operands prefetched by cp.async during D).
 #include <math.h>
 
 #include "df.cuh"
@@ -41,7 +41,7 @@ constexpr int NQ = 9;           // reconstructed scalars: 5 conserved, 4 flux co
 constexpr int NREC = 10;        // per interface: 5 jumps, the sum of u_{1+D}, 4 flux sums
 constexpr int LS = 36;          // line stride (floats) of the scalar planes: >= SEG*NSEG + 5 and a multiple of 4
 constexpr int L4 = NP;          // line stride (float4) of the Roe-input and viscous planes (odd: no bank conflicts)
-static_assert(SEG * (NSEG - 1) + SEG + 5 <= LS && LS % 4 == 0, "segment reads stay in the line");
+static_assert(SEG * (NSEG - 1) + 12 <= LS && LS % 4 == 0, "segment reads (three float4) stay in the line");
 // shared-memory plan (bytes)
 constexpr int OFF_Q = 0;                              // float  [NQ][W][LS]
 constexpr int OFF_R4 = OFF_Q + NQ * W * LS * 4;       // float4 [W][L4]: sqrt(rho), u, v, w
@@ -50,10 +50,12 @@ constexpr int OFF_V4 = OFF_H + ((W * L4 * 4 + 15) & ~15);  // float4 [W][L4]: vi
 constexpr int OFF_REC = OFF_V4 + W * L4 * 16;         // float  [NREC][W][NI]
 constexpr int FS = 30;          // line stride (doubles) of the interface fluxes (no bank conflicts in y, z)
 constexpr int OFF_F = OFF_REC + NREC * W * NI * 4;    // double [5][W][FS]: interface flux / dx
-constexpr int BYTES = OFF_F + 5 * W * FS * 8;
+constexpr int OFF_P2 = OFF_F + 5 * W * FS * 8;         // double [TP*W][10]: epilogue operands U_n and acc / u
+constexpr int BYTES = OFF_P2 + 10 * TP * W * 8;
 static_assert(FS >= NI, "interface-flux line");
 // epilogue operand k (5 doubles per point) prefetched into the scalar planes, dead after BC
 static_assert(5 * TP * W * 8 <= NQ * W * LS * 4, "prefetch slots fit the scalar planes");
+static_assert(BYTES + 1024 <= 233472 / 4, "four CTAs per SM");
 static_assert(OFF_R4 % 16 == 0 && OFF_V4 % 16 == 0 && OFF_F % 8 == 0 && OFF_REC % 16 == 0, "alignment");
 static_assert(TP * W <= THREADS && NI * W <= THREADS, "one point / interface per thread in D and E");
 
@@ -80,36 +82,38 @@ __device__ __forceinline__ float rsqrt_a(float x) {
   return r;
 }
 
-// Weighted WENO5 value from the squared scaled indicators B_k = (4 (eps + beta_k))^2 and the
-// candidate values: sum_k omega_k F_k with omega_k ~ c_k / B_k, c = (1, 6, 3)/10, written over the
-// common denominator.  F2x6 = 6 F_2 and F3x3 = 3 F_3 carry the linear weights.  Unscaled
-// products: valid while every B and product stays in the normal FP32 range (checked by the
-// caller), approximate division (2 ulp).
-__device__ __forceinline__ float weno_fast(float B1, float B2, float B3, float F1, float F2x6, float F3x3) {
-  const float p23 = B2 * B3, p13 = B1 * B3, p12 = B1 * B2;
-  const float num = fmaf(p23, F1, fmaf(p13, F2x6, p12 * F3x3));
-  const float den = fmaf(6.0f, p13, fmaf(3.0f, p12, p23));
-  return __fdividef(num, den);
+// Weighted WENO5 value written as an offset from the candidate c with the linear weight 6/10
+// (Sec. 2.2: sum_k omega_k F_k = F_2 + omega_1 (F_1 - F_2) + omega_3 (F_3 - F_2)), the candidate
+// differences being third differences of the data: with omega_k ~ c_k / B_k, c = (1, 6, 3)/10
+// and B_k = (4 (eps + beta_k))^2, over the common denominator,
+//   value = c + (B2 B3 d1 + 3 B1 B2 d3) / (B2 B3 + 6 B1 B3 + 3 B1 B2),
+// d1 = F_1 - F_2, d3 = F_3 - F_2.  Unscaled products and an approximate reciprocal: valid while
+// every B and product stays in the normal FP32 range (checked by the caller).
+__device__ __forceinline__ float weno_fast(float B1, float B2, float B3, float c, float d1, float d3x3) {
+  const float p23 = B2 * B3, p12 = B1 * B2;
+  const float den = fmaf(6.0f * B1, B3, fmaf(3.0f, p12, p23));
+  const float num = fmaf(p23, d1, p12 * d3x3);
+  return fmaf(num, rcp_a(den), c);
 }
 
 // The same with the indicators rescaled by their common power of two and an IEEE division: any
 // data whose indicators are finite.
-__device__ __forceinline__ float weno_safe(float B1, float B2, float B3, float F1, float F2x6, float F3x3) {
+__device__ __forceinline__ float weno_safe(float B1, float B2, float B3, float c, float d1, float d3x3) {
   const int E = max(exponent_of(B1), max(exponent_of(B2), exponent_of(B3)));
   const float sc = pow2f(max(-E, -126));
   B1 *= sc;
   B2 *= sc;
   B3 *= sc;
-  const float p23 = B2 * B3, p13 = B1 * B3, p12 = B1 * B2;
-  const float num = fmaf(p23, F1, fmaf(p13, F2x6, p12 * F3x3));
-  const float den = fmaf(6.0f, p13, fmaf(3.0f, p12, p23));
-  return __fdiv_rn(num, den);
+  const float p23 = B2 * B3, p12 = B1 * B2;
+  const float den = fmaf(6.0f * B1, B3, fmaf(3.0f, p12, p23));
+  const float num = fmaf(p23, d1, p12 * d3x3);
+  return c + __fdiv_rn(num, den);
 }
 
-// Accumulation / RK epilogue with the operand k from the prefetch slots kp (other operands from
-// global memory, plain loads: the last stage writes the state it reads); the arithmetic of
-// dir_epilogue.
-__device__ __forceinline__ void epilogue32(const DirArgs& a, long long p, const double cv[5], const double* kp) {
+// Accumulation / RK epilogue with its operands from the prefetch slots: kp = k, ops = U_n then
+// acc or the stage input; the arithmetic of dir_epilogue.
+__device__ __forceinline__ void dir_epilogue_pre32(const DirArgs& a, long long p, const double cv[5], const double* kp,
+                                                   const double* ops) {
   const long long N = a.g.N;
   switch (a.epi) {
     case EPI_ACC_WRITE:
@@ -128,7 +132,7 @@ __device__ __forceinline__ void epilogue32(const DirArgs& a, long long p, const 
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const double K = kp[v] + cv[v];
-        a.out[v * N + p] = fma(a.a, K, a.un[v * N + p]);
+        a.out[v * N + p] = fma(a.a, K, ops[v]);
         a.acc[v * N + p] = K;
       }
       break;
@@ -136,36 +140,36 @@ __device__ __forceinline__ void epilogue32(const DirArgs& a, long long p, const 
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const double K = kp[v] + cv[v];
-        a.out[v * N + p] = fma(a.a, K, a.un[v * N + p]);
-        a.acc[v * N + p] = fma(2.0, K, a.acc[v * N + p]);
+        a.out[v * N + p] = fma(a.a, K, ops[v]);
+        a.acc[v * N + p] = fma(2.0, K, ops[5 + v]);
       }
       break;
     case EPI_RK4_LAST:
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const double K = kp[v] + cv[v];
-        a.out[v * N + p] = fma(a.a, a.acc[v * N + p] + K, a.un[v * N + p]);
+        a.out[v * N + p] = fma(a.a, ops[5 + v] + K, ops[v]);
       }
       break;
     case EPI_SSP_1:
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const double K = kp[v] + cv[v];
-        a.out[v * N + p] = fma(a.a, K, a.un[v * N + p]);
+        a.out[v * N + p] = fma(a.a, K, ops[v]);
       }
       break;
     case EPI_SSP_2:
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const double K = kp[v] + cv[v];
-        a.out[v * N + p] = 0.75 * a.un[v * N + p] + 0.25 * fma(a.a, K, a.u[v * N + p]);
+        a.out[v * N + p] = 0.75 * ops[v] + 0.25 * fma(a.a, K, ops[5 + v]);
       }
       break;
     case EPI_SSP_3:
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const double K = kp[v] + cv[v];
-        a.out[v * N + p] = (1.0 / 3.0) * a.un[v * N + p] + (2.0 / 3.0) * fma(a.a, K, a.u[v * N + p]);
+        a.out[v * N + p] = (1.0 / 3.0) * ops[v] + (2.0 / 3.0) * fma(a.a, K, ops[5 + v]);
       }
       break;
     default:
@@ -183,6 +187,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_dir32(const DirArgs a) {
   float* REC = reinterpret_cast<float*>(smem + OFF_REC);
   double* FD = reinterpret_cast<double*>(smem + OFF_F);
   double* PRE = reinterpret_cast<double*>(smem + OFF_Q);
+  double* PRE2 = reinterpret_cast<double*>(smem + OFF_P2);
 
   constexpr int AX = (D == 0) ? 1 : 0;
   const int nD = a.g.n[D], na = a.g.n[AX];
@@ -245,26 +250,43 @@ __global__ void __launch_bounds__(THREADS, 4) k_dir32(const DirArgs a) {
   __syncthreads();
 
   // ---- BC: WENO5 left/right values, SEG interfaces of one scalar on one line per item -------
+  // Items run over lines fastest, then segments, then scalars, so that the 8 threads of a
+  // shared-memory phase read and write 8 different banks.
   {
     const float eps4 = (float)a.eps4;
     const bool eps_ok = eps4 >= 1e-9f && eps4 <= 1.0f;  // unscaled products stay in range (see below)
     for (int it = tid; it < NQ * W * NSEG; it += THREADS) {
       const int m = it / (W * NSEG);
       const int rem = it - m * (W * NSEG);
-      const int line = rem / NSEG, seg = rem - line * NSEG;
+      const int seg = rem / W, line = rem - seg * W;
       const float* q = Q + (m * W + line) * LS + SEG * seg;
       const float4 qa = *reinterpret_cast<const float4*>(q);
       const float4 qb = *reinterpret_cast<const float4*>(q + 4);
-      const float P[SEG + 5] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w, q[8]};
-      // window indicators: window w = points w, w+1, w+2; roles 1..3 (its first-derivative term
-      // taken at its right end, centre, left end)
-      float B[SEG + 3][3];
+      const float4 qc = *reinterpret_cast<const float4*>(q + 8);
+      const float P[SEG + 5] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w, qc.x};
+      // first, second and third differences; window w = points w, w+1, w+2
+      float g[SEG + 4], sd[SEG + 3], T3[SEG + 2], T2[SEG + 2];
       float gmax = 0.0f;
 #pragma unroll
+      for (int k = 0; k < SEG + 4; ++k) {
+        g[k] = P[k + 1] - P[k];
+        gmax = fmaxf(gmax, fabsf(g[k]));
+      }
+#pragma unroll
+      for (int w = 0; w < SEG + 3; ++w) sd[w] = g[w + 1] - g[w];
+#pragma unroll
+      for (int k = 0; k < SEG + 2; ++k) {
+        const float T = sd[k + 1] - sd[k];
+        T3[k] = (1.0f / 3.0f) * T;
+        T2[k] = 0.5f * T;
+      }
+      // window indicators, roles 1..3 (first-derivative term at the window's right end, centre,
+      // left end)
+      float B[SEG + 3][3];
+#pragma unroll
       for (int w = 0; w < SEG + 3; ++w) {
-        const float gm = P[w + 1] - P[w], gp = P[w + 2] - P[w + 1], sd = gp - gm;
-        gmax = fmaxf(gmax, fmaxf(fabsf(gm), fabsf(gp)));
-        const float aa = fmaf((13.0f / 3.0f) * sd, sd, eps4);
+        const float gm = g[w], gp = g[w + 1];
+        const float aa = fmaf((13.0f / 3.0f) * sd[w], sd[w], eps4);
         const float u1 = fmaf(3.0f, gp, -gm), u2 = gm + gp, u3 = fmaf(-3.0f, gm, gp);
         const float b1 = fmaf(u1, u1, aa), b2 = fmaf(u2, u2, aa), b3 = fmaf(u3, u3, aa);
         B[w][0] = b1 * b1;
@@ -273,22 +295,22 @@ __global__ void __launch_bounds__(THREADS, 4) k_dir32(const DirArgs a) {
       }
       // With every first difference <= 64 in magnitude and 1e-9 <= 4 eps <= 1, each B lies in
       // [(4 eps)^2, (34 * 64^2 + 1)^2] and the products and the numerator stay within the normal
-      // FP32 range for values up to ~1e16: the unscaled form is exact to FP32 rounding.
+      // FP32 range: the unscaled form is exact to FP32 rounding.
       const bool fast = eps_ok && gmax <= 64.0f;
       float vL[SEG], vR[SEG];
 #pragma unroll
       for (int j = 0; j < SEG; ++j) {
-        const float P0 = P[j], P1 = P[j + 1], P2 = P[j + 2], P3 = P[j + 3], P4 = P[j + 4], P5 = P[j + 5];
-        const float xR = fmaf(11.0f / 6.0f, P2, fmaf(-7.0f / 6.0f, P1, (1.0f / 3.0f) * P0));
-        const float eR = fmaf(1.0f / 3.0f, P3, fmaf(5.0f / 6.0f, P2, (-1.0f / 6.0f) * P1));
-        const float eL = fmaf(-1.0f / 6.0f, P4, fmaf(5.0f / 6.0f, P3, (1.0f / 3.0f) * P2));
-        const float xL = fmaf(1.0f / 3.0f, P5, fmaf(-7.0f / 6.0f, P4, (11.0f / 6.0f) * P3));
+        // interface j: left-biased from points j..j+4, right-biased from j+1..j+5; candidate-2
+        // values eR (left) and eL (right); F_1 - F_2 = -T_j/3, F_3 - F_2 = -T_{j+1}/6 (left),
+        // F_1 - F_2 = T_{j+2}/3, F_3 - F_2 = T_{j+1}/6 (right)
+        const float eR = fmaf(1.0f / 3.0f, g[j + 2], fmaf(1.0f / 6.0f, g[j + 1], P[j + 2]));
+        const float eL = fmaf(-1.0f / 6.0f, g[j + 3], fmaf(-1.0f / 3.0f, g[j + 2], P[j + 3]));
         if (fast) {
-          vL[j] = weno_fast(B[j][0], B[j + 1][1], B[j + 2][2], xR, 6.0f * eR, 3.0f * eL);
-          vR[j] = weno_fast(B[j + 3][2], B[j + 2][1], B[j + 1][0], xL, 6.0f * eL, 3.0f * eR);
+          vL[j] = weno_fast(B[j][0], B[j + 1][1], B[j + 2][2], eR, -T3[j], -T2[j + 1]);
+          vR[j] = weno_fast(B[j + 3][2], B[j + 2][1], B[j + 1][0], eL, T3[j + 2], T2[j + 1]);
         } else {
-          vL[j] = weno_safe(B[j][0], B[j + 1][1], B[j + 2][2], xR, 6.0f * eR, 3.0f * eL);
-          vR[j] = weno_safe(B[j + 3][2], B[j + 2][1], B[j + 1][0], xL, 6.0f * eL, 3.0f * eR);
+          vL[j] = weno_safe(B[j][0], B[j + 1][1], B[j + 2][2], eR, -T3[j], -T2[j + 1]);
+          vR[j] = weno_safe(B[j + 3][2], B[j + 2][1], B[j + 1][0], eL, T3[j + 2], T2[j + 1]);
         }
       }
       float* r = REC + line * NI + SEG * seg;
@@ -317,14 +339,23 @@ __global__ void __launch_bounds__(THREADS, 4) k_dir32(const DirArgs a) {
       line = it - pp * W;
     }
   };
-  const bool need_k = (a.epi != EPI_ACC_WRITE);
-  if (need_k && tid < TP * W) {
+  const int nops = epilogue_operands(a.epi);  // k, then U_n, then acc or the stage input
+  if (nops > 0 && tid < TP * W) {
     int pp, line;
     point_of(tid, pp, line);
     if (s0 + pp < nD && a0 + line < na) {
       const long long p = tile_flat<D>(a.g, s0 + pp, a0 + line, bz);
 #pragma unroll
       for (int v = 0; v < 5; ++v) cp_async8(PRE + 5 * tid + v, a.k + v * N + p);
+      if (nops >= 10) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) cp_async8(PRE2 + 10 * tid + v, a.un + v * N + p);
+      }
+      if (nops == 15) {
+        const double* third = (a.epi == EPI_SSP_2 || a.epi == EPI_SSP_3) ? a.u : a.acc;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) cp_async8(PRE2 + 10 * tid + 5 + v, third + v * N + p);
+      }
     }
   }
   cp_async_commit();
@@ -420,7 +451,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_dir32(const DirArgs a) {
       double cv[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) cv[v] = fd[v * W * FS] - fd[v * W * FS + 1];
-      epilogue32(a, tile_flat<D>(a.g, s0 + pp, a0 + line, bz), cv, PRE + 5 * tid);
+      dir_epilogue_pre32(a, tile_flat<D>(a.g, s0 + pp, a0 + line, bz), cv, PRE + 5 * tid, PRE2 + 10 * tid);
     }
   }
 }
