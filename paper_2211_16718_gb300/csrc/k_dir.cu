@@ -1,6 +1,7 @@
 // Standalone launches of the fused direction pass (one tile per CTA); the tile
 // computation itself is dir_tile in k_dir_impl.cuh.  Tile shapes (points along
-// the pencil x lines) are template variants chosen per grid by the autotuner:
+// the pencil x lines) are template variants: a context uses the one set by
+// ns3d_set_variant (default 0); an ensemble's autotuner picks one per grid size.
 //   MODE 0 (all FP64):              32 x 4
 //   MODE 1 (FP64 + double-float):   variant 0: 24 x 4, 1: 16 x 4, 2: 40 x 2
 // All variants compute bitwise identical results (the per-interface arithmetic

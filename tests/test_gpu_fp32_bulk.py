@@ -129,3 +129,25 @@ def test_fp32_bulk_tile_variants_bitwise_identical(ns3d):
         s.close()
     for v in (1, 2):
         assert np.array_equal(outs[v][0], outs[0][0]) and np.array_equal(outs[v][1], outs[0][1])
+
+
+def test_fp32_bulk_hit256_sampled_points(ns3d, orc):
+    """256^3 decaying turbulence (the tile shape leaves ragged tiles at 256): the FP32-bulk
+    RHS at 2048 sampled points, including the periodic seams and tile edges, against the
+    oracle's local evaluation, within the FP32 bound."""
+    import torch
+    n = 256
+    u = I.isotropic_turbulence(n, seed=0)
+    mu = I.hit_mu_eff()
+    s = ns3d.Solver(n, n, n, mu_eff=mu, precision=ns3d.NS3D_FP32_BULK)
+    r = s.rhs(_gpu(u))
+    rng = np.random.default_rng(3)
+    edges = [0, 1, 26, 27, 28, 53, 54, 242, 243, 255]
+    extra = [(k * n + j) * n + i for i in edges for j in (0, 27, 255) for k in (0, 128, 255)]
+    idx = np.unique(np.concatenate([rng.choice(n ** 3, size=2048, replace=False), extra]))
+    r32 = r.reshape(5, -1)[:, torch.from_numpy(idx).cuda()].cpu().numpy()
+    del r
+    s.close()
+    r64 = orc.rhs_points(orc.Params(n, n, n, mu_eff=mu), u, idx).T
+    err = np.abs(r32 - r64).max() / flux_scale(u, (2 * math.pi,) * 3)
+    assert err <= FLUX_TOL, err
