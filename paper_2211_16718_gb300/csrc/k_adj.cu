@@ -577,45 +577,43 @@ __global__ void __launch_bounds__(APL::THREADS, 2) k_adj_dir(const AdjArgs a) {
 // the adjoint input, each tile divides lambda by the power of two of its largest magnitude
 // and multiplies its results back (exact).
 // ============================================================================================
-template <int TP_, int W_>
+template <int TP_, int W_, int THREADS_, int MIN_CTAS_>
 struct AdjPlanDF {
   static constexpr int TP = TP_;
   static constexpr int W = W_;
-  static constexpr int THREADS = 256;
+  static constexpr int THREADS = THREADS_;
+  static constexpr int MIN_CTAS = MIN_CTAS_;
   static constexpr int NP = TP + 10;  // points incl. a halo of 5 each side
   static constexpr int NI = TP + 5;   // interfaces
   static constexpr int NW = TP + 8;   // 3-point windows starting at 0 .. NW-1
   static constexpr int OFF_Q = 0;                        // [9][NP*W] doubles
-  static constexpr int OFF_RI = OFF_Q + 9 * NP * W;      // [6][NP*W]
-  static constexpr int OFF_L = OFF_RI + 6 * NP * W;      // [5][NP*W] lambda / 2^E
+  static constexpr int OFF_RI = OFF_Q + 9 * NP * W;      // [8][NP*W] double-float sqrt(rho), u, v, w, H;
+                                                         //   FP64 p; double-float rho, e
+  static constexpr int OFF_L = OFF_RI + 8 * NP * W;      // [5][NP*W] lambda / 2^E
   static constexpr int OFF_G = OFF_L + 5 * NP * W;       // [9][NP*W] float2 first differences
-  static constexpr int OFF_B = OFF_G + 9 * NP * W;       // [9][3][NW*W] float2 b_k of every window
+  static constexpr int OFF_B = OFF_G + 9 * NP * W;       // [9][3][NW*W] float2 1/b_k of every window
   static constexpr int OFF_REC = OFF_B + 27 * NW * W;    // [10][NI*W] doubles: u^L, u^R of u_0..u_4
-  static constexpr int OFF_RD = OFF_REC + 10 * NI * W;   // [15][NI*W] doubles: Roe adjoints
+  static constexpr int OFF_RD = OFF_REC + 10 * NI * W;   // [15][NI*W] double-float Roe adjoints
   static constexpr int OFF_WC = OFF_RD + 15 * NI * W;    // [9][6][NI*W] float2 stencil contributions
   static constexpr int WORDS = OFF_WC + 54 * NI * W;
   static constexpr int BYTES = WORDS * 8;
 };
-using APF = AdjPlanDF<16, 4>;
+using APF = AdjPlanDF<32, 2, 256, 2>;
 
 __device__ __forceinline__ df df_sub(df x, df y) { return df_add_fast(x, df_neg(y)); }
 __device__ __forceinline__ float2 df_pack(df x) { return make_float2(x.hi, x.lo); }
 __device__ __forceinline__ df df_unpack(float2 v) { return df{v.x, v.y}; }
 
-// The three weights of one reconstruction from its b_k (candidate order 0, 1, 2; optimal
-// weights 1, 6, 3 over 10), with a common power-of-two scaling (omega is scale-free).
+// The three weights of one reconstruction from the reciprocals r_k = 1/b_k of its window
+// terms (candidate order 0, 1, 2; optimal weights 1, 6, 3 over 10):
+// omega_k = c_k r_k^2 / sum_j c_j r_j^2.  With the window terms' range checked (b <= 1e18,
+// b >= 4 eps), r^2 stays inside the float range and needs no rescaling.
 // Products and positive sums in this section are left unnormalised where they feed another
 // double-float operation (df_mul_u and friends: the same values, |lo| a few ulp(hi)).
-__device__ __forceinline__ void df_omega(df b0, df b1, df b2, df om[3]) {
-  df B0 = df_sqr_u(b0), B1 = df_sqr_u(b1), B2 = df_sqr_u(b2);
-  const int E = max(exponent_of(B0.hi), max(exponent_of(B1.hi), exponent_of(B2.hi)));
-  const float sc = pow2f(-E);
-  B0 = df{B0.hi * sc, B0.lo * sc};
-  B1 = df{B1.hi * sc, B1.lo * sc};
-  B2 = df{B2.hi * sc, B2.lo * sc};
-  const df a0 = df_mul_u(B1, B2);
-  const df a1 = df_mul_f_u(df_mul_u(B0, B2), 6.0f);
-  const df a2 = df_mul_f_u(df_mul_u(B0, B1), 3.0f);
+__device__ __forceinline__ void df_omega(df r0, df r1, df r2, df om[3]) {
+  const df a0 = df_sqr_u(r0);
+  const df a1 = df_mul_f_u(df_sqr_u(r1), 6.0f);
+  const df a2 = df_mul_f_u(df_sqr_u(r2), 3.0f);
   const df r = df_div(df{1.0f, 0.0f}, df_add_pos_u(a0, df_add_pos_u(a1, a2)));
   om[0] = df_mul_u(a0, r);
   om[1] = df_mul_u(a1, r);
@@ -639,8 +637,9 @@ __device__ __forceinline__ df df_offset(df g0, df g1, df g2, df g3, const df om[
 
 
 // y * d(value)/d(q_t), t = 0..4, of the reconstruction of stencil differences g0..g3 with
-// window terms b0..b2 and weights om (as weno_adjoint, in double-float).
-__device__ __forceinline__ void df_recon_adjoint(df g0, df g1, df g2, df g3, df b0, df b1, df b2, const df om[3],
+// the reciprocals rb0..rb2 of its window terms and weights om (as weno_adjoint, in
+// double-float).
+__device__ __forceinline__ void df_recon_adjoint(df g0, df g1, df g2, df g3, df rb0, df rb1, df rb2, const df om[3],
                                                  df y, const DFConst& k, df out[5]) {
   df s[3], E0, E2;
   const df M = df_offset(g0, g1, g2, g3, om, k, E0, E2, s);
@@ -649,9 +648,9 @@ __device__ __forceinline__ void df_recon_adjoint(df g0, df g1, df g2, df g3, df 
   const df v2 = df_sub(g3, df_mul_f_u(g2, 3.0f));
   const df y0 = df_mul_u(y, om[0]), y1 = df_mul_u(y, om[1]), y2 = df_mul_u(y, om[2]);
   // adjoints of b_k: -2 y_k (q_k - q) / b_k with q_0 - q = E0 - M, q_1 - q = -M, q_2 - q = E2 - M
-  const df k0 = df_twice(df_div(df_mul_u(y0, df_sub(M, E0)), b0));
-  const df k1 = df_twice(df_div(df_mul_u(y1, M), b1));
-  const df k2 = df_twice(df_div(df_mul_u(y2, df_sub(M, E2)), b2));
+  const df k0 = df_twice(df_mul(df_mul_u(y0, df_sub(M, E0)), rb0));
+  const df k1 = df_twice(df_mul(df_mul_u(y1, M), rb1));
+  const df k2 = df_twice(df_mul(df_mul_u(y2, df_sub(M, E2)), rb2));
   // direct term sum_k y_k dq_k/dq_t
   out[0] = df_mul_u(y0, k.third);
   out[1] = df_neg(df_mul_u(df_add_fast(df_mul_f_u(y0, 7.0f), y1), k.sixth));
@@ -677,8 +676,176 @@ __device__ __forceinline__ void df_recon_adjoint(df g0, df g1, df g2, df g3, df 
 
 __device__ __forceinline__ double pow2d(int k) { return __hiloint2double((k + 1023) << 20, 0); }
 
+__device__ __forceinline__ df df_half(df x) { return df{0.5f * x.hi, 0.5f * x.lo}; }
+// a * b + c with an unnormalised product (normalised result)
+__device__ __forceinline__ df df_fma(df a, df b, df c) { return df_add_fast(df_mul_u(a, b), c); }
+
+// |lambda| with Harten's fix in double-float (harten<> in FP64): value, d/dlambda, d/ddelta.
+__device__ __forceinline__ df harten_df(df lam, df delta, df& dl, df& dd) {
+  const df a = df_abs(lam);
+  if (df_lt(a, delta)) {
+    const df rd = df_div(df{1.0f, 0.0f}, delta);
+    const df lr = df_mul(lam, rd);
+    dl = lr;
+    dd = df_sub(df{0.5f, 0.0f}, df_half(df_sqr(lr)));
+    return df_half(df_mul(df_add_pos(df_sqr(lam), df_sqr(delta)), rd));
+  }
+  dl = df{(lam.hi > 0.0f) ? 1.0f : ((lam.hi < 0.0f) ? -1.0f : 0.0f), 0.0f};
+  dd = df{0.0f, 0.0f};
+  return a;
+}
+
+// Adjoint of the Roe flux at one interface in double-float arithmetic on the FP32 pipe: the
+// algebra of roe_adjoint (Sec. 2.2, Eq. Roe, wave strengths, Harten's fix, Roe average of the
+// grid-point states a = i, b = i+1), every quantity as a double-float (~48 bits) instead of
+// FP64.  du: the jump of the conserved reconstructions, Lh: the adjoint of the interface flux;
+// returns dub (adjoint of du) and ga, gb (adjoints of the two conserved point states).  Returns
+// 1 for a non-physical Roe state, 2 for values outside the float range of the double-float
+// arithmetic.
 template <int D>
-__global__ void __launch_bounds__(APF::THREADS, 2) k_adj_dir_df(const AdjArgs a) {
+__device__ __forceinline__ int roe_adjoint_df(const df du[5], const df Lh[5], df ra, df rb, const df Va[3],
+                                              const df Vb[3], df Ha, df Hb, df rho_a, df e_a, df rho_b, df e_b,
+                                              df gamma, df gm1, df hdelta, df dub[5], df ga[5], df gb[5]) {
+  constexpr int T1 = (D == 0) ? 1 : 0;
+  constexpr int T2 = (D == 2) ? 1 : 2;
+  const df one{1.0f, 0.0f}, zero{0.0f, 0.0f};
+  const df rsum = df_add_pos(ra, rb);
+  const df rs = df_div(one, rsum);
+  const df wa = df_mul(ra, rs), wb = df_mul(rb, rs);
+  df V[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) V[m] = df_add_fast(df_mul_u(wa, Va[m]), df_mul_u(wb, Vb[m]));
+  const df H = df_add_pos(df_mul_u(wa, Ha), df_mul_u(wb, Hb));
+  const df q2 = df_add_pos_u(df_sqr_u(V[0]), df_add_pos_u(df_sqr_u(V[1]), df_sqr_u(V[2])));
+  const df q2h = fast_two_sum(0.5f * q2.hi, 0.5f * q2.lo);
+  const df c2 = df_mul(df_sub(H, q2h), gm1);
+  int flags = (c2.hi > 0.0f) ? 0 : 1;
+  flags |= (c2.hi > 1e-30f && c2.hi < 1e30f && rsum.hi > 1e-30f && rsum.hi < 1e30f && rho_a.hi > 1e-30f &&
+            rho_a.hi < 1e30f && rho_b.hi > 1e-30f && rho_b.hi < 1e30f && fabsf(H.hi) < 1e30f)
+               ? 0
+               : 2;
+  const df c = df_sqrt(c2);
+  const df rc = df_div(one, c);
+  const df un = V[D], vt1 = V[T1], vt2 = V[T2];
+  const df rc2 = df_sqr(rc);
+  const df b1 = df_mul(gm1, rc2);
+  const df vdm = df_add_fast(df_mul_u(V[0], du[1]), df_add_fast(df_mul_u(V[1], du[2]), df_mul_u(V[2], du[3])));
+  const df Y = df_sub(df_fma(q2h, du[0], du[4]), vdm);
+  const df phi = df_mul(b1, Y);
+  const df X = df_sub(df_mul_u(un, du[0]), du[1 + D]);
+  const df ach = df_half(df_mul(X, rc));
+  const df a2 = df_sub(du[0], phi);
+  const df a3 = df_sub(du[1 + T1], df_mul_u(vt1, du[0]));
+  const df a4 = df_sub(du[1 + T2], df_mul_u(vt2, du[0]));
+  const df phh = df_half(phi);
+  const df a1 = df_add_fast(phh, ach), a5 = df_sub(phh, ach);
+  const df delta = df_mul(hdelta, c);
+  df dl1, dd1, dl5, dd5;
+  const df l1 = harten_df(df_sub(un, c), delta, dl1, dd1);
+  const df l5 = harten_df(df_add_fast(un, c), delta, dl5, dd5);
+  const df l2 = df_abs(un);
+  const float sg2 = (un.hi > 0.0f) ? 1.0f : ((un.hi < 0.0f) ? -1.0f : 0.0f);
+  const df A1 = df_mul(l1, a1), A2 = df_mul(l2, a2), A3 = df_mul(l2, a3), A4 = df_mul(l2, a4), A5 = df_mul(l5, a5);
+  const df S = df_add_fast(A1, A5), d0 = df_add_fast(S, A2), cD = df_mul(c, df_sub(A5, A1));
+  // backward: the adjoint of the dissipation vector is -Lhat/2
+  df Db[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Db[v] = df{-0.5f * Lh[v].hi, -0.5f * Lh[v].lo};
+  const df d0b = df_fma(Db[1 + D], un, df_fma(Db[1 + T1], vt1, df_fma(Db[1 + T2], vt2, Db[0])));
+  const df cDb = df_fma(Db[4], un, Db[1 + D]);
+  const df Sb = df_fma(Db[4], H, d0b);
+  const df A2b = df_fma(Db[4], q2h, d0b);
+  const df A3b = df_fma(Db[4], vt1, Db[1 + T1]);
+  const df A4b = df_fma(Db[4], vt2, Db[1 + T2]);
+  const df ccDb = df_mul(c, cDb);
+  const df A1b = df_sub(Sb, ccDb), A5b = df_add_fast(Sb, ccDb);
+  df unb = df_add_fast(df_mul_u(Db[1 + D], d0), df_mul_u(Db[4], cD));
+  df vt1b = df_add_fast(df_mul_u(Db[1 + T1], d0), df_mul_u(Db[4], A3));
+  df vt2b = df_add_fast(df_mul_u(Db[1 + T2], d0), df_mul_u(Db[4], A4));
+  df Hbar = df_mul(Db[4], S);
+  df q2hb = df_mul(Db[4], A2);
+  df cb = df_mul(cDb, df_sub(A5, A1));
+  // A_k = l_k a_k
+  const df a1b = df_mul(A1b, l1), a2b = df_mul(A2b, l2), a3b = df_mul(A3b, l2), a4b = df_mul(A4b, l2);
+  const df a5b = df_mul(A5b, l5);
+  const df l1b = df_mul(A1b, a1), l5b = df_mul(A5b, a5);
+  const df l2b = df_fma(A2b, a2, df_fma(A3b, a3, df_mul_u(A4b, a4)));
+  const df t1 = df_mul_u(dl1, l1b), t5 = df_mul_u(dl5, l5b);
+  unb = df_add_fast(df_add_fast(t1, t5), df_add_fast(df{sg2 * l2b.hi, sg2 * l2b.lo}, unb));
+  cb = df_add_fast(df_add_fast(df_sub(t5, t1), df_mul_u(hdelta, df_fma(dd1, l1b, df_mul_u(dd5, l5b)))), cb);
+  // wave strengths
+  const df phib = df_sub(df_half(df_add_fast(a1b, a5b)), a2b);
+  const df achb = df_sub(a1b, a5b);
+  dub[0] = df_sub(a2b, df_add_fast(df_mul_u(vt1, a3b), df_mul_u(vt2, a4b)));
+  dub[1 + T1] = a3b;
+  dub[1 + T2] = a4b;
+  vt1b = df_sub(vt1b, df_mul_u(a3b, du[0]));
+  vt2b = df_sub(vt2b, df_mul_u(a4b, du[0]));
+  const df Xb = df_half(df_mul(rc, achb));
+  df rcb = df_half(df_mul(X, achb));
+  unb = df_fma(Xb, du[0], unb);
+  dub[0] = df_fma(Xb, un, dub[0]);
+  dub[1 + D] = df_neg(Xb);
+  const df b1b = df_mul(phib, Y);
+  const df Yb = df_mul(phib, b1);
+  q2hb = df_fma(Yb, du[0], q2hb);
+  dub[0] = df_fma(Yb, q2h, dub[0]);
+  dub[4] = Yb;
+  df Vbar[3];
+  Vbar[D] = unb;
+  Vbar[T1] = vt1b;
+  Vbar[T2] = vt2b;
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    Vbar[m] = df_sub(Vbar[m], df_mul_u(Yb, du[1 + m]));  // vdm = V . du_m
+    dub[1 + m] = df_sub(dub[1 + m], df_mul_u(Yb, V[m]));
+  }
+  rcb = df_fma(b1b, df_twice(df_mul(gm1, rc)), rcb);
+  cb = df_sub(cb, df_mul_u(rcb, rc2));
+  // c = sqrt(gm1 (H - q2h))
+  const df c2b = df_half(df_mul(cb, rc));
+  Hbar = df_fma(gm1, c2b, Hbar);
+  q2hb = df_sub(q2hb, df_mul_u(gm1, c2b));
+#pragma unroll
+  for (int m = 0; m < 3; ++m) Vbar[m] = df_fma(q2hb, V[m], Vbar[m]);
+  // Roe average of the point states a, b
+  df rab = df_mul_u(Hbar, df_sub(Ha, H)), rbb = df_mul_u(Hbar, df_sub(Hb, H));
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    rab = df_fma(Vbar[m], df_sub(Va[m], V[m]), rab);
+    rbb = df_fma(Vbar[m], df_sub(Vb[m], V[m]), rbb);
+  }
+  rab = df_mul(rab, rs);
+  rbb = df_mul(rbb, rs);
+  // point primitives: V = m/rho, H = gamma e/rho - gm1 |V|^2/2, sqrt(rho)
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const df wgt = side ? wb : wa;
+    const df* Vp = side ? Vb : Va;
+    const df rho = side ? rho_b : rho_a, e = side ? e_b : e_a, sr = side ? rb : ra;
+    const df rr = df_div(one, rho);
+    const df Hb_ = df_mul(wgt, Hbar);
+    const df gH = df_mul(Hb_, gm1);
+    const df srb = side ? rbb : rab;
+    df Vt[3], vdot = zero;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      Vt[m] = df_sub(df_mul_u(wgt, Vbar[m]), df_mul_u(gH, Vp[m]));
+      vdot = df_fma(Vt[m], Vp[m], vdot);
+    }
+    df* gs = side ? gb : ga;
+    const df Hg = df_mul(Hb_, gamma);
+    gs[4] = df_mul(Hg, rr);
+    // d sqrt(rho)/d rho = 1/(2 sqrt(rho)) = sqrt(rho) / (2 rho)
+    gs[0] = df_sub(df_mul_u(df_half(srb), df_mul(sr, rr)), df_mul_u(df_fma(Hg, df_mul(e, rr), vdot), rr));
+#pragma unroll
+    for (int m = 0; m < 3; ++m) gs[1 + m] = df_mul(Vt[m], rr);
+  }
+  return flags;
+}
+
+template <int D>
+__global__ void __launch_bounds__(APF::THREADS, APF::MIN_CTAS) k_adj_dir_df(const AdjArgs a) {
   extern __shared__ double sm[];
   __shared__ int s_emax;
   constexpr int TP = APF::TP, NP = APF::NP, NI = APF::NI, NW = APF::NW, W = APF::W;
@@ -732,12 +899,15 @@ __global__ void __launch_bounds__(APF::THREADS, 2) k_adj_dir_df(const AdjArgs a)
     q[6 * NP * W + s] = (D == 1) ? fma(U[2], un, pr) : U[2] * un;
     q[7 * NP * W + s] = (D == 2) ? fma(U[3], un, pr) : U[3] * un;
     q[8 * NP * W + s] = (U[4] + pr) * un;
-    ri[0 * NP * W + s] = __ldg(a.pm + PM_SR * N + p);
-    ri[1 * NP * W + s] = vx;
-    ri[2 * NP * W + s] = vy;
-    ri[3 * NP * W + s] = vz;
-    ri[4 * NP * W + s] = __ldg(a.pm + PM_H * N + p);
+    float2* rf = reinterpret_cast<float2*>(ri);
+    rf[0 * NP * W + s] = df_pack(d2df_bits(__ldg(a.pm + PM_SR * N + p)));
+    rf[1 * NP * W + s] = df_pack(d2df_bits(vx));
+    rf[2 * NP * W + s] = df_pack(d2df_bits(vy));
+    rf[3 * NP * W + s] = df_pack(d2df_bits(vz));
+    rf[4 * NP * W + s] = df_pack(d2df_bits(__ldg(a.pm + PM_H * N + p)));
     ri[5 * NP * W + s] = pr;
+    rf[6 * NP * W + s] = df_pack(d2df_bits(U[0]));
+    rf[7 * NP * W + s] = df_pack(d2df_bits(U[4]));
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       const double l = a.lam_scale * __ldg(a.lam + v * N + p);
@@ -771,7 +941,7 @@ __global__ void __launch_bounds__(APF::THREADS, 2) k_adj_dir_df(const AdjArgs a)
   }
   __syncthreads();
 
-  // ---- B: b_k of every window ------------------------------------------------------------
+  // ---- B: window terms b_k of every window, stored as 1/b_k -----------------------------------
   for (int item = tid; item < 9 * NW * W; item += APF::THREADS) {
     const int m = item / (NW * W);
     int w, line;
@@ -784,9 +954,11 @@ __global__ void __launch_bounds__(APF::THREADS, 2) k_adj_dir_df(const AdjArgs a)
     const df b1 = df_add_pos_u(df_sqr_u(df_add_fast(g0, g1)), aa);
     const df b2 = df_add_pos_u(df_sqr_u(df_sub(g1, df_mul_f_u(g0, 3.0f))), aa);
     const int o = tile_idx<D, W>(w, line, NW);
-    Bw[(m * 3 + 0) * NW * W + o] = df_pack(b0);
-    Bw[(m * 3 + 1) * NW * W + o] = df_pack(b1);
-    Bw[(m * 3 + 2) * NW * W + o] = df_pack(b2);
+    // their reciprocals: the weights (c_k / b_k^2) and the adjoints of b_k (omega_k / b_k) need only those
+    const df one{1.0f, 0.0f};
+    Bw[(m * 3 + 0) * NW * W + o] = df_pack(df_div(one, b0));
+    Bw[(m * 3 + 1) * NW * W + o] = df_pack(df_div(one, b1));
+    Bw[(m * 3 + 2) * NW * W + o] = df_pack(df_div(one, b2));
     // b^2 must stay inside the float range (differences of the data up to ~1e9)
     range_bad |= !(fmaxf(b0.hi, fmaxf(b1.hi, b2.hi)) < 1e18f);
   }
@@ -825,34 +997,38 @@ __global__ void __launch_bounds__(APF::THREADS, 2) k_adj_dir_df(const AdjArgs a)
   }
   __syncthreads();
 
-  // ---- D: adjoint of the Roe flux -----------------------------------------------------------
+  // ---- D: adjoint of the Roe flux, in double-float -----------------------------------------
   {
     int bad = 0;
+    const df gam = d2df_bits(a.gamma), gm1 = d2df_bits(a.gamma - 1.0), hd = d2df_bits(a.hdelta);
+    const float2* rf = reinterpret_cast<const float2*>(ri);
+    float2* rdf = reinterpret_cast<float2*>(rd);
     for (int item = tid; item < NI * W; item += APF::THREADS) {
       int f, line;
       tile_split<D, W>(item, NI, f, line);
       const int o = tile_idx<D, W>(f, line, NI);
       const int sa = tile_idx<D, W>(f + 2, line, NP), sb = tile_idx<D, W>(f + 3, line, NP);
-      double du[5], Lh[5], Va[3], Vb[3];
+      df du[5], Lh[5], Va[3], Vb[3];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const df j = df_unpack(reinterpret_cast<const float2*>(rec)[v * NI * W + o]);
-        du[v] = f2d_bits(j.hi) + f2d_bits(j.lo);
-        Lh[v] = (lm[v * NP * W + sb] - lm[v * NP * W + sa]) * rdx;
+        du[v] = df_unpack(reinterpret_cast<const float2*>(rec)[v * NI * W + o]);
+        Lh[v] = d2df_bits((lm[v * NP * W + sb] - lm[v * NP * W + sa]) * rdx);
       }
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
-        Va[m] = ri[(1 + m) * NP * W + sa];
-        Vb[m] = ri[(1 + m) * NP * W + sb];
+        Va[m] = df_unpack(rf[(1 + m) * NP * W + sa]);
+        Vb[m] = df_unpack(rf[(1 + m) * NP * W + sb]);
       }
-      double dub[5], ga[5], gb[5];
-      bad |= roe_adjoint<D, true>(du, Lh, ri[sa], ri[sb], Va, Vb, ri[4 * NP * W + sa], ri[4 * NP * W + sb], q[sa],
-                                  q[4 * NP * W + sa], q[sb], q[4 * NP * W + sb], a.gamma, a.hdelta, dub, ga, gb);
+      df dub[5], ga[5], gb[5];
+      bad |= roe_adjoint_df<D>(du, Lh, df_unpack(rf[sa]), df_unpack(rf[sb]), Va, Vb, df_unpack(rf[4 * NP * W + sa]),
+                               df_unpack(rf[4 * NP * W + sb]), df_unpack(rf[6 * NP * W + sa]),
+                               df_unpack(rf[7 * NP * W + sa]), df_unpack(rf[6 * NP * W + sb]),
+                               df_unpack(rf[7 * NP * W + sb]), gam, gm1, hd, dub, ga, gb);
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        rd[v * NI * W + o] = dub[v];
-        rd[(5 + v) * NI * W + o] = ga[v];
-        rd[(10 + v) * NI * W + o] = gb[v];
+        rdf[v * NI * W + o] = df_pack(dub[v]);
+        rdf[(5 + v) * NI * W + o] = df_pack(ga[v]);
+        rdf[(10 + v) * NI * W + o] = df_pack(gb[v]);
       }
     }
     if (__any_sync(0xffffffffu, bad & 1) && (tid & 31) == 0) atomicOr(a.status, ST_NONPHYS);
@@ -867,22 +1043,20 @@ __global__ void __launch_bounds__(APF::THREADS, 2) k_adj_dir_df(const AdjArgs a)
     tile_split<D, W>(item - m * NI * W, NI, f, line);
     const int o = tile_idx<D, W>(f, line, NI);
     const int sa = tile_idx<D, W>(f + 2, line, NP), sb = tile_idx<D, W>(f + 3, line, NP);
-    double yL, yR;
+    df yL, yR;
     if (m < 5) {
-      const double gdu = rd[m * NI * W + o];
-      yL = -gdu;
+      const df gdu = df_unpack(reinterpret_cast<const float2*>(rd)[m * NI * W + o]);
+      yL = df_neg(gdu);
       yR = gdu;
       if (m == 1 + D) {  // mass flux f_0 = u_{1+D}: (f^L + f^R)/2 part
-        const double h0 = 0.5 * ((lm[sb] - lm[sa]) * rdx);
-        yL += h0;
-        yR += h0;
+        const df h0 = d2df_bits(0.5 * ((lm[sb] - lm[sa]) * rdx));
+        yL = df_add_fast(yL, h0);
+        yR = df_add_fast(yR, h0);
       }
     } else {
-      const double hm = 0.5 * ((lm[(m - 4) * NP * W + sb] - lm[(m - 4) * NP * W + sa]) * rdx);
-      yL = hm;
-      yR = hm;
+      yL = yR = d2df_bits(0.5 * ((lm[(m - 4) * NP * W + sb] - lm[(m - 4) * NP * W + sa]) * rdx));
     }
-    range_bad |= !(fabs(yL) < 1e30 && fabs(yR) < 1e30);
+    range_bad |= !(fabsf(yL.hi) < 1e30f && fabsf(yR.hi) < 1e30f);
     const float2* Gm = G + m * NP * W;
     df g[5];
 #pragma unroll
@@ -902,9 +1076,9 @@ __global__ void __launch_bounds__(APF::THREADS, 2) k_adj_dir_df(const AdjArgs a)
       df_omega(ldb(2, f + 3), ldb(1, f + 2), ldb(0, f + 1), omR);
     }
     df cL[5], cR[5];
-    df_recon_adjoint(g[0], g[1], g[2], g[3], ldb(0, f), ldb(1, f + 1), ldb(2, f + 2), omL, d2df_bits(yL), kc, cL);
+    df_recon_adjoint(g[0], g[1], g[2], g[3], ldb(0, f), ldb(1, f + 1), ldb(2, f + 2), omL, yL, kc, cL);
     df_recon_adjoint(df_neg(g[4]), df_neg(g[3]), df_neg(g[2]), df_neg(g[1]), ldb(2, f + 3), ldb(1, f + 2),
-                     ldb(0, f + 1), omR, d2df_bits(yR), kc, cR);
+                     ldb(0, f + 1), omR, yR, kc, cR);
     wm[0 * NI * W + o] = df_pack(cL[0]);
 #pragma unroll
     for (int j = 1; j < 5; ++j) wm[j * NI * W + o] = df_pack(df_add_fast(cL[j], cR[5 - j]));
@@ -921,22 +1095,30 @@ __global__ void __launch_bounds__(APF::THREADS, 2) k_adj_dir_df(const AdjArgs a)
     tile_split<D, W>(item, TP, pp, line);
     if (s0 + pp >= nD || a0 + line >= na) continue;
     const int pos = pp + 5;
-    double gsum[9];
+    const int oa = tile_idx<D, W>(pos - 2, line, NI), ob = tile_idx<D, W>(pos - 3, line, NI);
+    const float2* rdf = reinterpret_cast<const float2*>(rd);
+    double gsum[9], cv[5];
 #pragma unroll
     for (int m = 0; m < 9; ++m) {
       const float2* wm = wc + m * 6 * NI * W;
       df acc = df_unpack(wm[tile_idx<D, W>(pos, line, NI)]);
 #pragma unroll
       for (int j = 1; j < 6; ++j) acc = df_add_fast(acc, df_unpack(wm[j * NI * W + tile_idx<D, W>(pos - j, line, NI)]));
+      if (m < 5)  // the Roe-average adjoints of the two interfaces next to the point
+        acc = df_add_fast(acc, df_add_fast(df_unpack(rdf[(5 + m) * NI * W + oa]), df_unpack(rdf[(10 + m) * NI * W + ob])));
       gsum[m] = f2d_bits(acc.hi) + f2d_bits(acc.lo);
     }
-    const int oa = tile_idx<D, W>(pos - 2, line, NI), ob = tile_idx<D, W>(pos - 3, line, NI);
-    double cv[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) cv[v] = gsum[v] + (rd[(5 + v) * NI * W + oa] + rd[(10 + v) * NI * W + ob]);
+    for (int v = 0; v < 5; ++v) cv[v] = gsum[v];
     const int s = tile_idx<D, W>(pos, line, NP);
     const double rho = q[s], e = q[4 * NP * W + s], pr = ri[5 * NP * W + s];
-    const double V[3] = {ri[1 * NP * W + s], ri[2 * NP * W + s], ri[3 * NP * W + s]};
+    const float2* rfs = reinterpret_cast<const float2*>(ri) + s;
+    double V[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float2 vk = rfs[(1 + k) * NP * W];
+      V[k] = f2d_bits(vk.x) + f2d_bits(vk.y);
+    }
     const double un = V[D];
     const double Fbm[3] = {gsum[5], gsum[6], gsum[7]};
     const double Fb4 = gsum[8];
@@ -1159,12 +1341,15 @@ cudaError_t prepare_adj_kernels() {
   cudaError_t e = cudaFuncSetAttribute(k_adj_dir<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, APL::BYTES);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_dir<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, APL::BYTES);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_dir<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, APL::BYTES);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_adj_dir_df<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, APF::BYTES);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_adj_dir_df<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, APF::BYTES);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_adj_dir_df<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, APF::BYTES);
+  auto df_attr = [](auto* kernel) {
+    cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, APF::BYTES);
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    return r;
+  };
+  if (e == cudaSuccess) e = df_attr(k_adj_dir_df<0>);
+  if (e == cudaSuccess) e = df_attr(k_adj_dir_df<1>);
+  if (e == cudaSuccess) e = df_attr(k_adj_dir_df<2>);
   return e;
 }
 
