@@ -617,10 +617,14 @@ def _e2e(solver, u0_dev, dt, steps: int, world: int, device_step_ms: float) -> d
     uh = uh_t.numpy()
     solver.step_host(uh, dt, 1)  # warm-up (allocates the device copy and the copy stream)
     barrier(world)
+    solver.timing_enable(True)
     t0 = time.perf_counter()
     for _ in range(steps):
         solver.step_host(uh, dt, 1)
     el = max_over_ranks(time.perf_counter() - t0, world)
+    kt = solver.timing_read()
+    solver.timing_enable(False)
+    kernel_ms = sum(v[0] for v in kt.values()) / steps
     pts = sum_over_ranks(float(n ** 3 * RK_STAGES * steps), world)
     state_bytes = 5 * n ** 3 * 8
     # pinned-copy bandwidth of this machine, one whole state each way
@@ -654,6 +658,7 @@ def _e2e(solver, u0_dev, dt, steps: int, world: int, device_step_ms: float) -> d
             "pinned_copy_gbs": bw, "copy_ms_per_step_serial": t_copy * 1e3,
             "call_without_steps_ms": t_call_copies * 1e3,
             "device_ms_per_step": device_step_ms,
+            "kernel_ms_per_step_during_e2e": kernel_ms,
             "copy_time_hidden_frac": max(0.0, min(1.0, (serial - t_step) / t_copy)) if t_copy > 0 else None}
 
 
