@@ -184,6 +184,7 @@ class ClockSampler:
 
 
 KDIR_SOURCES = ("k_dir.cu", "k_dir_impl.cuh", "k_dir_common.cuh", "k_point_impl.cuh", "df.cuh")
+KDIR32_SOURCES = ("k_dir32.cu", "k_dir_common.cuh", "df.cuh")
 
 
 def kernel_source_sha(names=KDIR_SOURCES) -> str:
@@ -200,31 +201,32 @@ def kernel_source_sha(names=KDIR_SOURCES) -> str:
     return h.hexdigest()[:16]
 
 
+def _profile_line(tag: str, kernel: str, field: str, sha: str):
+    """(value, file, grid) of the committed ncu figure `tag kernel field=value grid=G ...
+    source_sha256=sha` under profiles/ taken on the largest grid, or None if no line matches the
+    current kernel code."""
+    import glob
+    import re
+    best = None
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            m = re.match(rf"{tag} {kernel} {field}=([0-9.]+) grid=(\d+) \S+ source_sha256=(\w+)", line)
+            if m and m.group(3) == sha and (best is None or int(m.group(2)) > best[2]):
+                best = (float(m.group(1)), os.path.basename(path), int(m.group(2)))
+    return best
+
+
 def ncu_traffic_per_point(kernel: str, sha: str):
     """DRAM bytes per grid point of one launch (dram__bytes_read.sum + dram__bytes_write.sum
     from a committed ncu summary under profiles/), or None if the kernel sources have changed
     since the counters were taken."""
-    import glob
-    import re
-    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
-        for line in open(path):
-            m = re.match(rf"TRAFFIC {kernel} bytes_per_point=([0-9.]+) grid=(\d+) \S+ source_sha256=(\w+)", line)
-            if m and m.group(3) == sha:
-                return float(m.group(1)), os.path.basename(path), int(m.group(2))
-    return None
+    return _profile_line("TRAFFIC", kernel, "bytes_per_point", sha)
 
 
 def ncu_issue_per_point(kernel: str, sha: str):
     """Warp instructions issued per grid point of one launch (smsp__inst_executed.sum from a
     committed ncu summary), or None if the kernel sources have changed since."""
-    import glob
-    import re
-    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
-        for line in open(path):
-            m = re.match(rf"ISSUE {kernel} warp_instr_per_point=([0-9.]+) grid=(\d+) \S+ source_sha256=(\w+)", line)
-            if m and m.group(3) == sha:
-                return float(m.group(1)), os.path.basename(path), int(m.group(2))
-    return None
+    return _profile_line("ISSUE", kernel, "warp_instr_per_point", sha)
 
 
 def measured_peaks() -> dict:
@@ -524,8 +526,8 @@ def run_ours(args, world, rank, local):
     if tr is not None:
         bpp, src, grid = tr
         roofline["traffic"] = bpp * N
-        roofline["traffic_note"] = (f"ncu dram read+write per launch at {grid}^3 ({src}), "
-                                    f"{bpp:.1f} B/point scaled to {n}^3 (streaming kernel: traffic ~ points)")
+        roofline["traffic_note"] = (f"ncu dram read+write per launch at {grid}^3 ({src}), {bpp:.1f} B/point"
+                                    + ("" if grid == n else f" scaled to {n}^3 (streaming kernel: traffic ~ points)"))
         roofline["hbm_frac_measured"] = bpp * N / avg_launch_s / 1e9 / HBM
 
     # sampled parity of the headline's initial right-hand side against the oracle
@@ -685,7 +687,32 @@ def _fp32_compare(timed_loop, u64, st64, n_cmp, K, W, value64, world, N, ns3d) -
             "mass_rel_drift": float(abs(b[-1, 0] - b[0, 0]) / abs(b[0, 0])),
             "energy_rel_drift": float(abs(b[-1, 4] - b[0, 4]) / abs(b[0, 4])),
             "status_ok": bool(np.all(b[:, 10] == 0)),
-            "kernel_ms_per_step": {k: v[0] / K for k, v in kt3.items() if v[1] > 0}}
+            "kernel_ms_per_step": {k: v[0] / K for k, v in kt3.items() if v[1] > 0},
+            "roofline": _fp32_roofline(kt3, N)}
+
+
+def _fp32_roofline(kt, N) -> dict:
+    """Roofline of the FP32-bulk direction pass (k_dir32): DRAM traffic (ncu, per point, keyed
+    to the kernel code) and the method's algorithmic bytes over the live average launch time,
+    against the measured HBM copy peak; the issue rate against the issue peak."""
+    dir_ms = sum(kt[k][0] for k in ("dir_x", "dir_y", "dir_z"))
+    launches = sum(kt[k][1] for k in ("dir_x", "dir_y", "dir_z"))
+    avg_s = dir_ms / launches * 1e-3
+    hbm = measured_peaks()["hbm_gbs"]
+    out = {"kernel": "k_dir32 (FP32-bulk direction pass)", "avg_launch_ms": avg_s * 1e3,
+           "method_hbm_frac": 60.0 * N / avg_s / 1e9 / hbm, "hbm_peak_gbs": hbm, "bound": None}
+    sha = kernel_source_sha(KDIR32_SOURCES)
+    tr = ncu_traffic_per_point("k_dir32", sha)
+    if tr is not None:
+        out["traffic"] = tr[0] * N
+        out["hbm_frac_measured"] = tr[0] * N / avg_s / 1e9 / hbm
+        out["traffic_source"] = f"ncu dram read+write per launch at {tr[2]}^3 ({tr[1]})"
+    iss = ncu_issue_per_point("k_dir32", sha)
+    if iss is not None:
+        out["issue_frac"] = iss[0] * N / avg_s / 1e9 / ISSUE_PEAK_G
+    if tr is not None and iss is not None:
+        out["bound"] = "alu" if out["issue_frac"] >= out["hbm_frac_measured"] else "hbm"
+    return out
 
 
 ADJ_N, ADJ_STEPS, ADJ_EVERY, ADJ_MU, ADJ_CFL, ADJ_FD_DIRS, ADJ_FD_EPS = 64, 256, 16, 2.5e-4, 0.5, 8, 1e-6

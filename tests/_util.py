@@ -27,3 +27,20 @@ def inc_rel_err(x, y, u0) -> float:
     y = np.asarray(y)
     d = y - np.asarray(u0)
     return float(np.abs(x - y).max() / np.abs(d).max())
+
+
+def flux_scale(u, lengths, gamma: float = 1.4) -> float:
+    """max over points, components and directions of |f_d(u)|, divided by the smallest grid
+    spacing: the scale of the right-hand side that FP32 rounding of the interface fluxes acts on."""
+    rho = u[0]
+    vel = u[1:4] / rho
+    p = (gamma - 1) * (u[4] - 0.5 * rho * (vel ** 2).sum(axis=0))
+    fmax = 0.0
+    for d in range(3):
+        un = vel[d]
+        comps = [u[1 + d], u[1] * un, u[2] * un, u[3] * un, (u[4] + p) * un]
+        comps[1 + d] = comps[1 + d] + p
+        fmax = max(fmax, max(float(np.abs(c).max()) for c in comps))
+    nz, ny, nx = u.shape[1:]
+    dx = min(lengths[0] / nx, lengths[1] / ny, lengths[2] / nz)
+    return fmax / dx

@@ -18,6 +18,8 @@ import pytest
 
 from paper_2211_16718_gb300 import inputs as I
 
+from tests._util import flux_scale
+
 pytestmark = pytest.mark.gpu
 
 FLUX_TOL = 1e-5
@@ -43,23 +45,6 @@ def orc(oracle):
 def _gpu(u):
     import torch
     return torch.from_numpy(np.ascontiguousarray(u)).cuda()
-
-
-def flux_scale(u, lengths):
-    """max over points/components/directions of |f_d(u)| divided by the smallest dx."""
-    gamma = 1.4
-    rho = u[0]
-    vel = u[1:4] / rho
-    p = (gamma - 1) * (u[4] - 0.5 * rho * (vel ** 2).sum(axis=0))
-    fmax = 0.0
-    for d in range(3):
-        un = vel[d]
-        comps = [u[1 + d], u[1] * un, u[2] * un, u[3] * un, (u[4] + p) * un]
-        comps[1 + d] = comps[1 + d] + p
-        fmax = max(fmax, max(np.abs(c).max() for c in comps))
-    nz, ny, nx = u.shape[1:]
-    dx = min(lengths[0] / nx, lengths[1] / ny, lengths[2] / nz)
-    return fmax / dx
 
 
 CASES = [

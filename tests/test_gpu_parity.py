@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from paper_2211_16718_gb300 import inputs as I
-from tests._util import inc_rel_err, rel_err, rel_err_var
+from tests._util import flux_scale, inc_rel_err, rel_err, rel_err_var
 
 pytestmark = pytest.mark.gpu
 
@@ -427,7 +427,8 @@ def test_hit256_one_rk4_step_full_field(ns3d, orc):
 
 
 def test_hit512_rhs_sampled_points(ns3d, orc):
-    """Largest configuration (512^3, 5.4 GB per state): sampled RHS parity."""
+    """Largest configuration (512^3, 5.4 GB per state): sampled RHS parity of the FP64 path,
+    and of the FP32-bulk path within its bound."""
     import torch
     n = 512
     u = I.isotropic_turbulence(n, seed=0)
@@ -440,6 +441,15 @@ def test_hit512_rhs_sampled_points(ns3d, orc):
     r_gpu = r.reshape(5, -1)[:, torch.from_numpy(idx).cuda()].cpu().numpy()
     del r, ud
     s.close()
+    # the FP32-bulk path on the same field and points, within its FP32 bound (1e-5 of the flux
+    # scale max|f|/dx, derived from the arithmetic)
+    s32 = ns3d.Solver(n, n, n, mu_eff=mu, precision=ns3d.NS3D_FP32_BULK)
+    ud = _gpu(u)
+    r = s32.rhs(ud)
+    r32 = r.reshape(5, -1)[:, torch.from_numpy(idx).cuda()].cpu().numpy()
+    del r, ud
+    s32.close()
     r_orc = orc.rhs_points(orc.Params(n, n, n, mu_eff=mu), u, idx)
     assert rel_err(r_gpu, r_orc.T) <= RHS_TOL
     assert rel_err_var(r_gpu, r_orc.T) <= RHS_VAR_TOL
+    assert np.abs(r32 - r_orc.T).max() <= 1e-5 * flux_scale(u, (2 * math.pi,) * 3)
