@@ -19,7 +19,8 @@
 //      part, the viscous interface flux (-f_{i-1} + 7 f_i + 7 f_{i+1} - f_{i+2})/12,
 //      divided by dx and widened to FP64;
 //  E   per point: FP64 difference of its two interface fluxes, then the
-//      accumulation / RK epilogue (its operands prefetched by cp.async during D).
+//      accumulation / RK epilogue (its operands prefetched by cp.async during D; in the y
+//      and z passes a thread takes two x-adjacent points and moves 16-byte pairs).
 #include <math.h>
 
 #include "df.cuh"
@@ -177,6 +178,84 @@ __device__ __forceinline__ void dir_epilogue_pre32(const DirArgs& a, long long p
   }
 }
 
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned), L2 only.
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// dir_epilogue_pre32 for two x-adjacent points p and p + 1 (p even), their operands and results
+// moved as 16-byte pairs: kp[v] = (k at p, k at p + 1), ops[j] likewise; the same arithmetic.
+__device__ __forceinline__ void dir_epilogue_pre32x2(const DirArgs& a, long long p, const double c0[5],
+                                                     const double c1[5], const double2* kp, const double2* ops) {
+  const long long N = a.g.N;
+  auto st = [&](double* base, int v, double x0, double x1) {
+    *reinterpret_cast<double2*>(base + v * N + p) = make_double2(x0, x1);
+  };
+  switch (a.epi) {
+    case EPI_ACC_WRITE:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) st(a.k, v, c0[v], c1[v]);
+      break;
+    case EPI_ACC_ADD:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) st(a.k, v, kp[v].x + c0[v], kp[v].y + c1[v]);
+      break;
+    case EPI_RHS_OUT:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) st(a.out, v, kp[v].x + c0[v], kp[v].y + c1[v]);
+      break;
+    case EPI_RK4_FIRST:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K0 = kp[v].x + c0[v], K1 = kp[v].y + c1[v];
+        st(a.out, v, fma(a.a, K0, ops[v].x), fma(a.a, K1, ops[v].y));
+        st(a.acc, v, K0, K1);
+      }
+      break;
+    case EPI_RK4_MID:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K0 = kp[v].x + c0[v], K1 = kp[v].y + c1[v];
+        st(a.out, v, fma(a.a, K0, ops[v].x), fma(a.a, K1, ops[v].y));
+        st(a.acc, v, fma(2.0, K0, ops[5 + v].x), fma(2.0, K1, ops[5 + v].y));
+      }
+      break;
+    case EPI_RK4_LAST:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K0 = kp[v].x + c0[v], K1 = kp[v].y + c1[v];
+        st(a.out, v, fma(a.a, ops[5 + v].x + K0, ops[v].x), fma(a.a, ops[5 + v].y + K1, ops[v].y));
+      }
+      break;
+    case EPI_SSP_1:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K0 = kp[v].x + c0[v], K1 = kp[v].y + c1[v];
+        st(a.out, v, fma(a.a, K0, ops[v].x), fma(a.a, K1, ops[v].y));
+      }
+      break;
+    case EPI_SSP_2:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K0 = kp[v].x + c0[v], K1 = kp[v].y + c1[v];
+        st(a.out, v, 0.75 * ops[v].x + 0.25 * fma(a.a, K0, ops[5 + v].x),
+           0.75 * ops[v].y + 0.25 * fma(a.a, K1, ops[5 + v].y));
+      }
+      break;
+    case EPI_SSP_3:
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double K0 = kp[v].x + c0[v], K1 = kp[v].y + c1[v];
+        st(a.out, v, (1.0 / 3.0) * ops[v].x + (2.0 / 3.0) * fma(a.a, K0, ops[5 + v].x),
+           (1.0 / 3.0) * ops[v].y + (2.0 / 3.0) * fma(a.a, K1, ops[5 + v].y));
+      }
+      break;
+    default:
+      break;
+  }
+}
+
 template <int D>
 __global__ void __launch_bounds__(THREADS, 4) k_dir32(const DirArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -199,7 +278,8 @@ __global__ void __launch_bounds__(THREADS, 4) k_dir32(const DirArgs a) {
   const int tid = threadIdx.x;
   const float* fvf = reinterpret_cast<const float*>(a.fv);
   const long long fv_plane = (long long)(a.fv_dstride * D);
-  const float gamma = (float)a.gamma, gm1 = gamma - 1.0f;
+  // FP32 parameters rounded on the host (an FP64 -> FP32 conversion per thread would occupy the FP64 pipe)
+  const float gm1 = a.gm1_hi;
 
   // ---- A: load, convert, primitive variables and point fluxes -------------------------
   int bad = 0;
@@ -253,7 +333,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_dir32(const DirArgs a) {
   // Items run over lines fastest, then segments, then scalars, so that the 8 threads of a
   // shared-memory phase read and write 8 different banks.
   {
-    const float eps4 = (float)a.eps4;
+    const float eps4 = a.eps4_hi;
     const bool eps_ok = eps4 >= 1e-9f && eps4 <= 1.0f;  // unscaled products stay in range (see below)
     for (int it = tid; it < NQ * W * NSEG; it += THREADS) {
       const int m = it / (W * NSEG);
@@ -340,7 +420,30 @@ __global__ void __launch_bounds__(THREADS, 4) k_dir32(const DirArgs a) {
     }
   };
   const int nops = epilogue_operands(a.epi);  // k, then U_n, then acc or the stage input
-  if (nops > 0 && tid < TP * W) {
+  // y and z passes on grids with nx even: a thread owns two x-adjacent points (lines 2j, 2j+1 of
+  // the tile; their flat index is even, so every operand pair is 16-byte aligned)
+  const bool pairs = (D != 0) && ((a.g.n[0] & 1) == 0);
+  const double* third = (a.epi == EPI_SSP_2 || a.epi == EPI_SSP_3) ? a.u : a.acc;
+  if (pairs) {
+    if (nops > 0 && tid < TP * W / 2) {
+      const int pp = tid / (W / 2), l0 = 2 * (tid - pp * (W / 2));
+      if (s0 + pp < nD && a0 + l0 < na) {  // na = nx is even: the second point exists too
+        const long long p = tile_flat<D>(a.g, s0 + pp, a0 + l0, bz);
+        double2* kp = reinterpret_cast<double2*>(PRE) + 5 * tid;
+        double2* op = reinterpret_cast<double2*>(PRE2) + 10 * tid;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) cp_async16(kp + v, a.k + v * N + p);
+        if (nops >= 10) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) cp_async16(op + v, a.un + v * N + p);
+        }
+        if (nops == 15) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) cp_async16(op + 5 + v, third + v * N + p);
+        }
+      }
+    }
+  } else if (nops > 0 && tid < TP * W) {
     int pp, line;
     point_of(tid, pp, line);
     if (s0 + pp < nD && a0 + line < na) {
@@ -352,7 +455,6 @@ __global__ void __launch_bounds__(THREADS, 4) k_dir32(const DirArgs a) {
         for (int v = 0; v < 5; ++v) cp_async8(PRE2 + 10 * tid + v, a.un + v * N + p);
       }
       if (nops == 15) {
-        const double* third = (a.epi == EPI_SSP_2 || a.epi == EPI_SSP_3) ? a.u : a.acc;
 #pragma unroll
         for (int v = 0; v < 5; ++v) cp_async8(PRE2 + 10 * tid + 5 + v, third + v * N + p);
       }
@@ -403,7 +505,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_dir32(const DirArgs a) {
     const float a1 = ph + ach, a5 = ph - ach;
     float l1 = fabsf(un - c), l5 = fabsf(un + c);
     const float l2 = fabsf(un);
-    const float hd = (float)a.hdelta;
+    const float hd = a.hd_hi;
     const float delta = hd * c;
     if (l1 < delta) l1 = fmaf(l1, l1, delta * delta) * __fdividef(0.5f, delta);
     if (l5 < delta) l5 = fmaf(l5, l5, delta * delta) * __fdividef(0.5f, delta);
@@ -425,7 +527,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_dir32(const DirArgs a) {
     const float G1 = fmaf(7.0f / 12.0f, f0.y + f1.y, (-1.0f / 12.0f) * (fm1.y + f2.y));
     const float G2 = fmaf(7.0f / 12.0f, f0.z + f1.z, (-1.0f / 12.0f) * (fm1.z + f2.z));
     const float G3 = fmaf(7.0f / 12.0f, f0.w + f1.w, (-1.0f / 12.0f) * (fm1.w + f2.w));
-    const float rdx = (float)a.g.rh[D];
+    const float rdx = a.g.rh_f[D];
     const float F0 = 0.5f * (S0 - diss[0]);
     const float F1 = fmaf(0.5f, S1 - diss[1], -G0);
     const float F2 = fmaf(0.5f, S2 - diss[2], -G1);
@@ -443,7 +545,24 @@ __global__ void __launch_bounds__(THREADS, 4) k_dir32(const DirArgs a) {
   __syncthreads();
 
   // ---- E: FP64 conservative difference + epilogue ----------------------------------------
-  if (tid < TP * W) {
+  if (pairs) {
+    if (tid < TP * W / 2) {
+      const int pp = tid / (W / 2), l0 = 2 * (tid - pp * (W / 2));
+      if (s0 + pp < nD && a0 + l0 < na) {
+        const double* f0 = FD + l0 * FS + pp;
+        const double* f1 = f0 + FS;
+        double c0[5], c1[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          c0[v] = f0[v * W * FS] - f0[v * W * FS + 1];
+          c1[v] = f1[v * W * FS] - f1[v * W * FS + 1];
+        }
+        dir_epilogue_pre32x2(a, tile_flat<D>(a.g, s0 + pp, a0 + l0, bz), c0, c1,
+                             reinterpret_cast<const double2*>(PRE) + 5 * tid,
+                             reinterpret_cast<const double2*>(PRE2) + 10 * tid);
+      }
+    }
+  } else if (tid < TP * W) {
     int pp, line;
     point_of(tid, pp, line);
     if (s0 + pp < nD && a0 + line < na) {

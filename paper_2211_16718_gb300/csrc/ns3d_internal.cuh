@@ -37,6 +37,7 @@ struct Grid {
   double rh[3];      // 1/dx, 1/dy, 1/dz            (host-computed: no FP64 division per thread)
   double r12h[3];    // 1/(12 dx), 1/(12 dy), 1/(12 dz)
   double hrh[3];     // 1/(2 dx), 1/(2 dy), 1/(2 dz)
+  float rh_f[3];     // 1/dx, 1/dy, 1/dz rounded to FP32 (host-rounded: no FP64 conversion per thread)
 };
 
 // Spacing of the periodic box [0,lx) x [0,ly) x [0,lz) on the grid g.n (Sec. 2.2: x_i = i dx).
@@ -47,6 +48,7 @@ inline void grid_set_spacing(Grid& g, double lx, double ly, double lz) {
     g.rh[d] = 1.0 / g.h[d];
     g.r12h[d] = 1.0 / (12.0 * g.h[d]);
     g.hrh[d] = 0.5 / g.h[d];
+    g.rh_f[d] = (float)g.rh[d];
   }
 }
 
