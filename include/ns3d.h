@@ -70,8 +70,13 @@ enum { NS3D_RK4 = 0, NS3D_SSPRK3 = 1 };           /* time integrators (Sec. 2.2)
  *                   (two FP32 words, ~48 bits) on the FP32 pipe.  Agrees with the all-FP64
  *                   evaluation to within the parity tolerance of the FP64 path (1e-12
  *                   relative on the right-hand side).  Requires weno_eps >= 1e-15.
- *  NS3D_FP32_BULK   smoothness indicators, weights, interface values and Roe flux in
- *                   FP32; state, RK accumulation and reductions in FP64.
+ *  NS3D_FP32_BULK   primitive variables, point fluxes, smoothness indicators, weights,
+ *                   interface values, Roe flux and viscous fluxes in FP32; the total
+ *                   interface flux is widened to FP64 before the conservative difference
+ *                   (exact telescoping: a free stream gives a zero RHS, the grid sums are
+ *                   conserved to FP64 rounding); state, RK accumulation and reductions in
+ *                   FP64.  Relative RHS error ~1e-7 of the flux scale max|f|/dx.
+ *                   Requires weno_eps >= 1e-15.
  *  NS3D_FP64_STRICT every operation in FP64 (one FP64 division per reconstruction). */
 enum { NS3D_FP64 = 0, NS3D_FP32_BULK = 1, NS3D_FP64_STRICT = 2 };
 /* Storage of the viscous flux vectors (same results, bitwise, in every mode):

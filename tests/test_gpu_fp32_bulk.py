@@ -98,8 +98,28 @@ def test_fp32_bulk_rk4_ten_steps(ns3d, orc):
     assert err <= bound, (err, bound)
 
 
+@pytest.mark.parametrize("n", [(32, 32, 32), (33, 20, 18)], ids=["nx_even_paired_epilogue", "nx_odd"])
+def test_fp32_bulk_ssprk3_steps(ns3d, orc, n):
+    """5 SSP-RK3 steps (every SSP stage epilogue) on a grid whose nx is even (the y and z passes
+    move their epilogue operands as 16-byte pairs) and odd (one point per thread): state error
+    <= 5 dt FLUX_TOL S_F against the oracle."""
+    u0 = I.random_smooth(*n, seed=8, amp=0.15, mach=0.5)
+    mu = 2e-3
+    P = orc.Params(*n, mu_eff=mu)
+    dt = 0.4 / orc.stats(P, u0)["max_wavespeed_over_dx"]
+    s = ns3d.Solver(*n, mu_eff=mu, rk=ns3d.NS3D_SSPRK3, precision=ns3d.NS3D_FP32_BULK)
+    ud = _gpu(u0)
+    s.rk_step(ud, dt, 5)
+    s.check()
+    err = np.abs(ud.cpu().numpy() - orc.rk_step(P, u0, dt, 5, scheme="ssprk3")).max()
+    bound = 5 * dt * FLUX_TOL * flux_scale(u0, (2 * math.pi,) * 3)
+    assert err <= bound, (err, bound)
+    s.close()
+
+
 def test_fp32_bulk_tile_variants_bitwise_identical(ns3d):
-    """The y and z passes' tile shapes (32 x 4, 16 x 8) give the same bits."""
+    """The FP32-bulk passes have one tile shape: setting another variant on the context changes
+    nothing (the same bits), on a grid with nx even (the y and z passes' paired epilogue)."""
     import torch
     n = (20, 36, 18)
     u = I.random_smooth(*n, seed=6, amp=0.1, mach=0.5)
