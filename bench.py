@@ -183,7 +183,7 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
 
 
-KDIR_SOURCES = ("k_dir.cu", "k_dir_impl.cuh", "k_dir_common.cuh", "k_point_impl.cuh", "df.cuh")
+KDIR_SOURCES = ("k_dir.cu", "k_dir_impl.cuh", "k_dir_common.cuh", "k_point_impl.cuh", "df.cuh", "df2.cuh")
 KDIR32_SOURCES = ("k_dir32.cu", "k_dir_common.cuh", "df.cuh")
 
 

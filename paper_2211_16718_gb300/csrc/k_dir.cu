@@ -14,7 +14,7 @@ namespace {
 
 template <int D, int MODE, int TP, int W>
 __global__ void __launch_bounds__(Plan<MODE, TP, W>::THREADS, Plan<MODE, TP, W>::MIN_CTAS) k_dir(const DirArgs a) {
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) double sm[];
   if (D == 2) {
     const int tz = a.zorder ? blockIdx.y : blockIdx.x, tl = a.zorder ? blockIdx.x : blockIdx.y;
     dir_tile<D, MODE, TP, W>(a, sm, a.t0 + tz, tl, blockIdx.z);

@@ -34,6 +34,10 @@
 // (P_{i+1} - P_i) + dR - dL, both kept in double-float, so the FP64 pipe sees
 // only the first differences, the point sums and one combination per flux
 // component.  The result agrees with the all-FP64 evaluation to rounding.
+// Phases A2, B and C of MODE 1 take two lines of the tile per item and run their
+// double-float arithmetic on both at once with the packed FP32 instructions
+// (df2.cuh): each lane computes what a one-line evaluation would, with half the
+// issued instructions.
 #include <math.h>
 
 #include <type_traits>
@@ -41,6 +45,7 @@
 #pragma once
 
 #include "df.cuh"
+#include "df2.cuh"
 #include "k_dir_common.cuh"
 #include "k_point_impl.cuh"
 #include "ns3d_internal.cuh"
@@ -56,13 +61,15 @@ constexpr int NQ = 9;             // reconstructed scalars
 //           R [18][NI*W] interface values, later [5][NI*W] interface fluxes.
 //   MODE 1: Q [NQ][NP*W], dead after phase A2: ROE [5][NP*W] and FV [4][NP*W] then
 //           arrive there by cp.async (as FP64) while phases B and C run;
-//           B [NQ][3][NW*W] (double-float), dead after phase C: the epilogue
-//           operands then arrive there; S [NQ][NW*W] third differences;
-//           G [NQ][NG*W] first differences; R [10][NI*W]: jumps du of u_0..u_4
+//           B [NQ][3][NW*W/2] squared indicators, dead after phase C: the epilogue
+//           operands then arrive there; S [NQ][NW*W/2] third differences;
+//           G [NQ][NG*W/2] first differences (B, S, G: double-float values of the two
+//           lines of a line pair side by side, 16 bytes (hi0, hi1, lo0, lo1), indexed
+//           like the lines with W/2 line pairs); R [10][NI*W]: jumps du of u_0..u_4
 //           (double-float, slots 0-4) and the sums of the five flux scalars
 //           (FP64, slots 5-9), later [5][NI*W] interface fluxes.
 //   The MODE 1 plan of a 24 x 4 tile is 57.2 KB, so that four CTAs of 256 threads
-//   (64 registers) share an SM.
+//   (64 registers) share an SM.  MODE 1 tiles have an even number of lines.
 template <int MODE, int TP_, int W_>
 struct Plan {
   static constexpr int TP = TP_;                    // points per tile along the pencil
@@ -106,7 +113,7 @@ __device__ __forceinline__ double weno_combine(double B1, double B2, double B3, 
   return num / den;
 }
 
-// Range of the squared indicators inside which df_offset needs no rescaling: products of
+// Range of the squared indicators inside which df2_offset needs no rescaling: products of
 // two stay below 2^80, so that they times a third difference (below 2^12 for such tiles,
 // since |third difference| <= 4 |first differences| <= 4 B^(1/4)) and the denominator times
 // the candidate difference stay inside the float range; and above 2^-100, so that their
@@ -122,21 +129,25 @@ constexpr float DFW_LO = 0x1p-50f, DFW_HI = 0x1p40f;
 // e = -(2 g2 + g3), ta = s3 - s2, tb = -(s1 - s2).
 // SCALE: rescale the B_k by a common power of two first (the weights are scale-free);
 // without it every B_k must lie in [DFW_LO, DFW_HI).
+// Evaluated for two lines at once (two-lane double-float; each lane exactly as the
+// one-lane evaluation, its scale chosen from its own B_k).
 template <bool SCALE = true>
-__device__ __forceinline__ df df_offset(df B1, df B2, df B3, df e, df ta, df tb) {
+__device__ __forceinline__ df2 df2_offset(df2 B1, df2 B2, df2 B3, df2 e, df2 ta, df2 tb) {
   if (SCALE) {
-    const int E = max(exponent_of(B1.hi), max(exponent_of(B2.hi), exponent_of(B3.hi)));
-    const float sc = pow2f(-E);
-    B1 = df{B1.hi * sc, B1.lo * sc};
-    B2 = df{B2.hi * sc, B2.lo * sc};
-    B3 = df{B3.hi * sc, B3.lo * sc};
+    const int E0 = max(exponent_of(B1.hi.x), max(exponent_of(B2.hi.x), exponent_of(B3.hi.x)));
+    const int E1 = max(exponent_of(B1.hi.y), max(exponent_of(B2.hi.y), exponent_of(B3.hi.y)));
+    const float2 sc = make_float2(pow2f(-E0), pow2f(-E1));
+    B1 = df2_scale(B1, sc);
+    B2 = df2_scale(B2, sc);
+    B3 = df2_scale(B3, sc);
   }
-  const df p23 = df_mul_u(B2, B3);
-  const df p13 = df_mul_u(B1, B3);
-  const df p12 = df_mul_u(B1, B2);
-  const df den = df_add_pos_u(p23, df_add_pos_u(df_mul_f_u(p13, 6.0f), df_mul_f_u(p12, 3.0f)));
-  const df num = df_add_fast(df_mul_u(den, e), df_add_fast(df_twice(df_mul_u(p23, ta)), df_mul_f_u(df_mul_u(p12, tb), 3.0f)));
-  return df_div(num, df_mul_f_u(den, 6.0f));
+  const df2 p23 = df2_mul_u(B2, B3);
+  const df2 p13 = df2_mul_u(B1, B3);
+  const df2 p12 = df2_mul_u(B1, B2);
+  const df2 den = df2_add_pos_u(p23, df2_add_pos_u(df2_mul_f_u(p13, 6.0f), df2_mul_f_u(p12, 3.0f)));
+  const df2 num = df2_add_fast(df2_mul_u(den, e),
+                               df2_add_fast(df2_twice(df2_mul_u(p23, ta)), df2_mul_f_u(df2_mul_u(p12, tb), 3.0f)));
+  return df2_div(num, df2_mul_f_u(den, 6.0f));
 }
 
 // One tile (tx, ty, tz) of the direction-D pass, executed by the whole CTA on the
@@ -148,6 +159,8 @@ template <int D, int MODE, int TP_, int W_, bool NC = true>
 __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, int ty, int tz) {
   using PL = Plan<MODE, TP_, W_>;
   constexpr int TP = PL::TP, NP = PL::NP, NW = PL::NW, NI = PL::NI, W = PL::W;
+  constexpr int W2 = (W + 1) / 2;  // line pairs (MODE 1)
+  static_assert(MODE == 0 || W % 2 == 0, "MODE 1 tiles pair their lines");
   const int nD = a.g.n[D];
   constexpr int AX = (D == 0) ? 1 : 0;   // axis of the W lines
   constexpr int BX = (D == 2) ? 1 : 2;   // axis of blockIdx.z
@@ -211,17 +224,23 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
   if constexpr (MODE == 1) {
     constexpr int NG = PL::NG;
     const double* q = sm + PL::OFF_Q;
-    float2* G = reinterpret_cast<float2*>(sm + PL::OFF_G);
+    float4* G = reinterpret_cast<float4*>(sm + PL::OFF_G);
     double* R = sm + PL::OFF_R;
-    for (int item = tid; item < NQ * NG * W; item += PL::THREADS) {
-      const int m = item / (NG * W);
-      int j, line;
-      tile_split<D, W>(item - m * NG * W, NG, j, line);
+    // one item per line pair (lines 2 lp, 2 lp + 1), stored as (hi0, hi1, lo0, lo1)
+    for (int item = tid; item < NQ * NG * W2; item += PL::THREADS) {
+      const int m = item / (NG * W2);
+      int j, lp;
+      tile_split<D, W2>(item - m * NG * W2, NG, j, lp);
       const double* qm = q + m * NP * W;
-      const double qa = qm[tile_idx<D, W>(j, line, NP)], qb = qm[tile_idx<D, W>(j + 1, line, NP)];
-      const df g = d2df_bits(qb - qa);
-      G[m * NG * W + tile_idx<D, W>(j, line, NG)] = make_float2(g.hi, g.lo);
-      if (m >= 4 && j >= 2 && j < NI + 2) R[(1 + m) * NI * W + tile_idx<D, W>(j - 2, line, NI)] = qa;
+      const int l0 = 2 * lp, l1 = l0 + 1;
+      const double qa0 = qm[tile_idx<D, W>(j, l0, NP)], qb0 = qm[tile_idx<D, W>(j + 1, l0, NP)];
+      const double qa1 = qm[tile_idx<D, W>(j, l1, NP)], qb1 = qm[tile_idx<D, W>(j + 1, l1, NP)];
+      const df g0 = d2df_bits(qb0 - qa0), g1 = d2df_bits(qb1 - qa1);
+      G[m * NG * W2 + tile_idx<D, W2>(j, lp, NG)] = make_float4(g0.hi, g1.hi, g0.lo, g1.lo);
+      if (m >= 4 && j >= 2 && j < NI + 2) {
+        R[(1 + m) * NI * W + tile_idx<D, W>(j - 2, l0, NI)] = qa0;
+        R[(1 + m) * NI * W + tile_idx<D, W>(j - 2, l1, NI)] = qa1;
+      }
     }
     __syncthreads();
     // the point values are dead: fetch the Roe-average inputs and the viscous flux into
@@ -250,69 +269,80 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
 
   // ---- B: squared scaled smoothness indicators of every window ----------------
   int need_scale = 0;
-  {
+  if constexpr (MODE == 0) {
     const double* q = sm + PL::OFF_Q;
-    int range_bad = 0;
     for (int item = tid; item < NQ * NW * W; item += PL::THREADS) {
       const int m = item / (NW * W);
       int w, line;
       tile_split<D, W>(item - m * NW * W, NW, w, line);
       const int o = tile_idx<D, W>(w, line, NW);
-      if (MODE == 0) {
-        const double* qm = q + m * NP * W;
-        const double x = qm[tile_idx<D, W>(w, line, NP)];
-        const double y = qm[tile_idx<D, W>(w + 1, line, NP)];
-        const double z = qm[tile_idx<D, W>(w + 2, line, NP)];
-        const double gm = y - x, gp = z - y, s = gp - gm;
-        double* bw = sm + PL::OFF_B;
-        const double aa = fma((13.0 / 3.0) * s, s, a.eps4);
-        const double u1 = fma(3.0, gp, -gm);   // x - 4y + 3z
-        const double u2 = gm + gp;             // z - x
-        const double u3 = fma(-3.0, gm, gp);   // 3x - 4y + z
-        const double b1 = fma(u1, u1, aa), b2 = fma(u2, u2, aa), b3 = fma(u3, u3, aa);
-        bw[(m * 3 + 0) * NW * W + o] = b1 * b1;
-        bw[(m * 3 + 1) * NW * W + o] = b2 * b2;
-        bw[(m * 3 + 2) * NW * W + o] = b3 * b3;
-      } else {
-        float2* bw = reinterpret_cast<float2*>(sm + PL::OFF_B);
-        const float2* G = reinterpret_cast<const float2*>(sm + PL::OFF_G) + m * PL::NG * W;
-        const float2 g0 = G[tile_idx<D, W>(w, line, PL::NG)], g1 = G[tile_idx<D, W>(w + 1, line, PL::NG)];
-        const df dgm = df{g0.x, g0.y}, dgp = df{g1.x, g1.y};
-        const df ds = df_add_fast(dgp, df_neg(dgm));  // second difference s_w
-        // third difference T_w = s_w - s_{w+1} (phase C needs T_f, T_{f+1}, T_{f+2}; the last
-        // window has no s_{w+1} in the tile and its T is never read)
-        df T{0.0f, 0.0f};
-        if (w + 2 < PL::NG) {
-          const float2 g2 = G[tile_idx<D, W>(w + 2, line, PL::NG)];
-          T = df_add_fast(ds, df_neg(df_add_fast(df{g2.x, g2.y}, df_neg(dgp))));
-        }
-        reinterpret_cast<float2*>(sm + PL::OFF_S)[m * NW * W + o] = make_float2(T.hi, T.lo);
-        // scaled indicators b_k = u_k^2 + aa, aa = (13/3) s^2 + 4 eps, with u_2 = z - x and
-        // u_1 = x - 4y + 3z = u_2 + 2s, u_3 = 3x - 4y + z = 2s - u_2:
-        //   b_2 = u_2^2 + aa,  b_{1,3} = (b_2 + 4 s^2) +- 4 u_2 s   (b_k >= aa >= (13/3) s^2, so
-        // b_2 + 4 s^2 <= ~3 b_{1,3}: no harmful cancellation)
-        const df s2 = df_sqr_u(ds);
-        const df aa = df_add_pos_u(df_mul_u(s2, df{a.c133_hi, a.c133_lo}), df{a.eps4_hi, a.eps4_lo});
-        const df u2 = df_add_fast(dgm, dgp);
-        const df b2 = df_add_pos_u(df_sqr_u(u2), aa);
-        // Fast2Sum order with margins: b_2 >= aa >= (13/12) 4 s^2, and
-        // pq = u_2^2 + (4 + 13/3) s^2 + 4 eps >= 1.44 |4 u_2 s| (minimum over u_2)
-        const df pq = df_add_ordered_u(b2, df_twice(df_twice(s2)));
-        const df r4 = df_twice(df_twice(df_mul_u(u2, ds)));
-        const df B1 = df_sqr_u(df_add_ordered(pq, r4));
-        const df B2 = df_sqr_u(b2);
-        const df B3 = df_sqr_u(df_add_ordered(pq, df_neg(r4)));
-        bw[(m * 3 + 0) * NW * W + o] = make_float2(B1.hi, B1.lo);
-        bw[(m * 3 + 1) * NW * W + o] = make_float2(B2.hi, B2.lo);
-        bw[(m * 3 + 2) * NW * W + o] = make_float2(B3.hi, B3.lo);
-        // the float exponent range bounds the indicators (differences of the data
-        // up to ~1e9); beyond it the host reports NS3D_ERANGE instead of a NaN
-        const float bmax = fmaxf(B1.hi, fmaxf(B2.hi, B3.hi));
-        range_bad |= !(bmax < 1e36f);
-        need_scale |= !(bmax < DFW_HI && fminf(B1.hi, fminf(B2.hi, B3.hi)) >= DFW_LO);
-      }
+      const double* qm = q + m * NP * W;
+      const double x = qm[tile_idx<D, W>(w, line, NP)];
+      const double y = qm[tile_idx<D, W>(w + 1, line, NP)];
+      const double z = qm[tile_idx<D, W>(w + 2, line, NP)];
+      const double gm = y - x, gp = z - y, s = gp - gm;
+      double* bw = sm + PL::OFF_B;
+      const double aa = fma((13.0 / 3.0) * s, s, a.eps4);
+      const double u1 = fma(3.0, gp, -gm);   // x - 4y + 3z
+      const double u2 = gm + gp;             // z - x
+      const double u3 = fma(-3.0, gm, gp);   // 3x - 4y + z
+      const double b1 = fma(u1, u1, aa), b2 = fma(u2, u2, aa), b3 = fma(u3, u3, aa);
+      bw[(m * 3 + 0) * NW * W + o] = b1 * b1;
+      bw[(m * 3 + 1) * NW * W + o] = b2 * b2;
+      bw[(m * 3 + 2) * NW * W + o] = b3 * b3;
     }
-    if (MODE == 1 && __any_sync(0xffffffffu, range_bad) && (tid & 31) == 0) atomicOr(a.status, ST_DF_RANGE);
+  } else {
+    // one item per line pair: two-lane double-float arithmetic (packed FP32 instructions)
+    int range_bad = 0;
+    float4* bw = reinterpret_cast<float4*>(sm + PL::OFF_B);
+    float4* S = reinterpret_cast<float4*>(sm + PL::OFF_S);
+    const df2 c133 = df2_splat(df{a.c133_hi, a.c133_lo});
+    const df2 eps4 = df2_splat(df{a.eps4_hi, a.eps4_lo});
+    for (int item = tid; item < NQ * NW * W2; item += PL::THREADS) {
+      const int m = item / (NW * W2);
+      int w, lp;
+      tile_split<D, W2>(item - m * NW * W2, NW, w, lp);
+      const int o = tile_idx<D, W2>(w, lp, NW);
+      const float4* G = reinterpret_cast<const float4*>(sm + PL::OFF_G) + m * PL::NG * W2;
+      const df2 dgm = df2_from4(G[tile_idx<D, W2>(w, lp, PL::NG)]);
+      const df2 dgp = df2_from4(G[tile_idx<D, W2>(w + 1, lp, PL::NG)]);
+      const df2 ds = df2_add_fast(dgp, df2_neg(dgm));  // second difference s_w
+      // third difference T_w = s_w - s_{w+1} (phase C needs T_f, T_{f+1}, T_{f+2}; the last
+      // window has no s_{w+1} in the tile and its T is never read)
+      df2 T{f2splat(0.0f), f2splat(0.0f)};
+      if (w + 2 < PL::NG) {
+        const df2 g2 = df2_from4(G[tile_idx<D, W2>(w + 2, lp, PL::NG)]);
+        T = df2_add_fast(ds, df2_neg(df2_add_fast(g2, df2_neg(dgp))));
+      }
+      S[m * NW * W2 + o] = df2_to4(T);
+      // scaled indicators b_k = u_k^2 + aa, aa = (13/3) s^2 + 4 eps, with u_2 = z - x and
+      // u_1 = x - 4y + 3z = u_2 + 2s, u_3 = 3x - 4y + z = 2s - u_2:
+      //   b_2 = u_2^2 + aa,  b_{1,3} = (b_2 + 4 s^2) +- 4 u_2 s   (b_k >= aa >= (13/3) s^2, so
+      // b_2 + 4 s^2 <= ~3 b_{1,3}: no harmful cancellation)
+      const df2 s2 = df2_sqr_u(ds);
+      const df2 aa = df2_add_pos_u(df2_mul_u(s2, c133), eps4);
+      const df2 u2 = df2_add_fast(dgm, dgp);
+      const df2 b2 = df2_add_pos_u(df2_sqr_u(u2), aa);
+      // Fast2Sum order with margins: b_2 >= aa >= (13/12) 4 s^2, and
+      // pq = u_2^2 + (4 + 13/3) s^2 + 4 eps >= 1.44 |4 u_2 s| (minimum over u_2)
+      const df2 pq = df2_add_ordered_u(b2, df2_twice(df2_twice(s2)));
+      const df2 r4 = df2_twice(df2_twice(df2_mul_u(u2, ds)));
+      const df2 B1 = df2_sqr_u(df2_add_ordered(pq, r4));
+      const df2 B2 = df2_sqr_u(b2);
+      const df2 B3 = df2_sqr_u(df2_add_ordered(pq, df2_neg(r4)));
+      bw[(m * 3 + 0) * NW * W2 + o] = df2_to4(B1);
+      bw[(m * 3 + 1) * NW * W2 + o] = df2_to4(B2);
+      bw[(m * 3 + 2) * NW * W2 + o] = df2_to4(B3);
+      // the float exponent range bounds the indicators (differences of the data
+      // up to ~1e9); beyond it the host reports NS3D_ERANGE instead of a NaN
+      const float bmax0 = fmaxf(B1.hi.x, fmaxf(B2.hi.x, B3.hi.x));
+      const float bmax1 = fmaxf(B1.hi.y, fmaxf(B2.hi.y, B3.hi.y));
+      const float bmin0 = fminf(B1.hi.x, fminf(B2.hi.x, B3.hi.x));
+      const float bmin1 = fminf(B1.hi.y, fminf(B2.hi.y, B3.hi.y));
+      range_bad |= !(bmax0 < 1e36f) || !(bmax1 < 1e36f);
+      need_scale |= !(bmax0 < DFW_HI && bmin0 >= DFW_LO && bmax1 < DFW_HI && bmin1 >= DFW_LO);
+    }
+    if (__any_sync(0xffffffffu, range_bad) && (tid & 31) == 0) atomicOr(a.status, ST_DF_RANGE);
   }
   // one CTA-wide decision: rescaled weights only for tiles with extreme indicators
   const bool tile_scale = __syncthreads_or(need_scale) != 0;
@@ -354,44 +384,38 @@ __device__ __forceinline__ void dir_tile(const DirArgs& a, double* sm, int tx, i
     // formed in FP64: the Roe flux needs only
     //   du    = g2 + dR - dL       (fhat_R - fhat_L, for the u-scalars; double-float)
     //   fhat_L + fhat_R = 2 P2 + (g2 + dL + dR)   (for the flux scalars; FP64)
+    // One item per line pair, in two-lane double-float arithmetic.
     float2* rf = reinterpret_cast<float2*>(sm + PL::OFF_R);
     auto phase_c = [&](auto scaled) {
       constexpr bool SCALE = decltype(scaled)::value;
-      for (int item = tid; item < NQ * NI * W; item += PL::THREADS) {
-        const int m = item / (NI * W);
-        int f, line;
-        tile_split<D, W>(item - m * NI * W, NI, f, line);
-        const float2* S = reinterpret_cast<const float2*>(sm + PL::OFF_S) + m * NW * W;
-        const float2* G = reinterpret_cast<const float2*>(sm + PL::OFF_G) + m * PL::NG * W;
-        auto ldS = [&](int w) {
-          const float2 v = S[tile_idx<D, W>(w, line, NW)];
-          return df{v.x, v.y};
-        };
-        auto ldG = [&](int j) {
-          const float2 v = G[tile_idx<D, W>(j, line, PL::NG)];
-          return df{v.x, v.y};
-        };
+      for (int item = tid; item < NQ * NI * W2; item += PL::THREADS) {
+        const int m = item / (NI * W2);
+        int f, lp;
+        tile_split<D, W2>(item - m * NI * W2, NI, f, lp);
+        const float4* S = reinterpret_cast<const float4*>(sm + PL::OFF_S) + m * NW * W2;
+        const float4* G = reinterpret_cast<const float4*>(sm + PL::OFF_G) + m * PL::NG * W2;
+        const float4* b = reinterpret_cast<const float4*>(sm + PL::OFF_B) + m * 3 * NW * W2;
+        auto ldS = [&](int w) { return df2_from4(S[tile_idx<D, W2>(w, lp, NW)]); };
+        auto ldG = [&](int j) { return df2_from4(G[tile_idx<D, W2>(j, lp, PL::NG)]); };
+        auto ld = [&](int k, int w) { return df2_from4(b[k * NW * W2 + tile_idx<D, W2>(w, lp, NW)]); };
         // third differences (phase B): s0 - s1 = T_f, s1 - s2 = T_{f+1}, s3 - s2 = -T_{f+2}
-        const df t0 = ldS(f), tC = ldS(f + 1), t2 = df_neg(ldS(f + 2));
-        const df g1 = ldG(f + 1), g2 = ldG(f + 2), g3 = ldG(f + 3);
-        const float2* b = reinterpret_cast<const float2*>(sm + PL::OFF_B) + m * 3 * NW * W;
-        auto ld = [&](int k, int w) {
-          const float2 v = b[k * NW * W + tile_idx<D, W>(w, line, NW)];
-          return df{v.x, v.y};
-        };
-        const df g22 = df_twice(g2);
-        const df dL = df_offset<SCALE>(ld(0, f), ld(1, f + 1), ld(2, f + 2), df_add_fast(g22, g1), t0, tC);
-        const df dR = df_offset<SCALE>(ld(2, f + 3), ld(1, f + 2), ld(0, f + 1), df_neg(df_add_fast(g22, g3)), t2,
-                                       df_neg(tC));
-        const int o = tile_idx<D, W>(f, line, NI);
+        const df2 t0 = ldS(f), tC = ldS(f + 1), t2 = df2_neg(ldS(f + 2));
+        const df2 g1 = ldG(f + 1), g2 = ldG(f + 2), g3 = ldG(f + 3);
+        const df2 g22 = df2_twice(g2);
+        const df2 dL = df2_offset<SCALE>(ld(0, f), ld(1, f + 1), ld(2, f + 2), df2_add_fast(g22, g1), t0, tC);
+        const df2 dR = df2_offset<SCALE>(ld(2, f + 3), ld(1, f + 2), ld(0, f + 1), df2_neg(df2_add_fast(g22, g3)), t2,
+                                         df2_neg(tC));
+        const int o0 = tile_idx<D, W>(f, 2 * lp, NI), o1 = tile_idx<D, W>(f, 2 * lp + 1, NI);
         if (m < 5) {
-          const df du = df_add_fast(g2, df_add_fast(dR, df_neg(dL)));
-          rf[m * NI * W + o] = make_float2(du.hi, du.lo);
+          const df2 du = df2_add_fast(g2, df2_add_fast(dR, df2_neg(dL)));
+          rf[m * NI * W + o0] = make_float2(du.hi.x, du.lo.x);
+          rf[m * NI * W + o1] = make_float2(du.hi.y, du.lo.y);
         }
         if (m >= 4) {  // flux scalar: fhat_L + fhat_R = 2 P2 + (g2 + dL + dR), P2 copied in phase A2
-          const df t = df_add_fast(g2, df_add_fast(dL, dR));
-          double* F = sm + PL::OFF_R + (1 + m) * NI * W + o;
-          *F = fma(2.0, *F, f2d_bits(t.hi)) + f2d_bits(t.lo);
+          const df2 t = df2_add_fast(g2, df2_add_fast(dL, dR));
+          double* F = sm + PL::OFF_R + (1 + m) * NI * W;
+          F[o0] = fma(2.0, F[o0], f2d_bits(t.hi.x)) + f2d_bits(t.lo.x);
+          F[o1] = fma(2.0, F[o1], f2d_bits(t.hi.y)) + f2d_bits(t.lo.y);
         }
       }
     };

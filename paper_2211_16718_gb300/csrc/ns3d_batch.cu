@@ -114,7 +114,7 @@ __device__ __forceinline__ void phase_dir(const BatchView& b, int s, double* sm,
 template <int MODE, int TP, int W>
 __global__ void __launch_bounds__(Plan<MODE, TP, W>::THREADS, Plan<MODE, TP, W>::MIN_CTAS) kb_persistent(BatchView b,
                                                                                            int nsteps) {
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) double sm[];
   cg::grid_group grid = cg::this_grid();
   const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
