@@ -96,6 +96,13 @@ __device__ __forceinline__ df2 df2_mul_u(df2 x, df2 y) {
   e = f2fma(x.lo, y.hi, e);
   return df2{p.hi, e};
 }
+// As df_mul (normalised product).
+__device__ __forceinline__ df2 df2_mul(df2 x, df2 y) {
+  const df2 p = two_prod2(x.hi, y.hi);
+  float2 e = f2fma(x.hi, y.lo, p.lo);
+  e = f2fma(x.lo, y.hi, e);
+  return fast_two_sum2(p.hi, e);
+}
 __device__ __forceinline__ df2 df2_sqr_u(df2 x) {
   const df2 p = two_prod2(x.hi, x.hi);
   return df2{p.hi, f2fma(f2add(x.hi, x.hi), x.lo, p.lo)};

@@ -32,6 +32,7 @@
 #include <math.h>
 
 #include "df.cuh"
+#include "df2.cuh"
 #include "k_dir_common.cuh"
 #include "k_point_impl.cuh"
 #include "ns3d_internal.cuh"
@@ -571,9 +572,10 @@ __global__ void __launch_bounds__(APL::THREADS, 2) k_adj_dir(const AdjArgs a) {
 // candidate differences q_0 - q_1 = (s_0 - s_1)/3 and q_2 - q_1 = (s_1 - s_2)/6, and
 // q_k - q = (q_k - q_1) - M with M = omega_0 (q_0 - q_1) + omega_2 (q_2 - q_1).  The value
 // itself is q = P_c + (2 g_2 + g_1)/6 + M (P_c the stencil centre), the same offset form as
-// the forward pass.  The interface fluxes' adjoints and the Roe adjoint stay in FP64 (Newton
-// reciprocals); the per-point sums of the reconstruction contributions are converted back
-// to FP64 once.  To keep double-float values inside the float range whatever the scale of
+// the forward pass.  The Roe-flux adjoint is double-float too (one interface per item); the
+// window terms, weights, reconstruction adjoints and the per-point gather take the tile's two
+// lines at once with the packed FP32 instructions (df2.cuh).  The per-point sums of the
+// reconstruction contributions are converted back to FP64 once.  To keep double-float values inside the float range whatever the scale of
 // the adjoint input, each tile divides lambda by the power of two of its largest magnitude
 // and multiplies its results back (exact).
 // ============================================================================================
@@ -590,11 +592,11 @@ struct AdjPlanDF {
   static constexpr int OFF_RI = OFF_Q + 9 * NP * W;      // [8][NP*W] double-float sqrt(rho), u, v, w, H;
                                                          //   FP64 p; double-float rho, e
   static constexpr int OFF_L = OFF_RI + 8 * NP * W;      // [5][NP*W] lambda / 2^E
-  static constexpr int OFF_G = OFF_L + 5 * NP * W;       // [9][NP*W] float2 first differences
-  static constexpr int OFF_B = OFF_G + 9 * NP * W;       // [9][3][NW*W] float2 1/b_k of every window
+  static constexpr int OFF_G = OFF_L + 5 * NP * W;       // [9][NP] first differences of both lines
+  static constexpr int OFF_B = OFF_G + 9 * NP * W;       // [9][3][NW] 1/b_k of every window, both lines
   static constexpr int OFF_REC = OFF_B + 27 * NW * W;    // [10][NI*W] doubles: u^L, u^R of u_0..u_4
   static constexpr int OFF_RD = OFF_REC + 10 * NI * W;   // [15][NI*W] double-float Roe adjoints
-  static constexpr int OFF_WC = OFF_RD + 15 * NI * W;    // [9][6][NI*W] float2 stencil contributions
+  static constexpr int OFF_WC = OFF_RD + 15 * NI * W;    // [9][6][NI] stencil contributions, both lines
   static constexpr int WORDS = OFF_WC + 54 * NI * W;
   static constexpr int BYTES = WORDS * 8;
 };
@@ -604,74 +606,80 @@ __device__ __forceinline__ df df_sub(df x, df y) { return df_add_fast(x, df_neg(
 __device__ __forceinline__ float2 df_pack(df x) { return make_float2(x.hi, x.lo); }
 __device__ __forceinline__ df df_unpack(float2 v) { return df{v.x, v.y}; }
 
-// The three weights of one reconstruction from the reciprocals r_k = 1/b_k of its window
-// terms (candidate order 0, 1, 2; optimal weights 1, 6, 3 over 10):
-// omega_k = c_k r_k^2 / sum_j c_j r_j^2.  With the window terms' range checked (b <= 1e18,
-// b >= 4 eps), r^2 stays inside the float range and needs no rescaling.
-// Products and positive sums in this section are left unnormalised where they feed another
-// double-float operation (df_mul_u and friends: the same values, |lo| a few ulp(hi)).
-__device__ __forceinline__ void df_omega(df r0, df r1, df r2, df om[3]) {
-  const df a0 = df_sqr_u(r0);
-  const df a1 = df_mul_f_u(df_sqr_u(r1), 6.0f);
-  const df a2 = df_mul_f_u(df_sqr_u(r2), 3.0f);
-  const df r = df_div(df{1.0f, 0.0f}, df_add_pos_u(a0, df_add_pos_u(a1, a2)));
-  om[0] = df_mul_u(a0, r);
-  om[1] = df_mul_u(a1, r);
-  om[2] = df_mul_u(a2, r);
-}
-
 struct DFConst {
   df third, sixth, c263;  // 1/3, 1/6, 26/3
 };
 
-// Offset M of the reconstruction from its candidate 1, and the candidate differences.
-__device__ __forceinline__ df df_offset(df g0, df g1, df g2, df g3, const df om[3], const DFConst& k, df& E0, df& E2,
-                                        df s[3]) {
-  s[0] = df_sub(g1, g0);
-  s[1] = df_sub(g2, g1);
-  s[2] = df_sub(g3, g2);
-  E0 = df_mul_u(df_sub(s[0], s[1]), k.third);
-  E2 = df_mul_u(df_sub(s[1], s[2]), k.sixth);
-  return df_add_fast(df_mul_u(om[0], E0), df_mul_u(om[2], E2));
+// The WENO pieces below take the two lines of a tile at once (two-lane double-float,
+// df2.cuh: each lane computes what one line would).
+// Products and positive sums in this section are left unnormalised where they feed another
+// double-float operation (df2_mul_u and friends: the same values, |lo| a few ulp(hi)).
+struct DF2Const {
+  df2 third, sixth, c263;
+};
+__device__ __forceinline__ df2 df2_sub(df2 x, df2 y) { return df2_add_fast(x, df2_neg(y)); }
+
+// The three weights of one reconstruction from the reciprocals r_k = 1/b_k of its window
+// terms (candidate order 0, 1, 2; optimal weights 1, 6, 3 over 10):
+// omega_k = c_k r_k^2 / sum_j c_j r_j^2.  With the window terms' range checked (b <= 1e18,
+// b >= 4 eps), r^2 stays inside the float range and needs no rescaling.
+__device__ __forceinline__ void df2_omega(df2 r0, df2 r1, df2 r2, df2 om[3]) {
+  const df2 a0 = df2_sqr_u(r0);
+  const df2 a1 = df2_mul_f_u(df2_sqr_u(r1), 6.0f);
+  const df2 a2 = df2_mul_f_u(df2_sqr_u(r2), 3.0f);
+  const df2 r = df2_div(df2{f2splat(1.0f), f2splat(0.0f)}, df2_add_pos_u(a0, df2_add_pos_u(a1, a2)));
+  om[0] = df2_mul_u(a0, r);
+  om[1] = df2_mul_u(a1, r);
+  om[2] = df2_mul_u(a2, r);
 }
 
+// Offset M of the reconstruction from its candidate 1, and the candidate differences.
+__device__ __forceinline__ df2 df2_adj_offset(df2 g0, df2 g1, df2 g2, df2 g3, const df2 om[3], const DF2Const& k,
+                                              df2& E0, df2& E2, df2 s[3]) {
+  s[0] = df2_sub(g1, g0);
+  s[1] = df2_sub(g2, g1);
+  s[2] = df2_sub(g3, g2);
+  E0 = df2_mul_u(df2_sub(s[0], s[1]), k.third);
+  E2 = df2_mul_u(df2_sub(s[1], s[2]), k.sixth);
+  return df2_add_fast(df2_mul_u(om[0], E0), df2_mul_u(om[2], E2));
+}
 
 // y * d(value)/d(q_t), t = 0..4, of the reconstruction of stencil differences g0..g3 with
 // the reciprocals rb0..rb2 of its window terms and weights om (as weno_adjoint, in
 // double-float).
-__device__ __forceinline__ void df_recon_adjoint(df g0, df g1, df g2, df g3, df rb0, df rb1, df rb2, const df om[3],
-                                                 df y, const DFConst& k, df out[5]) {
-  df s[3], E0, E2;
-  const df M = df_offset(g0, g1, g2, g3, om, k, E0, E2, s);
-  const df v0 = df_sub(df_mul_f_u(g1, 3.0f), g0);
-  const df v1 = df_add_fast(g1, g2);
-  const df v2 = df_sub(g3, df_mul_f_u(g2, 3.0f));
-  const df y0 = df_mul_u(y, om[0]), y1 = df_mul_u(y, om[1]), y2 = df_mul_u(y, om[2]);
+__device__ __forceinline__ void df2_recon_adjoint(df2 g0, df2 g1, df2 g2, df2 g3, df2 rb0, df2 rb1, df2 rb2,
+                                                  const df2 om[3], df2 y, const DF2Const& k, df2 out[5]) {
+  df2 s[3], E0, E2;
+  const df2 M = df2_adj_offset(g0, g1, g2, g3, om, k, E0, E2, s);
+  const df2 v0 = df2_sub(df2_mul_f_u(g1, 3.0f), g0);
+  const df2 v1 = df2_add_fast(g1, g2);
+  const df2 v2 = df2_sub(g3, df2_mul_f_u(g2, 3.0f));
+  const df2 y0 = df2_mul_u(y, om[0]), y1 = df2_mul_u(y, om[1]), y2 = df2_mul_u(y, om[2]);
   // adjoints of b_k: -2 y_k (q_k - q) / b_k with q_0 - q = E0 - M, q_1 - q = -M, q_2 - q = E2 - M
-  const df k0 = df_twice(df_mul(df_mul_u(y0, df_sub(M, E0)), rb0));
-  const df k1 = df_twice(df_mul(df_mul_u(y1, M), rb1));
-  const df k2 = df_twice(df_mul(df_mul_u(y2, df_sub(M, E2)), rb2));
+  const df2 k0 = df2_twice(df2_mul(df2_mul_u(y0, df2_sub(M, E0)), rb0));
+  const df2 k1 = df2_twice(df2_mul(df2_mul_u(y1, M), rb1));
+  const df2 k2 = df2_twice(df2_mul(df2_mul_u(y2, df2_sub(M, E2)), rb2));
   // direct term sum_k y_k dq_k/dq_t
-  out[0] = df_mul_u(y0, k.third);
-  out[1] = df_neg(df_mul_u(df_add_fast(df_mul_f_u(y0, 7.0f), y1), k.sixth));
-  out[2] = df_mul_u(df_add_fast(df_mul_f_u(y0, 11.0f), df_add_fast(df_mul_f_u(y1, 5.0f), df_twice(y2))), k.sixth);
-  out[3] = df_mul_u(df_add_fast(df_twice(y1), df_mul_f_u(y2, 5.0f)), k.sixth);
-  out[4] = df_neg(df_mul_u(y2, k.sixth));
+  out[0] = df2_mul_u(y0, k.third);
+  out[1] = df2_neg(df2_mul_u(df2_add_fast(df2_mul_f_u(y0, 7.0f), y1), k.sixth));
+  out[2] = df2_mul_u(df2_add_fast(df2_mul_f_u(y0, 11.0f), df2_add_fast(df2_mul_f_u(y1, 5.0f), df2_twice(y2))), k.sixth);
+  out[3] = df2_mul_u(df2_add_fast(df2_twice(y1), df2_mul_f_u(y2, 5.0f)), k.sixth);
+  out[4] = df2_neg(df2_mul_u(y2, k.sixth));
   // db/d(x, y, z) of a window = 26/3 s (1, -2, 1) + 2 v dv/d(x, y, z)
-  df t = df_mul_u(df_mul_u(s[0], k0), k.c263), r = df_twice(df_mul_u(v0, k0));  // dv = (1, -4, 3)
-  out[0] = df_add_fast(out[0], df_add_fast(t, r));
-  out[1] = df_sub(out[1], df_add_fast(df_twice(t), df_twice(df_twice(r))));
-  out[2] = df_add_fast(out[2], df_add_fast(t, df_mul_f_u(r, 3.0f)));
-  t = df_mul_u(df_mul_u(s[1], k1), k.c263);
-  r = df_twice(df_mul_u(v1, k1));  // dv = (-1, 0, 1)
-  out[1] = df_add_fast(out[1], df_sub(t, r));
-  out[2] = df_sub(out[2], df_twice(t));
-  out[3] = df_add_fast(out[3], df_add_fast(t, r));
-  t = df_mul_u(df_mul_u(s[2], k2), k.c263);
-  r = df_twice(df_mul_u(v2, k2));  // dv = (3, -4, 1)
-  out[2] = df_add_fast(out[2], df_add_fast(t, df_mul_f_u(r, 3.0f)));
-  out[3] = df_sub(out[3], df_add_fast(df_twice(t), df_twice(df_twice(r))));
-  out[4] = df_add_fast(out[4], df_add_fast(t, r));
+  df2 t = df2_mul_u(df2_mul_u(s[0], k0), k.c263), r = df2_twice(df2_mul_u(v0, k0));  // dv = (1, -4, 3)
+  out[0] = df2_add_fast(out[0], df2_add_fast(t, r));
+  out[1] = df2_sub(out[1], df2_add_fast(df2_twice(t), df2_twice(df2_twice(r))));
+  out[2] = df2_add_fast(out[2], df2_add_fast(t, df2_mul_f_u(r, 3.0f)));
+  t = df2_mul_u(df2_mul_u(s[1], k1), k.c263);
+  r = df2_twice(df2_mul_u(v1, k1));  // dv = (-1, 0, 1)
+  out[1] = df2_add_fast(out[1], df2_sub(t, r));
+  out[2] = df2_sub(out[2], df2_twice(t));
+  out[3] = df2_add_fast(out[3], df2_add_fast(t, r));
+  t = df2_mul_u(df2_mul_u(s[2], k2), k.c263);
+  r = df2_twice(df2_mul_u(v2, k2));  // dv = (3, -4, 1)
+  out[2] = df2_add_fast(out[2], df2_add_fast(t, df2_mul_f_u(r, 3.0f)));
+  out[3] = df2_sub(out[3], df2_add_fast(df2_twice(t), df2_twice(df2_twice(r))));
+  out[4] = df2_add_fast(out[4], df2_add_fast(t, r));
 }
 
 __device__ __forceinline__ double pow2d(int k) { return __hiloint2double((k + 1023) << 20, 0); }
@@ -846,7 +854,7 @@ __device__ __forceinline__ int roe_adjoint_df(const df du[5], const df Lh[5], df
 
 template <int D>
 __global__ void __launch_bounds__(APF::THREADS, APF::MIN_CTAS) k_adj_dir_df(const AdjArgs a) {
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) double sm[];
   __shared__ int s_emax;
   constexpr int TP = APF::TP, NP = APF::NP, NI = APF::NI, NW = APF::NW, W = APF::W;
   constexpr int AX = (D == 0) ? 1 : 0;
@@ -861,11 +869,13 @@ __global__ void __launch_bounds__(APF::THREADS, APF::MIN_CTAS) k_adj_dir_df(cons
   double* q = sm + APF::OFF_Q;
   double* ri = sm + APF::OFF_RI;
   double* lm = sm + APF::OFF_L;
-  float2* G = reinterpret_cast<float2*>(sm + APF::OFF_G);
-  float2* Bw = reinterpret_cast<float2*>(sm + APF::OFF_B);
+  // G, Bw and wc hold the two lines of the tile side by side (hi0, hi1, lo0, lo1)
+  static_assert(W == 2, "the two-lane phases take the tile's two lines together");
+  float4* G4 = reinterpret_cast<float4*>(sm + APF::OFF_G);    // [9][NP]
+  float4* Bw4 = reinterpret_cast<float4*>(sm + APF::OFF_B);   // [9][3][NW]
   double* rec = sm + APF::OFF_REC;
   double* rd = sm + APF::OFF_RD;
-  float2* wc = reinterpret_cast<float2*>(sm + APF::OFF_WC);
+  float4* wc4 = reinterpret_cast<float4*>(sm + APF::OFF_WC);  // [9][6][NI]
   DFConst kc;
   {
     const double third = 1.0 / 3.0, sixth = 1.0 / 6.0, c263 = 26.0 / 3.0;
@@ -873,6 +883,7 @@ __global__ void __launch_bounds__(APF::THREADS, APF::MIN_CTAS) k_adj_dir_df(cons
     kc.sixth = df{(float)sixth, (float)(sixth - (double)(float)sixth)};
     kc.c263 = df{(float)c263, (float)(c263 - (double)(float)c263)};
   }
+  const DF2Const kc2{df2_splat(kc.third), df2_splat(kc.sixth), df2_splat(kc.c263)};
   const df eps4{(float)a.eps4, (float)(a.eps4 - (double)(float)a.eps4)};
   const df c133{(float)(13.0 / 3.0), (float)(13.0 / 3.0 - (double)(float)(13.0 / 3.0))};
   if (tid == 0) s_emax = -2000;
@@ -930,69 +941,71 @@ __global__ void __launch_bounds__(APF::THREADS, APF::MIN_CTAS) k_adj_dir_df(cons
 #pragma unroll
     for (int v = 0; v < 5; ++v) lm[v * NP * W + s] *= down;
   }
-  // first differences of the 9 scalars, FP64, kept as double-float
-  for (int item = tid; item < 9 * (NP - 1) * W; item += APF::THREADS) {
-    const int m = item / ((NP - 1) * W);
-    int j, line;
-    tile_split<D, W>(item - m * (NP - 1) * W, NP - 1, j, line);
+  // first differences of the 9 scalars, FP64, kept as double-float; both lines of the tile
+  // per item, stored side by side (hi0, hi1, lo0, lo1) for the two-lane phases below
+  for (int item = tid; item < 9 * (NP - 1); item += APF::THREADS) {
+    const int m = item / (NP - 1);
+    const int j = item - m * (NP - 1);
     const double* qm = q + m * NP * W;
-    const double d = qm[tile_idx<D, W>(j + 1, line, NP)] - qm[tile_idx<D, W>(j, line, NP)];
-    G[m * NP * W + tile_idx<D, W>(j, line, NP)] = df_pack(d2df_bits(d));
+    const double d0 = qm[tile_idx<D, W>(j + 1, 0, NP)] - qm[tile_idx<D, W>(j, 0, NP)];
+    const double d1 = qm[tile_idx<D, W>(j + 1, 1, NP)] - qm[tile_idx<D, W>(j, 1, NP)];
+    G4[m * NP + j] = df2_to4(df2_pack(d2df_bits(d0), d2df_bits(d1)));
   }
   __syncthreads();
 
-  // ---- B: window terms b_k of every window, stored as 1/b_k -----------------------------------
-  for (int item = tid; item < 9 * NW * W; item += APF::THREADS) {
-    const int m = item / (NW * W);
-    int w, line;
-    tile_split<D, W>(item - m * NW * W, NW, w, line);
-    const float2* Gm = G + m * NP * W;
-    const df g0 = df_unpack(Gm[tile_idx<D, W>(w, line, NP)]), g1 = df_unpack(Gm[tile_idx<D, W>(w + 1, line, NP)]);
-    const df sw = df_sub(g1, g0);
-    const df aa = df_add_pos_u(df_mul_u(df_sqr_u(sw), c133), eps4);
-    const df b0 = df_add_pos_u(df_sqr_u(df_sub(df_mul_f_u(g1, 3.0f), g0)), aa);
-    const df b1 = df_add_pos_u(df_sqr_u(df_add_fast(g0, g1)), aa);
-    const df b2 = df_add_pos_u(df_sqr_u(df_sub(g1, df_mul_f_u(g0, 3.0f))), aa);
-    const int o = tile_idx<D, W>(w, line, NW);
-    // their reciprocals: the weights (c_k / b_k^2) and the adjoints of b_k (omega_k / b_k) need only those
-    const df one{1.0f, 0.0f};
-    Bw[(m * 3 + 0) * NW * W + o] = df_pack(df_div(one, b0));
-    Bw[(m * 3 + 1) * NW * W + o] = df_pack(df_div(one, b1));
-    Bw[(m * 3 + 2) * NW * W + o] = df_pack(df_div(one, b2));
-    // b^2 must stay inside the float range (differences of the data up to ~1e9)
-    range_bad |= !(fmaxf(b0.hi, fmaxf(b1.hi, b2.hi)) < 1e18f);
+  // ---- B: window terms b_k of every window, stored as 1/b_k (both lines at once) -----------------
+  {
+    const df2 c133_2 = df2_splat(c133), eps4_2 = df2_splat(eps4);
+    const df2 one{f2splat(1.0f), f2splat(0.0f)};
+    for (int item = tid; item < 9 * NW; item += APF::THREADS) {
+      const int m = item / NW;
+      const int w = item - m * NW;
+      const float4* Gm = G4 + m * NP;
+      const df2 g0 = df2_from4(Gm[w]), g1 = df2_from4(Gm[w + 1]);
+      const df2 sw = df2_sub(g1, g0);
+      const df2 aa = df2_add_pos_u(df2_mul_u(df2_sqr_u(sw), c133_2), eps4_2);
+      const df2 b0 = df2_add_pos_u(df2_sqr_u(df2_sub(df2_mul_f_u(g1, 3.0f), g0)), aa);
+      const df2 b1 = df2_add_pos_u(df2_sqr_u(df2_add_fast(g0, g1)), aa);
+      const df2 b2 = df2_add_pos_u(df2_sqr_u(df2_sub(g1, df2_mul_f_u(g0, 3.0f))), aa);
+      // their reciprocals: the weights (c_k / b_k^2) and the adjoints of b_k (omega_k / b_k) need only those
+      Bw4[(m * 3 + 0) * NW + w] = df2_to4(df2_div(one, b0));
+      Bw4[(m * 3 + 1) * NW + w] = df2_to4(df2_div(one, b1));
+      Bw4[(m * 3 + 2) * NW + w] = df2_to4(df2_div(one, b2));
+      // b^2 must stay inside the float range (differences of the data up to ~1e9)
+      range_bad |= !(fmaxf(b0.hi.x, fmaxf(b1.hi.x, b2.hi.x)) < 1e18f) || !(fmaxf(b0.hi.y, fmaxf(b1.hi.y, b2.hi.y)) < 1e18f);
+    }
   }
   __syncthreads();
 
-  // ---- C: jumps of the u reconstructions (for the Roe adjoint) ----------------------------
-  for (int item = tid; item < 5 * NI * W; item += APF::THREADS) {
-    const int m = item / (NI * W);
-    int f, line;
-    tile_split<D, W>(item - m * NI * W, NI, f, line);
-    const float2* Gm = G + m * NP * W;
-    df g[5];
+  // ---- C: jumps of the u reconstructions (for the Roe adjoint), both lines at once -----------
+  for (int item = tid; item < 5 * NI; item += APF::THREADS) {
+    const int m = item / NI;
+    const int f = item - m * NI;
+    const float4* Gm = G4 + m * NP;
+    df2 g[5];
 #pragma unroll
-    for (int j = 0; j < 5; ++j) g[j] = df_unpack(Gm[tile_idx<D, W>(f + j, line, NP)]);
-    const float2* B = Bw + m * 3 * NW * W;
-    auto ldb = [&](int k, int w) { return df_unpack(B[k * NW * W + tile_idx<D, W>(w, line, NW)]); };
-    df omL[3], omR[3], s[3], E0, E2;
-    df_omega(ldb(0, f), ldb(1, f + 1), ldb(2, f + 2), omL);
-    const df ML = df_offset(g[0], g[1], g[2], g[3], omL, kc, E0, E2, s);
-    df_omega(ldb(2, f + 3), ldb(1, f + 2), ldb(0, f + 1), omR);
-    const df MR = df_offset(df_neg(g[4]), df_neg(g[3]), df_neg(g[2]), df_neg(g[1]), omR, kc, E0, E2, s);
+    for (int j = 0; j < 5; ++j) g[j] = df2_from4(Gm[f + j]);
+    const float4* B = Bw4 + m * 3 * NW;
+    auto ldb = [&](int k, int w) { return df2_from4(B[k * NW + w]); };
+    df2 omL[3], omR[3], s[3], E0, E2;
+    df2_omega(ldb(0, f), ldb(1, f + 1), ldb(2, f + 2), omL);
+    const df2 ML = df2_adj_offset(g[0], g[1], g[2], g[3], omL, kc2, E0, E2, s);
+    df2_omega(ldb(2, f + 3), ldb(1, f + 2), ldb(0, f + 1), omR);
+    const df2 MR = df2_adj_offset(df2_neg(g[4]), df2_neg(g[3]), df2_neg(g[2]), df2_neg(g[1]), omR, kc2, E0, E2, s);
     // the jump ûR - ûL = (P3 - P2) - (2 g2 + g3)/6 + MR - (2 g2 + g1)/6 - ML, in double-float
     // (the values themselves are not needed)
-    const df g22 = df_twice(g[2]);
-    const df lin = df_mul_u(df_add_fast(df_add_fast(g22, g[1]), df_add_fast(g22, g[3])), kc.sixth);
-    const df du = df_add_fast(df_add_fast(g[2], df_neg(lin)), df_add_fast(MR, df_neg(ML)));
-    const int o = tile_idx<D, W>(f, line, NI);
-    reinterpret_cast<float2*>(rec)[m * NI * W + o] = df_pack(du);
+    const df2 g22 = df2_twice(g[2]);
+    const df2 lin = df2_mul_u(df2_add_fast(df2_add_fast(g22, g[1]), df2_add_fast(g22, g[3])), kc2.sixth);
+    const df2 du = df2_add_fast(df2_add_fast(g[2], df2_neg(lin)), df2_add_fast(MR, df2_neg(ML)));
+    float2* rj = reinterpret_cast<float2*>(rec) + m * NI * W;
+    rj[tile_idx<D, W>(f, 0, NI)] = df_pack(df2_lane0(du));
+    rj[tile_idx<D, W>(f, 1, NI)] = df_pack(df2_lane1(du));
     // the weights, for phase E (which overwrites these slots with its contributions)
-    float2* wm = wc + m * 6 * NI * W;
+    float4* wm = wc4 + m * 6 * NI;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      wm[k * NI * W + o] = df_pack(omL[k]);
-      wm[(3 + k) * NI * W + o] = df_pack(omR[k]);
+      wm[k * NI + f] = df2_to4(omL[k]);
+      wm[(3 + k) * NI + f] = df2_to4(omR[k]);
     }
   }
   __syncthreads();
@@ -1036,53 +1049,60 @@ __global__ void __launch_bounds__(APF::THREADS, APF::MIN_CTAS) k_adj_dir_df(cons
   }
   __syncthreads();
 
-  // ---- E: reconstruction adjoints -> six stencil contributions per scalar and interface -----
-  for (int item = tid; item < 9 * NI * W; item += APF::THREADS) {
-    const int m = item / (NI * W);
-    int f, line;
-    tile_split<D, W>(item - m * NI * W, NI, f, line);
-    const int o = tile_idx<D, W>(f, line, NI);
-    const int sa = tile_idx<D, W>(f + 2, line, NP), sb = tile_idx<D, W>(f + 3, line, NP);
-    df yL, yR;
-    if (m < 5) {
-      const df gdu = df_unpack(reinterpret_cast<const float2*>(rd)[m * NI * W + o]);
-      yL = df_neg(gdu);
-      yR = gdu;
-      if (m == 1 + D) {  // mass flux f_0 = u_{1+D}: (f^L + f^R)/2 part
-        const df h0 = d2df_bits(0.5 * ((lm[sb] - lm[sa]) * rdx));
-        yL = df_add_fast(yL, h0);
-        yR = df_add_fast(yR, h0);
-      }
-    } else {
-      yL = yR = d2df_bits(0.5 * ((lm[(m - 4) * NP * W + sb] - lm[(m - 4) * NP * W + sa]) * rdx));
-    }
-    range_bad |= !(fabsf(yL.hi) < 1e30f && fabsf(yR.hi) < 1e30f);
-    const float2* Gm = G + m * NP * W;
-    df g[5];
+  // ---- E: reconstruction adjoints -> six stencil contributions per scalar and interface, -----
+  //      both lines at once
+  for (int item = tid; item < 9 * NI; item += APF::THREADS) {
+    const int m = item / NI;
+    const int f = item - m * NI;
+    df y2[2][2];  // [line][left, right]
 #pragma unroll
-    for (int j = 0; j < 5; ++j) g[j] = df_unpack(Gm[tile_idx<D, W>(f + j, line, NP)]);
-    const float2* B = Bw + m * 3 * NW * W;
-    auto ldb = [&](int k, int w) { return df_unpack(B[k * NW * W + tile_idx<D, W>(w, line, NW)]); };
-    float2* wm = wc + m * 6 * NI * W;
-    df omL[3], omR[3];
+    for (int line = 0; line < 2; ++line) {
+      const int o = tile_idx<D, W>(f, line, NI);
+      const int sa = tile_idx<D, W>(f + 2, line, NP), sb = tile_idx<D, W>(f + 3, line, NP);
+      df yL, yR;
+      if (m < 5) {
+        const df gdu = df_unpack(reinterpret_cast<const float2*>(rd)[m * NI * W + o]);
+        yL = df_neg(gdu);
+        yR = gdu;
+        if (m == 1 + D) {  // mass flux f_0 = u_{1+D}: (f^L + f^R)/2 part
+          const df h0 = d2df_bits(0.5 * ((lm[sb] - lm[sa]) * rdx));
+          yL = df_add_fast(yL, h0);
+          yR = df_add_fast(yR, h0);
+        }
+      } else {
+        yL = yR = d2df_bits(0.5 * ((lm[(m - 4) * NP * W + sb] - lm[(m - 4) * NP * W + sa]) * rdx));
+      }
+      range_bad |= !(fabsf(yL.hi) < 1e30f && fabsf(yR.hi) < 1e30f);
+      y2[line][0] = yL;
+      y2[line][1] = yR;
+    }
+    const float4* Gm = G4 + m * NP;
+    df2 g[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) g[j] = df2_from4(Gm[f + j]);
+    const float4* B = Bw4 + m * 3 * NW;
+    auto ldb = [&](int k, int w) { return df2_from4(B[k * NW + w]); };
+    float4* wm = wc4 + m * 6 * NI;
+    df2 omL[3], omR[3];
     if (m < 5) {  // stored by phase C
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        omL[k] = df_unpack(wm[k * NI * W + o]);
-        omR[k] = df_unpack(wm[(3 + k) * NI * W + o]);
+        omL[k] = df2_from4(wm[k * NI + f]);
+        omR[k] = df2_from4(wm[(3 + k) * NI + f]);
       }
     } else {
-      df_omega(ldb(0, f), ldb(1, f + 1), ldb(2, f + 2), omL);
-      df_omega(ldb(2, f + 3), ldb(1, f + 2), ldb(0, f + 1), omR);
+      df2_omega(ldb(0, f), ldb(1, f + 1), ldb(2, f + 2), omL);
+      df2_omega(ldb(2, f + 3), ldb(1, f + 2), ldb(0, f + 1), omR);
     }
-    df cL[5], cR[5];
-    df_recon_adjoint(g[0], g[1], g[2], g[3], ldb(0, f), ldb(1, f + 1), ldb(2, f + 2), omL, yL, kc, cL);
-    df_recon_adjoint(df_neg(g[4]), df_neg(g[3]), df_neg(g[2]), df_neg(g[1]), ldb(2, f + 3), ldb(1, f + 2),
-                     ldb(0, f + 1), omR, yR, kc, cR);
-    wm[0 * NI * W + o] = df_pack(cL[0]);
+    df2 cL[5], cR[5];
+    df2_recon_adjoint(g[0], g[1], g[2], g[3], ldb(0, f), ldb(1, f + 1), ldb(2, f + 2), omL,
+                             df2_pack(y2[0][0], y2[1][0]), kc2, cL);
+    df2_recon_adjoint(df2_neg(g[4]), df2_neg(g[3]), df2_neg(g[2]), df2_neg(g[1]), ldb(2, f + 3),
+                             ldb(1, f + 2), ldb(0, f + 1), omR, df2_pack(y2[0][1], y2[1][1]), kc2, cR);
+    wm[0 * NI + f] = df2_to4(cL[0]);
 #pragma unroll
-    for (int j = 1; j < 5; ++j) wm[j * NI * W + o] = df_pack(df_add_fast(cL[j], cR[5 - j]));
-    wm[5 * NI * W + o] = df_pack(cR[0]);
+    for (int j = 1; j < 5; ++j) wm[j * NI + f] = df2_to4(df2_add_fast(cL[j], cR[5 - j]));
+    wm[5 * NI + f] = df2_to4(cR[0]);
   }
   if (__any_sync(0xffffffffu, range_bad) && (tid & 31) == 0) atomicOr(a.status, ST_DF_RANGE);
   __syncthreads();
@@ -1090,6 +1110,7 @@ __global__ void __launch_bounds__(APF::THREADS, APF::MIN_CTAS) k_adj_dir_df(cons
   // ---- F: gather, adjoint of the point fluxes, scale back, epilogue ----------------------------
   const double up = pow2d(E);
   const double gm1 = a.gamma - 1.0;
+  const float* wcf = reinterpret_cast<const float*>(wc4);  // lane `line` of a pair: hi at +line, lo at +2+line
   for (int item = tid; item < TP * W; item += APF::THREADS) {
     int pp, line;
     tile_split<D, W>(item, TP, pp, line);
@@ -1097,13 +1118,13 @@ __global__ void __launch_bounds__(APF::THREADS, APF::MIN_CTAS) k_adj_dir_df(cons
     const int pos = pp + 5;
     const int oa = tile_idx<D, W>(pos - 2, line, NI), ob = tile_idx<D, W>(pos - 3, line, NI);
     const float2* rdf = reinterpret_cast<const float2*>(rd);
+    auto ldw = [&](int slot) { return df{wcf[4 * slot + line], wcf[4 * slot + 2 + line]}; };
     double gsum[9], cv[5];
 #pragma unroll
     for (int m = 0; m < 9; ++m) {
-      const float2* wm = wc + m * 6 * NI * W;
-      df acc = df_unpack(wm[tile_idx<D, W>(pos, line, NI)]);
+      df acc = ldw(m * 6 * NI + pos);
 #pragma unroll
-      for (int j = 1; j < 6; ++j) acc = df_add_fast(acc, df_unpack(wm[j * NI * W + tile_idx<D, W>(pos - j, line, NI)]));
+      for (int j = 1; j < 6; ++j) acc = df_add_fast(acc, ldw((m * 6 + j) * NI + pos - j));
       if (m < 5)  // the Roe-average adjoints of the two interfaces next to the point
         acc = df_add_fast(acc, df_add_fast(df_unpack(rdf[(5 + m) * NI * W + oa]), df_unpack(rdf[(10 + m) * NI * W + ob])));
       gsum[m] = f2d_bits(acc.hi) + f2d_bits(acc.lo);
