@@ -1110,25 +1110,38 @@ __global__ void __launch_bounds__(APF::THREADS, APF::MIN_CTAS) k_adj_dir_df(cons
   // ---- F: gather, adjoint of the point fluxes, scale back, epilogue ----------------------------
   const double up = pow2d(E);
   const double gm1 = a.gamma - 1.0;
-  const float* wcf = reinterpret_cast<const float*>(wc4);  // lane `line` of a pair: hi at +line, lo at +2+line
+  // F1: the gather, one (scalar, point, line) per item, into the dead window-term space
+  static_assert(9 * TP * W <= 27 * NW * W, "gathered sums fit the window-term space");
+  double* gsm = sm + APF::OFF_B;  // [9][TP*W]
+  {
+    const float* wcf = reinterpret_cast<const float*>(wc4);  // lane `line` of a pair: hi at +line, lo at +2+line
+    const float2* rdf = reinterpret_cast<const float2*>(rd);
+    for (int item = tid; item < 9 * TP * W; item += APF::THREADS) {
+      const int m = item / (TP * W);
+      int pp, line;
+      tile_split<D, W>(item - m * TP * W, TP, pp, line);
+      const int pos = pp + 5;
+      auto ldw = [&](int slot) { return df{wcf[4 * slot + line], wcf[4 * slot + 2 + line]}; };
+      df acc = ldw(m * 6 * NI + pos);
+#pragma unroll
+      for (int j = 1; j < 6; ++j) acc = df_add_fast(acc, ldw((m * 6 + j) * NI + pos - j));
+      if (m < 5) {  // the Roe-average adjoints of the two interfaces next to the point
+        const int oa = tile_idx<D, W>(pos - 2, line, NI), ob = tile_idx<D, W>(pos - 3, line, NI);
+        acc = df_add_fast(acc, df_add_fast(df_unpack(rdf[(5 + m) * NI * W + oa]), df_unpack(rdf[(10 + m) * NI * W + ob])));
+      }
+      gsm[m * TP * W + tile_idx<D, W>(pp, line, TP)] = f2d_bits(acc.hi) + f2d_bits(acc.lo);
+    }
+  }
+  __syncthreads();
+  // F2: adjoint of the point fluxes, scale back, epilogue (one point per item)
   for (int item = tid; item < TP * W; item += APF::THREADS) {
     int pp, line;
     tile_split<D, W>(item, TP, pp, line);
     if (s0 + pp >= nD || a0 + line >= na) continue;
     const int pos = pp + 5;
-    const int oa = tile_idx<D, W>(pos - 2, line, NI), ob = tile_idx<D, W>(pos - 3, line, NI);
-    const float2* rdf = reinterpret_cast<const float2*>(rd);
-    auto ldw = [&](int slot) { return df{wcf[4 * slot + line], wcf[4 * slot + 2 + line]}; };
     double gsum[9], cv[5];
 #pragma unroll
-    for (int m = 0; m < 9; ++m) {
-      df acc = ldw(m * 6 * NI + pos);
-#pragma unroll
-      for (int j = 1; j < 6; ++j) acc = df_add_fast(acc, ldw((m * 6 + j) * NI + pos - j));
-      if (m < 5)  // the Roe-average adjoints of the two interfaces next to the point
-        acc = df_add_fast(acc, df_add_fast(df_unpack(rdf[(5 + m) * NI * W + oa]), df_unpack(rdf[(10 + m) * NI * W + ob])));
-      gsum[m] = f2d_bits(acc.hi) + f2d_bits(acc.lo);
-    }
+    for (int m = 0; m < 9; ++m) gsum[m] = gsm[m * TP * W + tile_idx<D, W>(pp, line, TP)];
 #pragma unroll
     for (int v = 0; v < 5; ++v) cv[v] = gsum[v];
     const int s = tile_idx<D, W>(pos, line, NP);
