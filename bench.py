@@ -518,10 +518,11 @@ def run_ours(args, world, rank, local):
                   "fp64_pipe_part": "point values, first differences, point fluxes, interface-flux sums, flux "
                                     "difference, RK update",
                   "fp32_pipe_part": "WENO weights and offsets, interface jumps, Roe dissipation, viscous "
-                                    "fluxes and divergence, as double-float (~4.3k FP32 instructions per point "
-                                    "and pass, ncu)"},
+                                    "fluxes and divergence, as double-float; the differences, indicators and "
+                                    "reconstructions of two lines per packed FP32 instruction"},
         "note": "method_fp64_frac above 1 means the formulation runs the method faster than the FP64 pipe "
-                "could in all-FP64 arithmetic; the binding resource is instruction issue (frac)"}
+                "could in all-FP64 arithmetic; instruction issue (frac), the FP64 pipe (~46 % busy, ncu) "
+                "and the phase barriers bound it together"}
     tr = ncu_traffic_per_point("k_dir", kernel_source_sha())
     if tr is not None:
         bpp, src, grid = tr
