@@ -9,7 +9,7 @@
 // Every operation here except df2_div performs, in each lane, exactly the IEEE
 // operations of its scalar counterpart in df.cuh in the same order (a - b as a + (-b),
 // which IEEE 754 defines identically), so a two-lane result equals the two scalar
-// results bit for bit (checked on the GPU over a million random lanes, operation by
+// results bit for bit (tests/test_gpu_df2.py: a million random lane pairs, operation by
 // operation and for the compositions the direction pass uses); df2_div differs from
 // df_div in its last step (see there).
 // Layout: hi = (hi of lane 0, hi of lane 1), lo = (lo of lane 0, lo of lane 1).
