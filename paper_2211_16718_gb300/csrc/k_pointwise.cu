@@ -8,6 +8,7 @@
 #include <math.h>
 
 #include "df.cuh"
+#include "df2.cuh"
 #include "k_point_impl.cuh"
 #include "ns3d_internal.cuh"
 
@@ -46,27 +47,39 @@ __global__ void __launch_bounds__(PW_THREADS) k_visc(const double* __restrict__ 
   visc_point_ijk(pm, fv, nx, ny, nz, i, j, k, r12, mu, kappa, only_d);
 }
 
-// Tiled NS3D_FP64 viscous-flux kernel (primitives in the layout of prim_point<true>).  A CTA owns a 32 x 8 block of x-y columns and
-// marches along z through VT_CZ planes.  Each plane of (u, v, w, T), with a 2-point x-y
-// halo, is converted to double-float once into a ring of 5 planes (z-2 .. z+2) in shared
-// memory, so every stencil value is converted once rather than once per stencil that
-// uses it (12 times).  The per-point arithmetic is that of visc_point_df_ijk: the same
-// conversions, the same gradient and flux operations, so the same bits.
+// Tiled NS3D_FP64 viscous-flux kernel (primitives in the layout of prim_point<true>).  A CTA
+// owns a 32 x 8 block of x-y columns and marches along z through VT_CZ planes.  Each plane of
+// (u, v, w, T), with a 2-point x-y halo, is converted to double-float once into a ring of 5
+// planes (z-2 .. z+2) in shared memory, so every stencil value is converted once rather than
+// once per stencil that uses it (12 times).  The ring holds the fields in pairs, (u, v) and
+// (w, T), each position a 16-byte record (hi, hi, lo, lo): the 12 gradient stencils run as 6
+// two-lane double-float stencils on the packed FP32 instructions (df2.cuh; each lane the
+// operations of d4_dfv), the flux assembly reads the lanes as scalars.  The per-point
+// arithmetic is that of visc_point_df_ijk: the same conversions, the same gradient and flux
+// operations, so the same bits.
 constexpr int VT_X = 32, VT_Y = 8, VT_HX = VT_X + 4, VT_HY = VT_Y + 4, VT_PLANE = VT_HX * VT_HY;
 constexpr int VT_RING = 5, VT_CZ = VISC_ZCHUNK;
-constexpr int VT_SMEM = VT_RING * 4 * VT_PLANE * (int)sizeof(float2);  // 69,120 bytes
+constexpr int VT_SMEM = VT_RING * 2 * VT_PLANE * (int)sizeof(float4);  // 69,120 bytes
+
+// d4_dfv on two lanes.
+__device__ __forceinline__ df2 d4_dfv2(df2 qm2, df2 qm1, df2 qp1, df2 qp2, df2 r12h) {
+  const df2 d1 = df2_add_fast(qp1, df2_neg(qm1));
+  const df2 d2 = df2_add_fast(qp2, df2_neg(qm2));
+  return df2_mul_u(df2_add_fast(df2_mul_f_u(d1, 8.0f), df2_neg(d2)), r12h);
+}
 
 __global__ void __launch_bounds__(VT_X * VT_Y, 3) k_visc_tiled(const double* __restrict__ pm, double* __restrict__ fv,
                                                                 const Grid g, double mu, double kappa, int only_d,
                                                                 int zc0) {
-  extern __shared__ float2 ring[];  // [VT_RING][4][VT_HY][VT_HX]
+  extern __shared__ float4 ring4[];  // [VT_RING][2][VT_HY][VT_HX]: (u, v) and (w, T)
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const long long N = g.N;
   const int x0 = blockIdx.x * VT_X, y0 = blockIdx.y * VT_Y, z0 = (zc0 + blockIdx.z) * VT_CZ;
   const int z1 = min(z0 + VT_CZ, nz);
   const int tid = threadIdx.x, tx = tid % VT_X, ty = tid / VT_X;
-  const df r12[3] = {d2df_bits(g.r12h[0]), d2df_bits(g.r12h[1]), d2df_bits(g.r12h[2])};
-  auto slot = [&](int zz) { return ring + ((zz - z0 + 2) % VT_RING) * 4 * VT_PLANE; };
+  const df2 r12[3] = {df2_splat(d2df_bits(g.r12h[0])), df2_splat(d2df_bits(g.r12h[1])),
+                      df2_splat(d2df_bits(g.r12h[2]))};
+  auto slot = [&](int zz) { return ring4 + ((zz - z0 + 2) % VT_RING) * 2 * VT_PLANE; };
   // in-plane offsets of this thread's halo-tile positions (the same for every plane)
   constexpr int NPOS = (VT_PLANE + VT_X * VT_Y - 1) / (VT_X * VT_Y);
   int xy[NPOS];
@@ -79,43 +92,54 @@ __global__ void __launch_bounds__(VT_X * VT_Y, 3) k_visc_tiled(const double* __r
   const long long plane_n = (long long)nx * ny;
   auto load_plane = [&](int zz) {  // plane zz (periodic) of the four fields, with halo
     const long long zoff = (long long)wrap_idx(zz, nz) * plane_n;
-    float2* R = slot(zz);
+    float4* R = slot(zz);
 #pragma unroll
     for (int k = 0; k < NPOS; ++k) {
       const int pos = tid + k * VT_X * VT_Y;
       if (pos >= VT_PLANE) break;
       const long long p = zoff + xy[k];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const df v = d2df_bits(__ldg(pm + (long long)q * N + p));
-        R[q * VT_PLANE + pos] = make_float2(v.hi, v.lo);
-      }
-      R[3 * VT_PLANE + pos] = __ldg(reinterpret_cast<const float2*>(pm + (long long)PM_T * N + p));  // double-float plane
+      const df vu = d2df_bits(__ldg(pm + (long long)PM_U * N + p));
+      const df vv = d2df_bits(__ldg(pm + (long long)PM_V * N + p));
+      const df vw = d2df_bits(__ldg(pm + (long long)PM_W * N + p));
+      const float2 vT = __ldg(reinterpret_cast<const float2*>(pm + (long long)PM_T * N + p));  // double-float plane
+      R[pos] = make_float4(vu.hi, vv.hi, vu.lo, vv.lo);
+      R[VT_PLANE + pos] = make_float4(vw.hi, vT.x, vw.lo, vT.y);
     }
   };
-  auto ld = [](const float2* P, int i) { const float2 v = P[i]; return df{v.x, v.y}; };
+  auto ld = [](const float4* P, int i) { return df2_from4(P[i]); };
   for (int zz = z0 - 2; zz < z0 + 2; ++zz) load_plane(zz);
   for (int z = z0; z < z1; ++z) {
     load_plane(z + 2);
     __syncthreads();
     if (x0 + tx < nx && y0 + ty < ny) {
       const int c = (ty + 2) * VT_HX + (tx + 2);
-      const float2 *Zm2 = slot(z - 2), *Zm1 = slot(z - 1), *Z0 = slot(z), *Zp1 = slot(z + 1), *Zp2 = slot(z + 2);
+      const float4 *Zm2 = slot(z - 2), *Zm1 = slot(z - 1), *Z0 = slot(z), *Zp1 = slot(z + 1), *Zp2 = slot(z + 2);
       // the flux along only_d (lean storage) needs 8 of the 12 gradients: d(u, v, w, T)/dx_d, the
       // derivatives of the velocity component along only_d, and the diagonal (divergence)
+      auto need = [&](int q, int e) { return only_d < 0 || e == only_d || (q < 3 && (q == only_d || q == e)); };
       df G[4][3];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float2* P = Z0 + q * VT_PLANE;
-        auto need = [&](int e) { return only_d < 0 || e == only_d || (q < 3 && (q == only_d || q == e)); };
-        const df zero{0.0f, 0.0f};
-        G[q][0] = need(0) ? d4_dfv(ld(P, c - 2), ld(P, c - 1), ld(P, c + 1), ld(P, c + 2), r12[0]) : zero;
-        G[q][1] = need(1) ? d4_dfv(ld(P, c - 2 * VT_HX), ld(P, c - VT_HX), ld(P, c + VT_HX), ld(P, c + 2 * VT_HX), r12[1])
-                          : zero;
-        const int o = q * VT_PLANE + c;
-        G[q][2] = need(2) ? d4_dfv(ld(Zm2, o), ld(Zm1, o), ld(Zp1, o), ld(Zp2, o), r12[2]) : zero;
+      for (int k = 0; k < 2; ++k) {  // field pair k: (u, v) or (w, T)
+        const float4* P = Z0 + k * VT_PLANE;
+        const int o = k * VT_PLANE + c;
+        df2 Gk[3];
+        const df2 zero{f2splat(0.0f), f2splat(0.0f)};
+        Gk[0] = (need(2 * k, 0) || need(2 * k + 1, 0))
+                    ? d4_dfv2(ld(P, c - 2), ld(P, c - 1), ld(P, c + 1), ld(P, c + 2), r12[0]) : zero;
+        Gk[1] = (need(2 * k, 1) || need(2 * k + 1, 1))
+                    ? d4_dfv2(ld(P, c - 2 * VT_HX), ld(P, c - VT_HX), ld(P, c + VT_HX), ld(P, c + 2 * VT_HX), r12[1])
+                    : zero;
+        Gk[2] = (need(2 * k, 2) || need(2 * k + 1, 2)) ? d4_dfv2(ld(Zm2, o), ld(Zm1, o), ld(Zp1, o), ld(Zp2, o), r12[2])
+                                                      : zero;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          const df dz{0.0f, 0.0f};
+          G[2 * k][e] = need(2 * k, e) ? df2_lane0(Gk[e]) : dz;
+          G[2 * k + 1][e] = need(2 * k + 1, e) ? df2_lane1(Gk[e]) : dz;
+        }
       }
-      const df vel[3] = {ld(Z0, c), ld(Z0 + VT_PLANE, c), ld(Z0 + 2 * VT_PLANE, c)};
+      const df2 uv = ld(Z0, c), wT = ld(Z0 + VT_PLANE, c);
+      const df vel[3] = {df2_lane0(uv), df2_lane1(uv), df2_lane0(wT)};
       visc_fluxes_df(G, vel, mu, kappa, fv, N, flat3(x0 + tx, y0 + ty, z, nx, ny), only_d);
     }
     __syncthreads();  // the slot of plane z - 2 takes plane z + 3 next
