@@ -29,7 +29,10 @@
 // 4th-order central difference.  Two point kernels: (1) adjoint of Fv -> adjoint of G
 // and of the velocities, (2) -sum_e D_e of the G adjoint plus the velocity adjoint ->
 // adjoint of u through u_k = m_k/rho, T = gamma (gamma - 1)(e/rho - |m|^2/(2 rho^2)).
+#include <limits.h>
 #include <math.h>
+
+#include <algorithm>
 
 #include "df.cuh"
 #include "df2.cuh"
@@ -1311,6 +1314,158 @@ __global__ void __launch_bounds__(256) k_visc_adj2(const Grid g, const double* _
   }
 }
 
+// The two viscous adjoint kernels in the NS3D_FP64 form: the stencils, stresses, heat flux and
+// their adjoints in double-float on the FP32 pipe (the same algebra as k_visc_adj1/2), the 15
+// scratch planes stored as double-float pairs; kernel 2 converts the adjoint of (u, v, w, T)
+// to FP64 once and finishes as k_visc_adj2.  The viscous terms are ~mu |grad u| in size, so
+// the double-float rounding (2^-48) lands far below the FP64 rounding of the direction
+// adjoints they are added to, as in the forward viscous kernel.
+// Largest binary exponent of lam_scale * lambda over the planes 1..4 of lambda, into *out (which
+// holds a large negative value before; it stays so if they all vanish).
+__global__ void __launch_bounds__(256) k_lam_expo(const double* __restrict__ lam, long long N, double lam_scale,
+                                                  int* out) {
+  int emax = INT_MIN;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < 4 * N; i += (long long)gridDim.x * 256) {
+    const double l = lam_scale * __ldg(lam + N + i);
+    if (l != 0.0) emax = max(emax, ((__double2hiint(l) >> 20) & 0x7ff) - 1023);
+  }
+  emax = __reduce_max_sync(0xffffffffu, emax);
+  if ((threadIdx.x & 31) == 0 && emax != INT_MIN) atomicMax(out, emax);
+}
+
+// The common exponent E of the two kernels (0 if lambda vanishes), inside the FP64 range.
+__device__ __forceinline__ int visc_adj_expo(const int* expo) {
+  const int e = *expo;
+  return (e < -1000) ? 0 : min(e, 1000);
+}
+
+__global__ void __launch_bounds__(256) k_visc_adj1_df(const Grid g, const double* __restrict__ pm,
+                                                      const double* __restrict__ lam, double lam_scale,
+                                                      double* __restrict__ sc, double mu, double kappa,
+                                                      const int* __restrict__ expo) {
+  const long long N = g.N;
+  // lambda * lam_scale relative to 2^E (exact power-of-two scaling): every double-float value of
+  // this kernel stays inside the float range whatever the scale of lambda
+  const double ls = lam_scale * pow2d(-visc_adj_expo(expo));
+  const int i = blockIdx.x * 32 + threadIdx.x % 32, j = blockIdx.y * 8 + threadIdx.x / 32, k = blockIdx.z;
+  if (i >= g.n[0] || j >= g.n[1]) return;
+  const long long p = flat3(i, j, k, g.n[0], g.n[1]);
+  df G[4][3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    long long nb[4];
+    neighbours(i, j, k, d, g, nb);
+    const df r12 = d2df_bits(g.r12h[d]);
+#pragma unroll
+    for (int qv = 0; qv < 4; ++qv) {
+      const double* A = pm + (long long)((qv < 3) ? qv : PM_T) * N;
+      G[qv][d] = d4_df(__ldg(A + nb[0]), __ldg(A + nb[1]), __ldg(A + nb[2]), __ldg(A + nb[3]), r12);
+    }
+  }
+  const df vel[3] = {d2df_bits(pm[PM_U * N + p]), d2df_bits(pm[PM_V * N + p]), d2df_bits(pm[PM_W * N + p])};
+  const double two3 = 2.0 / 3.0;
+  const df c23{(float)two3, (float)(two3 - (double)(float)two3)};
+  const df dmu = d2df_bits(mu), dkap = d2df_bits(kappa);
+  const df mu2 = df_twice(dmu), mmu23 = df_neg(df_mul(dmu, c23));  // 2 mu and -(2/3) mu
+  const df tdiv = df_mul_u(df_add_fast(G[0][0], df_add_fast(G[1][1], G[2][2])), c23);
+  const df zero{0.0f, 0.0f};
+  df Gb[4][3], vb[3] = {zero, zero, zero}, divb = zero;
+#pragma unroll
+  for (int qv = 0; qv < 4; ++qv)
+#pragma unroll
+    for (int e = 0; e < 3; ++e) Gb[qv][e] = zero;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    long long nb[4];
+    neighbours(i, j, k, d, g, nb);
+    const df r12 = d2df_bits(g.r12h[d]);
+    df Fb[4];  // adjoint of the viscous flux along d: -D_d lambda_{1+c}
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const double* L = lam + (long long)(1 + cc) * N;
+      Fb[cc] = df_neg(d4_df(ls * __ldg(L + nb[0]), ls * __ldg(L + nb[1]), ls * __ldg(L + nb[2]), ls * __ldg(L + nb[3]),
+                            r12));
+    }
+    Gb[3][d] = df_add_fast(df_mul_u(dkap, Fb[3]), Gb[3][d]);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const df tau = (m == d) ? df_mul(dmu, df_add_fast(df_twice(G[d][d]), df_neg(tdiv)))
+                              : df_mul(dmu, df_add_fast(G[m][d], G[d][m]));
+      const df tb = df_add_fast(df_mul_u(Fb[3], vel[m]), Fb[m]);
+      vb[m] = df_add_fast(df_mul_u(Fb[3], tau), vb[m]);
+      if (m == d) {
+        Gb[d][d] = df_add_fast(df_mul_u(mu2, tb), Gb[d][d]);
+        divb = df_add_fast(df_mul_u(mmu23, tb), divb);
+      } else {
+        const df t = df_mul_u(dmu, tb);
+        Gb[m][d] = df_add_fast(t, Gb[m][d]);
+        Gb[d][m] = df_add_fast(t, Gb[d][m]);
+      }
+    }
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) Gb[d][d] = df_add_fast(Gb[d][d], divb);
+#pragma unroll
+  for (int qv = 0; qv < 4; ++qv)
+#pragma unroll
+    for (int e = 0; e < 3; ++e) store_df(sc + (long long)(qv * 3 + e) * N + p, Gb[qv][e]);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) store_df(sc + (long long)(12 + m) * N + p, vb[m]);
+}
+
+__global__ void __launch_bounds__(256) k_visc_adj2_df(const Grid g, const double* __restrict__ u,
+                                                      const double* __restrict__ sc, double gamma,
+                                                      double* __restrict__ out, int accumulate,
+                                                      const int* __restrict__ expo) {
+  const long long N = g.N;
+  const double up = pow2d(visc_adj_expo(expo));  // back from the scale of k_visc_adj1_df
+  const int i = blockIdx.x * 32 + threadIdx.x % 32, j = blockIdx.y * 8 + threadIdx.x / 32, k = blockIdx.z;
+  if (i >= g.n[0] || j >= g.n[1]) return;
+  const long long p = flat3(i, j, k, g.n[0], g.n[1]);
+  const float2* S = reinterpret_cast<const float2*>(sc);
+  auto ld = [&](long long idx) { const float2 v = __ldg(S + idx); return df{v.x, v.y}; };
+  const df zero{0.0f, 0.0f};
+  df W[4] = {zero, zero, zero, zero};
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    long long nb[4];
+    neighbours(i, j, k, e, g, nb);
+    const df r12 = d2df_bits(g.r12h[e]);
+#pragma unroll
+    for (int qv = 0; qv < 4; ++qv) {
+      const long long b = (long long)(qv * 3 + e) * N;
+      W[qv] = df_add_fast(W[qv], df_neg(d4_dfv(ld(b + nb[0]), ld(b + nb[1]), ld(b + nb[2]), ld(b + nb[3]), r12)));
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 3; ++m) W[m] = df_add_fast(W[m], ld((long long)(12 + m) * N + p));
+  double Wb[4];
+#pragma unroll
+  for (int qv = 0; qv < 4; ++qv) Wb[qv] = (f2d_bits(W[qv].hi) + f2d_bits(W[qv].lo)) * up;
+  const double rho = u[p], e = u[4 * N + p];
+  const double rr = 1.0 / rho;
+  const double V[3] = {u[N + p] * rr, u[2 * N + p] * rr, u[3 * N + p] * rr};
+  const double gg = gamma * (gamma - 1.0);
+  const double Tb = gg * Wb[3];
+  double ub[5];
+  ub[4] = Tb * rr;
+  double v2 = 0.0, wv = 0.0;
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    ub[1 + m] = fma(-Tb, V[m], Wb[m]) * rr;
+    v2 = fma(V[m], V[m], v2);
+    wv = fma(Wb[m], V[m], wv);
+  }
+  ub[0] = fma(Tb, v2 - e * rr, -wv) * rr;
+  if (accumulate) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) out[v * N + p] += ub[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) out[v * N + p] = ub[v];
+  }
+}
+
 // d(mean of rho |v|^2/2)/du: (-|V|^2/2, V) / N, 0 for the energy.
 __global__ void __launch_bounds__(256) k_ke_seed(const Grid g, const double* __restrict__ u,
                                                  double* __restrict__ out) {
@@ -1409,14 +1564,24 @@ cudaError_t launch_adj_dir(int d, const AdjArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_visc_adj1(const Grid& g, const double* pm, const double* lam, double lam_scale, double* scratch,
-                             double mu, double kappa, cudaStream_t s) {
-  k_visc_adj1<<<plane_blocks(g), 256, 0, s>>>(g, pm, lam, lam_scale, scratch, mu, kappa);
+                             double mu, double kappa, cudaStream_t s, int* expo) {
+  if (expo) {
+    cudaError_t e = cudaMemsetAsync(expo, 0x80, sizeof(int), s);  // 0x80808080: below every exponent
+    if (e != cudaSuccess) return e;
+    const long long blocks = std::min<long long>((4 * g.N + 255) / 256, 4096);
+    k_lam_expo<<<(int)blocks, 256, 0, s>>>(lam, g.N, lam_scale, expo);
+    k_visc_adj1_df<<<plane_blocks(g), 256, 0, s>>>(g, pm, lam, lam_scale, scratch, mu, kappa, expo);
+  } else
+    k_visc_adj1<<<plane_blocks(g), 256, 0, s>>>(g, pm, lam, lam_scale, scratch, mu, kappa);
   return cudaGetLastError();
 }
 
 cudaError_t launch_visc_adj2(const Grid& g, const double* u, const double* scratch, double gamma, double* out,
-                             int accumulate, int with_rho, cudaStream_t s) {
-  k_visc_adj2<<<plane_blocks(g), 256, 0, s>>>(g, u, scratch, gamma, out, accumulate, with_rho);
+                             int accumulate, int with_rho, cudaStream_t s, const int* expo) {
+  if (expo && !with_rho)  // the double-float scratch of k_visc_adj1_df
+    k_visc_adj2_df<<<plane_blocks(g), 256, 0, s>>>(g, u, scratch, gamma, out, accumulate, expo);
+  else
+    k_visc_adj2<<<plane_blocks(g), 256, 0, s>>>(g, u, scratch, gamma, out, accumulate, with_rho);
   return cudaGetLastError();
 }
 

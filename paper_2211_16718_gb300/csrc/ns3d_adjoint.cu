@@ -17,12 +17,16 @@ enum { AB_S2 = 0, AB_S3 = 1, AB_S4 = 2, AB_UBS = 3, AB_LA = 4, AB_LB = 5, AB_STA
 
 double* adj_buf(ns3d_ctx* c, int i) { return c->adj + (size_t)i * 5 * (size_t)c->g.N; }
 double* adj_scratch(ns3d_ctx* c) { return c->adj + (size_t)AB_STATES * 5 * (size_t)c->g.N; }
+// the exponent word of the double-float viscous adjoint (after the scratch planes)
+int* adj_expo(ns3d_ctx* c) {
+  return reinterpret_cast<int*>(c->adj + ((size_t)AB_STATES * 5 + ADJ_SCRATCH_PLANES) * (size_t)c->g.N);
+}
 
 int adj_ready(ns3d_ctx* c) {
   if (c->p.precision == NS3D_FP32_BULK)
     return set_err(c, NS3D_EINVAL, "the adjoint is available for NS3D_FP64 and NS3D_FP64_STRICT contexts");
   if (c->adj) return NS3D_OK;
-  const size_t words = ((size_t)AB_STATES * 5 + ADJ_SCRATCH_PLANES) * (size_t)c->g.N;
+  const size_t words = ((size_t)AB_STATES * 5 + ADJ_SCRATCH_PLANES) * (size_t)c->g.N + 1;  // + adj_expo
   cudaError_t e = prepare_adj_kernels();
   if (e != cudaSuccess) return cuda_fail(c, e, "adjoint kernel attributes");
   if (!dev_alloc(c, (void**)&c->adj, words * sizeof(double)))
@@ -51,14 +55,16 @@ int vjp_pass(ns3d_ctx* c, const double* u, const double* lam, double scale, AdjA
                  "primitive kernel");
   if (rc) return rc;
   const bool visc = c->p.mu_eff > 0.0;
+  const int df = (c->p.precision == NS3D_FP64_STRICT) ? 0 : 1;
   if (visc) {
     const double kappa = c->p.mu_eff / ((c->p.gamma - 1.0) * c->p.prandtl);
     rc = timed(c, NS3D_K_ADJ_VISC, [&] {
-      return launch_visc_adj1(c->g, c->pm, lam, scale, adj_scratch(c), c->p.mu_eff, kappa, c->stream);
+      return launch_visc_adj1(c->g, c->pm, lam, scale, adj_scratch(c), c->p.mu_eff, kappa, c->stream,
+                              df ? adj_expo(c) : nullptr);
     }, "viscous adjoint kernel 1");
     if (rc) return rc;
     rc = timed(c, NS3D_K_ADJ_VISC, [&] {
-      return launch_visc_adj2(c->g, u, adj_scratch(c), c->p.gamma, c->k, 0, 0, c->stream);
+      return launch_visc_adj2(c->g, u, adj_scratch(c), c->p.gamma, c->k, 0, 0, c->stream, df ? adj_expo(c) : nullptr);
     }, "viscous adjoint kernel 2");
     if (rc) return rc;
   }

@@ -150,12 +150,15 @@ constexpr int ADJ_SCRATCH_PLANES = 16;  // viscous-adjoint scratch: grad adjoint
 cudaError_t prepare_adj_kernels();
 cudaError_t launch_adj_dir(int d, const AdjArgs& a, cudaStream_t s);
 // scratch = adjoint of the velocity/temperature gradients and of the velocities
+// expo non-null: the NS3D_FP64 (double-float) forms, whose scratch planes hold double-float pairs
+// relative to 2^E, E = the largest binary exponent of lam_scale * lambda, kept in *expo by kernel 1
+// for kernel 2
 cudaError_t launch_visc_adj1(const Grid& g, const double* pm, const double* lam, double lam_scale, double* scratch,
-                             double mu, double kappa, cudaStream_t s);
+                             double mu, double kappa, cudaStream_t s, int* expo = nullptr);
 // out (= or +=) adjoint of u through the primitives, from the scratch planes;
 // with_rho adds the direct density plane (scratch plane 15)
 cudaError_t launch_visc_adj2(const Grid& g, const double* u, const double* scratch, double gamma, double* out,
-                             int accumulate, int with_rho, cudaStream_t s);
+                             int accumulate, int with_rho, cudaStream_t s, const int* expo = nullptr);
 // gradient of the mean kinetic energy with respect to u
 cudaError_t launch_ke_seed(const Grid& g, const double* u, double* grad, cudaStream_t s);
 // scratch planes of the enstrophy gradient (finished by launch_visc_adj2 with with_rho)
