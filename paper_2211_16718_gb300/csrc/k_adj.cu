@@ -1,5 +1,8 @@
 // Hand-written adjoint (vector-Jacobian product g = J(u)^T lambda) of the
-// right-hand side of arXiv 2211.16718, Sec. 2.1-2.2, all in FP64.
+// right-hand side of arXiv 2211.16718, Sec. 2.1-2.2: all in FP64 for NS3D_FP64_STRICT
+// contexts (k_adj_dir, k_visc_adj1/2); for NS3D_FP64 contexts the WENO5, Roe and viscous
+// adjoints in double-float on the FP32 pipe (k_adj_dir_df, k_visc_adj1_df/2_df), with FP64
+// for the point-flux adjoint and the final point algebra.
 //
 // Hyperbolic part, per direction D: R_i -= (Fhat_{i+1/2} - Fhat_{i-1/2})/h, so the
 // adjoint of the interface flux is Lhat_{i+1/2} = (lambda_{i+1} - lambda_i)/h.  With
@@ -29,6 +32,8 @@
 // 4th-order central difference.  Two point kernels: (1) adjoint of Fv -> adjoint of G
 // and of the velocities, (2) -sum_e D_e of the G adjoint plus the velocity adjoint ->
 // adjoint of u through u_k = m_k/rho, T = gamma (gamma - 1)(e/rho - |m|^2/(2 rho^2)).
+// The double-float forms work relative to one power of two of lambda for the whole grid
+// (k_lam_expo), so that their result scales exactly with lambda.
 #include <limits.h>
 #include <math.h>
 
