@@ -76,9 +76,14 @@ def test_rhs_vjp_equals_dense_oracle_adjoint(ns3d, oracle, dual, name, precision
     assert err <= TOL_DENSE, err
 
 
+# The grids put one, two and three adjoint tiles (32 points in the NS3D_FP64 form, 16 in the
+# strict one) along each pencil, with ragged last tiles: the tile seams and the halos that cross
+# them are exercised in every direction.
 @pytest.mark.parametrize("n,kw,seed", [((20, 16, 12), dict(mu_eff=5e-3), 1),
                                        ((33, 18, 17), dict(mu_eff=0.0), 2),
-                                       ((12, 40, 9), dict(mu_eff=1e-3, harten_delta=0.4), 3)])
+                                       ((12, 40, 9), dict(mu_eff=1e-3, harten_delta=0.4), 3),
+                                       ((10, 12, 72), dict(mu_eff=2e-3), 4),
+                                       ((70, 9, 10), dict(mu_eff=2e-3), 5)])
 def test_rhs_vjp_dot_product_identity(ns3d, oracle, dual, n, kw, seed):
     u = I.random_smooth(*n, seed=seed, amp=0.15, mach=0.6)
     P = oracle.Params(*n, **kw)
